@@ -1,0 +1,445 @@
+"""Plain FP64 CPU oracle for the ADMM reconstruction of Dogan & Oktem,
+"Efficient Algorithms for Convolutional Inverse Problems in Multidimensional
+Imaging" (arXiv 2006.08303).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this module.  It shares no code with the CUDA
+library (no kernels, tables, constants or helpers); it uses NumPy alone.
+
+Everything is float64 / complex128 and written for readability, not speed:
+  * the 2D DFT is the explicit separable DFT matrix product (entries
+    exp(-2 pi i ((j k) mod N) / N)), unnormalised forward, 1/N^2 inverse;
+  * the forward operator H is a spatial circular convolution;
+  * per-frequency matrices are formed and inverted with numpy.linalg.
+
+Notation follows the paper: K measurements, S (here M) unknown channels,
+N x N images, Lambda = DFT of the PSFs (Section IV-A, "Image update"),
+Psi = rho g(w) I + beta Lambda^H Lambda, t auxiliary, u scaled dual.
+
+Readings where the paper is silent or garbled (each listed in the design notes):
+  R1 anisotropic TV: T = [D_h; D_v] circular forward differences; the
+     x-update uses the general closed form with T^H T (Eq. solx_Trans) whose
+     DFT eigenvalues g(w) come from the circulant kernel of D^T D.
+  R2 at bins where g(w) = 0 (the DC bin of TV) Psi is singular when all PSFs
+     have unit sum; the oracle takes the min-norm pseudo-inverse (eigenvalues
+     below 1e-10 * max eigenvalue dropped), which is what a least-squares
+     solve of the dense system returns.
+  R3 Psi_{i,j} = rho delta_{ij} I + beta sum_k Lambda_{k,i}^H Lambda_{k,j}
+     (the printed block formula drops rho and swaps indices).
+  R4 Lambda is the unnormalised DFT of h, so H_{k,s} = F^H diag(Lambda) F.
+  R5 t^0 = u^0 = 0 (and z^0 = 0 for the synthesis prior).
+  R9 synthesis objective uses 1/2 ||D z - x||^2 and rho/2 ||z - t + u||^2.
+  R10 Sherman-Morrison per bin with theta~_n = conj(theta_n):
+      v = (c - conj(theta) (theta^T c) / (rho + ||theta||^2)) / rho.
+  R11 residuals as in Eq. paramS: r = ||Tx - t||, s = rho ||t - t_prev||;
+      relative forms r / max(||Tx||, ||t||) and s / ||rho u||.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# DFT (Section IV-A: F_2D diagonalises each BCCB block H_{k,s})
+# ---------------------------------------------------------------------------
+def dft_matrix(N: int, sign: int = -1) -> np.ndarray:
+    """Explicit N x N DFT matrix, entry (j,k) = exp(sign 2 pi i ((j k) mod N) / N)."""
+    jk = np.outer(np.arange(N), np.arange(N)) % N
+    ang = 2.0 * math.pi * jk / N
+    return np.cos(ang) + 1j * sign * np.sin(ang)
+
+
+def dft2(x: np.ndarray) -> np.ndarray:
+    """Unnormalised 2D DFT over the last two axes, X = F x F^T (F symmetric)."""
+    N = x.shape[-1]
+    assert x.shape[-2] == N
+    F = dft_matrix(N, -1)
+    return F @ x @ F
+
+
+def idft2(X: np.ndarray) -> np.ndarray:
+    """Inverse of dft2 (1/N^2 normalisation); returns complex."""
+    N = X.shape[-1]
+    G = dft_matrix(N, +1)
+    return (G @ X @ G) / (N * N)
+
+
+# ---------------------------------------------------------------------------
+# Forward model, Section II (Eq. forward model): y_k = sum_s x_s (*) h_{k,s}
+# ---------------------------------------------------------------------------
+def circconv2(x: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """Spatial circular convolution y[n] = sum_j x[j] h[(n - j) mod N] over the
+    last two axes (x and h broadcast over leading axes)."""
+    N = x.shape[-1]
+    y = np.zeros(np.broadcast_shapes(x.shape, h.shape), dtype=np.result_type(x, h))
+    for a in range(N):
+        for b in range(N):
+            y = y + h[..., a:a + 1, b:b + 1] * np.roll(x, shift=(a, b), axis=(-2, -1))
+    return y
+
+
+def circcorr2(y: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """Adjoint of circconv2 in x: x[j] = sum_n y[n] h[(n - j) mod N]."""
+    N = y.shape[-1]
+    x = np.zeros(np.broadcast_shapes(y.shape, h.shape), dtype=np.result_type(y, h))
+    for a in range(N):
+        for b in range(N):
+            x = x + h[..., a:a + 1, b:b + 1] * np.roll(y, shift=(-a, -b), axis=(-2, -1))
+    return x
+
+
+def forward_H(x: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """Stacked forward operator (Eq. forwardModel): x [M,N,N] -> y [K,N,N]."""
+    K, M = h.shape[:2]
+    return np.stack([sum(circconv2(x[m], h[k, m]) for m in range(M)) for k in range(K)])
+
+
+def adjoint_H(y: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """H^T y: [K,N,N] -> [M,N,N]."""
+    K, M = h.shape[:2]
+    return np.stack([sum(circcorr2(y[k], h[k, m]) for k in range(K)) for m in range(M)])
+
+
+# ---------------------------------------------------------------------------
+# Analysis operators T (Eq. analysis) and their adjoints
+# ---------------------------------------------------------------------------
+def tv_forward(x: np.ndarray) -> np.ndarray:
+    """Anisotropic TV (reading R1): [..., N, N] -> [..., 2, N, N];
+    component 0 = x[r, c+1] - x[r, c], component 1 = x[r+1, c] - x[r, c] (circular)."""
+    dh = np.roll(x, -1, axis=-1) - x
+    dv = np.roll(x, -1, axis=-2) - x
+    return np.stack([dh, dv], axis=-3)
+
+
+def tv_adjoint(w: np.ndarray) -> np.ndarray:
+    """D^T: [..., 2, N, N] -> [..., N, N]; D_h^T a = a[r, c-1] - a[r, c], likewise along rows."""
+    ah, av = w[..., 0, :, :], w[..., 1, :, :]
+    return (np.roll(ah, 1, axis=-1) - ah) + (np.roll(av, 1, axis=-2) - av)
+
+
+def dct8_matrix() -> np.ndarray:
+    """Orthonormal 8-point DCT-II, C[k, n] = a_k cos(pi (2n+1) k / 16),
+    a_0 = sqrt(1/8), a_k = sqrt(2/8)."""
+    k = np.arange(8)[:, None]
+    n = np.arange(8)[None, :]
+    C = np.cos(math.pi * (2 * n + 1) * k / 16.0)
+    C[0, :] *= math.sqrt(1.0 / 8.0)
+    C[1:, :] *= math.sqrt(2.0 / 8.0)
+    return C
+
+
+def _blocks(x: np.ndarray) -> np.ndarray:
+    N = x.shape[-1]
+    lead = x.shape[:-2]
+    return x.reshape(*lead, N // 8, 8, N // 8, 8)
+
+
+def _unblocks(b: np.ndarray) -> np.ndarray:
+    lead = b.shape[:-4]
+    N = b.shape[-4] * 8
+    return b.reshape(*lead, N, N)
+
+
+def dct8_forward(x: np.ndarray) -> np.ndarray:
+    """Blockwise orthonormal 8x8 DCT-II, blocks aligned at (0,0): [..., N, N] -> [..., 1, N, N]."""
+    C = dct8_matrix()
+    b = _blocks(x)
+    w = np.einsum("ka,...iajb,lb->...ikjl", C, b, C)
+    return _unblocks(w)[..., None, :, :]
+
+
+def dct8_adjoint(w: np.ndarray) -> np.ndarray:
+    """Inverse (= adjoint) of dct8_forward: [..., 1, N, N] -> [..., N, N]."""
+    C = dct8_matrix()
+    b = _blocks(w[..., 0, :, :])
+    x = np.einsum("ka,...ikjl,lb->...iajb", C, b, C)
+    return _unblocks(x)
+
+
+def l1_forward(x: np.ndarray) -> np.ndarray:
+    """T = I (plain l1 prior)."""
+    return x[..., None, :, :].copy()
+
+
+def l1_adjoint(w: np.ndarray) -> np.ndarray:
+    return w[..., 0, :, :].copy()
+
+
+PRIORS = {
+    "tv": (tv_forward, tv_adjoint),
+    "dct8": (dct8_forward, dct8_adjoint),
+    "l1": (l1_forward, l1_adjoint),
+}
+
+
+def gram_eigenvalues(prior: str, N: int) -> np.ndarray:
+    """g(w): DFT eigenvalues of the circulant T^T T.  Computed as the DFT of
+    the kernel T^T T delta (Eq. solx_Trans with BCCB T^T T).  For an
+    orthonormal T (DCT, identity) T^T T = I and g = 1 (Eq. solx_Trans_DFT)."""
+    if prior in ("dct8", "l1"):
+        return np.ones((N, N))
+    fwd, adj = PRIORS[prior]
+    delta = np.zeros((N, N))
+    delta[0, 0] = 1.0
+    kern = adj(fwd(delta))
+    g = dft2(kern)
+    return g.real
+
+
+def soft(w: np.ndarray, tau: float) -> np.ndarray:
+    """Soft-thresholding (Eq. solt_trans): sign(w) max(|w| - tau, 0), with
+    sign(w) = 1 for w > 0 and -1 otherwise."""
+    s = np.where(w > 0, 1.0, -1.0)
+    return s * np.maximum(np.abs(w) - tau, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Per-frequency algebra (Section IV-A, Eqs. solx_Trans_DFT and recinv)
+# ---------------------------------------------------------------------------
+def psf_spectra(h: np.ndarray) -> np.ndarray:
+    """Lambda[k, m] = unnormalised DFT of h_{k,m} (reading R4)."""
+    return dft2(h)
+
+
+def per_bin_lambda(Lam: np.ndarray) -> np.ndarray:
+    """[K, M, N, N] -> [N, N, K, M]: the K x M matrix Lambda(w) at each bin."""
+    return np.transpose(Lam, (2, 3, 0, 1))
+
+
+def form_psi(Lam: np.ndarray, g: np.ndarray, rho: float, beta: float) -> np.ndarray:
+    """Psi(w) = rho g(w) I + beta Lambda(w)^H Lambda(w)  -> [N, N, M, M] (reading R3)."""
+    Lb = per_bin_lambda(Lam)
+    M = Lb.shape[-1]
+    LhL = np.einsum("abki,abkj->abij", Lb.conj(), Lb)
+    return rho * g[..., None, None] * np.eye(M) + beta * LhL
+
+
+def pinv_hermitian(A: np.ndarray, rel_cut: float = 1e-10) -> np.ndarray:
+    """Min-norm pseudo-inverse of a Hermitian PSD matrix (reading R2)."""
+    ev, V = np.linalg.eigh(A)
+    cut = rel_cut * max(ev.max(), 0.0)
+    inv = np.where(ev > cut, 1.0 / np.where(ev > cut, ev, 1.0), 0.0)
+    return (V * inv) @ V.conj().T
+
+
+def invert_psi(Psi: np.ndarray, g: np.ndarray, gz: float = 1e-12) -> np.ndarray:
+    """Psi^{-1} at every bin; pseudo-inverse where g(w) = 0 (reading R2)."""
+    out = np.linalg.inv(np.where((g <= gz * g.max())[..., None, None],
+                                 np.eye(Psi.shape[-1]), Psi))
+    sing = np.argwhere(g <= gz * g.max())
+    for a, b in sing:
+        out[a, b] = pinv_hermitian(Psi[a, b])
+    return out
+
+
+def recursive_block_inverse(P: np.ndarray) -> np.ndarray:
+    """Inverse of one S x S matrix by the 2 x 2 block recursion of Eq. recinv:
+    with S_c = P22 - P21 P11^{-1} P12 and B = -S_c^{-1},
+    inv = [[P11^{-1} - P11^{-1} P12 B P21 P11^{-1}, P11^{-1} P12 B],
+           [B P21 P11^{-1}, -B]]."""
+    S = P.shape[0]
+    if S == 1:
+        return np.array([[1.0 / P[0, 0]]])
+    h = S // 2
+    P11, P12, P21, P22 = P[:h, :h], P[:h, h:], P[h:, :h], P[h:, h:]
+    P11i = recursive_block_inverse(P11)
+    B = -recursive_block_inverse(P22 - P21 @ P11i @ P12)
+    A = P11i - P11i @ P12 @ B @ P21 @ P11i
+    top = np.concatenate([A, P11i @ P12 @ B], axis=1)
+    bot = np.concatenate([B @ P21 @ P11i, -B], axis=1)
+    return np.concatenate([top, bot], axis=0)
+
+
+def rhs_bhat(Lam: np.ndarray, y: np.ndarray, beta: float) -> np.ndarray:
+    """b(w) = beta Lambda(w)^H (F y)(w)  -> [M, N, N] (Alg. 1, setup)."""
+    Y = dft2(y)
+    return beta * np.einsum("kmab,kab->mab", Lam.conj(), Y)
+
+
+def apply_per_bin(Pinv: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """x(w) = Pinv(w) v(w); Pinv [N,N,M,M], v [M,N,N] -> [M,N,N]."""
+    return np.einsum("abij,jab->iab", Pinv, v)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 (analysis prior)
+# ---------------------------------------------------------------------------
+@dataclass
+class AnalysisSetup:
+    N: int
+    M: int
+    prior: str
+    lam: float
+    rho: float
+    beta: float
+    Lam: np.ndarray     # [K, M, N, N]
+    g: np.ndarray       # [N, N]
+    Pinv: np.ndarray    # [N, N, M, M]
+    bhat: np.ndarray    # [M, N, N]
+
+
+def analysis_setup(h: np.ndarray, y: np.ndarray, prior: str, lam: float, rho: float,
+                   beta: float) -> AnalysisSetup:
+    """Alg. 1 setup: Psi^{-1} = (rho T^H T + beta Lambda^H Lambda)^{-1} per bin and
+    beta Lambda^H F y."""
+    K, M, N, _ = h.shape
+    Lam = psf_spectra(h)
+    g = gram_eigenvalues(prior, N)
+    Psi = form_psi(Lam, g, rho, beta)
+    Pinv = invert_psi(Psi, g)
+    return AnalysisSetup(N, M, prior, lam, rho, beta, Lam, g, Pinv, rhs_bhat(Lam, y, beta))
+
+
+def x_update(S: AnalysisSetup, t: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Eq. solx_Trans_DFT: x = F^H Psi^{-1} (beta Lambda^H F y + rho F T^H (t - u))."""
+    _, adj = PRIORS[S.prior]
+    q = adj(t - u)
+    xhat = apply_per_bin(S.Pinv, S.bhat + S.rho * dft2(q))
+    return idft2(xhat).real
+
+
+def t_u_update(S: AnalysisSetup, x: np.ndarray, u: np.ndarray):
+    """Eq. solt_trans and Eq. subu_trans: t = soft(Tx + u, lambda/rho); u += Tx - t."""
+    fwd, _ = PRIORS[S.prior]
+    w = fwd(x)
+    t = soft(w + u, S.lam / S.rho)
+    return t, u + w - t, w
+
+
+@dataclass
+class IterRecord:
+    x: np.ndarray
+    t: np.ndarray
+    u: np.ndarray
+    r: float            # ||Tx - t||
+    s: float            # rho ||t - t_prev||
+    r_rel: float
+    s_rel: float
+
+
+def analysis_step(S: AnalysisSetup, t: np.ndarray, u: np.ndarray):
+    """One iteration of Alg. 1 (x, then t, then u).  Returns (x, t_new, u_new, w=Tx)."""
+    x = x_update(S, t, u)
+    t_new, u_new, w = t_u_update(S, x, u)
+    return x, t_new, u_new, w
+
+
+def run_analysis(S: AnalysisSetup, iters: int, t0=None, u0=None, keep_history: bool = False):
+    """Alg. 1 for a fixed number of iterations from t^0 = u^0 = 0 (reading R5)."""
+    ncomp = 2 if S.prior == "tv" else 1
+    t = np.zeros((S.M, ncomp, S.N, S.N)) if t0 is None else t0.copy()
+    u = np.zeros_like(t) if u0 is None else u0.copy()
+    hist: List[IterRecord] = []
+    x = None
+    for _ in range(iters):
+        x, t_new, u_new, w = analysis_step(S, t, u)
+        r = float(np.linalg.norm(w - t_new))
+        s = S.rho * float(np.linalg.norm(t_new - t))
+        den_r = max(float(np.linalg.norm(w)), float(np.linalg.norm(t_new)), 1e-300)
+        den_s = max(S.rho * float(np.linalg.norm(u_new)), 1e-300)
+        if keep_history:
+            hist.append(IterRecord(x, t_new, u_new, r, s, r / den_r, s / den_s))
+        t, u = t_new, u_new
+    return x, t, u, hist
+
+
+def objective(x: np.ndarray, h: np.ndarray, y: np.ndarray, prior: str, lam: float, beta: float) -> float:
+    """Eq. rls with the analysis prior: beta/2 ||y - Hx||^2 + lambda ||Tx||_1 (H spatial)."""
+    fwd, _ = PRIORS[prior]
+    res = y - forward_H(x, h)
+    return 0.5 * beta * float(np.sum(res * res)) + lam * float(np.sum(np.abs(fwd(x))))
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2 (synthesis prior, 2D convolutional dictionary per slice)
+# ---------------------------------------------------------------------------
+@dataclass
+class ConvDictSetup:
+    N: int
+    M: int
+    L: int
+    lam: float
+    rho: float
+    beta: float
+    Lam: np.ndarray     # [K, M, N, N]
+    theta: np.ndarray   # [L, N, N]  DFT of the embedded filters
+    Pinv: np.ndarray    # [N, N, M, M] (I + beta Lambda^H Lambda)^{-1}
+    bhat: np.ndarray    # [M, N, N]
+
+
+def embed_filters(d: np.ndarray, N: int) -> np.ndarray:
+    """P x P filter (centre P//2) placed on the N x N torus, centre at (0,0)."""
+    L, P, _ = d.shape
+    c = P // 2
+    out = np.zeros((L, N, N))
+    for l in range(L):
+        for i in range(P):
+            for j in range(P):
+                out[l, (i - c) % N, (j - c) % N] = d[l, i, j]
+    return out
+
+
+def convdict_setup(h: np.ndarray, y: np.ndarray, d: np.ndarray, lam: float, rho: float,
+                   beta: float) -> ConvDictSetup:
+    """Alg. 2 setup with t = 1 (P = I for the convolutional dictionary, Eq. solx_synt)."""
+    K, M, N, _ = h.shape
+    Lam = psf_spectra(h)
+    Psi = form_psi(Lam, np.ones((N, N)), 1.0, beta)
+    Pinv = np.linalg.inv(Psi)
+    theta = dft2(embed_filters(d, N))
+    return ConvDictSetup(N, M, d.shape[0], lam, rho, beta, Lam, theta, Pinv, rhs_bhat(Lam, y, beta))
+
+
+def sherman_morrison(theta_n: np.ndarray, c_n: np.ndarray, rho: float) -> np.ndarray:
+    """Eq. solz_DFT_SM at one bin (reading R10): solve (rho I + conj(theta) theta^T) v = c."""
+    a = theta_n.conj()
+    return (c_n - a * (theta_n @ c_n) / (rho + np.vdot(theta_n, theta_n).real)) / rho
+
+
+def convdict_step(C: ConvDictSetup, z: np.ndarray, t: np.ndarray, u: np.ndarray):
+    """One iteration of Alg. 2: x (Eq. solx_synt_DFT), z (Eqs. solz_DFT,
+    solz_DFT_SM), t (Eq. softADMM), u (Eq. subu_dic).  z, t, u: [L, M, N, N]."""
+    Z = dft2(z)                                            # F z per (l, m)
+    p = np.einsum("lab,lmab->mab", C.theta, Z)             # F D z per channel
+    xhat = apply_per_bin(C.Pinv, C.bhat + p)
+    x = idft2(xhat).real
+    c = C.theta.conj()[:, None] * dft2(x)[None] + C.rho * dft2(t - u)
+    v = np.empty_like(c)
+    for a in range(C.N):
+        for b in range(C.N):
+            th = C.theta[:, a, b]
+            for m in range(C.M):
+                v[:, m, a, b] = sherman_morrison(th, c[:, m, a, b], C.rho)
+    z_new = idft2(v).real
+    t_new = soft(z_new + u, C.lam / C.rho)
+    u_new = u + z_new - t_new
+    return x, z_new, t_new, u_new
+
+
+def run_convdict(C: ConvDictSetup, iters: int, keep_history: bool = False):
+    """Alg. 2 from z^0 = t^0 = u^0 = 0 (reading R5)."""
+    z = np.zeros((C.L, C.M, C.N, C.N))
+    t = np.zeros_like(z)
+    u = np.zeros_like(z)
+    hist = []
+    x = None
+    for _ in range(iters):
+        x, z, t_new, u = convdict_step(C, z, t, u)
+        if keep_history:
+            hist.append((x, z, t_new, u))
+        t = t_new
+    return x, z, t, u, hist
+
+
+def convdict_objective(x, z, d, h, y, lam, beta) -> float:
+    """beta/2 ||y - Hx||^2 + 1/2 ||sum_l d_l (*) z_l - x||^2 + lambda ||z||_1 (reading R9)."""
+    N = x.shape[-1]
+    de = embed_filters(d, N)
+    Dz = np.stack([sum(circconv2(z[l, m], de[l]) for l in range(z.shape[0])) for m in range(x.shape[0])])
+    r1 = y - forward_H(x, h)
+    r2 = Dz - x
+    return 0.5 * beta * float(np.sum(r1 * r1)) + 0.5 * float(np.sum(r2 * r2)) + lam * float(np.sum(np.abs(z)))

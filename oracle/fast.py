@@ -1,0 +1,157 @@
+"""FP64 CPU oracle, fast form: the same steps as ``oracle.admm`` (Alg. 1 and
+Alg. 2 of Dogan & Oktem, arXiv 2006.08303), with the naive DFT replaced by
+scipy.fft's real FFT (pocketfft, all host cores) and the spatial convolution
+never formed.  Used for image sizes the naive oracle cannot reach and as the
+timed CPU baseline.  It is cross-checked against ``oracle.admm`` in the CPU
+tests.
+
+TEST INFRASTRUCTURE ONLY: imported by tests, the smoke check and the
+benchmark's CPU-baseline leg, never by the library.  It shares no code with
+the CUDA path and only reuses the operator definitions of ``oracle.admm``.
+"""
+from __future__ import annotations
+
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.fft as sfft
+
+from . import admm as ref
+
+WORKERS = os.cpu_count() or 1
+
+
+def rfft2(x):
+    return sfft.rfft2(x, workers=WORKERS)
+
+
+def irfft2(X, N):
+    return sfft.irfft2(X, s=(N, N), workers=WORKERS)
+
+
+def gram_eigenvalues_half(prior: str, N: int) -> np.ndarray:
+    """g(w) on the half spectrum [N, N/2+1] (DFT of the kernel T^T T delta)."""
+    if prior in ("dct8", "l1"):
+        return np.ones((N, N // 2 + 1))
+    fwd, adj = ref.PRIORS[prior]
+    delta = np.zeros((N, N))
+    delta[0, 0] = 1.0
+    return rfft2(adj(fwd(delta))).real
+
+
+@dataclass
+class FastAnalysis:
+    N: int
+    M: int
+    prior: str
+    lam: float
+    rho: float
+    beta: float
+    Pinv: np.ndarray   # [N, N/2+1, M, M]
+    bhat: np.ndarray   # [N, N/2+1, M]
+
+
+def analysis_setup(h, y, prior, lam, rho, beta) -> FastAnalysis:
+    """Alg. 1 setup on the half spectrum (same readings as oracle.admm)."""
+    K, M, N, _ = h.shape
+    Lam = np.moveaxis(rfft2(h), (0, 1), (2, 3))                 # [N, H, K, M]
+    g = gram_eigenvalues_half(prior, N)
+    Psi = rho * g[..., None, None] * np.eye(M) + beta * np.einsum("abki,abkj->abij", Lam.conj(), Lam)
+    sing = g <= 1e-12 * g.max()
+    Pinv = np.linalg.inv(np.where(sing[..., None, None], np.eye(M), Psi))
+    for a, b in np.argwhere(sing):
+        Pinv[a, b] = ref.pinv_hermitian(Psi[a, b])
+    Y = np.moveaxis(rfft2(y), 0, 2)                             # [N, H, K]
+    bhat = beta * np.einsum("abkm,abk->abm", Lam.conj(), Y)
+    return FastAnalysis(N, M, prior, lam, rho, beta, Pinv, bhat)
+
+
+def x_update(S: FastAnalysis, t, u):
+    """Eq. solx_Trans_DFT on the half spectrum."""
+    _, adj = ref.PRIORS[S.prior]
+    Q = np.moveaxis(rfft2(adj(t - u)), 0, 2)                    # [N, H, M]
+    X = np.matmul(S.Pinv, (S.bhat + S.rho * Q)[..., None])[..., 0]
+    return irfft2(np.moveaxis(X, 2, 0), S.N)
+
+
+def analysis_step(S: FastAnalysis, t, u):
+    fwd, _ = ref.PRIORS[S.prior]
+    x = x_update(S, t, u)
+    w = fwd(x)
+    t_new = ref.soft(w + u, S.lam / S.rho)
+    return x, t_new, u + w - t_new, w
+
+
+def run_analysis(S: FastAnalysis, iters: int, t0=None, u0=None, tol: float = 0.0):
+    """Alg. 1; with tol > 0 stops when both relative residuals (reading R11) fall below tol.
+    Returns (x, t, u, iterations_done, (r_rel, s_rel))."""
+    ncomp = 2 if S.prior == "tv" else 1
+    t = np.zeros((S.M, ncomp, S.N, S.N)) if t0 is None else t0.copy()
+    u = np.zeros_like(t) if u0 is None else u0.copy()
+    x = None
+    rr = (np.inf, np.inf)
+    done = 0
+    for it in range(iters):
+        x, t_new, u_new, w = analysis_step(S, t, u)
+        done = it + 1
+        if tol > 0:
+            r = np.linalg.norm(w - t_new)
+            s = S.rho * np.linalg.norm(t_new - t)
+            rr = (r / max(np.linalg.norm(w), np.linalg.norm(t_new), 1e-300),
+                  s / max(S.rho * np.linalg.norm(u_new), 1e-300))
+        t, u = t_new, u_new
+        if tol > 0 and rr[0] < tol and rr[1] < tol:
+            break
+    return x, t, u, done, rr
+
+
+@dataclass
+class FastConvDict:
+    N: int
+    M: int
+    L: int
+    lam: float
+    rho: float
+    beta: float
+    Pinv: np.ndarray   # [N, H, M, M]
+    bhat: np.ndarray   # [N, H, M]
+    theta: np.ndarray  # [N, H, L]
+
+
+def convdict_setup(h, y, d, lam, rho, beta) -> FastConvDict:
+    K, M, N, _ = h.shape
+    Lam = np.moveaxis(rfft2(h), (0, 1), (2, 3))
+    Psi = np.eye(M) + beta * np.einsum("abki,abkj->abij", Lam.conj(), Lam)
+    Pinv = np.linalg.inv(Psi)
+    Y = np.moveaxis(rfft2(y), 0, 2)
+    bhat = beta * np.einsum("abkm,abk->abm", Lam.conj(), Y)
+    theta = np.moveaxis(rfft2(ref.embed_filters(d, N)), 0, 2)
+    return FastConvDict(N, M, d.shape[0], lam, rho, beta, Pinv, bhat, theta)
+
+
+def convdict_step(C: FastConvDict, z, t, u):
+    """Alg. 2 iteration (same order as oracle.admm.convdict_step), z/t/u [L, M, N, N]."""
+    Z = np.moveaxis(rfft2(z), (0, 1), (2, 3))                   # [N, H, L, M]
+    p = np.einsum("abl,ablm->abm", C.theta, Z)
+    X = np.matmul(C.Pinv, (C.bhat + p)[..., None])[..., 0]     # [N, H, M]
+    x = irfft2(np.moveaxis(X, 2, 0), C.N)
+    G = np.moveaxis(rfft2(t - u), (0, 1), (2, 3))               # [N, H, L, M]
+    c = C.theta.conj()[..., None] * X[:, :, None, :] + C.rho * G
+    th = C.theta[..., None]
+    dot = np.sum(th * c, axis=2, keepdims=True)                 # theta^T c
+    nrm = np.sum(np.abs(C.theta) ** 2, axis=2)[..., None, None]
+    v = (c - th.conj() * dot / (C.rho + nrm)) / C.rho
+    z_new = irfft2(np.moveaxis(v, (2, 3), (0, 1)), C.N)
+    t_new = ref.soft(z_new + u, C.lam / C.rho)
+    return x, z_new, t_new, u + z_new - t_new
+
+
+def run_convdict(C: FastConvDict, iters: int):
+    z = np.zeros((C.L, C.M, C.N, C.N))
+    t = np.zeros_like(z)
+    u = np.zeros_like(z)
+    x = None
+    for _ in range(iters):
+        x, z, t, u = convdict_step(C, z, t, u)
+    return x, z, t, u

@@ -1,0 +1,363 @@
+"""Pins for the FP64 oracle against mathematics and library routines, not
+against itself.  Each test names the paper passage it pins; a plausible
+mistake in the oracle (dropped term, wrong sign or index, transposed operand,
+missing conjugate) fails at least one of them.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+import scipy.fft as sfft
+
+from oracle import admm
+from oracle import fast
+from paper_2006_08303_gb300 import inputs
+
+RNG = np.random.default_rng(1234)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def random_psfs(rng, K, M, N):
+    """Asymmetric, non-unit-sum PSFs so that Lambda is complex and K x M is not square-symmetric."""
+    return rng.uniform(0.0, 1.0, size=(K, M, N, N)) * (rng.random((K, M, N, N)) < 0.4)
+
+
+def dense_operator(apply, in_shape):
+    """Columns = apply(unit vector)."""
+    n = int(np.prod(in_shape))
+    cols = []
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        cols.append(np.asarray(apply(e.reshape(in_shape))).ravel())
+    return np.stack(cols, axis=1)
+
+
+# ----------------------------------------------------------------- DFT & conv
+@pytest.mark.parametrize("N", [4, 8, 16])
+def test_dft_matches_library(N):
+    """Section IV-A: F_2D is the 2D DFT; pinned to numpy.fft (textbook DFT)."""
+    x = RNG.standard_normal((2, N, N)) + 1j * RNG.standard_normal((2, N, N))
+    assert np.abs(admm.dft2(x) - np.fft.fft2(x)).max() < 1e-12 * N * N
+    assert np.abs(admm.idft2(np.fft.fft2(x)) - x).max() < 1e-12
+
+
+def test_parseval():
+    x = RNG.standard_normal((8, 8))
+    assert abs(np.sum(np.abs(admm.dft2(x)) ** 2) / 64 - np.sum(x * x)) < 1e-12
+
+
+def test_circular_convolution_shift_and_theorem():
+    """Eq. forward model: circular convolution with origin at (0,0).
+    A delta at (1,2) shifts h by (1,2); the DFT of a convolution is the product (Section IV-A, BCCB)."""
+    N = 8
+    h = RNG.standard_normal((N, N))
+    d = np.zeros((N, N)); d[1, 2] = 1.0
+    y = admm.circconv2(d, h)
+    assert np.array_equal(y, np.roll(h, (1, 2), axis=(0, 1)))
+    x = RNG.standard_normal((N, N))
+    y = admm.circconv2(x, h)
+    assert np.abs(admm.dft2(y) - admm.dft2(x) * admm.dft2(h)).max() < 1e-10
+    # brute-force definition at one output pixel
+    n1, n2 = 3, 6
+    direct = sum(x[j1, j2] * h[(n1 - j1) % N, (n2 - j2) % N] for j1 in range(N) for j2 in range(N))
+    assert abs(y[n1, n2] - direct) < 1e-12
+
+
+def test_forward_adjoint_pair():
+    """H^T is the adjoint of H (needed by Eq. solx_Trans)."""
+    K, M, N = 3, 2, 8
+    h = random_psfs(RNG, K, M, N)
+    x = RNG.standard_normal((M, N, N))
+    y = RNG.standard_normal((K, N, N))
+    lhs = np.sum(admm.forward_H(x, h) * y)
+    rhs = np.sum(x * admm.adjoint_H(y, h))
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+# ----------------------------------------------------------------- priors
+def test_tv_explicit_values():
+    """Anisotropic TV with circular forward differences (reading R1), hand example."""
+    x = np.array([[0., 1., 3., 6.], [1., 1., 1., 1.], [2., 0., 2., 0.], [5., 4., 3., 2.]])
+    w = admm.tv_forward(x)
+    assert np.array_equal(w[0, 0], [1., 2., 3., -6.])          # x[0,c+1]-x[0,c], wraps 0-6
+    assert np.array_equal(w[1][:, 0], [1., 1., 3., -5.])       # x[r+1,0]-x[r,0], wraps 0-5
+
+
+@pytest.mark.parametrize("prior", ["tv", "dct8", "l1"])
+def test_prior_adjoint(prior):
+    """<Tx, w> = <x, T^T w> for every analysis operator."""
+    fwd, adj = admm.PRIORS[prior]
+    N = 16
+    x = RNG.standard_normal((2, N, N))
+    w = RNG.standard_normal(fwd(x).shape)
+    assert abs(np.sum(fwd(x) * w) - np.sum(x * adj(w))) < 1e-11
+
+
+def test_dct8_is_library_orthonormal_dct():
+    """Block DCT (reading R12) equals scipy's orthonormal DCT-II on each aligned 8x8 block."""
+    N = 16
+    x = RNG.standard_normal((N, N))
+    w = admm.dct8_forward(x)[0]
+    for bi in range(0, N, 8):
+        for bj in range(0, N, 8):
+            ref = sfft.dctn(x[bi:bi + 8, bj:bj + 8], type=2, norm="ortho")
+            assert np.abs(w[bi:bi + 8, bj:bj + 8] - ref).max() < 1e-13
+    C = admm.dct8_matrix()
+    assert np.abs(C @ C.T - np.eye(8)).max() < 1e-14
+    assert np.abs(admm.dct8_adjoint(admm.dct8_forward(x)) - x).max() < 1e-13
+
+
+@pytest.mark.parametrize("N", [8, 16])
+def test_tv_gram_eigenvalues_closed_form(N):
+    """g(w) for D^T D equals 4 sin^2(pi k1/N) + 4 sin^2(pi k2/N) (textbook Laplacian spectrum)."""
+    g = admm.gram_eigenvalues("tv", N)
+    k = np.arange(N)
+    cf = 4 * np.sin(np.pi * k / N)[:, None] ** 2 + 4 * np.sin(np.pi * k / N)[None, :] ** 2
+    assert np.abs(g - cf).max() < 1e-12
+
+
+def test_soft_threshold_is_prox():
+    """Eq. solt_trans: soft(v, lam/rho) = argmin_t lam|t| + rho/2 (t - v)^2, by grid search."""
+    lam, rho = 0.3, 1.7
+    grid = np.linspace(-3, 3, 600001)
+    for v in [-2.1, -0.17, 0.0, 0.05, 0.176, 0.9, 2.4]:
+        f = lam * np.abs(grid) + 0.5 * rho * (grid - v) ** 2
+        tb = grid[np.argmin(f)]
+        assert abs(admm.soft(np.array(v), lam / rho) - tb) < 2e-5
+    assert admm.soft(np.array(-1.0), 0.5) == -0.5 and admm.soft(np.array(0.2), 0.5) == 0.0
+
+
+# ----------------------------------------------------------------- per-bin algebra
+@pytest.mark.parametrize("S", [1, 2, 3, 5, 10])
+def test_recursive_block_inverse(S):
+    """Eq. recinv (2x2 block recursion) agrees with a library inverse and inverts Psi."""
+    A = RNG.standard_normal((S + 2, S)) + 1j * RNG.standard_normal((S + 2, S))
+    P = 0.3 * np.eye(S) + A.conj().T @ A
+    Ri = admm.recursive_block_inverse(P)
+    assert np.abs(Ri - np.linalg.inv(P)).max() < 1e-12 * np.abs(Ri).max()
+    assert np.abs(P @ Ri - np.eye(S)).max() < 1e-12
+
+
+def test_psi_block_formula_reading():
+    """Reading R3: Psi_{ij}(w) = rho delta_ij + beta sum_k conj(Lam_{k,i}) Lam_{k,j}; checked entrywise."""
+    K, M, N = 3, 2, 4
+    h = random_psfs(RNG, K, M, N)
+    Lam = admm.psf_spectra(h)
+    g = np.ones((N, N)) * 0.7
+    Psi = admm.form_psi(Lam, g, 2.0, 3.0)
+    a, b = 1, 2
+    for i in range(M):
+        for j in range(M):
+            e = 2.0 * 0.7 * (i == j) + 3.0 * sum(np.conj(Lam[k, i, a, b]) * Lam[k, j, a, b] for k in range(K))
+            assert abs(Psi[a, b, i, j] - e) < 1e-12
+
+
+# ----------------------------------------------------------------- x-update vs dense LS
+@pytest.mark.parametrize("prior,K,M,unit_sum", [("tv", 2, 2, True), ("tv", 3, 2, False),
+                                                 ("dct8", 2, 3, False), ("l1", 3, 2, False),
+                                                 ("tv", 1, 1, True)])
+def test_x_update_equals_dense_least_squares(prior, K, M, unit_sum):
+    """Eq. iter_ADMM1 solved densely: x = argmin beta/2||y-Hx||^2 + rho/2||Tx - t + u||^2,
+    i.e. lstsq on [sqrt(beta) H; sqrt(rho) T] x = [sqrt(beta) y; sqrt(rho)(t-u)] (min-norm where singular,
+    which pins reading R2).  The oracle's frequency-domain Eq. solx_Trans_DFT must match it."""
+    N = 8
+    rng = np.random.default_rng(7 + K + 10 * M)
+    if unit_sum:
+        h = inputs.gaussian_psf_bank(N, K, M)
+        h = h * (1 + 0.2 * rng.random((K, M, N, N)))
+        h /= h.sum(axis=(-2, -1), keepdims=True)
+    else:
+        h = random_psfs(rng, K, M, N)
+    x_true = rng.standard_normal((M, N, N))
+    y = admm.forward_H(x_true, h) + 0.1 * rng.standard_normal((K, N, N))
+    beta, rho, lam = 1.3, 0.7, 0.05
+    fwd, _ = admm.PRIORS[prior]
+    ncomp = 2 if prior == "tv" else 1
+    t = rng.standard_normal((M, ncomp, N, N))
+    u = rng.standard_normal((M, ncomp, N, N))
+    H = dense_operator(lambda v: admm.forward_H(v, h), (M, N, N))
+    T = dense_operator(fwd, (M, N, N))
+    A = np.concatenate([math.sqrt(beta) * H, math.sqrt(rho) * T])
+    b = np.concatenate([math.sqrt(beta) * y.ravel(), math.sqrt(rho) * (t - u).ravel()])
+    x_ls = np.linalg.lstsq(A, b, rcond=1e-11)[0].reshape(M, N, N)
+    S = admm.analysis_setup(h, y, prior, lam, rho, beta)
+    x_or = admm.x_update(S, t, u)
+    assert rel(x_or, x_ls) < 1e-9
+
+
+def test_normal_equation_residual_tiny_workload():
+    """At 64x64x3 (tiny TV instance): (beta H^T H + rho T^T T) x = beta H^T y + rho T^T (t - u)
+    with H applied by spatial convolution, to 1e-12 relative."""
+    P = inputs.tiny_tv()
+    S = admm.analysis_setup(P.h, P.y, P.prior, P.lam, P.rho, P.beta)
+    rng = np.random.default_rng(3)
+    t, u = inputs.random_state(rng, "tv", P.M, P.N)
+    x = fast.x_update(fast.analysis_setup(P.h, P.y, P.prior, P.lam, P.rho, P.beta), t, u)
+    assert rel(x, admm.x_update(S, t, u)) < 1e-11
+    lhs = P.beta * admm.adjoint_H(admm.forward_H(x, P.h), P.h) + P.rho * admm.tv_adjoint(admm.tv_forward(x))
+    rhs = P.beta * admm.adjoint_H(P.y, P.h) + P.rho * admm.tv_adjoint(t - u)
+    # the DC null space (per-channel constants summing to zero) is invisible to both sides
+    assert rel(lhs, rhs) < 1e-11
+
+
+# ----------------------------------------------------------------- whole loop
+def test_closed_form_l1_identity():
+    """h = delta, K = M = 1, T = I: the problem min beta/2||y-x||^2 + lam||x||_1 has x* = soft(y, lam/beta)."""
+    N = 8
+    h = np.zeros((1, 1, N, N)); h[0, 0, 0, 0] = 1.0
+    y = RNG.standard_normal((1, N, N))
+    lam, beta, rho = 0.4, 1.0, 1.0
+    S = admm.analysis_setup(h, y, "l1", lam, rho, beta)
+    x, t, u, _ = admm.run_analysis(S, 400)
+    assert np.abs(x - admm.soft(y, lam / beta)).max() < 1e-10
+
+
+def test_closed_form_dct_identity():
+    """h = delta, T = orthonormal block DCT: x* = T^T soft(T y, lam/beta)."""
+    N = 16
+    h = np.zeros((1, 1, N, N)); h[0, 0, 0, 0] = 1.0
+    y = RNG.standard_normal((1, N, N))
+    lam, beta, rho = 0.3, 2.0, 1.5
+    S = admm.analysis_setup(h, y, "dct8", lam, rho, beta)
+    x, _, _, _ = admm.run_analysis(S, 600)
+    xs = admm.dct8_adjoint(admm.soft(admm.dct8_forward(y), lam / beta))
+    assert np.abs(x - xs).max() < 1e-9
+
+
+@pytest.fixture(scope="module")
+def tv16():
+    rng = np.random.default_rng(99)
+    N, M = 16, 2
+    x0 = inputs.rectangles_image(rng, N, M, n_rect=3)
+    h = inputs.gaussian_psf_bank(N, 3, M)
+    y, _ = inputs.measure(rng, x0, h, 30.0)
+    lam, rho, beta = 1e-2, 0.5, 1.0
+    S = admm.analysis_setup(h, y, "tv", lam, rho, beta)
+    x, t, u, hist = admm.run_analysis(S, 3000, keep_history=True)
+    return dict(h=h, y=y, lam=lam, rho=rho, beta=beta, S=S, x=x, t=t, u=u, hist=hist)
+
+
+def test_dual_invariant_every_iteration(tv16):
+    """From Eqs. solt_trans and subu_trans: u^{l+1} = clip(Tx + u^l, +-lam/rho), so |u| <= lam/rho and
+    u = sign(t) lam/rho wherever t != 0 (the scaled dual is a subgradient of lam||t||_1 / rho)."""
+    tau = tv16["lam"] / tv16["rho"]
+    for rec in tv16["hist"][:60]:
+        assert np.abs(rec.u).max() <= tau * (1 + 1e-12)
+        nz = rec.t != 0
+        assert np.abs(rec.u[nz] - np.sign(rec.t[nz]) * tau).max() < 1e-12
+
+
+def test_kkt_at_convergence(tv16):
+    """KKT certificate of Eq. rls with the TV prior: stationarity beta H^T(Hx - y) + rho T^T u = 0,
+    feasibility Tx = t."""
+    h, y, x, t, u = tv16["h"], tv16["y"], tv16["x"], tv16["t"], tv16["u"]
+    g = tv16["beta"] * admm.adjoint_H(admm.forward_H(x, h) - y, h) + tv16["rho"] * admm.tv_adjoint(u)
+    assert np.linalg.norm(g) / np.linalg.norm(tv16["beta"] * admm.adjoint_H(y, h)) < 1e-6
+    w = admm.tv_forward(x)
+    assert np.linalg.norm(w - t) <= 1e-6 * np.linalg.norm(w)
+
+
+def test_he_yuan_monotone(tv16):
+    """Two-block ADMM with fixed rho (He & Yuan 2015): rho(||t^{l+1}-t^l||^2 + ||u^{l+1}-u^l||^2)
+    is non-increasing."""
+    h = tv16["hist"]
+    q = [np.sum((b.t - a.t) ** 2) + np.sum((b.u - a.u) ** 2) for a, b in zip(h[:-1], h[1:])]
+    q = np.array(q[:800])
+    assert np.all(q[1:] <= q[:-1] * (1 + 1e-9) + 1e-28)
+
+
+def test_objective_decreases(tv16):
+    S, rec = tv16["S"], tv16["hist"]
+    f = lambda x: admm.objective(x, tv16["h"], tv16["y"], "tv", tv16["lam"], tv16["beta"])
+    assert f(rec[-1].x) < f(rec[0].x)
+    tail = np.array([f(r.x) for r in rec[-400::50]])
+    assert np.all(np.abs(np.diff(tail)) <= 1e-9 * abs(tail[-1]) + 1e-12) or np.all(np.diff(tail) <= 1e-12)
+
+
+# ----------------------------------------------------------------- synthesis (Alg. 2)
+def test_sherman_morrison_dense():
+    """Eq. solz_DFT_SM with reading R10 solves (rho I + conj(theta) theta^T) v = c."""
+    L = 32
+    th = RNG.standard_normal(L) + 1j * RNG.standard_normal(L)
+    c = RNG.standard_normal(L) + 1j * RNG.standard_normal(L)
+    rho = 0.8
+    A = rho * np.eye(L) + np.outer(th.conj(), th)
+    v = admm.sherman_morrison(th, c, rho)
+    assert np.abs(A @ v - c).max() < 1e-12
+
+
+@pytest.fixture(scope="module")
+def cd8():
+    rng = np.random.default_rng(5)
+    N, K, M, L, P = 8, 2, 2, 3, 3
+    d = rng.standard_normal((L, P, P))
+    d /= np.linalg.norm(d.reshape(L, -1), axis=1)[:, None, None]
+    h = random_psfs(rng, K, M, N)
+    x0 = rng.standard_normal((M, N, N))
+    y = admm.forward_H(x0, h)
+    C = admm.convdict_setup(h, y, d, 0.1, 0.9, 1.7)
+    z = rng.standard_normal((L, M, N, N))
+    t = rng.standard_normal((L, M, N, N))
+    u = rng.standard_normal((L, M, N, N))
+    return dict(rng=rng, N=N, K=K, M=M, L=L, d=d, h=h, y=y, C=C, z=z, t=t, u=u)
+
+
+def test_convdict_x_and_z_update_dense(cd8):
+    """Eq. iterd_ADMM1 and Eq. iterd_ADMM2 solved densely (reading R9: 1/2||Dz - x||^2,
+    rho/2 ||z - t + u||^2) match Eqs. solx_synt_DFT and solz_DFT/solz_DFT_SM of the oracle."""
+    N, M, L, d, h, y, C = cd8["N"], cd8["M"], cd8["L"], cd8["d"], cd8["h"], cd8["y"], cd8["C"]
+    z, t, u = cd8["z"], cd8["t"], cd8["u"]
+    de = admm.embed_filters(d, N)
+    Dop = lambda zz: np.stack([sum(admm.circconv2(zz[l, m], de[l]) for l in range(L)) for m in range(M)])
+    H = dense_operator(lambda v: admm.forward_H(v, h), (M, N, N))
+    D = dense_operator(Dop, (L, M, N, N))
+    beta, rho = C.beta, C.rho
+    A = np.concatenate([math.sqrt(beta) * H, np.eye(M * N * N)])
+    b = np.concatenate([math.sqrt(beta) * y.ravel(), Dop(z).ravel()])
+    x_ls = np.linalg.lstsq(A, b, rcond=None)[0].reshape(M, N, N)
+    A2 = np.concatenate([D, math.sqrt(rho) * np.eye(L * M * N * N)])
+    b2 = np.concatenate([x_ls.ravel(), math.sqrt(rho) * (t - u).ravel()])
+    z_ls = np.linalg.lstsq(A2, b2, rcond=None)[0].reshape(L, M, N, N)
+    x, z_new, t_new, u_new = admm.convdict_step(C, z, t, u)
+    assert rel(x, x_ls) < 1e-10
+    assert rel(z_new, z_ls) < 1e-9
+    assert np.allclose(t_new, admm.soft(z_new + u, C.lam / C.rho), atol=0)
+    assert np.allclose(u_new, u + z_new - t_new, atol=0)
+
+
+# ----------------------------------------------------------------- fast form vs naive
+@pytest.mark.parametrize("prior", ["tv", "dct8", "l1"])
+def test_fast_oracle_matches_naive(prior):
+    """The fast FP64 oracle (pocketfft) reproduces the naive DFT oracle to <= 1e-11."""
+    rng = np.random.default_rng(11)
+    N, K, M = 16, 3, 2
+    h = random_psfs(rng, K, M, N) if prior != "tv" else inputs.gaussian_psf_bank(N, K, M)
+    y = rng.standard_normal((K, N, N))
+    S = admm.analysis_setup(h, y, prior, 0.05, 0.7, 1.2)
+    F = fast.analysis_setup(h, y, prior, 0.05, 0.7, 1.2)
+    xs, ts, us, _ = admm.run_analysis(S, 20)
+    xf, tf, uf, _, _ = fast.run_analysis(F, 20)
+    assert rel(xf, xs) < 1e-11 and rel(uf, us) < 1e-11
+
+
+def test_fast_convdict_matches_naive(cd8):
+    C = cd8["C"]
+    F = fast.convdict_setup(cd8["h"], cd8["y"], cd8["d"], C.lam, C.rho, C.beta)
+    xs, zs, ts, us, _ = admm.run_convdict(C, 6)
+    xf, zf, tf, uf = fast.run_convdict(F, 6)
+    assert rel(xf, xs) < 1e-11 and rel(zf, zs) < 1e-11
+
+
+def test_fast_oracle_tiny_workload_residuals():
+    """At 64x64x3 the fast and naive oracles agree on 50 iterations of Alg. 1 and on the residuals."""
+    P = inputs.tiny_tv()
+    S = admm.analysis_setup(P.h, P.y, P.prior, P.lam, P.rho, P.beta)
+    F = fast.analysis_setup(P.h, P.y, P.prior, P.lam, P.rho, P.beta)
+    xs, _, us, hist = admm.run_analysis(S, 50, keep_history=True)
+    xf, _, uf, n, rr = fast.run_analysis(F, 50, tol=1e-30)
+    assert n == 50 and rel(xf, xs) < 1e-11
+    assert abs(rr[0] - hist[-1].r_rel) < 1e-9 * hist[-1].r_rel
+    assert abs(rr[1] - hist[-1].s_rel) < 1e-9 * hist[-1].s_rel
