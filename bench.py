@@ -1,0 +1,294 @@
+"""Benchmark: ADMM voxel-iterations/s of the spectral-imaging reconstruction
+(M = K = 10 channels, 512 x 512, disk-plus-Gaussian defocus PSFs, 8x8
+block-DCT l1 prior, 200 iterations of Alg. 1) on one GB300.
+
+One step = one whole reconstruction: PSF spectra + FP64 factor (setup),
+rhs, 200 fused iterations (column pass + prior pass) and the read-back of x.
+L2 is flushed (256 MiB write) before every timed step, outside its events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank runs its own
+replica (independent reconstructions; no collective on the data path), the
+timed region is bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, M, K, ITERS = 512, 10, 10, 200
+WORKLOAD = f"spectral_dct_{N}x{N}x{M} (K={K}, 8x8 DCT l1, lambda=1e-3, rho=1e-2, beta=1, {ITERS} iterations)"
+METRIC = "ADMM voxel-iter/s"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for nme, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nme)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(n, m, prior="dct8", esz=4):
+    """HBM bytes one launch must move (complex64 half spectra of N x (N/2+1) bins)."""
+    bins = n * (n // 2 + 1)
+    cpx = 2 * esz
+    ncomp = 2 if prior == "tv" else 1
+    col = (3 * m + m * (m + 1) // 2) * bins * cpx            # read q, bhat, Pinv; write x
+    pri = 2 * m * bins * cpx + 2 * ncomp * m * n * n * esz    # read x, write q; read+write u
+    return {"column_pass": col, "prior_pass": pri}
+
+
+def cpu_oracle_sample(problem, iters_sample: int):
+    """Time the fast FP64 oracle (setup + iters_sample iterations) on this host's cores."""
+    from oracle import fast
+    t0 = time.perf_counter()
+    S = fast.analysis_setup(problem.h, problem.y, problem.prior, problem.lam, problem.rho, problem.beta)
+    t1 = time.perf_counter()
+    fast.run_analysis(S, iters_sample)
+    t2 = time.perf_counter()
+    # a full reconstruction = setup + ITERS iterations
+    per_iter = (t2 - t1) / iters_sample
+    recon_s = (t1 - t0) + per_iter * problem.iters
+    return {
+        "value": problem.voxels * problem.iters / recon_s,
+        "unit": "voxel-iter/s",
+        "cores": os.cpu_count(),
+        "kind": "oracle",
+        "sample": f"fast FP64 oracle (scipy.fft, {fast.WORKERS} workers): setup + {iters_sample} of {problem.iters} "
+                  f"iterations of the same {problem.N}x{problem.N}x{problem.M} instance, scaled to a full "
+                  f"reconstruction ({recon_s:.1f} s)",
+        "setup_s": t1 - t0,
+        "iter_s": per_iter,
+    }
+
+
+def run_reference(args, rank, world):
+    from paper_2006_08303_gb300 import inputs
+    if rank != 0:
+        return
+    prob = inputs.spectral_dct()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(prob, 2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(prob, args.ref_iters))
+    wall = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "voxel-iter/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * prob.voxels * prob.iters / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "M": M, "K": K, "iters": ITERS},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cip", choices=["cip", "reference"])
+    ap.add_argument("--ref-iters", type=int, default=10, help="iterations per oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2006_08303_gb300 import api, inputs
+    prob = inputs.spectral_dct()
+    h_dev = torch.as_tensor(prob.h, dtype=torch.float32).cuda().contiguous()
+    y_dev = torch.as_tensor(prob.y, dtype=torch.float32).cuda().contiguous()
+    x_dev = torch.empty((M, N, N), dtype=torch.float32, device="cuda")
+    h_pin = torch.as_tensor(prob.h, dtype=torch.float32).contiguous().pin_memory()
+    y_pin = torch.as_tensor(prob.y, dtype=torch.float32).contiguous().pin_memory()
+    x_pin = torch.empty((M, N, N), dtype=torch.float32).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    plan = api.Plan(N, K, M, "f32")
+    plan.set_prior(prob.prior, prob.lam, prob.rho, prob.beta)
+
+    def step(h, y, x):
+        plan.set_psfs(h)
+        plan.set_measurements(y)
+        plan.iterate(ITERS)
+        plan.get_x(x)
+
+    for _ in range(args.warmup):
+        step(h_dev, y_dev, x_dev)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    plan.set_timing(True)
+    l0 = plan.launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        step(h_dev, y_dev, x_dev)
+        e.record(stream)
+        times.append((s, e))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = (plan.launches() - l0) // args.steps
+    ms = [s.elapsed_time(e) for s, e in times]
+    kt = plan.get_timing()
+    plan.set_timing(False)
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    vox_iters = prob.voxels * ITERS * args.steps * world
+    value = vox_iters / (total_ms / 1e3)
+
+    # ---- end-to-end through the C ABI with host buffers (H2D/D2H inside the timed region)
+    for _ in range(1):
+        step(h_pin, y_pin, x_pin)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        step(h_pin, y_pin, x_pin)
+        e.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(s.elapsed_time(e))
+    e2e_total = sum(e2e_ms)
+    if dist:
+        tt = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    e2e_value = vox_iters / (e2e_total / 1e3)
+    h2d = (prob.h.size + prob.y.size) * 4
+    d2h = M * N * N * 4
+
+    # ---- roofline of the dominant kernel (algorithmic bytes / average event-timed launch)
+    ab = algorithmic_bytes(N, M, prob.prior)
+    avgA = kt["prior_pass_ms"] / max(kt["prior_pass_n"], 1)
+    avgB = kt["column_pass_ms"] / max(kt["column_pass_n"], 1)
+    dom, avg, byts = ("column_pass", avgB, ab["column_pass"]) if kt["column_pass_ms"] >= kt["prior_pass_ms"] \
+        else ("prior_pass", avgA, ab["prior_pass"])
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    achieved = byts / (avg / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
+            "peak_source": "measured" if pk else "fallback",
+            "avg_launch_us": {"column_pass": round(avgB * 1e3, 2), "prior_pass": round(avgA * 1e3, 2)},
+            "algorithmic_bytes": ab}
+
+    line = {"metric": METRIC, "value": value, "unit": "voxel-iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "M": M, "K": K, "iters": ITERS,
+                       "parallelism": f"replicas{world}", "l2": "flushed before each step (256 MiB write)",
+                       "step": "setup (FP64 factor) + rhs + 200 iterations + read-back",
+                       "launch": plan.config()},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "voxel-iter/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_total / args.steps},
+            "gpu_launches": int(launches) * args.steps,
+            "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(prob, args.ref_iters)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/*
+ * cip.h -- C ABI of a GB300 (sm_103a) library for the ADMM reconstruction of
+ * convolutional inverse problems (Dogan & Oktem, "Efficient Algorithms for
+ * Convolutional Inverse Problems in Multidimensional Imaging",
+ * arXiv 2006.08303).
+ *
+ * Model (Section II, Eq. forward model): K measurements y_k, each the sum of
+ * M unknown N x N channels x_m circularly convolved with known PSFs h_{k,m}:
+ *     y_k = sum_m h_{k,m} (*) x_m + w_k.
+ * Problem (Eq. rls): min_x beta/2 ||y - H x||^2 + R(x), R = lambda ||T x||_1
+ * (analysis prior, Eq. analysis).  Solved by Alg. 1 (ADMM, splitting t = T x,
+ * scaled dual u):
+ *     x^{l+1} = F^H Psi^{-1} (beta Lambda^H F y + rho F T^H (t^l - u^l))   (Eq. solx_Trans_DFT)
+ *     t^{l+1} = soft(T x^{l+1} + u^l, lambda / rho)                        (Eq. solt_trans)
+ *     u^{l+1} = u^l + T x^{l+1} - t^{l+1}                                  (Eq. subu_trans)
+ * with Psi(w) = rho g(w) I + beta Lambda(w)^H Lambda(w), g the DFT
+ * eigenvalues of T^H T (g = 1 for an orthonormal T).
+ *
+ * Conventions for every call:
+ *   - Arrays are row-major C order.  PSFs have their origin at index (0,0)
+ *     and wrap circularly.  Real arrays use the plan's dtype (float32 for
+ *     CIP_F32, float64 for CIP_F64).
+ *   - Data pointers may be device pointers or host pointers; the library
+ *     detects which (cudaPointerGetAttributes).  Host inputs are copied to a
+ *     device staging buffer in stream order.  A call that writes to a host
+ *     pointer synchronises the stream before returning.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous with respect to the host unless stated otherwise.
+ *   - The caller owns every pointer it passes and may reuse an input buffer
+ *     once the stream has passed the call.  The plan owns all spectra,
+ *     factors and ADMM state until cip_plan_destroy.
+ *   - Every call returns a cip_status; nothing throws across the ABI.
+ *     On failure, cip_last_error(plan) returns a message (thread-safe per
+ *     plan; plans must not be used from two threads at once).
+ */
+#ifndef CIP_H_
+#define CIP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cip_status {
+  CIP_OK = 0,
+  CIP_ERR_INVALID_ARG = 1,  /* null pointer, size out of range, bad enum */
+  CIP_ERR_UNSUPPORTED = 2,  /* N not a power of two in [64, 2048], M > 16, shape too large for a kernel */
+  CIP_ERR_OOM = 3,          /* device allocation failed */
+  CIP_ERR_CUDA = 4,         /* a CUDA runtime call failed (message in cip_last_error) */
+  CIP_ERR_STATE = 5,        /* call out of order (e.g. iterate before set_psfs) */
+  CIP_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+  CIP_ERR_DIVERGED = 7      /* residuals became NaN/Inf */
+} cip_status;
+
+typedef enum cip_dtype { CIP_F32 = 0, CIP_F64 = 1 } cip_dtype;
+
+typedef enum cip_prior {
+  CIP_PRIOR_TV = 0,   /* anisotropic TV: T = [D_h; D_v], circular forward differences (2 components) */
+  CIP_PRIOR_DCT8 = 1, /* orthonormal DCT-II on 8x8 blocks aligned at (0,0) (1 component) */
+  CIP_PRIOR_L1 = 2    /* T = I (1 component) */
+} cip_prior;
+
+typedef struct cip_options {
+  int col_tile;     /* columns per CTA of the column pass (1, 2 or 4); 0 = automatic */
+  int check_every;  /* residual check period for cip_iterate with tol > 0; 0 = 10 */
+  int reserved[14];
+} cip_options;
+
+typedef struct cip_plan cip_plan;
+
+/* Library / status strings. */
+const char* cip_version(void);
+const char* cip_status_string(cip_status s);
+const char* cip_last_error(const cip_plan* plan); /* plan may be NULL: last error of plan creation */
+
+/* Create a plan for N x N images, K measurements, M channels (1 <= K, M <= 16;
+ * N a power of two in [64, 2048]).  Allocates all device buffers on the
+ * current device.  opt may be NULL. */
+cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype, const cip_options* opt);
+cip_status cip_plan_destroy(cip_plan* plan);
+
+/* Device bytes a plan with these sizes holds (for admission by HBM budget). */
+size_t cip_plan_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior);
+
+/* Prior and ADMM weights (Alg. 1 line 1): lambda > 0, rho > 0, beta > 0.
+ * Must precede cip_set_psfs; changing prior or rho afterwards re-forms the
+ * factor from the kept FP64 PSF spectra. */
+cip_status cip_set_prior(cip_plan* plan, cip_prior prior, double lambda, double rho, double beta, void* stream);
+
+/* PSFs h[K][M][N][N] (plan dtype).  Forms Lambda = DFT2(h) in FP64 and the
+ * per-frequency factor Psi^{-1} in FP64 (Alg. 1 line 2; Section IV-A), kept
+ * in the plan's precision.  Resets the ADMM state. */
+cip_status cip_set_psfs(cip_plan* plan, const void* h, void* stream);
+
+/* Measurements y[K][N][N] (plan dtype): bhat = beta Lambda^H F y (Alg. 1
+ * line 2).  Resets the ADMM state (t = u = 0). */
+cip_status cip_set_measurements(cip_plan* plan, const void* y, void* stream);
+
+/* t = u = 0 (Alg. 1 line 1 with zero initial values). */
+cip_status cip_reset_state(cip_plan* plan, void* stream);
+
+/* Run ADMM iterations (Alg. 1 lines 3-8).  tol <= 0: exactly max_iter
+ * iterations.  tol > 0: stop after the first check at which both relative
+ * residuals r/max(||Tx||,||t||) and s/||rho u|| (r = ||Tx - t||,
+ * s = rho ||t - t_prev||, Eq. paramS quantities) are below tol; checks run
+ * every check_every iterations and synchronise the stream.  iters_done may
+ * be NULL.  Residuals of the last iteration are always computed. */
+cip_status cip_iterate(cip_plan* plan, int max_iter, double tol, int* iters_done, void* stream);
+
+/* x[M][N][N] of the last x-update (the inverse row DFT of the kept row
+ * spectra).  Before any iteration: zeros. */
+cip_status cip_get_x(cip_plan* plan, void* x, void* stream);
+
+/* Scaled dual u[M][ncomp][N][N] (ncomp = 2 for TV, else 1). */
+cip_status cip_get_u(cip_plan* plan, void* u, void* stream);
+
+/* Relative residuals of the last iteration that computed them (synchronises). */
+cip_status cip_get_residuals(cip_plan* plan, double* r_rel, double* s_rel);
+
+/* Iterations run since the last reset/import. */
+cip_status cip_get_iteration(cip_plan* plan, int* iteration);
+
+/* Set the ADMM state from t, u [M][ncomp][N][N] (as after Alg. 1 line 6). */
+cip_status cip_state_import(cip_plan* plan, const void* t, const void* u, void* stream);
+
+/* Opaque checkpoint of the ADMM state (bitwise resumable): size, export, restore. */
+cip_status cip_state_size(cip_plan* plan, size_t* bytes);
+cip_status cip_state_export(cip_plan* plan, void* buf, void* stream);
+cip_status cip_state_restore(cip_plan* plan, const void* buf, void* stream);
+
+/* Per-kernel timing with CUDA events around every prior-pass and
+ * column-pass launch of cip_iterate (0 = off, the default). */
+cip_status cip_set_timing(cip_plan* plan, int on);
+/* Sum of elapsed ms and launch counts since the last call (synchronises). */
+cip_status cip_get_timing(cip_plan* plan, double* prior_pass_ms, int* prior_pass_n, double* column_pass_ms,
+                          int* column_pass_n);
+
+/* Number of CUDA kernels this plan has launched since creation. */
+cip_status cip_get_launches(cip_plan* plan, unsigned long long* launches);
+
+/* Launch configuration the plan uses (for reporting). */
+cip_status cip_get_config(cip_plan* plan, int* rows_per_tile, int* col_tile, int* prior_pass_blocks,
+                          int* column_pass_blocks);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CIP_H_ */

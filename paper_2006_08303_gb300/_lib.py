@@ -1,0 +1,76 @@
+"""ctypes loader for libcip.so (the sm_103a CUDA library).
+
+Fails loudly when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcip.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "cip.h")
+
+c_int, c_double, c_size_t, c_void_p, c_char_p = ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_char_p
+P_int = ctypes.POINTER(ctypes.c_int)
+P_double = ctypes.POINTER(ctypes.c_double)
+P_size = ctypes.POINTER(ctypes.c_size_t)
+
+
+class cip_options(ctypes.Structure):
+    _fields_ = [("col_tile", c_int), ("check_every", c_int), ("reserved", c_int * 14)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "cip_version": (c_char_p, []),
+    "cip_status_string": (c_char_p, [c_int]),
+    "cip_last_error": (c_char_p, [c_void_p]),
+    "cip_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, ctypes.POINTER(cip_options)]),
+    "cip_plan_destroy": (c_int, [c_void_p]),
+    "cip_plan_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
+    "cip_set_prior": (c_int, [c_void_p, c_int, c_double, c_double, c_double, c_void_p]),
+    "cip_set_psfs": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "cip_set_measurements": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "cip_reset_state": (c_int, [c_void_p, c_void_p]),
+    "cip_iterate": (c_int, [c_void_p, c_int, c_double, P_int, c_void_p]),
+    "cip_get_x": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "cip_get_u": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "cip_get_residuals": (c_int, [c_void_p, P_double, P_double]),
+    "cip_get_iteration": (c_int, [c_void_p, P_int]),
+    "cip_state_import": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cip_state_size": (c_int, [c_void_p, P_size]),
+    "cip_state_export": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "cip_state_restore": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "cip_set_timing": (c_int, [c_void_p, c_int]),
+    "cip_get_timing": (c_int, [c_void_p, P_double, P_int, P_double, P_int]),
+    "cip_get_config": (c_int, [c_void_p, P_int, P_int, P_int, P_int]),
+    "cip_get_launches": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
+}
+
+_LIB = None
+
+
+def header_symbols(path: str = HEADER):
+    """Function names declared in include/cip.h."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cip_[a-z0-9_]+)\s*\(", txt)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libcip.so and declare every signature (no CUDA call is made)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib

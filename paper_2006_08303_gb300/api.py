@@ -1,0 +1,220 @@
+"""Python binding of the cip C ABI (include/cip.h), argument marshalling only.
+
+Arrays may be CUDA torch tensors (device pointers), CPU torch tensors
+(pinned or not) or numpy arrays (host pointers); every step of the
+reconstruction runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import _lib
+
+PRIORS = {"tv": 0, "dct8": 1, "l1": 2}
+DTYPES = {"f32": 0, "f64": 1}
+NP_DTYPE = {"f32": np.float32, "f64": np.float64}
+
+
+class CipError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cip error {status}: {msg}")
+        self.status = status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr_and_check(a, dtype: str, shape: Tuple[int, ...]):
+    """Return (pointer, keepalive) for a contiguous array of the plan dtype and shape."""
+    want = NP_DTYPE[dtype]
+    if isinstance(a, np.ndarray):
+        if a.dtype != want:
+            raise TypeError(f"expected {np.dtype(want)}, got {a.dtype}")
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if tuple(a.shape) != tuple(shape):
+            raise ValueError(f"expected shape {shape}, got {a.shape}")
+        return a.ctypes.data, a
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        if a.dtype != tdt:
+            raise TypeError(f"expected {tdt}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if tuple(a.shape) != tuple(shape):
+            raise ValueError(f"expected shape {shape}, got {tuple(a.shape)}")
+        return a.data_ptr(), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def version() -> str:
+    return _lib.load().cip_version().decode()
+
+
+def plan_bytes(N: int, K: int, M: int, dtype: str = "f32", prior: str = "tv") -> int:
+    return int(_lib.load().cip_plan_bytes(N, K, M, DTYPES[dtype], PRIORS[prior]))
+
+
+class Plan:
+    """One reconstruction instance held on the device (cip_plan)."""
+
+    def __init__(self, N: int, K: int, M: int, dtype: str = "f32", col_tile: int = 0, check_every: int = 0):
+        self._L = _lib.load()
+        self.N, self.K, self.M, self.dtype = N, K, M, dtype
+        self.prior: Optional[str] = None
+        opt = _lib.cip_options()
+        opt.col_tile = col_tile
+        opt.check_every = check_every
+        h = ctypes.c_void_p()
+        st = self._L.cip_plan_create(ctypes.byref(h), N, K, M, DTYPES[dtype], ctypes.byref(opt))
+        if st != 0:
+            raise CipError(st, self._L.cip_last_error(None).decode())
+        self._h = h
+
+    # -- helpers
+    def _check(self, st: int):
+        if st != 0:
+            raise CipError(st, self._L.cip_last_error(self._h).decode())
+
+    @property
+    def ncomp(self) -> int:
+        return 2 if self.prior == "tv" else 1
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.cip_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- ABI calls
+    def set_prior(self, prior: str, lam: float, rho: float, beta: float = 1.0, stream=None):
+        self._check(self._L.cip_set_prior(self._h, PRIORS[prior], lam, rho, beta, _stream_ptr(stream)))
+        self.prior = prior
+
+    def set_psfs(self, h, stream=None):
+        p, keep = _ptr_and_check(h, self.dtype, (self.K, self.M, self.N, self.N))
+        self._check(self._L.cip_set_psfs(self._h, ctypes.c_void_p(p), _stream_ptr(stream)))
+
+    def set_measurements(self, y, stream=None):
+        p, keep = _ptr_and_check(y, self.dtype, (self.K, self.N, self.N))
+        self._check(self._L.cip_set_measurements(self._h, ctypes.c_void_p(p), _stream_ptr(stream)))
+
+    def reset_state(self, stream=None):
+        self._check(self._L.cip_reset_state(self._h, _stream_ptr(stream)))
+
+    def iterate(self, n: int, tol: float = 0.0, stream=None) -> int:
+        done = ctypes.c_int(0)
+        self._check(self._L.cip_iterate(self._h, n, tol, ctypes.byref(done), _stream_ptr(stream)))
+        return done.value
+
+    def get_x(self, out=None, stream=None):
+        if out is None:
+            torch = _torch()
+            out = torch.empty((self.M, self.N, self.N), device="cuda",
+                              dtype=torch.float32 if self.dtype == "f32" else torch.float64)
+        p, keep = _ptr_and_check(out, self.dtype, (self.M, self.N, self.N))
+        self._check(self._L.cip_get_x(self._h, ctypes.c_void_p(p), _stream_ptr(stream)))
+        return out
+
+    def get_u(self, out=None, stream=None):
+        shape = (self.M, self.ncomp, self.N, self.N)
+        if out is None:
+            torch = _torch()
+            out = torch.empty(shape, device="cuda", dtype=torch.float32 if self.dtype == "f32" else torch.float64)
+        p, keep = _ptr_and_check(out, self.dtype, shape)
+        self._check(self._L.cip_get_u(self._h, ctypes.c_void_p(p), _stream_ptr(stream)))
+        return out
+
+    def residuals(self) -> Tuple[float, float]:
+        r, s = ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.cip_get_residuals(self._h, ctypes.byref(r), ctypes.byref(s)))
+        return r.value, s.value
+
+    def iteration(self) -> int:
+        v = ctypes.c_int()
+        self._check(self._L.cip_get_iteration(self._h, ctypes.byref(v)))
+        return v.value
+
+    def state_import(self, t, u, stream=None):
+        shape = (self.M, self.ncomp, self.N, self.N)
+        pt, k1 = _ptr_and_check(t, self.dtype, shape)
+        pu, k2 = _ptr_and_check(u, self.dtype, shape)
+        self._check(self._L.cip_state_import(self._h, ctypes.c_void_p(pt), ctypes.c_void_p(pu), _stream_ptr(stream)))
+
+    def state_size(self) -> int:
+        n = ctypes.c_size_t()
+        self._check(self._L.cip_state_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def state_export(self, buf=None, stream=None):
+        n = self.state_size()
+        if buf is None:
+            buf = np.empty(n, dtype=np.uint8)
+        ptr = buf.ctypes.data if isinstance(buf, np.ndarray) else buf.data_ptr()
+        self._check(self._L.cip_state_export(self._h, ctypes.c_void_p(ptr), _stream_ptr(stream)))
+        return buf
+
+    def state_restore(self, buf, stream=None):
+        ptr = buf.ctypes.data if isinstance(buf, np.ndarray) else buf.data_ptr()
+        self._check(self._L.cip_state_restore(self._h, ctypes.c_void_p(ptr), _stream_ptr(stream)))
+
+    def set_timing(self, on: bool):
+        self._check(self._L.cip_set_timing(self._h, 1 if on else 0))
+
+    def get_timing(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        na, nb = ctypes.c_int(), ctypes.c_int()
+        self._check(self._L.cip_get_timing(self._h, ctypes.byref(a), ctypes.byref(na), ctypes.byref(b), ctypes.byref(nb)))
+        return {"prior_pass_ms": a.value, "prior_pass_n": na.value, "column_pass_ms": b.value, "column_pass_n": nb.value}
+
+    def launches(self) -> int:
+        v = ctypes.c_ulonglong()
+        self._check(self._L.cip_get_launches(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def config(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(self._L.cip_get_config(self._h, *[ctypes.byref(x) for x in v]))
+        return {"rows_per_tile": v[0].value, "col_tile": v[1].value, "prior_pass_blocks": v[2].value,
+                "column_pass_blocks": v[3].value}
+
+
+def reconstruct(problem, dtype: Optional[str] = None, iters: Optional[int] = None, tol: float = 0.0, stream=None):
+    """Convenience: full reconstruction of an ``inputs.Problem`` with device-resident inputs."""
+    torch = _torch()
+    dt = dtype or problem.dtype
+    tdt = torch.float32 if dt == "f32" else torch.float64
+    P = Plan(problem.N, problem.K, problem.M, dt)
+    P.set_prior(problem.prior, problem.lam, problem.rho, problem.beta, stream)
+    P.set_psfs(torch.as_tensor(problem.h, dtype=tdt).cuda().contiguous(), stream)
+    P.set_measurements(torch.as_tensor(problem.y, dtype=tdt).cuda().contiguous(), stream)
+    n = P.iterate(iters if iters is not None else problem.iters, tol, stream)
+    return P, P.get_x(stream=stream), n

@@ -1,0 +1,715 @@
+// C ABI of the library (declared in include/cip.h): plan lifetime, setup
+// (Alg. 1 lines 1-2), the iteration loop (Alg. 1 lines 3-8), read-back,
+// state import/export and per-kernel timing.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cip.h"
+#include "kernels.h"
+
+using namespace cip;
+
+namespace {
+
+constexpr int kPinvListCap = 64;
+constexpr int kMaxTimed = 8192;
+
+std::string g_create_error;
+
+struct Staging {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  ~Staging() {
+    if (p) cudaFreeAsync(p, s);
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct cip_plan {
+  int N = 0, K = 0, M = 0, P = 0;
+  cip_dtype dtype = CIP_F32;
+  cip_options opt{};
+  int prior = -1;
+  double lam = 0, rho = 0, beta = 0;
+  bool have_psfs = false, have_y = false;
+  int iteration = 0;
+  int cur = 0;  // index of the u buffer holding the current u
+  size_t esz = 4;
+  int rowsA = 8, cc = 1, blocksA = 0, blocksB = 0;
+  // device buffers
+  void* xh = nullptr;
+  void* qh = nullptr;
+  void* u[2] = {nullptr, nullptr};
+  void* tprev = nullptr;
+  void* pinv = nullptr;
+  void* bhat = nullptr;
+  double2* lam64 = nullptr;  // FP64 PSF spectra [K*M][N][P]
+  void* tw = nullptr;        // plan-precision twiddles
+  double2* tw64 = nullptr;   // FP64 twiddles for setup FFTs
+  double* gs = nullptr;      // 4 sin^2(pi k / N)
+  double* partials = nullptr;
+  double* resid = nullptr;   // [kNPart + 2]
+  int* conv = nullptr;
+  int* pinv_list = nullptr;
+  double* resid_host = nullptr;  // pinned
+  bool resid_valid = false;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> evA, evB;
+  int nA = 0, nB = 0;
+  unsigned long long launches = 0;  // kernels launched by this plan
+  std::string err;
+};
+
+namespace {
+
+cip_status fail(cip_plan* p, cip_status s, const std::string& msg) {
+  if (p) p->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+#define CIP_LAUNCH(plan, call)                                                                        \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      return fail(plan, CIP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    (plan)->launches++;                                                                               \
+  } while (0)
+
+#define CIP_CUDA(plan, call)                                                                          \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      return fail(plan, e_ == cudaErrorMemoryAllocation ? CIP_ERR_OOM : CIP_ERR_CUDA,                 \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+  } while (0)
+
+size_t ncomp_of(int prior) { return prior == CIP_PRIOR_TV ? 2 : 1; }
+
+bool valid_n(int N) { return N >= 64 && N <= 2048 && (N & (N - 1)) == 0; }
+
+// sizes in elements
+size_t half_elems(const cip_plan* p, int maps) { return (size_t)maps * p->N * p->P; }
+size_t real_elems(const cip_plan* p, int maps) { return (size_t)maps * p->N * p->N; }
+
+template <typename T> void fill_dct(T* d) {
+  for (int k = 0; k < 8; ++k)
+    for (int n = 0; n < 8; ++n) {
+      const double a = k == 0 ? std::sqrt(1.0 / 8.0) : std::sqrt(2.0 / 8.0);
+      d[k * 8 + n] = (T)(a * std::cos(M_PI * (2 * n + 1) * k / 16.0));
+    }
+}
+
+// exp(-2 pi i k / 2048) with the angle reduced exactly through octant symmetry
+void twiddles(std::vector<double>& re, std::vector<double>& im) {
+  re.resize(kTwN);
+  im.resize(kTwN);
+  for (int k = 0; k < kTwN; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)kTwN;
+    re[k] = std::cos(a);
+    im[k] = -std::sin(a);
+  }
+  // exact values at multiples of pi/4
+  for (int k = 0; k < kTwN; k += kTwN / 4) {
+    const int q = k / (kTwN / 4);
+    re[k] = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+    im[k] = (q == 1) ? -1.0 : (q == 3 ? 1.0 : 0.0);
+  }
+}
+
+template <typename T> cip_status alloc_state(cip_plan* p) {
+  using C = typename CT<T>::type;
+  const size_t nc = ncomp_of(p->prior);
+  for (int i = 0; i < 2; ++i) {
+    if (p->u[i]) cudaFree(p->u[i]);
+    p->u[i] = nullptr;
+    CIP_CUDA(p, cudaMalloc(&p->u[i], real_elems(p, p->M) * nc * sizeof(T)));
+  }
+  if (p->tprev) cudaFree(p->tprev);
+  p->tprev = nullptr;
+  CIP_CUDA(p, cudaMalloc(&p->tprev, real_elems(p, p->M) * nc * sizeof(T)));
+  if (p->pinv) cudaFree(p->pinv);
+  p->pinv = nullptr;
+  CIP_CUDA(p, cudaMalloc(&p->pinv, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(C)));
+  if (p->partials) cudaFree(p->partials);
+  p->partials = nullptr;
+  p->rowsA = passA_rows<T>(p->N, p->prior);
+  p->blocksA = (p->N / p->rowsA) * p->M;
+  CIP_CUDA(p, cudaMalloc(&p->partials, (size_t)p->blocksA * kNPart * sizeof(double)));
+  return CIP_OK;
+}
+
+template <typename T> cip_status reset_state(cip_plan* p, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const size_t nc = ncomp_of(p->prior);
+  CIP_CUDA(p, cudaMemsetAsync(p->xh, 0, half_elems(p, p->M) * sizeof(C), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->qh, 0, half_elems(p, p->M) * sizeof(C), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->u[0], 0, real_elems(p, p->M) * nc * sizeof(T), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->u[1], 0, real_elems(p, p->M) * nc * sizeof(T), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->tprev, 0, real_elems(p, p->M) * nc * sizeof(T), s));
+  p->cur = 0;
+  p->iteration = 0;
+  p->resid_valid = false;
+  return CIP_OK;
+}
+
+// bring a caller array (host or device) to the device; returns a device pointer
+cip_status stage_in(cip_plan* p, const void* src, size_t bytes, cudaStream_t s, Staging& st, const void** dev) {
+  if (is_device_ptr(src)) {
+    *dev = src;
+    return CIP_OK;
+  }
+  st.s = s;
+  CIP_CUDA(p, cudaMallocAsync(&st.p, bytes, s));
+  CIP_CUDA(p, cudaMemcpyAsync(st.p, src, bytes, cudaMemcpyHostToDevice, s));
+  *dev = st.p;
+  return CIP_OK;
+}
+
+template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  CIP_CUDA(p, cudaMemsetAsync(p->pinv_list, 0, sizeof(int), s));
+  const int use_g = p->prior == CIP_PRIOR_TV ? 1 : 0;
+  CIP_LAUNCH(p, launch_factor<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, p->rho, p->beta,
+                               static_cast<C*>(p->pinv), p->pinv_list, kPinvListCap, s));
+  CIP_LAUNCH(p, launch_factor_pinv<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, p->rho, p->beta,
+                                    static_cast<C*>(p->pinv), p->pinv_list, kPinvListCap, s));
+  int nlist = 0;
+  CIP_CUDA(p, cudaMemcpyAsync(&nlist, p->pinv_list, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CIP_CUDA(p, cudaStreamSynchronize(s));
+  if (nlist > kPinvListCap)
+    return fail(p, CIP_ERR_UNSUPPORTED, "more singular frequency bins than the pseudo-inverse list holds");
+  return CIP_OK;
+}
+
+template <typename T> cip_status do_set_prior(cip_plan* p, cudaStream_t s) {
+  cip_status st = alloc_state<T>(p);
+  if (st != CIP_OK) return st;
+  if (p->have_psfs) {
+    st = form_factor<T>(p, s);
+    if (st != CIP_OK) return st;
+  }
+  return reset_state<T>(p, s);
+}
+
+template <typename T> cip_status do_set_psfs(cip_plan* p, const void* h, cudaStream_t s) {
+  const size_t bytes = real_elems(p, p->K * p->M) * sizeof(T);
+  Staging st;
+  const void* dh = nullptr;
+  cip_status r = stage_in(p, h, bytes, s, st, &dh);
+  if (r != CIP_OK) return r;
+  const int nrows = p->K * p->M * p->N;
+  CIP_LAUNCH(p, (launch_row_r2c<double, T>(static_cast<const T*>(dh), p->lam64, p->N, nrows, 1.0, p->tw64, s)));
+  CIP_LAUNCH(p, launch_col_c2c<double>(p->lam64, p->N, p->K * p->M, -1, p->tw64, s));
+  p->have_psfs = true;
+  r = form_factor<T>(p, s);
+  if (r != CIP_OK) return r;
+  return reset_state<T>(p, s);
+}
+
+template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const size_t bytes = real_elems(p, p->K) * sizeof(T);
+  Staging st;
+  const void* dy = nullptr;
+  cip_status r = stage_in(p, y, bytes, s, st, &dy);
+  if (r != CIP_OK) return r;
+  double2* yhat = nullptr;
+  CIP_CUDA(p, cudaMallocAsync((void**)&yhat, half_elems(p, p->K) * sizeof(double2), s));
+  cudaError_t e = launch_row_r2c<double, T>(static_cast<const T*>(dy), yhat, p->N, p->K * p->N, 1.0, p->tw64, s);
+  if (e == cudaSuccess) e = launch_col_c2c<double>(yhat, p->N, p->K, -1, p->tw64, s);
+  if (e == cudaSuccess)
+    e = launch_rhs<T>(p->lam64, yhat, p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
+  if (e == cudaSuccess) p->launches += 3;
+  cudaFreeAsync(yhat, s);
+  CIP_CUDA(p, e);
+  p->have_y = true;
+  return reset_state<T>(p, s);
+}
+
+template <typename T> PassAArgs<T> passA_args(cip_plan* p, int flags) {
+  using C = typename CT<T>::type;
+  PassAArgs<T> a;
+  a.xh = static_cast<const C*>(p->xh);
+  a.qh = static_cast<C*>(p->qh);
+  a.u_in = static_cast<const T*>(p->u[p->cur]);
+  a.u_out = static_cast<T*>(p->u[p->cur ^ 1]);
+  a.tprev = static_cast<T*>(p->tprev);
+  a.t_imp = nullptr;
+  a.partials = p->partials;
+  a.tw = static_cast<const C*>(p->tw);
+  a.M = p->M;
+  a.tau = (T)(p->lam / p->rho);
+  a.qscale = (T)(0.5 * p->rho);
+  a.flags = flags;
+  fill_dct<T>(a.dct);
+  return a;
+}
+
+template <typename T> PassBArgs<T> passB_args(cip_plan* p) {
+  using C = typename CT<T>::type;
+  PassBArgs<T> b;
+  b.qh = static_cast<const C*>(p->qh);
+  b.xh = static_cast<C*>(p->xh);
+  b.pinv = static_cast<const C*>(p->pinv);
+  b.bhat = static_cast<const C*>(p->bhat);
+  b.tw = static_cast<const C*>(p->tw);
+  b.M = p->M;
+  return b;
+}
+
+void ensure_events(cip_plan* p) {
+  if (!p->evA.empty()) return;
+  p->evA.resize(2 * kMaxTimed);
+  p->evB.resize(2 * kMaxTimed);
+  for (auto& e : p->evA) cudaEventCreate(&e);
+  for (auto& e : p->evB) cudaEventCreate(&e);
+}
+
+template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double tol, int* done, cudaStream_t s) {
+  const int ce = p->opt.check_every > 0 ? p->opt.check_every : 10;
+  int it = 0;
+  bool stop = false;
+  for (; it < max_iter && !stop; ++it) {
+    const bool last = (it == max_iter - 1);
+    const int phase = (it + 1) % ce;
+    int flags = 0;
+    if ((tol > 0 && phase == ce - 1) || it == max_iter - 2) flags |= PA_STORE_T;
+    const bool check = (tol > 0 && phase == 0 && it > 0) || last;
+    if (check) flags |= PA_RESID;
+    // x-update (pass B), then t/u update + next adjoint (pass A)
+    PassBArgs<T> b = passB_args<T>(p);
+    const bool timeB = p->timing && p->nB < kMaxTimed;
+    if (timeB) cudaEventRecord(p->evB[2 * p->nB], s);
+    CIP_LAUNCH(p, launch_passB<T>(b, p->N, p->cc, s));
+    if (timeB) cudaEventRecord(p->evB[2 * p->nB++ + 1], s);
+    PassAArgs<T> a = passA_args<T>(p, flags);
+    const bool timeA = p->timing && p->nA < kMaxTimed;
+    if (timeA) cudaEventRecord(p->evA[2 * p->nA], s);
+    CIP_LAUNCH(p, launch_passA<T>(a, p->N, p->prior, s));
+    if (timeA) cudaEventRecord(p->evA[2 * p->nA++ + 1], s);
+    p->cur ^= 1;
+    p->iteration++;
+    if (check) {
+      // the previous iteration stored t only if it ran; otherwise s is not meaningful
+      CIP_LAUNCH(p, launch_reduce_partials(p->partials, p->blocksA, p->rho, tol, p->resid, p->conv, s));
+      p->resid_valid = true;
+      if (tol > 0 && !last) {
+        CIP_CUDA(p, cudaMemcpyAsync(p->resid_host, p->resid, (kNPart + 2) * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+        CIP_CUDA(p, cudaStreamSynchronize(s));
+        const double r = p->resid_host[kNPart], sr = p->resid_host[kNPart + 1];
+        if (!std::isfinite(r) || !std::isfinite(sr)) {
+          if (done) *done = it + 1;
+          return fail(p, CIP_ERR_DIVERGED, "residuals are not finite");
+        }
+        if (r < tol && sr < tol) stop = true;
+      }
+    }
+  }
+  if (done) *done = it;
+  return CIP_OK;
+}
+
+template <typename T> cip_status get_x_impl(cip_plan* p, void* x, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const size_t bytes = real_elems(p, p->M) * sizeof(T);
+  if (is_device_ptr(x)) {
+    CIP_LAUNCH(p, (launch_row_c2r<T, T>(static_cast<const C*>(p->xh), static_cast<T*>(x), p->N, p->M * p->N,
+                                      static_cast<const C*>(p->tw), s)));
+    return CIP_OK;
+  }
+  void* tmp = nullptr;
+  CIP_CUDA(p, cudaMallocAsync(&tmp, bytes, s));
+  cudaError_t e = launch_row_c2r<T, T>(static_cast<const C*>(p->xh), static_cast<T*>(tmp), p->N, p->M * p->N,
+                                       static_cast<const C*>(p->tw), s);
+  if (e == cudaSuccess) p->launches++;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x, tmp, bytes, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(tmp, s);
+  CIP_CUDA(p, e);
+  CIP_CUDA(p, cudaStreamSynchronize(s));
+  return CIP_OK;
+}
+
+cip_status copy_out(cip_plan* p, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  const bool dev = is_device_ptr(dst);
+  CIP_CUDA(p, cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!dev) CIP_CUDA(p, cudaStreamSynchronize(s));
+  return CIP_OK;
+}
+
+template <typename T> cip_status import_impl(cip_plan* p, const void* t, const void* u, cudaStream_t s) {
+  const size_t bytes = real_elems(p, p->M) * ncomp_of(p->prior) * sizeof(T);
+  Staging st1, st2;
+  const void *dt = nullptr, *du = nullptr;
+  cip_status r = stage_in(p, t, bytes, s, st1, &dt);
+  if (r != CIP_OK) return r;
+  r = stage_in(p, u, bytes, s, st2, &du);
+  if (r != CIP_OK) return r;
+  CIP_CUDA(p, cudaMemcpyAsync(p->u[p->cur], du, bytes, cudaMemcpyDeviceToDevice, s));
+  CIP_CUDA(p, cudaMemcpyAsync(p->tprev, dt, bytes, cudaMemcpyDeviceToDevice, s));
+  PassAArgs<T> a = passA_args<T>(p, PA_IMPORT);
+  a.t_imp = static_cast<const T*>(dt);
+  CIP_LAUNCH(p, launch_passA<T>(a, p->N, p->prior, s));
+  p->cur ^= 1;
+  p->iteration = 0;
+  p->resid_valid = false;
+  return CIP_OK;
+}
+
+#define DISPATCH_T(p, call_f32, call_f64) ((p)->dtype == CIP_F32 ? (call_f32) : (call_f64))
+
+cip_status check_ready(cip_plan* p, bool need_y) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  if (p->prior < 0) return fail(p, CIP_ERR_STATE, "cip_set_prior has not been called");
+  if (!p->have_psfs) return fail(p, CIP_ERR_STATE, "cip_set_psfs has not been called");
+  if (need_y && !p->have_y) return fail(p, CIP_ERR_STATE, "cip_set_measurements has not been called");
+  return CIP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cip_version(void) { return "cip 0.1 (sm_103a)"; }
+
+const char* cip_status_string(cip_status s) {
+  switch (s) {
+    case CIP_OK: return "ok";
+    case CIP_ERR_INVALID_ARG: return "invalid argument";
+    case CIP_ERR_UNSUPPORTED: return "unsupported size or option";
+    case CIP_ERR_OOM: return "out of device memory";
+    case CIP_ERR_CUDA: return "CUDA error";
+    case CIP_ERR_STATE: return "call out of order";
+    case CIP_ERR_TIMEOUT: return "device wait timed out";
+    case CIP_ERR_DIVERGED: return "iteration diverged";
+  }
+  return "unknown status";
+}
+
+const char* cip_last_error(const cip_plan* plan) { return plan ? plan->err.c_str() : g_create_error.c_str(); }
+
+size_t cip_plan_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior) {
+  if (!valid_n(N) || K < 1 || M < 1) return 0;
+  const size_t e = dtype == CIP_F64 ? 8 : 4;
+  const size_t P = (size_t)half_pitch(N), half = (size_t)N * P * 2 * e, real = (size_t)N * N * e;
+  const size_t nc = prior == CIP_PRIOR_TV ? 2 : 1;
+  size_t b = 0;
+  b += 3 * M * half;                          // xh, qh, bhat
+  b += (size_t)M * (M + 1) / 2 * half;        // pinv
+  b += 3 * nc * M * real;                     // u[2], tprev
+  b += (size_t)K * M * N * P * 16;            // FP64 PSF spectra
+  b += (size_t)kTwN * (16 + 2 * e) + N * 8;   // tables
+  b += (size_t)(N / 2) * M * kNPart * 8 + 4096;
+  return b;
+}
+
+cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype, const cip_options* opt) {
+  if (!out) return fail(nullptr, CIP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!valid_n(N)) return fail(nullptr, CIP_ERR_UNSUPPORTED, "N must be a power of two in [64, 2048]");
+  if (K < 1 || K > 16 || M < 1 || M > 16) return fail(nullptr, CIP_ERR_UNSUPPORTED, "K and M must be in [1, 16]");
+  if (dtype != CIP_F32 && dtype != CIP_F64) return fail(nullptr, CIP_ERR_INVALID_ARG, "bad dtype");
+  cip_plan* p = new cip_plan();
+  p->N = N;
+  p->K = K;
+  p->M = M;
+  p->P = half_pitch(N);
+  p->dtype = dtype;
+  p->esz = dtype == CIP_F64 ? 8 : 4;
+  if (opt) p->opt = *opt;
+  const size_t ce = 2 * p->esz;  // complex element size
+  int cc = p->opt.col_tile;
+  if (cc == 0) cc = dtype == CIP_F64 ? passB_cols<double>(N, M) : passB_cols<float>(N, M);
+  if (cc != 1 && cc != 2 && cc != 4) {
+    delete p;
+    return fail(nullptr, CIP_ERR_INVALID_ARG, "col_tile must be 0, 1, 2 or 4");
+  }
+  p->cc = cc;
+  const size_t smB = dtype == CIP_F64 ? passB_smem<double>(N, M, cc) : passB_smem<float>(N, M, cc);
+  int dev = 0, smem_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem_optin > 0 && smB > (size_t)smem_optin) {
+    delete p;
+    return fail(nullptr, CIP_ERR_UNSUPPORTED, "column tile does not fit in shared memory for this N, M and dtype");
+  }
+  p->blocksB = (N / 2 + 1 + cc - 1) / cc;
+#define ALLOC(ptr, bytes)                                                                       \
+  do {                                                                                          \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                                       \
+    if (e_ != cudaSuccess) {                                                                    \
+      cip_plan_destroy(p);                                                                      \
+      return fail(nullptr, CIP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e_)); \
+    }                                                                                           \
+  } while (0)
+  ALLOC(p->xh, half_elems(p, M) * ce);
+  ALLOC(p->qh, half_elems(p, M) * ce);
+  ALLOC(p->bhat, half_elems(p, M) * ce);
+  ALLOC(p->lam64, half_elems(p, K * M) * sizeof(double2));
+  ALLOC(p->tw, (size_t)kTwN * ce);
+  ALLOC(p->tw64, (size_t)kTwN * sizeof(double2));
+  ALLOC(p->gs, (size_t)N * sizeof(double));
+  ALLOC(p->resid, (kNPart + 2) * sizeof(double));
+  ALLOC(p->conv, sizeof(int));
+  ALLOC(p->pinv_list, (1 + kPinvListCap) * sizeof(int));
+#undef ALLOC
+  if (cudaMallocHost((void**)&p->resid_host, (kNPart + 2) * sizeof(double)) != cudaSuccess) {
+    cip_plan_destroy(p);
+    return fail(nullptr, CIP_ERR_OOM, "cudaMallocHost failed");
+  }
+  std::vector<double> re, im;
+  twiddles(re, im);
+  std::vector<double2> t64(kTwN);
+  std::vector<float2> t32(kTwN);
+  for (int k = 0; k < kTwN; ++k) {
+    t64[k] = make_double2(re[k], im[k]);
+    t32[k] = make_float2((float)re[k], (float)im[k]);
+  }
+  std::vector<double> gs(N);
+  for (int k = 0; k < N; ++k) {
+    // 4 sin^2(pi k / N), exact zero at k = 0
+    const double sn = std::sin(M_PI * (double)k / (double)N);
+    gs[k] = 4.0 * sn * sn;
+  }
+  gs[0] = 0.0;
+  cudaError_t e = cudaMemcpy(p->tw64, t64.data(), kTwN * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = dtype == CIP_F64 ? cudaMemcpy(p->tw, t64.data(), kTwN * sizeof(double2), cudaMemcpyHostToDevice)
+                         : cudaMemcpy(p->tw, t32.data(), kTwN * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->gs, gs.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cip_plan_destroy(p);
+    return fail(nullptr, CIP_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  }
+  *out = p;
+  return CIP_OK;
+}
+
+cip_status cip_plan_destroy(cip_plan* p) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  void* bufs[] = {p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->bhat, p->lam64, p->tw, p->tw64,
+                  p->gs, p->partials, p->resid, p->conv, p->pinv_list};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (p->resid_host) cudaFreeHost(p->resid_host);
+  for (auto& ev : p->evA) cudaEventDestroy(ev);
+  for (auto& ev : p->evB) cudaEventDestroy(ev);
+  delete p;
+  return CIP_OK;
+}
+
+cip_status cip_set_prior(cip_plan* p, cip_prior prior, double lambda, double rho, double beta, void* stream) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  if (prior != CIP_PRIOR_TV && prior != CIP_PRIOR_DCT8 && prior != CIP_PRIOR_L1)
+    return fail(p, CIP_ERR_INVALID_ARG, "unknown prior");
+  if (!(lambda > 0) || !(rho > 0) || !(beta > 0)) return fail(p, CIP_ERR_INVALID_ARG, "lambda, rho, beta must be > 0");
+  const int rows = p->dtype == CIP_F64 ? passA_rows<double>(p->N, prior) : passA_rows<float>(p->N, prior);
+  if (p->N % rows != 0) return fail(p, CIP_ERR_UNSUPPORTED, "image size not a multiple of the row tile");
+  const size_t smA = p->dtype == CIP_F64 ? passA_smem<double>(p->N, prior) : passA_smem<float>(p->N, prior);
+  int dev = 0, smem_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem_optin > 0 && smA > (size_t)smem_optin) return fail(p, CIP_ERR_UNSUPPORTED, "prior pass tile too large");
+  p->prior = prior;
+  p->lam = lambda;
+  p->rho = rho;
+  p->beta = beta;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return DISPATCH_T(p, do_set_prior<float>(p, s), do_set_prior<double>(p, s));
+}
+
+cip_status cip_set_psfs(cip_plan* p, const void* h, void* stream) {
+  if (!p || !h) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  if (p->prior < 0) return fail(p, CIP_ERR_STATE, "cip_set_prior must precede cip_set_psfs");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cip_status r = DISPATCH_T(p, do_set_psfs<float>(p, h, s), do_set_psfs<double>(p, h, s));
+  if (r == CIP_OK) p->have_y = false;
+  return r;
+}
+
+cip_status cip_set_measurements(cip_plan* p, const void* y, void* stream) {
+  if (!p || !y) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  cip_status r = check_ready(p, false);
+  if (r != CIP_OK) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return DISPATCH_T(p, do_set_y<float>(p, y, s), do_set_y<double>(p, y, s));
+}
+
+cip_status cip_reset_state(cip_plan* p, void* stream) {
+  cip_status r = check_ready(p, false);
+  if (r != CIP_OK) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return DISPATCH_T(p, reset_state<float>(p, s), reset_state<double>(p, s));
+}
+
+cip_status cip_iterate(cip_plan* p, int max_iter, double tol, int* iters_done, void* stream) {
+  cip_status r = check_ready(p, true);
+  if (r != CIP_OK) return r;
+  if (max_iter < 0) return fail(p, CIP_ERR_INVALID_ARG, "max_iter < 0");
+  if (p->timing) ensure_events(p);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return DISPATCH_T(p, iterate_impl<float>(p, max_iter, tol, iters_done, s),
+                    iterate_impl<double>(p, max_iter, tol, iters_done, s));
+}
+
+cip_status cip_get_x(cip_plan* p, void* x, void* stream) {
+  if (!p || !x) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  cip_status r = check_ready(p, false);
+  if (r != CIP_OK) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return DISPATCH_T(p, get_x_impl<float>(p, x, s), get_x_impl<double>(p, x, s));
+}
+
+cip_status cip_get_u(cip_plan* p, void* u, void* stream) {
+  if (!p || !u) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  cip_status r = check_ready(p, false);
+  if (r != CIP_OK) return r;
+  return copy_out(p, u, p->u[p->cur], real_elems(p, p->M) * ncomp_of(p->prior) * p->esz,
+                  static_cast<cudaStream_t>(stream));
+}
+
+cip_status cip_get_residuals(cip_plan* p, double* r_rel, double* s_rel) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  if (!p->resid_valid) return fail(p, CIP_ERR_STATE, "no residuals computed since the last reset");
+  double h[kNPart + 2];
+  CIP_CUDA(p, cudaMemcpy(h, p->resid, sizeof(h), cudaMemcpyDeviceToHost));
+  if (r_rel) *r_rel = h[kNPart];
+  if (s_rel) *s_rel = h[kNPart + 1];
+  return CIP_OK;
+}
+
+cip_status cip_get_iteration(cip_plan* p, int* iteration) {
+  if (!p || !iteration) return CIP_ERR_INVALID_ARG;
+  *iteration = p->iteration;
+  return CIP_OK;
+}
+
+cip_status cip_state_import(cip_plan* p, const void* t, const void* u, void* stream) {
+  if (!p || !t || !u) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  cip_status r = check_ready(p, false);
+  if (r != CIP_OK) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return DISPATCH_T(p, import_impl<float>(p, t, u, s), import_impl<double>(p, t, u, s));
+}
+
+cip_status cip_state_size(cip_plan* p, size_t* bytes) {
+  if (!p || !bytes) return CIP_ERR_INVALID_ARG;
+  if (p->prior < 0) return fail(p, CIP_ERR_STATE, "cip_set_prior has not been called");
+  *bytes = 2 * sizeof(int) + half_elems(p, p->M) * 2 * p->esz * 2 + real_elems(p, p->M) * ncomp_of(p->prior) * p->esz;
+  return CIP_OK;
+}
+
+cip_status cip_state_export(cip_plan* p, void* buf, void* stream) {
+  size_t total = 0;
+  cip_status r = cip_state_size(p, &total);
+  if (r != CIP_OK) return r;
+  if (!buf) return fail(p, CIP_ERR_INVALID_ARG, "null buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool dev = is_device_ptr(buf);
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  char* b = static_cast<char*>(buf);
+  int hdr[2] = {p->iteration, 0};
+  if (dev) CIP_CUDA(p, cudaMemcpyAsync(b, hdr, sizeof(hdr), cudaMemcpyHostToDevice, s));
+  else std::memcpy(b, hdr, sizeof(hdr));
+  size_t off = sizeof(hdr);
+  const size_t hb = half_elems(p, p->M) * 2 * p->esz;
+  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->xh, hb, k, s));
+  off += hb;
+  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->qh, hb, k, s));
+  off += hb;
+  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->u[p->cur], real_elems(p, p->M) * ncomp_of(p->prior) * p->esz, k, s));
+  CIP_CUDA(p, cudaStreamSynchronize(s));
+  return CIP_OK;
+}
+
+cip_status cip_state_restore(cip_plan* p, const void* buf, void* stream) {
+  size_t total = 0;
+  cip_status r = cip_state_size(p, &total);
+  if (r != CIP_OK) return r;
+  if (!buf) return fail(p, CIP_ERR_INVALID_ARG, "null buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool dev = is_device_ptr(buf);
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const char* b = static_cast<const char*>(buf);
+  int hdr[2];
+  if (dev) {
+    CIP_CUDA(p, cudaMemcpyAsync(hdr, b, sizeof(hdr), cudaMemcpyDeviceToHost, s));
+    CIP_CUDA(p, cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(hdr, b, sizeof(hdr));
+  }
+  size_t off = sizeof(hdr);
+  const size_t hb = half_elems(p, p->M) * 2 * p->esz;
+  CIP_CUDA(p, cudaMemcpyAsync(p->xh, b + off, hb, k, s));
+  off += hb;
+  CIP_CUDA(p, cudaMemcpyAsync(p->qh, b + off, hb, k, s));
+  off += hb;
+  CIP_CUDA(p, cudaMemcpyAsync(p->u[p->cur], b + off, real_elems(p, p->M) * ncomp_of(p->prior) * p->esz, k, s));
+  CIP_CUDA(p, cudaStreamSynchronize(s));
+  p->iteration = hdr[0];
+  p->resid_valid = false;
+  return CIP_OK;
+}
+
+cip_status cip_set_timing(cip_plan* p, int on) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  p->timing = on != 0;
+  p->nA = p->nB = 0;
+  return CIP_OK;
+}
+
+cip_status cip_get_timing(cip_plan* p, double* a_ms, int* a_n, double* b_ms, int* b_n) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  double ta = 0, tb = 0;
+  for (int i = 0; i < p->nA; ++i) {
+    float ms = 0;
+    CIP_CUDA(p, cudaEventSynchronize(p->evA[2 * i + 1]));
+    CIP_CUDA(p, cudaEventElapsedTime(&ms, p->evA[2 * i], p->evA[2 * i + 1]));
+    ta += ms;
+  }
+  for (int i = 0; i < p->nB; ++i) {
+    float ms = 0;
+    CIP_CUDA(p, cudaEventSynchronize(p->evB[2 * i + 1]));
+    CIP_CUDA(p, cudaEventElapsedTime(&ms, p->evB[2 * i], p->evB[2 * i + 1]));
+    tb += ms;
+  }
+  if (a_ms) *a_ms = ta;
+  if (a_n) *a_n = p->nA;
+  if (b_ms) *b_ms = tb;
+  if (b_n) *b_n = p->nB;
+  p->nA = p->nB = 0;
+  return CIP_OK;
+}
+
+cip_status cip_get_launches(cip_plan* p, unsigned long long* n) {
+  if (!p || !n) return CIP_ERR_INVALID_ARG;
+  *n = p->launches;
+  return CIP_OK;
+}
+
+cip_status cip_get_config(cip_plan* p, int* rows, int* cc, int* blocksA, int* blocksB) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  if (rows) *rows = p->rowsA;
+  if (cc) *cc = p->cc;
+  if (blocksA) *blocksA = p->blocksA;
+  if (blocksB) *blocksB = p->blocksB;
+  return CIP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Shared-memory Stockham FFT for power-of-two lengths 64..2048 (sm_103a).
+//
+// The 2D DFTs of Section IV-A (F_2D on every slice, Eq. solx_Trans_DFT) are
+// done as a row pass and a column pass; both run this 1D routine on data a
+// CTA has staged in shared memory.  A "team" of NTH threads owns NF
+// interleaved FFTs of length N (element n of FFT f sits at slot
+// spad(n*NF + f)); each thread keeps E = N*NF/NTH elements in registers and
+// applies radix-8 stages (plus one radix-2 or radix-4 stage when log2 N is
+// not a multiple of 3).  Stage s reads x[t + r N/R], multiplies by the
+// twiddles w_{Ls R}^{r (t mod Ls)}, does a radix-R DFT in registers and
+// writes y[(t/Ls) Ls R + t mod Ls + r Ls] (autosorting Stockham, natural
+// order in and out).  Twiddles come from a table of exp(-2 pi i k / 2048)
+// computed on the host in FP64 and rounded once.
+#pragma once
+#include "common.cuh"
+
+namespace cip {
+
+
+
+// Synchronisation of one team: a named barrier for teams wider than a warp,
+// a masked __syncwarp for teams inside one warp.
+struct TeamSync {
+  int bar_id;
+  int nthreads;
+  unsigned mask;
+  __device__ __forceinline__ void sync() const {
+    if (nthreads > 32) {
+      asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
+    } else {
+      __syncwarp(mask);
+    }
+  }
+};
+
+// Team of `team_threads` threads, team index `team` within the CTA (team 0
+// starts at thread 0).  Barrier ids 1..15 are used for multi-warp teams.
+__device__ __forceinline__ TeamSync make_team_sync(int team, int team_threads) {
+  TeamSync s;
+  s.nthreads = team_threads;
+  s.bar_id = 1 + team;
+  if (team_threads >= 32) {
+    s.mask = 0xffffffffu;
+  } else {
+    int lane0 = (team * team_threads) & 31;
+    s.mask = ((team_threads == 32) ? 0xffffffffu : ((1u << team_threads) - 1u)) << lane0;
+  }
+  return s;
+}
+
+// ---- radix-R DFTs in registers, SIGN = -1 forward, +1 inverse (unnormalised)
+template <int SIGN, typename C> __device__ __forceinline__ C mul_si(C a) {
+  // a * (SIGN * i)
+  C r;
+  if (SIGN < 0) { r.x = a.y; r.y = -a.x; } else { r.x = -a.y; r.y = a.x; }
+  return r;
+}
+
+template <int SIGN, typename C> __device__ __forceinline__ void dft2(C* a) {
+  C t = a[0];
+  a[0] = cadd(t, a[1]);
+  a[1] = csub(t, a[1]);
+}
+
+template <int SIGN, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_si<SIGN>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <int SIGN, typename C> __device__ __forceinline__ void dft4(C* a) { dft4<SIGN>(a[0], a[1], a[2], a[3]); }
+
+template <int SIGN, typename C> __device__ __forceinline__ void dft8(C* a) {
+  using R = decltype(a[0].x);
+  const R h = R(0.70710678118654752440);  // 1/sqrt(2)
+  C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4<SIGN>(e0, e1, e2, e3);
+  dft4<SIGN>(o0, o1, o2, o3);
+  // w^k = exp(SIGN i pi k / 4)
+  C w1o, w2o, w3o;
+  // w^1 = (1 + SIGN i)/sqrt2
+  w1o.x = h * (o1.x - R(SIGN) * o1.y);
+  w1o.y = h * (o1.y + R(SIGN) * o1.x);
+  w2o = mul_si<SIGN>(o2);
+  // w^3 = (-1 + SIGN i)/sqrt2
+  w3o.x = h * (-o3.x - R(SIGN) * o3.y);
+  w3o.y = h * (-o3.y + R(SIGN) * o3.x);
+  a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
+  a[1] = cadd(e1, w1o); a[5] = csub(e1, w1o);
+  a[2] = cadd(e2, w2o); a[6] = csub(e2, w2o);
+  a[3] = cadd(e3, w3o); a[7] = csub(e3, w3o);
+}
+
+template <int R, int SIGN, typename C> __device__ __forceinline__ void dft_r(C* a) {
+  if constexpr (R == 2) dft2<SIGN>(a);
+  else if constexpr (R == 4) dft4<SIGN>(a);
+  else dft8<SIGN>(a);
+}
+
+template <typename C, int LOGN, int NF, int E, int SIGN, int R, int LS>
+__device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* __restrict__ tw, const TeamSync& ts) {
+  constexpr int N = 1 << LOGN;
+  constexpr int B = E / R;
+  constexpr int TT = N / E;
+  static_assert(E % R == 0, "E must be a multiple of the radix");
+  C a[E];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int t = tt + TT * b;
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[b * R + r] = buf[spad((t + r * (N / R)) * NF + f)];
+  }
+  ts.sync();
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int t = tt + TT * b;
+    const int j = t & (LS - 1);
+    if constexpr (LS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = __ldg(&tw[r * j * (kTwN / (LS * R))]);
+        if (SIGN > 0) w.y = -w.y;
+        a[b * R + r] = cmul(a[b * R + r], w);
+      }
+    }
+    dft_r<R, SIGN>(&a[b * R]);
+    const int base = (t / LS) * LS * R + j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[spad((base + r * LS) * NF + f)] = a[b * R + r];
+  }
+  ts.sync();
+}
+
+// NF interleaved length-2^LOGN FFTs executed by the team's NTH = N*NF/E threads;
+// `tid` is the thread's index inside the team.
+template <typename C, int LOGN, int NF, int E, int SIGN>
+__device__ __forceinline__ void fft_team(C* buf, int tid, const C* __restrict__ tw, const TeamSync& ts) {
+  constexpr int S8 = LOGN / 3;
+  constexpr int REM = LOGN % 3;
+  const int f = tid % NF;
+  const int tt = tid / NF;
+  if constexpr (S8 >= 1) stockham_stage<C, LOGN, NF, E, SIGN, 8, 1>(buf, f, tt, tw, ts);
+  if constexpr (S8 >= 2) stockham_stage<C, LOGN, NF, E, SIGN, 8, 8>(buf, f, tt, tw, ts);
+  if constexpr (S8 >= 3) stockham_stage<C, LOGN, NF, E, SIGN, 8, 64>(buf, f, tt, tw, ts);
+  if constexpr (REM == 1) stockham_stage<C, LOGN, NF, E, SIGN, 2, (1 << (3 * S8))>(buf, f, tt, tw, ts);
+  if constexpr (REM == 2) stockham_stage<C, LOGN, NF, E, SIGN, 4, (1 << (3 * S8))>(buf, f, tt, tw, ts);
+}
+
+// ---- two real rows through one complex FFT ---------------------------------
+// Inverse: from the half spectra Xa[k], Xb[k] (k = 0..N/2) of two real rows,
+// build Z[k] = Xa[k] + i Xb[k] over the full length using Hermitian symmetry;
+// DC and Nyquist keep only their real parts (c2r semantics).
+template <typename C>
+__device__ __forceinline__ void pair_spectrum_put(C* z, int N, int k, C xa, C xb) {
+  if (k == 0 || k == N / 2) {
+    z[spad(k)] = mk<C>(xa.x, xb.x);
+  } else {
+    z[spad(k)] = mk<C>(xa.x - xb.y, xa.y + xb.x);
+    z[spad(N - k)] = mk<C>(xa.x + xb.y, xb.x - xa.y);
+  }
+}
+
+// Forward: Z = FFT(za + i zb) -> Qa[k] = (Z[k] + conj Z[N-k]) * s,
+// Qb[k] = -i (Z[k] - conj Z[N-k]) * s, with s = 1/2 folded by the caller.
+template <typename C>
+__device__ __forceinline__ void pair_spectrum_get(const C* z, int N, int k, C& qa, C& qb) {
+  C a = z[spad(k)];
+  C b = cconj(z[spad((N - k) & (N - 1))]);
+  qa = cadd(a, b);
+  C d = csub(a, b);
+  qb.x = d.y;
+  qb.y = -d.x;
+}
+
+}  // namespace cip

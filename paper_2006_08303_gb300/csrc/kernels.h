@@ -1,0 +1,95 @@
+// Internal launch interface between the C ABI (abi.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace cip {
+
+enum PriorKind { PRIOR_TV = 0, PRIOR_DCT8 = 1, PRIOR_L1 = 2, PRIOR_CONVDICT = 3 };
+
+// flags of the prior pass
+enum { PA_STORE_T = 1, PA_RESID = 2, PA_IMPORT = 4 };
+constexpr int kNPart = 5;  // sum (w-t)^2, sum w^2, sum t^2, sum u^2, sum (t - t_prev)^2
+
+inline int prior_ncomp(int prior) { return prior == PRIOR_TV ? 2 : 1; }
+
+// Prior pass (one ADMM t/u update + the adjoint for the next x-update):
+//   x = row-IDFT(xh)  ->  w = T x  ->  t = soft(w + u, tau)  ->  u' = u + w - t
+//   -> q = qscale * T^T (t - u')  ->  qh = row-DFT(q) (half spectrum, pair-extracted)
+// In IMPORT mode x is not used: t comes from t_imp and u' = u_in.
+template <typename T> struct PassAArgs {
+  using C = typename CT<T>::type;
+  const C* xh;      // [M][N][P]
+  C* qh;            // [M][N][P]
+  const T* u_in;    // [M][ncomp][N][N]
+  T* u_out;         // [M][ncomp][N][N]
+  T* tprev;         // [M][ncomp][N][N] (STORE_T writes t, RESID reads t_prev)
+  const T* t_imp;   // [M][ncomp][N][N] (IMPORT)
+  double* partials; // [gridDim.y * gridDim.x][kNPart] (RESID)
+  const C* tw;      // twiddle table, kTwN entries
+  int M;
+  T tau;            // lambda / rho
+  T qscale;         // rho / 2 (the 1/2 of the pair extraction is folded here)
+  int flags;
+  T dct[64];        // orthonormal DCT-II, dct[k*8+n]
+};
+
+// Column pass with the per-frequency solve (Eq. solx_Trans_DFT):
+//   Q = col-DFT(qh);  X(w) = Pinv(w) (bhat(w) + Q(w));  xh = col-IDFT(X)
+template <typename T> struct PassBArgs {
+  using C = typename CT<T>::type;
+  const C* qh;      // [M][N][P]
+  C* xh;            // [M][N][P]
+  const C* pinv;    // [M(M+1)/2][N][P] packed upper triangle, scaled by 1/N^2
+  const C* bhat;    // [M][N][P]
+  const C* tw;
+  int M;
+};
+
+template <typename T> int passA_rows(int N, int prior);
+template <typename T> size_t passA_smem(int N, int prior);
+template <typename T> cudaError_t launch_passA(const PassAArgs<T>& a, int N, int prior, cudaStream_t s);
+
+template <typename T> int passB_cols(int N, int M);
+template <typename T> size_t passB_smem(int N, int M, int cc);
+template <typename T> cudaError_t launch_passB(const PassBArgs<T>& a, int N, int cc, cudaStream_t s);
+
+// Setup / read-back FFTs (not fused).
+// rows: nrows real rows of length N -> half spectra with pitch P (unnormalised forward DFT)
+template <typename Tc, typename Tin>
+cudaError_t launch_row_r2c(const Tin* in, typename CT<Tc>::type* out, int N, int nrows, Tc scale,
+                           const typename CT<Tc>::type* tw, cudaStream_t s);
+// rows: half spectra -> real rows (unnormalised inverse DFT, c2r semantics)
+template <typename Tc, typename Tout>
+cudaError_t launch_row_c2r(const typename CT<Tc>::type* in, Tout* out, int N, int nrows,
+                           const typename CT<Tc>::type* tw, cudaStream_t s);
+// in-place column DFT of nmaps [N][P] half-spectrum maps
+template <typename Tc>
+cudaError_t launch_col_c2c(typename CT<Tc>::type* data, int N, int nmaps, int sign,
+                           const typename CT<Tc>::type* tw, cudaStream_t s);
+
+// Factor formation in FP64: Psi = rho g I + beta Lam^H Lam per bin; writes
+// Psi^{-1} / N^2 packed into `pinv`.  Bins needing a pseudo-inverse are
+// appended to `pinv_list` (count in pinv_list[0]).
+template <typename Tout>
+cudaError_t launch_factor(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
+                          double beta, typename CT<Tout>::type* pinv, int* pinv_list, int list_cap,
+                          cudaStream_t s);
+template <typename Tout>
+cudaError_t launch_factor_pinv(const double2* lam, const double* gs, int use_g, int K, int M, int N,
+                               double rho, double beta, typename CT<Tout>::type* pinv, const int* pinv_list,
+                               int list_cap, cudaStream_t s);
+// bhat = beta Lam^H yhat (FP64 spectra, result rounded to the plan precision)
+template <typename Tout>
+cudaError_t launch_rhs(const double2* lam, const double2* yhat, int K, int M, int N, double beta,
+                       typename CT<Tout>::type* bhat, cudaStream_t s);
+// copy FP64 spectra to the plan precision
+template <typename Tout>
+cudaError_t launch_spectra_store(const double2* src, typename CT<Tout>::type* dst, size_t n, cudaStream_t s);
+
+// deterministic reduction of pass-A partials: out[0..kNPart) sums, out[5]=r_rel, out[6]=s_rel,
+// conv[0] set to 1 when both relative residuals < tol (tol > 0)
+cudaError_t launch_reduce_partials(const double* partials, int nblocks, double rho, double tol, double* out,
+                                   int* conv, cudaStream_t s);
+
+}  // namespace cip

@@ -1,0 +1,49 @@
+"""The C-ABI library builds, loads and exports every symbol include/cip.h
+declares; argument checks that need no GPU.  CPU only (no compute call)."""
+import ctypes
+
+import pytest
+
+from paper_2006_08303_gb300 import _lib, build
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(L):
+    syms = _lib.header_symbols()
+    assert len(syms) >= 20
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert not missing, missing
+    assert set(syms) == set(_lib.SIGNATURES), "binding and header disagree"
+
+
+def test_status_strings_and_version(L):
+    assert L.cip_version().startswith(b"cip")
+    for s in range(8):
+        assert len(L.cip_status_string(s)) > 0
+
+
+def test_invalid_sizes_rejected_before_device_use(L):
+    h = ctypes.c_void_p()
+    opt = _lib.cip_options()
+    assert L.cip_plan_create(ctypes.byref(h), 100, 3, 3, 0, ctypes.byref(opt)) == 2   # not a power of two
+    assert b"power of two" in L.cip_last_error(None)
+    assert L.cip_plan_create(ctypes.byref(h), 4096, 3, 3, 0, ctypes.byref(opt)) == 2
+    assert L.cip_plan_create(ctypes.byref(h), 64, 3, 17, 0, ctypes.byref(opt)) == 2  # M > 16
+    assert L.cip_plan_create(None, 64, 3, 3, 0, ctypes.byref(opt)) == 1
+    assert L.cip_plan_create(ctypes.byref(h), 64, 3, 3, 7, ctypes.byref(opt)) == 1   # bad dtype
+
+
+def test_plan_bytes_accounts_for_factor_and_state(L):
+    # 512^2 x 10, f32, DCT: packed factor (55 planes of N*(N/2+4) complex64) and the kept
+    # FP64 PSF spectra (100 maps of N*(N/2+4) complex128) dominate
+    b = L.cip_plan_bytes(512, 10, 10, 0, 1)
+    factor = 55 * 512 * 260 * 8
+    lam64 = 100 * 512 * 260 * 16
+    assert factor + lam64 < b < 1.5 * (factor + lam64)
+    assert L.cip_plan_bytes(100, 1, 1, 0, 0) == 0
+    assert L.cip_plan_bytes(512, 10, 10, 1, 1) > b
