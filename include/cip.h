@@ -85,8 +85,9 @@ cip_status cip_plan_destroy(cip_plan* plan);
 size_t cip_plan_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior);
 
 /* Prior and ADMM weights (Alg. 1 line 1): lambda > 0, rho > 0, beta > 0.
- * Must precede cip_set_psfs; changing prior or rho afterwards re-forms the
- * factor from the kept FP64 PSF spectra. */
+ * Must precede cip_set_psfs; calling it again afterwards re-forms the factor
+ * from the kept FP64 PSF spectra and requires cip_set_measurements again
+ * (the precomputed data term depends on the factor). */
 cip_status cip_set_prior(cip_plan* plan, cip_prior prior, double lambda, double rho, double beta, void* stream);
 
 /* PSFs h[K][M][N][N] (plan dtype).  Forms Lambda = DFT2(h) in FP64 and the
@@ -94,8 +95,9 @@ cip_status cip_set_prior(cip_plan* plan, cip_prior prior, double lambda, double 
  * in the plan's precision.  Resets the ADMM state. */
 cip_status cip_set_psfs(cip_plan* plan, const void* h, void* stream);
 
-/* Measurements y[K][N][N] (plan dtype): bhat = beta Lambda^H F y (Alg. 1
- * line 2).  Resets the ADMM state (t = u = 0). */
+/* Measurements y[K][N][N] (plan dtype): the data term of the x-update,
+ * Psi^{-1} beta Lambda^H F y (Alg. 1 line 2), formed in FP64 and rounded
+ * once to the plan's precision.  Resets the ADMM state (t = u = 0). */
 cip_status cip_set_measurements(cip_plan* plan, const void* y, void* stream);
 
 /* t = u = 0 (Alg. 1 line 1 with zero initial values). */

@@ -56,7 +56,8 @@ struct cip_plan {
   void* u[2] = {nullptr, nullptr};
   void* tprev = nullptr;
   void* pinv = nullptr;
-  void* bhat = nullptr;
+  void* bhat = nullptr;       // data term xb = Psi^{-1} beta Lambda^H F y / N^2
+  double2* pinv64 = nullptr;  // FP64 copy of the packed factor
   double2* lam64 = nullptr;  // FP64 PSF spectra [K*M][N][P]
   void* tw = nullptr;        // plan-precision twiddles
   double2* tw64 = nullptr;   // FP64 twiddles for setup FFTs
@@ -146,6 +147,9 @@ template <typename T> cip_status alloc_state(cip_plan* p) {
   if (p->pinv) cudaFree(p->pinv);
   p->pinv = nullptr;
   CIP_CUDA(p, cudaMalloc(&p->pinv, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(C)));
+  if (p->pinv64) cudaFree(p->pinv64);
+  p->pinv64 = nullptr;
+  CIP_CUDA(p, cudaMalloc((void**)&p->pinv64, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(double2)));
   if (p->partials) cudaFree(p->partials);
   p->partials = nullptr;
   p->rowsA = passA_rows<T>(p->N, p->prior);
@@ -186,9 +190,9 @@ template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
   CIP_CUDA(p, cudaMemsetAsync(p->pinv_list, 0, sizeof(int), s));
   const int use_g = p->prior == CIP_PRIOR_TV ? 1 : 0;
   CIP_LAUNCH(p, launch_factor<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, p->rho, p->beta,
-                               static_cast<C*>(p->pinv), p->pinv_list, kPinvListCap, s));
+                                 static_cast<C*>(p->pinv), p->pinv64, p->pinv_list, kPinvListCap, s));
   CIP_LAUNCH(p, launch_factor_pinv<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, p->rho, p->beta,
-                                    static_cast<C*>(p->pinv), p->pinv_list, kPinvListCap, s));
+                                      static_cast<C*>(p->pinv), p->pinv64, p->pinv_list, kPinvListCap, s));
   int nlist = 0;
   CIP_CUDA(p, cudaMemcpyAsync(&nlist, p->pinv_list, sizeof(int), cudaMemcpyDeviceToHost, s));
   CIP_CUDA(p, cudaStreamSynchronize(s));
@@ -234,7 +238,7 @@ template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream
   cudaError_t e = launch_row_r2c<double, T>(static_cast<const T*>(dy), yhat, p->N, p->K * p->N, 1.0, p->tw64, s);
   if (e == cudaSuccess) e = launch_col_c2c<double>(yhat, p->N, p->K, -1, p->tw64, s);
   if (e == cudaSuccess)
-    e = launch_rhs<T>(p->lam64, yhat, p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
+    e = launch_rhs<T>(p->lam64, yhat, p->pinv64, p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
   if (e == cudaSuccess) p->launches += 3;
   cudaFreeAsync(yhat, s);
   CIP_CUDA(p, e);
@@ -412,6 +416,7 @@ size_t cip_plan_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior) {
   size_t b = 0;
   b += 3 * M * half;                          // xh, qh, bhat
   b += (size_t)M * (M + 1) / 2 * half;        // pinv
+  b += (size_t)M * (M + 1) / 2 * N * P * 16;  // FP64 copy of pinv (data term at set_measurements)
   b += 3 * nc * M * real;                     // u[2], tprev
   b += (size_t)K * M * N * P * 16;            // FP64 PSF spectra
   b += (size_t)kTwN * (16 + 2 * e) + N * 8;   // tables
@@ -503,7 +508,7 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->bhat, p->lam64, p->tw, p->tw64,
+  void* bufs[] = {p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -531,6 +536,7 @@ cip_status cip_set_prior(cip_plan* p, cip_prior prior, double lambda, double rho
   p->rho = rho;
   p->beta = beta;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->have_y = false;  // the data term depends on the factor: set_measurements again
   return DISPATCH_T(p, do_set_prior<float>(p, s), do_set_prior<double>(p, s));
 }
 

@@ -9,7 +9,7 @@
 //     (eigenvalues below 1e-10 of the largest dropped).  Results are scaled by
 //     1/N^2 (the inverse-DFT normalisation) and rounded once to the plan's
 //     precision, packed as the upper triangle row by row.
-//   * bhat(w) = beta Lambda(w)^H yhat(w).
+//   * xb(w) = Psi^{-1}(w) beta Lambda(w)^H yhat(w) in FP64 (the constant data term).
 //   * the deterministic reduction of the prior pass's residual partial sums.
 #include "kernels.h"
 
@@ -49,8 +49,8 @@ __device__ __forceinline__ double2 psi_entry(const double2* lam, size_t off, siz
 template <typename Tout>
 __global__ void __launch_bounds__(128) factor_kernel(const double2* __restrict__ lam, const double* __restrict__ gs,
                                                      int use_g, int K, int M, int N, double rho, double beta,
-                                                     typename CT<Tout>::type* __restrict__ pinv, int* list,
-                                                     int cap) {
+                                                     typename CT<Tout>::type* __restrict__ pinv,
+                                                     double2* __restrict__ pinv64, int* list, int cap) {
   using C = typename CT<Tout>::type;
   const int H = N / 2 + 1, P = half_pitch(N);
   const int bin = blockIdx.x * blockDim.x + threadIdx.x;
@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(128) factor_kernel(const double2* __restrict__
       for (int k = j; k < M; ++k) cfmac(s, W[k][i], W[k][j]);
       if (i == j) s.y = 0.0;
       pinv[(size_t)pk * mplane + off] = mk<C>(s.x * sc, s.y * sc);
+      if (pinv64) pinv64[(size_t)pk * mplane + off] = make_double2(s.x * sc, s.y * sc);
       ++pk;
     }
   }
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(128) factor_kernel(const double2* __restrict__
 template <typename Tout>
 __global__ void factor_pinv_kernel(const double2* __restrict__ lam, const double* __restrict__ gs, int use_g, int K,
                                    int M, int N, double rho, double beta, typename CT<Tout>::type* __restrict__ pinv,
-                                   const int* list, int cap) {
+                                   double2* __restrict__ pinv64, const int* list, int cap) {
   using C = typename CT<Tout>::type;
   const int n = min(list[0], cap);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,27 +189,44 @@ __global__ void factor_pinv_kernel(const double2* __restrict__ lam, const double
       }
       if (i == j) im = 0.0;
       pinv[(size_t)pk * mplane + off] = mk<C>(re * sc, im * sc);
+      if (pinv64) pinv64[(size_t)pk * mplane + off] = make_double2(re * sc, im * sc);
       ++pk;
     }
   }
 }
 
+// xb(w) = Psi^{-1}(w) / N^2 * beta Lambda(w)^H yhat(w), all in FP64, rounded once.
+// This is the data term of Eq. solx_Trans_DFT; it does not change across
+// iterations, so the ill-conditioned product with Psi^{-1} (cancellation at
+// bins where the PSFs are nearly dependent) is taken once in FP64 and the
+// per-iteration column pass only adds Psi^{-1} rho F T^H (t - u).
 template <typename Tout>
-__global__ void rhs_kernel(const double2* __restrict__ lam, const double2* __restrict__ yhat, int K,
-                           int M, int N, double beta, typename CT<Tout>::type* __restrict__ bhat) {
+__global__ void rhs_kernel(const double2* __restrict__ lam, const double2* __restrict__ yhat,
+                           const double2* __restrict__ pinv64, int K, int M, int N, double beta,
+                           typename CT<Tout>::type* __restrict__ xb) {
   using C = typename CT<Tout>::type;
   const int H = N / 2 + 1, P = half_pitch(N);
   const int bin = blockIdx.x * blockDim.x + threadIdx.x;
   if (bin >= N * H) return;
   const int k1 = bin / H, k2 = bin - k1 * H;
   const size_t off = (size_t)k1 * P + k2, mplane = (size_t)N * P;
+  double2 b[kMaxM], x[kMaxM];
   for (int m = 0; m < M; ++m) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k < K; ++k) {
-      cfmac(acc, lam[(size_t)(k * M + m) * mplane + off], yhat[(size_t)k * mplane + off]);
-    }
-    bhat[(size_t)m * mplane + off] = mk<C>(beta * acc.x, beta * acc.y);
+    for (int k = 0; k < K; ++k) cfmac(acc, lam[(size_t)(k * M + m) * mplane + off], yhat[(size_t)k * mplane + off]);
+    b[m] = make_double2(beta * acc.x, beta * acc.y);
+    x[m] = make_double2(0.0, 0.0);
   }
+  int pk = 0;
+  for (int i = 0; i < M; ++i) {
+    for (int j = i; j < M; ++j) {
+      const double2 pij = pinv64[(size_t)pk * mplane + off];
+      ++pk;
+      cfma(x[i], pij, b[j]);
+      if (j != i) cfmac(x[j], pij, b[i]);
+    }
+  }
+  for (int m = 0; m < M; ++m) xb[(size_t)m * mplane + off] = mk<C>(x[m].x, x[m].y);
 }
 
 template <typename Tout>
@@ -248,29 +266,31 @@ __global__ void reduce_kernel(const double* __restrict__ partials, int nblocks, 
 
 template <typename Tout>
 cudaError_t launch_factor(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
-                          double beta, typename CT<Tout>::type* pinv, int* pinv_list, int list_cap, cudaStream_t s) {
+                          double beta, typename CT<Tout>::type* pinv, double2* pinv64, int* pinv_list, int list_cap,
+                          cudaStream_t s) {
   if (M > kMaxM) return cudaErrorInvalidValue;
   const int nb = N * (N / 2 + 1);
-  factor_kernel<Tout><<<(nb + 127) / 128, 128, 0, s>>>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv_list,
+  factor_kernel<Tout><<<(nb + 127) / 128, 128, 0, s>>>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64, pinv_list,
                                                        list_cap);
   return cudaGetLastError();
 }
 
 template <typename Tout>
 cudaError_t launch_factor_pinv(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
-                               double beta, typename CT<Tout>::type* pinv, const int* pinv_list, int list_cap,
-                               cudaStream_t s) {
+                               double beta, typename CT<Tout>::type* pinv, double2* pinv64, const int* pinv_list,
+                               int list_cap, cudaStream_t s) {
   if (M > kMaxM) return cudaErrorInvalidValue;
-  factor_pinv_kernel<Tout><<<(list_cap + 31) / 32, 32, 0, s>>>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv_list,
-                                                               list_cap);
+  factor_pinv_kernel<Tout><<<(list_cap + 31) / 32, 32, 0, s>>>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64,
+                                                               pinv_list, list_cap);
   return cudaGetLastError();
 }
 
 template <typename Tout>
-cudaError_t launch_rhs(const double2* lam, const double2* yhat, int K, int M, int N, double beta,
-                       typename CT<Tout>::type* bhat, cudaStream_t s) {
+cudaError_t launch_rhs(const double2* lam, const double2* yhat, const double2* pinv64, int K, int M, int N,
+                       double beta, typename CT<Tout>::type* xb, cudaStream_t s) {
+  if (M > kMaxM) return cudaErrorInvalidValue;
   const int nb = N * (N / 2 + 1);
-  rhs_kernel<Tout><<<(nb + 255) / 256, 256, 0, s>>>(lam, yhat, K, M, N, beta, bhat);
+  rhs_kernel<Tout><<<(nb + 127) / 128, 128, 0, s>>>(lam, yhat, pinv64, K, M, N, beta, xb);
   return cudaGetLastError();
 }
 
@@ -287,17 +307,17 @@ cudaError_t launch_reduce_partials(const double* partials, int nblocks, double r
 }
 
 template cudaError_t launch_factor<float>(const double2*, const double*, int, int, int, int, double, double, float2*,
-                                          int*, int, cudaStream_t);
+                                          double2*, int*, int, cudaStream_t);
 template cudaError_t launch_factor<double>(const double2*, const double*, int, int, int, int, double, double,
-                                           double2*, int*, int, cudaStream_t);
+                                           double2*, double2*, int*, int, cudaStream_t);
 template cudaError_t launch_factor_pinv<float>(const double2*, const double*, int, int, int, int, double, double,
-                                               float2*, const int*, int, cudaStream_t);
+                                               float2*, double2*, const int*, int, cudaStream_t);
 template cudaError_t launch_factor_pinv<double>(const double2*, const double*, int, int, int, int, double, double,
-                                                double2*, const int*, int, cudaStream_t);
-template cudaError_t launch_rhs<float>(const double2*, const double2*, int, int, int, double, float2*,
-                                       cudaStream_t);
-template cudaError_t launch_rhs<double>(const double2*, const double2*, int, int, int, double, double2*,
-                                        cudaStream_t);
+                                                double2*, double2*, const int*, int, cudaStream_t);
+template cudaError_t launch_rhs<float>(const double2*, const double2*, const double2*, int, int, int, double,
+                                       float2*, cudaStream_t);
+template cudaError_t launch_rhs<double>(const double2*, const double2*, const double2*, int, int, int, double,
+                                        double2*, cudaStream_t);
 template cudaError_t launch_spectra_store<float>(const double2*, float2*, size_t, cudaStream_t);
 template cudaError_t launch_spectra_store<double>(const double2*, double2*, size_t, cudaStream_t);
 

@@ -34,14 +34,14 @@ template <typename T> struct PassAArgs {
   T dct[64];        // orthonormal DCT-II, dct[k*8+n]
 };
 
-// Column pass with the per-frequency solve (Eq. solx_Trans_DFT):
-//   Q = col-DFT(qh);  X(w) = Pinv(w) (bhat(w) + Q(w));  xh = col-IDFT(X)
+// Column pass with the per-frequency solve (Eq. solx_Trans_DFT), the data
+// term precomputed:  Q = col-DFT(qh);  X(w) = xb(w) + Pinv(w) Q(w);  xh = col-IDFT(X)
 template <typename T> struct PassBArgs {
   using C = typename CT<T>::type;
   const C* qh;      // [M][N][P]
   C* xh;            // [M][N][P]
   const C* pinv;    // [M(M+1)/2][N][P] packed upper triangle, scaled by 1/N^2
-  const C* bhat;    // [M][N][P]
+  const C* bhat;    // [M][N][P]: xb = Psi^{-1} beta Lambda^H F y / N^2 (FP64-formed)
   const C* tw;
   int M;
 };
@@ -71,18 +71,19 @@ cudaError_t launch_col_c2c(typename CT<Tc>::type* data, int N, int nmaps, int si
 // Factor formation in FP64: Psi = rho g I + beta Lam^H Lam per bin; writes
 // Psi^{-1} / N^2 packed into `pinv`.  Bins needing a pseudo-inverse are
 // appended to `pinv_list` (count in pinv_list[0]).
+// The FP64 copy `pinv64` (same layout) is written too when non-null.
 template <typename Tout>
 cudaError_t launch_factor(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
-                          double beta, typename CT<Tout>::type* pinv, int* pinv_list, int list_cap,
+                          double beta, typename CT<Tout>::type* pinv, double2* pinv64, int* pinv_list, int list_cap,
                           cudaStream_t s);
 template <typename Tout>
 cudaError_t launch_factor_pinv(const double2* lam, const double* gs, int use_g, int K, int M, int N,
-                               double rho, double beta, typename CT<Tout>::type* pinv, const int* pinv_list,
-                               int list_cap, cudaStream_t s);
-// bhat = beta Lam^H yhat (FP64 spectra, result rounded to the plan precision)
+                               double rho, double beta, typename CT<Tout>::type* pinv, double2* pinv64,
+                               const int* pinv_list, int list_cap, cudaStream_t s);
+// xb = Pinv64 (beta Lam^H yhat), all FP64, rounded once to the plan precision
 template <typename Tout>
-cudaError_t launch_rhs(const double2* lam, const double2* yhat, int K, int M, int N, double beta,
-                       typename CT<Tout>::type* bhat, cudaStream_t s);
+cudaError_t launch_rhs(const double2* lam, const double2* yhat, const double2* pinv64, int K, int M, int N,
+                       double beta, typename CT<Tout>::type* xb, cudaStream_t s);
 // copy FP64 spectra to the plan precision
 template <typename Tout>
 cudaError_t launch_spectra_store(const double2* src, typename CT<Tout>::type* dst, size_t n, cudaStream_t s);

@@ -4,10 +4,12 @@
 // One CTA owns CC adjacent half-spectrum columns k2 of every channel.  It
 // stages the M x N x CC tile in shared memory, runs the forward column DFTs
 // (CC interleaved FFTs per channel, one thread team per channel), then for
-// every frequency (k1, k2) of the tile reads the M channel values once and
-// applies the packed Hermitian M x M matrix Psi^{-1}(w) / N^2 to
-// bhat(w) + Q(w), and finally runs the inverse column DFTs and writes the
-// row-domain half spectra of the new x.
+// every frequency (k1, k2) of the tile reads the M channel values once,
+// applies the packed Hermitian M x M matrix Psi^{-1}(w) / N^2 to Q(w) and
+// adds the FP64-formed data term xb(w) = Psi^{-1} beta Lambda^H F y / N^2
+// (the same x-update by linearity, without rounding the ill-conditioned
+// product every iteration), and finally runs the inverse column DFTs and
+// writes the row-domain half spectra of the new x.
 #include "fft.cuh"
 #include "kernels.h"
 
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(512) passB_kernel(const PassBArgs<T> a) {
   }
   __syncthreads();
 
-  // per-frequency solve: x = Pinv (bhat + Q)
+  // per-frequency solve: x = xb + Pinv Q
   for (int idx = tid; idx < N * CC; idx += nth) {
     const int k1 = idx / CC, c = idx - k1 * CC;
     const int k2 = c0 + c;
@@ -71,8 +73,8 @@ __global__ void __launch_bounds__(512) passB_kernel(const PassBArgs<T> a) {
 #pragma unroll
     for (int i = 0; i < MMAX; ++i) {
       if (i < M) {
-        r[i] = cadd(a.bhat[i * mplane + off], data[i * ZS + spad(idx)]);
-        x[i] = mk<C>(0.0, 0.0);
+        r[i] = data[i * ZS + spad(idx)];
+        x[i] = a.bhat[i * mplane + off];
       }
     }
     int pk = 0;

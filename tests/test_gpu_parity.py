@@ -1,7 +1,7 @@
 """CUDA path vs the FP64 oracle through the C ABI.  GPU only.
 
 Tolerances: relative L2 per step <= 1e-5 and on the final x <= 1e-4 for the
-complex64 path (FP64-formed factor); <= 1e-10 for the FP64 path."""
+complex64 path (FP64-formed factor and data term); <= 1e-10 for the FP64 path."""
 import numpy as np
 import pytest
 
@@ -39,51 +39,125 @@ def make_plan(torch, h, y, prior, lam, rho, beta, dtype, **kw):
     return P
 
 
-def problem(seed, N, K, M, unit_sum=True):
+def problem(seed, N, K, M, kind="gauss"):
+    """Rectangles + Gaussian PSFs (kind 'gauss') or spectral image + disk-plus-Gaussian PSFs ('disk')."""
     rng = np.random.default_rng(seed)
-    x = inputs.rectangles_image(rng, N, M, n_rect=6)
-    if unit_sum:
+    if kind == "gauss":
+        x = inputs.rectangles_image(rng, N, M, n_rect=6)
         h = inputs.gaussian_psf_bank(N, K, M)
     else:
-        h = rng.uniform(0, 1, (K, M, N, N)) * (rng.random((K, M, N, N)) < 0.02)
-        h[:, :, 0, 0] += 1.0
+        x = inputs.spectral_image(rng, N, M)
+        h = inputs.disk_gaussian_psf_bank(N, K, M)
     y, _ = inputs.measure(rng, x, h, 30.0)
     return rng, h, y
 
 
-CASES = [
-    # prior, N, K, M, dtype, lam, rho
-    ("tv", 64, 3, 3, "f64", 1e-2, 1.0),
-    ("tv", 64, 3, 3, "f32", 1e-2, 1.0),
-    ("dct8", 64, 2, 3, "f32", 1e-3, 0.1),
-    ("l1", 64, 3, 2, "f32", 1e-2, 0.5),
-    ("dct8", 128, 3, 3, "f64", 1e-3, 0.1),
-    ("tv", 256, 5, 5, "f32", 1e-2, 1.0),
-    ("dct8", 256, 4, 10, "f32", 1e-3, 1e-2),
-    ("tv", 1024, 3, 3, "f32", 1e-2, 1.0),
-    ("l1", 2048, 1, 1, "f32", 1e-2, 1.0),
+def oracle_states(h, y, prior, lam, rho, ls, naive):
+    """Oracle iterates (t^l, u^l) at the requested l and the oracle's next step from each."""
+    mod = admm if naive else fast
+    S = mod.analysis_setup(h, y, prior, lam, rho, 1.0)
+    K, M, N, _ = h.shape
+    nc = 2 if prior == "tv" else 1
+    t = np.zeros((M, nc, N, N))
+    u = np.zeros_like(t)
+    out = []
+    for l in range(max(ls) + 1):
+        x1, t1, u1, _ = mod.analysis_step(S, t, u)
+        if l in ls:
+            out.append((l, t, u, x1, u1))
+        t, u = t1, u1
+    return out
+
+
+STEP_CASES = [
+    # prior, N, K, M, dtype, lam, rho, kind, states l
+    ("tv", 64, 3, 3, "f64", 1e-2, 1.0, "gauss", (0, 1, 10, 49)),
+    ("tv", 64, 3, 3, "f32", 1e-2, 1.0, "gauss", (0, 1, 10, 49)),
+    ("dct8", 64, 2, 3, "f32", 1e-3, 1e-2, "disk", (0, 1, 10, 40)),
+    ("l1", 64, 3, 2, "f32", 1e-2, 0.5, "gauss", (0, 1, 10)),
+    ("dct8", 128, 3, 3, "f64", 1e-3, 0.1, "disk", (0, 10)),
+    ("tv", 256, 5, 5, "f32", 1e-2, 1.0, "disk", (0, 1, 10, 30)),
+    ("dct8", 256, 10, 10, "f32", 1e-3, 1e-2, "disk", (0, 1, 10, 30)),
+    ("tv", 128, 1, 3, "f32", 1e-2, 1.0, "gauss", (0, 10)),     # K < M: rank-deficient Lambda^H Lambda
+    ("tv", 128, 5, 2, "f32", 1e-2, 1.0, "gauss", (0, 10)),     # K > M
+    ("l1", 2048, 1, 1, "f32", 1e-2, 1.0, "gauss", (0, 5)),     # largest N
+    ("tv", 1024, 3, 3, "f32", 1e-2, 1.0, "gauss", (0, 5)),
 ]
 
 
-@pytest.mark.parametrize("prior,N,K,M,dtype,lam,rho", CASES)
-def test_one_step_from_imported_state(torch, prior, N, K, M, dtype, lam, rho):
-    """Alg. 1 one iteration from a random (t, u): x (Eq. solx_Trans_DFT), u (Eqs. solt_trans, subu_trans)."""
-    rng, h, y = problem(100 + N + M, N, K, M, unit_sum=(prior == "tv"))
-    t, u = inputs.random_state(rng, prior, M, N, scale=0.05)
-    if N <= 64:
-        S = admm.analysis_setup(h, y, prior, lam, rho, 1.0)
-        x1, t1, u1, _ = admm.analysis_step(S, t, u)
-    else:
-        S = fast.analysis_setup(h, y, prior, lam, rho, 1.0)
-        x1, t1, u1, _ = fast.analysis_step(S, t, u)
+@pytest.mark.parametrize("prior,N,K,M,dtype,lam,rho,kind,ls", STEP_CASES)
+def test_step_parity_on_oracle_states(torch, prior, N, K, M, dtype, lam, rho, kind, ls):
+    """One GPU iteration of Alg. 1 from the oracle's (t^l, u^l) against the oracle's iteration l+1:
+    x (Eq. solx_Trans_DFT) and u (Eqs. solt_trans, subu_trans), relative L2 <= 1e-5 (complex64 path)."""
+    rng, h, y = problem(100 + N + M + K, N, K, M, kind)
     P = make_plan(torch, h, y, prior, lam, rho, 1.0, dtype)
-    P.state_import(tdev(torch, t, dtype), tdev(torch, u, dtype))
-    assert P.iterate(1) == 1
-    xg = P.get_x().double().cpu().numpy()
-    ug = P.get_u().double().cpu().numpy()
+    for l, t, u, x1, u1 in oracle_states(h, y, prior, lam, rho, ls, naive=(N <= 64)):
+        P.state_import(tdev(torch, t, dtype), tdev(torch, u, dtype))
+        assert P.iterate(1) == 1
+        xg = P.get_x().double().cpu().numpy()
+        ug = P.get_u().double().cpu().numpy()
+        ex = rel(xg, x1)
+        eu = rel(ug, u1) if np.linalg.norm(u1) > 0 else float(np.abs(ug).max())
+        assert ex <= STEP_TOL[dtype], (l, ex)
+        assert eu <= STEP_TOL[dtype], (l, eu)
     P.close()
-    assert rel(xg, x1) <= STEP_TOL[dtype], rel(xg, x1)
-    assert rel(ug, u1) <= STEP_TOL[dtype], rel(ug, u1)
+
+
+@pytest.mark.parametrize("prior,N,rho", [("tv", 64, 1.0), ("dct8", 64, 0.3), ("l1", 128, 0.5)])
+def test_step_random_state(torch, prior, N, rho):
+    """Property at white-noise (t, u): the complex64 step stays within 1e-4 of the FP64 oracle."""
+    rng, h, y = problem(7 + N, N, 3, 3, "gauss")
+    t, u = inputs.random_state(rng, prior, 3, N, scale=0.05)
+    mod = admm if N <= 64 else fast
+    S = mod.analysis_setup(h, y, prior, 1e-2, rho, 1.0)
+    x1, _, u1, _ = mod.analysis_step(S, t, u)
+    P = make_plan(torch, h, y, prior, 1e-2, rho, 1.0, "f32")
+    P.state_import(tdev(torch, t, "f32"), tdev(torch, u, "f32"))
+    P.iterate(1)
+    assert rel(P.get_x().double().cpu().numpy(), x1) <= 1e-4
+    assert rel(P.get_u().double().cpu().numpy(), u1) <= 1e-4
+    P.close()
+
+
+@pytest.fixture(scope="module")
+def spectral_full():
+    """The 512 x 512 x 10 spectral-imaging DCT workload and its FP64 oracle run (fast form)."""
+    Pr = inputs.spectral_dct()
+    S = fast.analysis_setup(Pr.h, Pr.y, Pr.prior, Pr.lam, Pr.rho, Pr.beta)
+    t = np.zeros((Pr.M, 1, Pr.N, Pr.N))
+    u = np.zeros_like(t)
+    keep = {}
+    x = None
+    for l in range(Pr.iters):
+        if l in (0, 10, 100):
+            keep[l] = (t, u)
+        x, t, u, _ = fast.analysis_step(S, t, u)
+    return Pr, S, keep, x, u
+
+
+def test_full_size_step_parity(torch, spectral_full):
+    """512 x 512 x 10 DCT workload in the benchmark's launch configuration: one step from the oracle's
+    states l = 0, 10, 100 within 1e-5."""
+    Pr, S, keep, _, _ = spectral_full
+    P = make_plan(torch, Pr.h, Pr.y, Pr.prior, Pr.lam, Pr.rho, Pr.beta, "f32")
+    for l, (t, u) in keep.items():
+        x1, _, u1, _ = fast.analysis_step(S, t, u)
+        P.state_import(tdev(torch, t, "f32"), tdev(torch, u, "f32"))
+        P.iterate(1)
+        ex = rel(P.get_x().double().cpu().numpy(), x1)
+        eu = rel(P.get_u().double().cpu().numpy(), u1)
+        assert ex <= 1e-5 and eu <= 1e-5, (l, ex, eu)
+    P.close()
+
+
+def test_full_size_final_x(torch, spectral_full):
+    """512 x 512 x 10 DCT workload: x after 200 free-running GPU iterations within 1e-4 of the oracle's."""
+    Pr, S, keep, x_ref, u_ref = spectral_full
+    P = make_plan(torch, Pr.h, Pr.y, Pr.prior, Pr.lam, Pr.rho, Pr.beta, "f32")
+    assert P.iterate(Pr.iters) == Pr.iters
+    xg = P.get_x().double().cpu().numpy()
+    P.close()
+    assert rel(xg, x_ref) <= 1e-4, rel(xg, x_ref)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -106,7 +180,7 @@ def test_tiny_tv_full_run(torch, dtype):
 
 def test_first_iterate_is_factor_times_rhs(torch):
     """x^1 from t = u = 0 is F^H Psi^{-1} beta Lambda^H F y: checks setup (PSF DFT, factor incl. the
-    DC pseudo-inverse of TV, rhs) through the C ABI."""
+    DC pseudo-inverse of TV, data term) through the C ABI."""
     Pr = inputs.tiny_tv(iters=1)
     S = admm.analysis_setup(Pr.h, Pr.y, "tv", Pr.lam, Pr.rho, Pr.beta)
     x1 = admm.x_update(S, np.zeros((3, 2, 64, 64)), np.zeros((3, 2, 64, 64)))
@@ -132,7 +206,8 @@ def test_host_pointers_match_device_pointers(torch):
     xh = np.empty((Pr.M, Pr.N, Pr.N), np.float32)
     Ph.get_x(xh)
     assert np.array_equal(xd, xh)
-    Pd.close(); Ph.close()
+    Pd.close()
+    Ph.close()
 
 
 def test_checkpoint_resume_is_bitwise(torch):
@@ -168,8 +243,8 @@ def test_tolerance_stop_matches_oracle(torch):
     Pr = inputs.tiny_tv(iters=300)
     S = fast.analysis_setup(Pr.h, Pr.y, Pr.prior, Pr.lam, Pr.rho, Pr.beta)
     tol = 1e-3
-    # oracle: residuals at iterations 10, 20, ...
-    t = np.zeros((3, 2, 64, 64)); u = np.zeros_like(t)
+    t = np.zeros((3, 2, 64, 64))
+    u = np.zeros_like(t)
     n_or = None
     for it in range(1, 301):
         x, t_new, u_new, w = fast.analysis_step(S, t, u)
