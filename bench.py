@@ -200,7 +200,7 @@ def main():
     # ---- device-resident timed region
     clocks = ClockSampler(local)
     clocks.start()
-    plan.set_timing(True)
+    time.sleep(0.5)  # let the sampler start before the timed region
     l0 = plan.launches()
     if dist:
         dist.barrier()
@@ -218,9 +218,18 @@ def main():
         dist.barrier()
     launches = (plan.launches() - l0) // args.steps
     ms = [s.elapsed_time(e) for s, e in times]
+    clk = clocks.stop()
+
+    # ---- per-kernel durations: CUDA events around every column-pass / prior-pass launch on the
+    # launching stream, over the same steps (kept out of the timed region above: ~400 event
+    # records per step would add to its time)
+    plan.set_timing(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step(h_dev, y_dev, x_dev)
+    torch.cuda.synchronize()
     kt = plan.get_timing()
     plan.set_timing(False)
-    clk = clocks.stop()
     total_ms = sum(ms)
     if dist:
         tt = torch.tensor([total_ms], device="cuda")
