@@ -293,7 +293,9 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
     const bool last = (it == max_iter - 1);
     const int phase = (it + 1) % ce;
     int flags = 0;
-    if ((tol > 0 && phase == ce - 1) || it == max_iter - 2) flags |= PA_STORE_T;
+    // t is kept on the iteration before a residual check and on the last iteration (so the next
+    // call's first dual residual compares against the right t_prev)
+    if ((tol > 0 && phase == ce - 1) || it == max_iter - 2 || last) flags |= PA_STORE_T;
     const bool check = (tol > 0 && phase == 0 && it > 0) || last;
     if (check) flags |= PA_RESID;
     // x-update (pass B), then t/u update + next adjoint (pass A)
@@ -617,7 +619,7 @@ cip_status cip_state_import(cip_plan* p, const void* t, const void* u, void* str
 cip_status cip_state_size(cip_plan* p, size_t* bytes) {
   if (!p || !bytes) return CIP_ERR_INVALID_ARG;
   if (p->prior < 0) return fail(p, CIP_ERR_STATE, "cip_set_prior has not been called");
-  *bytes = 2 * sizeof(int) + half_elems(p, p->M) * 2 * p->esz * 2 + real_elems(p, p->M) * ncomp_of(p->prior) * p->esz;
+  *bytes = 2 * sizeof(int) + half_elems(p, p->M) * 2 * p->esz * 2 + 2 * real_elems(p, p->M) * ncomp_of(p->prior) * p->esz;
   return CIP_OK;
 }
 
@@ -639,7 +641,10 @@ cip_status cip_state_export(cip_plan* p, void* buf, void* stream) {
   off += hb;
   CIP_CUDA(p, cudaMemcpyAsync(b + off, p->qh, hb, k, s));
   off += hb;
-  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->u[p->cur], real_elems(p, p->M) * ncomp_of(p->prior) * p->esz, k, s));
+  const size_t ub = real_elems(p, p->M) * ncomp_of(p->prior) * p->esz;
+  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->u[p->cur], ub, k, s));
+  off += ub;
+  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->tprev, ub, k, s));
   CIP_CUDA(p, cudaStreamSynchronize(s));
   return CIP_OK;
 }
@@ -666,7 +671,10 @@ cip_status cip_state_restore(cip_plan* p, const void* buf, void* stream) {
   off += hb;
   CIP_CUDA(p, cudaMemcpyAsync(p->qh, b + off, hb, k, s));
   off += hb;
-  CIP_CUDA(p, cudaMemcpyAsync(p->u[p->cur], b + off, real_elems(p, p->M) * ncomp_of(p->prior) * p->esz, k, s));
+  const size_t ub = real_elems(p, p->M) * ncomp_of(p->prior) * p->esz;
+  CIP_CUDA(p, cudaMemcpyAsync(p->u[p->cur], b + off, ub, k, s));
+  off += ub;
+  CIP_CUDA(p, cudaMemcpyAsync(p->tprev, b + off, ub, k, s));
   CIP_CUDA(p, cudaStreamSynchronize(s));
   p->iteration = hdr[0];
   p->resid_valid = false;
