@@ -146,6 +146,37 @@ cip_status cip_get_launches(cip_plan* plan, unsigned long long* launches);
 cip_status cip_get_config(cip_plan* plan, int* rows_per_tile, int* col_tile, int* prior_pass_blocks,
                           int* column_pass_blocks);
 
+/* Shrinkage, dual update and residual norms of one ADMM iteration without any
+ * device allocation.  The paper has no counterpart: this exists for callers
+ * that cannot allocate device memory -- code recording a CUDA stream capture
+ * that must not gain allocation nodes, host frameworks that hand the library
+ * a fixed arena and forbid it to grow its footprint, and real-time loops in
+ * which a driver allocation could stall.
+ *
+ * Given x[M][N][N] (an x-update's result), u_in and t_prev [M][ncomp][N][N]
+ * (ncomp = 2 for TV, else 1), all DEVICE pointers of the given dtype, it
+ * computes w = T x, t = soft(w + u_in, lambda/rho), u_out = u_in + w - t,
+ * writes u_out (and t_out unless it is NULL; both device pointers, not
+ * aliasing the inputs), and stores the relative residuals
+ * {r/max(||Tx||,||t||), s/||rho u_out||}, r = ||Tx - t||,
+ * s = rho ||t - t_prev||, into resid_out[2] (host or device pointer; a host
+ * pointer makes the call synchronise the stream).  Same results as the prior
+ * pass inside cip_iterate.
+ *
+ * No cudaMalloc, cudaFree or other allocating call is made.  Its scratch
+ * (per-block partial sums) is a fixed static device array of 1.25 MiB that
+ * every GPU loading the library holds until exit; sizes needing more than
+ * 32768 blocks (impossible within N <= 2048, M <= 16) return
+ * CIP_ERR_UNSUPPORTED.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current: make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (every value a call reads is written by the
+ * same call first); calls whose kernels overlap on the GPU race on it, so
+ * order them on one stream. */
+cip_status cip_shrink_dual_noalloc(cip_dtype dtype, cip_prior prior, int N, int M, double lambda, double rho,
+                                   const void* x, const void* u_in, const void* t_prev, void* u_out, void* t_out,
+                                   double* resid_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

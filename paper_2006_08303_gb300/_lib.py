@@ -47,6 +47,8 @@ SIGNATURES = {
     "cip_get_timing": (c_int, [c_void_p, P_double, P_int, P_double, P_int]),
     "cip_get_config": (c_int, [c_void_p, P_int, P_int, P_int, P_int]),
     "cip_get_launches": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "cip_shrink_dual_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_double, c_double, c_void_p, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 _LIB = None

@@ -207,6 +207,28 @@ class Plan:
                 "column_pass_blocks": v[3].value}
 
 
+def shrink_dual_noalloc(prior: str, lam: float, rho: float, x, u_in, t_prev, u_out, resid_out, t_out=None,
+                        stream=None):
+    """cip_shrink_dual_noalloc: t/u update and relative residuals from device tensors the caller owns,
+    with no device allocation by the library (for callers that cannot allocate, e.g. inside a
+    stream capture or a fixed memory arena).  resid_out: 2 float64 (device tensor or numpy array)."""
+    M, N = int(x.shape[0]), int(x.shape[-1])
+    dtype = "f32" if str(x.dtype).endswith("float32") else "f64"
+    ncomp = 2 if prior == "tv" else 1
+    px, k0 = _ptr_and_check(x, dtype, (M, N, N))
+    pu, k1 = _ptr_and_check(u_in, dtype, (M, ncomp, N, N))
+    pt, k2 = _ptr_and_check(t_prev, dtype, (M, ncomp, N, N))
+    po, k3 = _ptr_and_check(u_out, dtype, (M, ncomp, N, N))
+    ptout = _ptr_and_check(t_out, dtype, (M, ncomp, N, N))[0] if t_out is not None else None
+    pr = resid_out.ctypes.data if isinstance(resid_out, np.ndarray) else resid_out.data_ptr()
+    L = _lib.load()
+    st = L.cip_shrink_dual_noalloc(DTYPES[dtype], PRIORS[prior], N, M, lam, rho, ctypes.c_void_p(px),
+                                   ctypes.c_void_p(pu), ctypes.c_void_p(pt), ctypes.c_void_p(po),
+                                   ctypes.c_void_p(ptout), ctypes.c_void_p(pr), _stream_ptr(stream))
+    if st != 0:
+        raise CipError(st, L.cip_status_string(st).decode())
+
+
 def reconstruct(problem, dtype: Optional[str] = None, iters: Optional[int] = None, tol: float = 0.0, stream=None):
     """Convenience: full reconstruction of an ``inputs.Problem`` with device-resident inputs."""
     torch = _torch()

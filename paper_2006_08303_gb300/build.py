@@ -25,6 +25,7 @@ UNITS = [
     ("passB.cu", ["-DPASSB_T=double"], "passB_f64.o"),
     ("fft_kernels.cu", [], "fft_kernels.o"),
     ("factor.cu", [], "factor.o"),
+    ("noalloc.cu", [], "noalloc.o"),
 ]
 
 
