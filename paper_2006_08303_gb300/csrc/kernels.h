@@ -40,8 +40,8 @@ template <typename T> struct PassBArgs {
   using C = typename CT<T>::type;
   const C* qh;      // [M][N][P]
   C* xh;            // [M][N][P]
-  const C* pinv;    // [M(M+1)/2][N][P] packed upper triangle, scaled by 1/N^2
-  const C* bhat;    // [M][N][P]: xb = Psi^{-1} beta Lambda^H F y / N^2 (FP64-formed)
+  const C* pinv;    // [N/2+1][M(M+1)/2][N] packed upper triangle per bin, scaled by 1/N^2
+  const C* bhat;    // [N/2+1][M][N]: xb = Psi^{-1} beta Lambda^H F y / N^2 (FP64-formed)
   const C* tw;
   int M;
 };

@@ -4,10 +4,13 @@
 // One CTA owns R consecutive image rows of one channel (plus one halo row on
 // each side for TV).  It
 //   1. loads the row half-spectra of x (written by pass B) and inverts the row
-//      DFT two rows at a time (one complex FFT for two real rows);
+//      DFT two rows at a time (one complex FFT z = x_a + i x_b for two real
+//      rows, so shared memory holds the tile as row pairs);
 //   2. applies the analysis operator T (anisotropic TV differences, 8x8
 //      orthonormal block DCT, or identity), the soft-threshold t-update
-//      (Eq. solt_trans) and the dual update (Eq. subu_trans), writing u;
+//      (Eq. solt_trans) and the dual update (Eq. subu_trans), writing u; every
+//      thread works on both rows of a pair, so shared-memory accesses are
+//      whole 8- or 16-byte pairs;
 //   3. forms q = (rho/2) T^T (t - u) and takes its forward row DFT, writing
 //      the row half-spectra that pass B turns into the full 2D DFT.
 // Optionally it stores t (for the next iteration's dual residual) and writes
@@ -46,11 +49,11 @@ __device__ __forceinline__ void block_reduce_store(const double (&v)[kNPart], do
   }
 }
 
-template <typename T> struct PA {
-  using C = typename CT<T>::type;
-};
+// FFT elements per thread: 8 for complex64 up to N = 1024 (more warps per
+// tile), 16 otherwise (keeps the CTA within 1024 threads).
+template <typename T> constexpr int elems_a(int N) { return (sizeof(T) == 4 && N <= 1024) ? 8 : 16; }
 
-// rows per tile and smem size
+// rows per tile
 template <typename T> constexpr int rows_for(int N, int prior) {
   if (prior != PRIOR_TV) return 8;
   using C = typename CT<T>::type;
@@ -62,7 +65,7 @@ template <typename T> constexpr int rows_for(int N, int prior) {
   return 2;
 }
 
-template <typename T> size_t smem_for(int N, int prior, int R) {
+template <typename T> constexpr size_t smem_for(int N, int prior, int R) {
   using C = typename CT<T>::type;
   const int halo = prior == PRIOR_TV ? 1 : 0;
   size_t sm = (size_t)((R + 2 * halo) / 2) * spad(N) * sizeof(C);
@@ -70,31 +73,60 @@ template <typename T> size_t smem_for(int N, int prior, int R) {
   return sm;
 }
 
-template <typename T>
-__device__ __forceinline__ T zget(const typename CT<T>::type* zb, int ZS, int j, int c) {
-  const typename CT<T>::type& v = zb[(j >> 1) * ZS + spad(c)];
-  return (j & 1) ? v.y : v.x;
-}
-template <typename T>
-__device__ __forceinline__ void zset(typename CT<T>::type* zb, int ZS, int j, int c, T val) {
-  typename CT<T>::type& v = zb[(j >> 1) * ZS + spad(c)];
-  if (j & 1) v.y = val; else v.x = val;
+template <typename T> constexpr int threads_for(int N, int prior, int R) {
+  const int npin = (R + (prior == PRIOR_TV ? 2 : 0)) / 2;
+  const int n = npin * (N / elems_a<T>(N));
+  return ((n + 31) / 32) * 32;
 }
 
-// 8-point orthonormal DCT-II (FWD) or its inverse, matrix dct[k*8+n]
-template <typename T, bool FWD>
-__device__ __forceinline__ void dct8(const T* __restrict__ d, const T (&in)[8], T (&out)[8]) {
+template <typename T> constexpr int minblocks_for(int nth) { return nth >= 1024 ? 1 : 1024 / nth; }
+
+// 8-point orthonormal DCT-II (FWD) or its inverse on the two rows of a pair
+template <typename T, bool FWD, typename C>
+__device__ __forceinline__ void dct8_pair(const T* __restrict__ d, const C (&in)[8], C (&out)[8]) {
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    T acc = T(0);
+    T ax = T(0), ay = T(0);
 #pragma unroll
-    for (int n = 0; n < 8; ++n) acc = fma(FWD ? d[k * 8 + n] : d[n * 8 + k], in[n], acc);
-    out[k] = acc;
+    for (int n = 0; n < 8; ++n) {
+      const T cf = FWD ? d[k * 8 + n] : d[n * 8 + k];
+      ax = fma(cf, in[n].x, ax);
+      ay = fma(cf, in[n].y, ay);
+    }
+    out[k].x = ax;
+    out[k].y = ay;
+  }
+}
+
+template <typename T> __device__ __forceinline__ T dct_dot(const T* __restrict__ d, const T (&v)[8], int k, bool fwd) {
+  T acc = T(0);
+#pragma unroll
+  for (int n = 0; n < 8; ++n) acc = fma(fwd ? d[k * 8 + n] : d[n * 8 + k], v[n], acc);
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ void shrink(T w, T u, T tau, T& t, T& un) {
+  t = soft(w + u, tau);
+  un = u + w - t;
+}
+
+template <typename T>
+__device__ __forceinline__ void acc_resid(double (&part)[kNPart], T w, T t, T un, const T* tprev, size_t g) {
+  part[0] += (double)(w - t) * (double)(w - t);
+  part[1] += (double)w * w;
+  part[2] += (double)t * t;
+  part[3] += (double)un * un;
+  if (tprev) {
+    const T dt = t - tprev[g];
+    part[4] += (double)dt * dt;
   }
 }
 
 template <typename T, int LOGN, int PRIOR, int R>
-__global__ void __launch_bounds__(512) passA_kernel(const PassAArgs<T> a) {
+__global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
+                                  minblocks_for<T>(threads_for<T>(1 << LOGN, PRIOR, R)))
+    passA_kernel(const PassAArgs<T> a) {
   using C = typename CT<T>::type;
   constexpr int N = 1 << LOGN;
   constexpr int H = N / 2 + 1;
@@ -104,12 +136,13 @@ __global__ void __launch_bounds__(512) passA_kernel(const PassAArgs<T> a) {
   constexpr int NPIN = ROWS / 2;
   constexpr int NPOUT = R / 2;
   constexpr int ZS = spad(N);
-  constexpr int TEAM = N / 16;
+  constexpr int E = elems_a<T>(N);
+  constexpr int TEAM = N / E;
   constexpr int NCOMP = PRIOR == PRIOR_TV ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* zb = reinterpret_cast<C*>(smem_raw);
-  T* ah = reinterpret_cast<T*>(zb + NPIN * ZS);  // TV only: [R][N]
-  T* av = ah + R * N;                             // TV only: [R+1][N]
+  T* ah = reinterpret_cast<T*>(zb + NPIN * ZS);  // TV only: [R][N], a_h at tile rows 1..R
+  T* av = ah + R * N;                             // TV only: [R+1][N], a_v at tile rows 0..R
 
   const int tid = threadIdx.x;
   const int nth = blockDim.x;
@@ -124,6 +157,7 @@ __global__ void __launch_bounds__(512) passA_kernel(const PassAArgs<T> a) {
   T* u_out = a.u_out + (size_t)m * NCOMP * plane;
   T* tprev = a.tprev ? a.tprev + (size_t)m * NCOMP * plane : nullptr;
   const T* timp = a.t_imp ? a.t_imp + (size_t)m * NCOMP * plane : nullptr;
+  const T* tprev_rd = resid ? tprev : nullptr;
   double part[kNPart] = {0.0, 0.0, 0.0, 0.0, 0.0};
 
   auto grow = [&](int j) { return (r0 - HALO + j) & (N - 1); };
@@ -140,81 +174,85 @@ __global__ void __launch_bounds__(512) passA_kernel(const PassAArgs<T> a) {
     __syncthreads();
     {
       const int team = tid / TEAM;
-      if (team < NPIN) fft_team<C, LOGN, 1, 16, +1>(zb + team * ZS, tid % TEAM, a.tw, make_team_sync(team, TEAM));
+      if (team < NPIN) fft_team<C, LOGN, 1, E, +1>(zb + team * ZS, tid % TEAM, a.tw, make_team_sync(team, TEAM));
     }
     __syncthreads();
   }
 
   // 2. analysis operator, shrinkage, dual update; 3. q = qscale T^T (t - u')
   if constexpr (PRIOR == PRIOR_TV) {
-    const T* uh_in = u_in;
-    const T* uv_in = u_in + plane;
-    for (int idx = tid; idx < (R + 1) * N; idx += nth) {
-      const int j = idx / N, c = idx - j * N;
-      const size_t g = (size_t)grow(j) * N + c;
-      T x0 = T(0), wv = T(0), wh = T(0);
+    // a_v at tile rows 0..R, a_h at tile rows 1..R; thread = (row pair p, column c)
+    for (int idx = tid; idx < NPIN * N; idx += nth) {
+      const int p = idx / N, c = idx - p * N;
+      C z0 = mk<C>(0.0, 0.0), zr = z0, zd = z0;
       if (!import_mode) {
-        x0 = zget<T>(zb, ZS, j, c);
-        wv = zget<T>(zb, ZS, j + 1, c) - x0;
+        z0 = zb[p * ZS + spad(c)];
+        zr = zb[p * ZS + spad((c + 1) & (N - 1))];
+        if (p + 1 < NPIN) zd = zb[(p + 1) * ZS + spad(c)];
       }
-      // vertical component (rows j = 0..R; j = 0 is the halo row, not written)
-      T tv, uvn;
-      if (import_mode) {
-        tv = timp[plane + g];
-        uvn = uv_in[g];
-      } else {
-        const T uv = uv_in[g];
-        tv = soft(wv + uv, tau);
-        uvn = uv + wv - tv;
-      }
-      av[j * N + c] = tv - uvn;
-      if (j >= 1) {
-        u_out[plane + g] = uvn;
-        T th, uhn;
+      const T x0[2] = {z0.x, z0.y};
+      const T wv[2] = {z0.y - z0.x, zd.x - z0.y};
+      const T wh[2] = {zr.x - z0.x, zr.y - z0.y};
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int j = 2 * p + s;
+        if (j > R) continue;  // row R+1: neither component needed
+        const size_t g = (size_t)grow(j) * N + c;
+        T tv, uvn;
         if (import_mode) {
-          th = timp[g];
-          uhn = uh_in[g];
+          tv = timp[plane + g];
+          uvn = u_in[plane + g];
         } else {
-          wh = zget<T>(zb, ZS, j, (c + 1) & (N - 1)) - x0;
-          const T uh = uh_in[g];
-          th = soft(wh + uh, tau);
-          uhn = uh + wh - th;
+          shrink(wv[s], u_in[plane + g], tau, tv, uvn);
         }
-        ah[(j - 1) * N + c] = th - uhn;
-        u_out[g] = uhn;
-        if (resid) {
-          part[0] += (double)(wh - th) * (double)(wh - th) + (double)(wv - tv) * (double)(wv - tv);
-          part[1] += (double)wh * wh + (double)wv * wv;
-          part[2] += (double)th * th + (double)tv * tv;
-          part[3] += (double)uhn * uhn + (double)uvn * uvn;
-          if (tprev) {
-            const T dh = th - tprev[g], dv = tv - tprev[plane + g];
-            part[4] += (double)dh * dh + (double)dv * dv;
+        av[j * N + c] = tv - uvn;
+        if (j >= 1) {
+          u_out[plane + g] = uvn;
+          T th, uhn;
+          if (import_mode) {
+            th = timp[g];
+            uhn = u_in[g];
+          } else {
+            shrink(wh[s], u_in[g], tau, th, uhn);
+          }
+          ah[(j - 1) * N + c] = th - uhn;
+          u_out[g] = uhn;
+          if (resid) {
+            acc_resid(part, wh[s], th, uhn, tprev_rd, g);
+            acc_resid(part, wv[s], tv, uvn, tprev_rd ? tprev_rd + plane : nullptr, g);
+          }
+          if (store_t) {
+            tprev[g] = th;
+            tprev[plane + g] = tv;
           }
         }
-        if (store_t) {
-          tprev[g] = th;
-          tprev[plane + g] = tv;
-        }
+        (void)x0;
       }
     }
     __syncthreads();
-    for (int idx = tid; idx < R * N; idx += nth) {
-      const int jj = idx / N, c = idx - jj * N;
-      const T q = ah[jj * N + ((c - 1) & (N - 1))] - ah[jj * N + c] + av[jj * N + c] - av[(jj + 1) * N + c];
-      zset<T>(zb, ZS, jj, c, q * a.qscale);
+    // q at output rows jj = 0..R-1 (tile rows jj+1), written as row pairs
+    for (int idx = tid; idx < NPOUT * N; idx += nth) {
+      const int p = idx / N, c = idx - p * N;
+      const int cm = (c - 1) & (N - 1);
+      T q[2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int jj = 2 * p + s;
+        q[s] = (ah[jj * N + cm] - ah[jj * N + c] + av[jj * N + c] - av[(jj + 1) * N + c]) * a.qscale;
+      }
+      zb[p * ZS + spad(c)] = mk<C>(q[0], q[1]);
     }
   } else if constexpr (PRIOR == PRIOR_DCT8) {
     if (!import_mode) {
-      // row DCT of every 8-sample segment, in place (each thread owns its 8 slots)
-      for (int idx = tid; idx < R * (N / 8); idx += nth) {
-        const int j = idx / (N / 8), c0 = (idx - j * (N / 8)) * 8;
-        T v[8], o[8];
+      // row DCT of every 8-sample segment of both rows of a pair, in place
+      for (int idx = tid; idx < NPOUT * (N / 8); idx += nth) {
+        const int p = idx / (N / 8), c0 = (idx - p * (N / 8)) * 8;
+        C v[8], o[8];
 #pragma unroll
-        for (int n = 0; n < 8; ++n) v[n] = zget<T>(zb, ZS, j, c0 + n);
-        dct8<T, true>(a.dct, v, o);
+        for (int n = 0; n < 8; ++n) v[n] = zb[p * ZS + spad(c0 + n)];
+        dct8_pair<T, true>(a.dct, v, o);
 #pragma unroll
-        for (int n = 0; n < 8; ++n) zset<T>(zb, ZS, j, c0 + n, o[n]);
+        for (int n = 0; n < 8; ++n) zb[p * ZS + spad(c0 + n)] = o[n];
       }
       __syncthreads();
     }
@@ -224,8 +262,13 @@ __global__ void __launch_bounds__(512) passA_kernel(const PassAArgs<T> a) {
       T v[8], w[8], d[8];
       if (!import_mode) {
 #pragma unroll
-        for (int n = 0; n < 8; ++n) v[n] = zget<T>(zb, ZS, br * 8 + n, c);
-        dct8<T, true>(a.dct, v, w);
+        for (int q = 0; q < 4; ++q) {
+          const C z = zb[(br * 4 + q) * ZS + spad(c)];
+          v[2 * q] = z.x;
+          v[2 * q + 1] = z.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = dct_dot(a.dct, v, k, true);
       }
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
@@ -234,66 +277,52 @@ __global__ void __launch_bounds__(512) passA_kernel(const PassAArgs<T> a) {
         if (import_mode) {
           t = timp[g];
           un = u_in[g];
+          w[k] = T(0);
         } else {
-          const T u = u_in[g];
-          t = soft(w[k] + u, tau);
-          un = u + w[k] - t;
+          shrink(w[k], u_in[g], tau, t, un);
         }
         u_out[g] = un;
         d[k] = t - un;
-        if (resid) {
-          part[0] += (double)(w[k] - t) * (double)(w[k] - t);
-          part[1] += (double)w[k] * w[k];
-          part[2] += (double)t * t;
-          part[3] += (double)un * un;
-          if (tprev) {
-            const T dt = t - tprev[g];
-            part[4] += (double)dt * dt;
-          }
-        }
+        if (resid) acc_resid(part, w[k], t, un, tprev_rd, g);
         if (store_t) tprev[g] = t;
       }
-      dct8<T, false>(a.dct, d, v);
 #pragma unroll
-      for (int n = 0; n < 8; ++n) zset<T>(zb, ZS, br * 8 + n, c, v[n]);
+      for (int n = 0; n < 8; ++n) v[n] = dct_dot(a.dct, d, n, false);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) zb[(br * 4 + q) * ZS + spad(c)] = mk<C>(v[2 * q], v[2 * q + 1]);
     }
     __syncthreads();
-    for (int idx = tid; idx < R * (N / 8); idx += nth) {
-      const int j = idx / (N / 8), c0 = (idx - j * (N / 8)) * 8;
-      T v[8], o[8];
+    for (int idx = tid; idx < NPOUT * (N / 8); idx += nth) {
+      const int p = idx / (N / 8), c0 = (idx - p * (N / 8)) * 8;
+      C v[8], o[8];
 #pragma unroll
-      for (int n = 0; n < 8; ++n) v[n] = zget<T>(zb, ZS, j, c0 + n);
-      dct8<T, false>(a.dct, v, o);
+      for (int n = 0; n < 8; ++n) v[n] = zb[p * ZS + spad(c0 + n)];
+      dct8_pair<T, false>(a.dct, v, o);
 #pragma unroll
-      for (int n = 0; n < 8; ++n) zset<T>(zb, ZS, j, c0 + n, o[n] * a.qscale);
+      for (int n = 0; n < 8; ++n) zb[p * ZS + spad(c0 + n)] = mk<C>(o[n].x * a.qscale, o[n].y * a.qscale);
     }
   } else {  // PRIOR_L1: T = I
-    for (int idx = tid; idx < R * N; idx += nth) {
-      const int j = idx / N, c = idx - j * N;
-      const size_t g = (size_t)(r0 + j) * N + c;
-      T w = T(0), t, un;
-      if (import_mode) {
-        t = timp[g];
-        un = u_in[g];
-      } else {
-        w = zget<T>(zb, ZS, j, c);
-        const T u = u_in[g];
-        t = soft(w + u, tau);
-        un = u + w - t;
-      }
-      u_out[g] = un;
-      if (resid) {
-        part[0] += (double)(w - t) * (double)(w - t);
-        part[1] += (double)w * w;
-        part[2] += (double)t * t;
-        part[3] += (double)un * un;
-        if (tprev) {
-          const T dt = t - tprev[g];
-          part[4] += (double)dt * dt;
+    for (int idx = tid; idx < NPOUT * N; idx += nth) {
+      const int p = idx / N, c = idx - p * N;
+      const C z = zb[p * ZS + spad(c)];
+      const T w[2] = {z.x, z.y};
+      T q[2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const size_t g = (size_t)(r0 + 2 * p + s) * N + c;
+        T t, un;
+        if (import_mode) {
+          t = timp[g];
+          un = u_in[g];
+        } else {
+          shrink(w[s], u_in[g], tau, t, un);
         }
+        u_out[g] = un;
+        if (resid) acc_resid(part, import_mode ? T(0) : w[s], t, un, tprev_rd, g);
+        if (store_t) tprev[g] = t;
+        q[s] = (t - un) * a.qscale;
       }
-      if (store_t) tprev[g] = t;
-      zset<T>(zb, ZS, j, c, (t - un) * a.qscale);
+      zb[p * ZS + spad(c)] = mk<C>(q[0], q[1]);
     }
   }
   __syncthreads();
@@ -301,7 +330,7 @@ __global__ void __launch_bounds__(512) passA_kernel(const PassAArgs<T> a) {
   // 4. forward row DFT of q (two rows per FFT), 5. store row half-spectra
   {
     const int team = tid / TEAM;
-    if (team < NPOUT) fft_team<C, LOGN, 1, 16, -1>(zb + team * ZS, tid % TEAM, a.tw, make_team_sync(team, TEAM));
+    if (team < NPOUT) fft_team<C, LOGN, 1, E, -1>(zb + team * ZS, tid % TEAM, a.tw, make_team_sync(team, TEAM));
   }
   __syncthreads();
   C* qh = a.qh + (size_t)m * N * P;
@@ -319,18 +348,15 @@ template <typename T, int LOGN, int PRIOR>
 cudaError_t launchA(const PassAArgs<T>& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   constexpr int R = rows_for<T>(N, PRIOR);
-  constexpr int HALO = PRIOR == PRIOR_TV ? 1 : 0;
-  constexpr int NPIN = (R + 2 * HALO) / 2;
-  constexpr int TEAM = N / 16;
-  int nth = NPIN * TEAM;
-  nth = ((nth + 31) / 32) * 32;
-  if (nth < 128) nth = 128;
-  const size_t sm = smem_for<T>(N, PRIOR, R);
+  constexpr int nth = threads_for<T>(N, PRIOR, R);
+  constexpr size_t sm = smem_for<T>(N, PRIOR, R);
   auto kern = passA_kernel<T, LOGN, PRIOR, R>;
-  if (sm > 48 * 1024) {
+  static bool attr_done = false;
+  if (!attr_done && sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
+  attr_done = true;
   dim3 grid(N / R, a.M);
   kern<<<grid, nth, sm, s>>>(a);
   return cudaGetLastError();

@@ -1,80 +1,100 @@
 // Pass B: column DFT, per-frequency solve and inverse column DFT, fused
-// (the x-update of Eq. solx_Trans_DFT / Eq. solx_synt_DFT).
+// (the x-update of Eq. solx_Trans_DFT).
 //
-// One CTA owns CC adjacent half-spectrum columns k2 of every channel.  It
-// stages the M x N x CC tile in shared memory, runs the forward column DFTs
-// (CC interleaved FFTs per channel, one thread team per channel), then for
-// every frequency (k1, k2) of the tile reads the M channel values once,
-// applies the packed Hermitian M x M matrix Psi^{-1}(w) / N^2 to Q(w) and
-// adds the FP64-formed data term xb(w) = Psi^{-1} beta Lambda^H F y / N^2
-// (the same x-update by linearity, without rounding the ill-conditioned
-// product every iteration), and finally runs the inverse column DFTs and
-// writes the row-domain half spectra of the new x.
+// A thread-block cluster of M CTAs owns CC adjacent half-spectrum columns k2;
+// CTA m of the cluster holds channel m's N x CC tile in its shared memory.
+//   1. every CTA loads its channel's row-domain half spectra q and runs the
+//      forward column DFTs of its CC columns (interleaved in smem);
+//   2. cluster barrier; the bins of the tile are split over the M CTAs and
+//      for each bin the thread reads the M channel values from the M CTAs'
+//      shared memory (distributed shared memory), forms
+//        X(w) = xb(w) + Psi^{-1}(w)/N^2 Q(w)
+//      with the packed Hermitian M x M factor and the FP64-formed data term
+//      xb = Psi^{-1} beta Lambda^H F y / N^2 (the same x-update by linearity),
+//      and writes the M results back into the owners' shared memory;
+//   3. cluster barrier; every CTA runs the inverse column DFTs and writes its
+//      channel's row-domain half spectra of the new x.
+// Each channel value of a bin is read from HBM once and written once; the
+// factor and the data term are stored column-major per bin plane
+// ([k2][plane][k1]) so that the bins of one column are contiguous.
+#include <cooperative_groups.h>
+
 #include "fft.cuh"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace cip {
 
 namespace {
 
-constexpr int kE = 16;  // FFT elements per thread
+template <typename T> constexpr int elems_for() { return sizeof(T) == 4 ? 8 : 16; }
 
 template <typename T> int cols_for(int N, int M) {
-  using C = typename CT<T>::type;
-  // widest tile whose smem stays within 2 CTAs per SM, and at least 1
-  for (int cc = 4; cc >= 1; cc /= 2) {
-    size_t sm = (size_t)M * spad(N * cc) * sizeof(C);
-    if (sm <= 110 * 1024) return cc;
-  }
-  return 1;
+  (void)M;
+  if (N <= 128) return 4;
+  if (N >= 2048) return 2;  // keeps the CTA at <= 512 threads
+  return sizeof(T) == 4 ? 4 : 2;
+}
+
+// register budget: at most ~80 registers per thread so that several CTAs share an SM
+constexpr int minblocks_b(int nt) {
+  const int b = 65536 / (nt * 80);
+  return b < 1 ? 1 : (b > 32 ? 32 : b);
 }
 
 template <typename T, int LOGN, int CC, int MMAX>
-__global__ void __launch_bounds__(512) passB_kernel(const PassBArgs<T> a) {
+__global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
+                                  minblocks_b((1 << LOGN) * CC / elems_for<T>()))
+    passB_kernel(const PassBArgs<T> a) {
   using C = typename CT<T>::type;
   constexpr int N = 1 << LOGN;
   constexpr int H = N / 2 + 1;
   constexpr int P = half_pitch(N);
-  constexpr int ZS = spad(N * CC);
-  constexpr int TEAM = N * CC / kE;
+  constexpr int E = elems_for<T>();
+  constexpr int NT = N * CC / E;  // threads = one team
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* data = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
   const int M = a.M;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int c0 = blockIdx.x * CC;
+  const int m = blockIdx.x;  // channel == rank in the cluster
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.y * CC;
   const size_t mplane = (size_t)N * P;
+  const C* qh = a.qh + (size_t)m * mplane;
 
-  // load q-hat tile: [m][n1][c]
-  for (int idx = tid; idx < M * N * CC; idx += nth) {
-    const int m = idx / (N * CC);
-    const int rem = idx - m * (N * CC);
-    const int n1 = rem / CC, c = rem - n1 * CC;
+  for (int idx = tid; idx < N * CC; idx += NT) {
+    const int n1 = idx / CC, c = idx - n1 * CC;
     const int k2 = c0 + c;
-    C v = mk<C>(0.0, 0.0);
-    if (k2 < H) v = a.qh[m * mplane + (size_t)n1 * P + k2];
-    data[m * ZS + spad(rem)] = v;
+    buf[spad(idx)] = (k2 < H) ? qh[(size_t)n1 * P + k2] : mk<C>(0.0, 0.0);
   }
+  TeamSync ts;
+  ts.bar_id = 0;
+  ts.nthreads = NT;
+  ts.mask = 0xffffffffu;
   __syncthreads();
-  const int nteams = nth / TEAM;
-  const int team = tid / TEAM;
-  if (team < nteams) {
-    const TeamSync ts = make_team_sync(team, TEAM);
-    for (int m = team; m < M; m += nteams) fft_team<C, LOGN, CC, kE, -1>(data + m * ZS, tid % TEAM, a.tw, ts);
-  }
-  __syncthreads();
+  fft_team<C, LOGN, CC, E, -1>(buf, tid, a.tw, ts);
+  cluster.sync();
 
-  // per-frequency solve: x = xb + Pinv Q
-  for (int idx = tid; idx < N * CC; idx += nth) {
-    const int k1 = idx / CC, c = idx - k1 * CC;
+  // per-frequency solve over this CTA's share of the tile's bins
+  const int nbins = N * CC;
+  const int per = (nbins + M - 1) / M;
+  const int b0 = m * per;
+  const int b1 = min(nbins, b0 + per);
+  const int npk = M * (M + 1) / 2;
+  for (int b = b0 + tid; b < b1; b += NT) {
+    const int k1 = b / CC, c = b - k1 * CC;
     const int k2 = c0 + c;
     if (k2 >= H) continue;
-    const size_t off = (size_t)k1 * P + k2;
+    const C* pcol = a.pinv + ((size_t)k2 * npk) * N + k1;  // plane stride N
+    const C* xcol = a.bhat + ((size_t)k2 * M) * N + k1;
     C r[MMAX], x[MMAX];
 #pragma unroll
     for (int i = 0; i < MMAX; ++i) {
       if (i < M) {
-        r[i] = data[i * ZS + spad(idx)];
-        x[i] = a.bhat[i * mplane + off];
+        const C* peer = cluster.map_shared_rank(buf, i);
+        r[i] = peer[spad(b)];
+        x[i] = xcol[(size_t)i * N];
       }
     }
     int pk = 0;
@@ -84,7 +104,7 @@ __global__ void __launch_bounds__(512) passB_kernel(const PassBArgs<T> a) {
 #pragma unroll
         for (int j = i; j < MMAX; ++j) {
           if (j < M) {
-            const C pij = a.pinv[(size_t)pk * mplane + off];
+            const C pij = pcol[(size_t)pk * N];
             ++pk;
             cfma(x[i], pij, r[j]);
             if (j != i) cfmac(x[j], pij, r[i]);
@@ -93,53 +113,63 @@ __global__ void __launch_bounds__(512) passB_kernel(const PassBArgs<T> a) {
       }
     }
 #pragma unroll
-    for (int i = 0; i < MMAX; ++i)
-      if (i < M) data[i * ZS + spad(idx)] = x[i];
+    for (int i = 0; i < MMAX; ++i) {
+      if (i < M) {
+        C* peer = cluster.map_shared_rank(buf, i);
+        peer[spad(b)] = x[i];
+      }
+    }
   }
+  cluster.sync();
+  fft_team<C, LOGN, CC, E, +1>(buf, tid, a.tw, ts);
   __syncthreads();
-  if (team < nteams) {
-    const TeamSync ts = make_team_sync(team, TEAM);
-    for (int m = team; m < M; m += nteams) fft_team<C, LOGN, CC, kE, +1>(data + m * ZS, tid % TEAM, a.tw, ts);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < M * N * CC; idx += nth) {
-    const int m = idx / (N * CC);
-    const int rem = idx - m * (N * CC);
-    const int n1 = rem / CC, c = rem - n1 * CC;
+  C* xh = a.xh + (size_t)m * mplane;
+  for (int idx = tid; idx < N * CC; idx += NT) {
+    const int n1 = idx / CC, c = idx - n1 * CC;
     const int k2 = c0 + c;
-    if (k2 < H) a.xh[m * mplane + (size_t)n1 * P + k2] = data[m * ZS + spad(rem)];
+    if (k2 < H) xh[(size_t)n1 * P + k2] = buf[spad(idx)];
   }
 }
 
 template <typename T, int LOGN, int CC, int MMAX>
 cudaError_t launchB(const PassBArgs<T>& a, cudaStream_t s) {
-  constexpr int N = 1 << LOGN;
-  constexpr int TEAM = N * CC / kE;
   using C = typename CT<T>::type;
-  // teams: as many channels in parallel as fit in 512 threads / 15 named barriers,
-  // balanced so every team runs the same number of channel FFTs
-  int maxteams = 512 / TEAM;
-  if (maxteams > 15) maxteams = 15;
-  if (maxteams < 1) maxteams = 1;
-  const int rounds = (a.M + maxteams - 1) / maxteams;
-  const int nteams = (a.M + rounds - 1) / rounds;
-  int nth = nteams * TEAM;
-  if (nth < 128) nth = 128;
-  nth = ((nth + 31) / 32) * 32;
-  const size_t sm = (size_t)a.M * spad(N * CC) * sizeof(C);
+  constexpr int N = 1 << LOGN;
+  constexpr int NT = N * CC / elems_for<T>();
+  const size_t sm = (size_t)spad(N * CC) * sizeof(C);
   auto kern = passB_kernel<T, LOGN, CC, MMAX>;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static bool attr_done = false;
+  if (!attr_done) {
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
+    attr_done = true;
   }
-  const int ntiles = (N / 2 + 1 + CC - 1) / CC;
-  kern<<<ntiles, nth, sm, s>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.M, (N / 2 + 1 + CC - 1) / CC, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.M;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 template <typename T, int LOGN, int CC>
 cudaError_t dispatchB_m(const PassBArgs<T>& a, cudaStream_t s) {
   if (a.M <= 4) return launchB<T, LOGN, CC, 4>(a, s);
+  if (sizeof(T) == 4) {
+    if (a.M <= 8) return launchB<T, LOGN, CC, 8>(a, s);
+    if (a.M <= 12) return launchB<T, LOGN, CC, 12>(a, s);
+  }
   if (a.M <= 16) return launchB<T, LOGN, CC, 16>(a, s);
   return cudaErrorInvalidValue;
 }
@@ -158,7 +188,8 @@ cudaError_t dispatchB_c(const PassBArgs<T>& a, int cc, cudaStream_t s) {
 
 template <typename T> int passB_cols(int N, int M) { return cols_for<T>(N, M); }
 template <typename T> size_t passB_smem(int N, int M, int cc) {
-  return (size_t)M * spad(N * cc) * sizeof(typename CT<T>::type);
+  (void)M;
+  return (size_t)spad(N * cc) * sizeof(typename CT<T>::type);
 }
 
 template <typename T> cudaError_t launch_passB(const PassBArgs<T>& a, int N, int cc, cudaStream_t s) {
