@@ -65,7 +65,9 @@ typedef enum cip_prior {
 typedef struct cip_options {
   int col_tile;     /* columns per CTA of the column pass (1, 2 or 4); 0 = automatic */
   int check_every;  /* residual check period for cip_iterate with tol > 0; 0 = 10 */
-  int reserved[14];
+  int column_pass;  /* 0 = autotuned at cip_set_measurements (fused vs split, tile width; cached per
+                       N, M, dtype), 1 = fused cluster kernel, 2 = split (column FFT / solve / FFT) */
+  int reserved[13];
 } cip_options;
 
 typedef struct cip_plan cip_plan;
@@ -144,7 +146,7 @@ cip_status cip_get_launches(cip_plan* plan, unsigned long long* launches);
 
 /* Launch configuration the plan uses (for reporting). */
 cip_status cip_get_config(cip_plan* plan, int* rows_per_tile, int* col_tile, int* prior_pass_blocks,
-                          int* column_pass_blocks);
+                          int* column_pass_blocks, int* column_pass);
 
 /* Shrinkage, dual update and residual norms of one ADMM iteration without any
  * device allocation.  The paper has no counterpart: this exists for callers

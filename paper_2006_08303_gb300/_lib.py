@@ -19,7 +19,7 @@ P_size = ctypes.POINTER(ctypes.c_size_t)
 
 
 class cip_options(ctypes.Structure):
-    _fields_ = [("col_tile", c_int), ("check_every", c_int), ("reserved", c_int * 14)]
+    _fields_ = [("col_tile", c_int), ("check_every", c_int), ("column_pass", c_int), ("reserved", c_int * 13)]
 
 
 # name -> (restype, argtypes)
@@ -45,7 +45,7 @@ SIGNATURES = {
     "cip_state_restore": (c_int, [c_void_p, c_void_p, c_void_p]),
     "cip_set_timing": (c_int, [c_void_p, c_int]),
     "cip_get_timing": (c_int, [c_void_p, P_double, P_int, P_double, P_int]),
-    "cip_get_config": (c_int, [c_void_p, P_int, P_int, P_int, P_int]),
+    "cip_get_config": (c_int, [c_void_p, P_int, P_int, P_int, P_int, P_int]),
     "cip_get_launches": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
     "cip_shrink_dual_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_double, c_double, c_void_p, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

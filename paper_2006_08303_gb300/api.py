@@ -75,13 +75,15 @@ def plan_bytes(N: int, K: int, M: int, dtype: str = "f32", prior: str = "tv") ->
 class Plan:
     """One reconstruction instance held on the device (cip_plan)."""
 
-    def __init__(self, N: int, K: int, M: int, dtype: str = "f32", col_tile: int = 0, check_every: int = 0):
+    def __init__(self, N: int, K: int, M: int, dtype: str = "f32", col_tile: int = 0, check_every: int = 0,
+                 column_pass: int = 0):
         self._L = _lib.load()
         self.N, self.K, self.M, self.dtype = N, K, M, dtype
         self.prior: Optional[str] = None
         opt = _lib.cip_options()
         opt.col_tile = col_tile
         opt.check_every = check_every
+        opt.column_pass = column_pass
         h = ctypes.c_void_p()
         st = self._L.cip_plan_create(ctypes.byref(h), N, K, M, DTYPES[dtype], ctypes.byref(opt))
         if st != 0:
@@ -201,10 +203,10 @@ class Plan:
         return int(v.value)
 
     def config(self):
-        v = [ctypes.c_int() for _ in range(4)]
+        v = [ctypes.c_int() for _ in range(5)]
         self._check(self._L.cip_get_config(self._h, *[ctypes.byref(x) for x in v]))
         return {"rows_per_tile": v[0].value, "col_tile": v[1].value, "prior_pass_blocks": v[2].value,
-                "column_pass_blocks": v[3].value}
+                "column_pass_blocks": v[3].value, "column_pass": {1: "fused", 2: "split"}.get(v[4].value, "?")}
 
 
 def shrink_dual_noalloc(prior: str, lam: float, rho: float, x, u_in, t_prev, u_out, resid_out, t_out=None,

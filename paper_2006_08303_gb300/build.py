@@ -26,6 +26,7 @@ UNITS = [
     ("fft_kernels.cu", [], "fft_kernels.o"),
     ("factor.cu", [], "factor.o"),
     ("noalloc.cu", [], "noalloc.o"),
+    ("colsplit.cu", [], "colsplit.o"),
 ]
 
 

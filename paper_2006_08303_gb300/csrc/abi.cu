@@ -4,6 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -50,6 +53,7 @@ struct cip_plan {
   int cur = 0;  // index of the u buffer holding the current u
   size_t esz = 4;
   int rowsA = 8, cc = 1, blocksA = 0, blocksB = 0;
+  int colmode = 1;  // column pass: 1 fused cluster kernel, 2 split (FFT / solve / FFT)
   // device buffers
   void* xh = nullptr;
   void* qh = nullptr;
@@ -57,6 +61,7 @@ struct cip_plan {
   void* tprev = nullptr;
   void* pinv = nullptr;
   void* bhat = nullptr;       // data term xb = Psi^{-1} beta Lambda^H F y / N^2
+  void* colbuf = nullptr;     // split column pass: column-contiguous spectra [N/2+1][M][N]
   double2* pinv64 = nullptr;  // FP64 copy of the packed factor
   double2* lam64 = nullptr;  // FP64 PSF spectra [K*M][N][P]
   void* tw = nullptr;        // plan-precision twiddles
@@ -226,6 +231,8 @@ template <typename T> cip_status do_set_psfs(cip_plan* p, const void* h, cudaStr
   return reset_state<T>(p, s);
 }
 
+template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s);
+
 template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream_t s) {
   using C = typename CT<T>::type;
   const size_t bytes = real_elems(p, p->K) * sizeof(T);
@@ -243,6 +250,10 @@ template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream
   cudaFreeAsync(yhat, s);
   CIP_CUDA(p, e);
   p->have_y = true;
+  if (p->opt.column_pass == 0 && p->opt.col_tile == 0) {
+    r = autotune<T>(p, s);
+    if (r != CIP_OK) return r;
+  }
   return reset_state<T>(p, s);
 }
 
@@ -263,6 +274,79 @@ template <typename T> PassAArgs<T> passA_args(cip_plan* p, int flags) {
   a.flags = flags;
   fill_dct<T>(a.dct);
   return a;
+}
+
+template <typename T> PassBArgs<T> passB_args(cip_plan* p);
+
+// the column pass in the plan's chosen form
+template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mode, int cc) {
+  using C = typename CT<T>::type;
+  PassBArgs<T> b = passB_args<T>(p);
+  if (mode == 2) {
+    if (!p->colbuf) return fail(p, CIP_ERR_STATE, "split column pass selected without its column buffer");
+    int n = 0;
+    CIP_CUDA(p, launch_passB_split<T>(b, static_cast<C*>(p->colbuf), p->N, s, &n));
+    p->launches += n;
+  } else {
+    CIP_LAUNCH(p, launch_passB<T>(b, p->N, cc, s));
+  }
+  return CIP_OK;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;  // (N, M, dtype) -> (mode, cc)
+
+// Autotuner: times the fused column pass at each tile width and the split
+// form on this plan's buffers (the column pass only rewrites x-hat from q-hat,
+// so repeating it leaves the state as it was) and keeps the fastest, cached
+// per (N, M, dtype) for the process.
+template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const auto key = std::make_tuple(p->N, p->M, (int)p->dtype);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      p->colmode = it->second.first;
+      p->cc = it->second.second;
+      // a cached choice of the split form still needs this plan's own column buffer
+      if (p->colmode == 2 && !p->colbuf) CIP_CUDA(p, cudaMalloc(&p->colbuf, half_elems(p, p->M) * sizeof(C)));
+      return CIP_OK;
+    }
+  }
+  if (!p->colbuf) CIP_CUDA(p, cudaMalloc(&p->colbuf, half_elems(p, p->M) * sizeof(C)));
+  std::vector<std::pair<int, int>> cands = {{1, 1}, {1, 2}, {1, 4}, {2, 0}};
+  cudaEvent_t e0, e1;
+  CIP_CUDA(p, cudaEventCreate(&e0));
+  CIP_CUDA(p, cudaEventCreate(&e1));
+  float best = 1e30f;
+  std::pair<int, int> pick = {p->colmode, p->cc};
+  for (auto& c : cands) {
+    if (c.first == 1 && passB_smem<T>(p->N, p->M, c.second) > 200 * 1024) continue;
+    if (c.first == 1 && p->N * c.second / (sizeof(T) == 4 ? 8 : 16) > 1024) continue;
+    cip_status st = CIP_OK;
+    for (int w = 0; w < 2 && st == CIP_OK; ++w) st = column_pass<T>(p, s, c.first, c.second);
+    if (st != CIP_OK) return st;
+    cudaEventRecord(e0, s);
+    for (int w = 0; w < 5 && st == CIP_OK; ++w) st = column_pass<T>(p, s, c.first, c.second);
+    if (st != CIP_OK) return st;
+    cudaEventRecord(e1, s);
+    CIP_CUDA(p, cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->colmode = pick.first;
+  if (pick.first == 1) p->cc = pick.second;
+  p->blocksB = p->M * ((p->N / 2 + 1 + p->cc - 1) / p->cc);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = {p->colmode, p->cc};
+  return CIP_OK;
 }
 
 template <typename T> PassBArgs<T> passB_args(cip_plan* p) {
@@ -299,10 +383,10 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
     const bool check = (tol > 0 && phase == 0 && it > 0) || last;
     if (check) flags |= PA_RESID;
     // x-update (pass B), then t/u update + next adjoint (pass A)
-    PassBArgs<T> b = passB_args<T>(p);
     const bool timeB = p->timing && p->nB < kMaxTimed;
     if (timeB) cudaEventRecord(p->evB[2 * p->nB], s);
-    CIP_LAUNCH(p, launch_passB<T>(b, p->N, p->cc, s));
+    cip_status cst = column_pass<T>(p, s, p->colmode, p->cc);
+    if (cst != CIP_OK) return cst;
     if (timeB) cudaEventRecord(p->evB[2 * p->nB++ + 1], s);
     PassAArgs<T> a = passA_args<T>(p, flags);
     const bool timeA = p->timing && p->nA < kMaxTimed;
@@ -457,6 +541,11 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
     return fail(nullptr, CIP_ERR_UNSUPPORTED, "column tile does not fit in shared memory for this N, M and dtype");
   }
   p->blocksB = (N / 2 + 1 + cc - 1) / cc;
+  p->colmode = p->opt.column_pass == 2 ? 2 : 1;
+  if (p->opt.column_pass < 0 || p->opt.column_pass > 2) {
+    delete p;
+    return fail(nullptr, CIP_ERR_INVALID_ARG, "column_pass must be 0, 1 or 2");
+  }
 #define ALLOC(ptr, bytes)                                                                       \
   do {                                                                                          \
     cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                                       \
@@ -475,6 +564,7 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
   ALLOC(p->resid, (kNPart + 2) * sizeof(double));
   ALLOC(p->conv, sizeof(int));
   ALLOC(p->pinv_list, (1 + kPinvListCap) * sizeof(int));
+  if (p->colmode == 2) ALLOC(p->colbuf, half_elems(p, M) * ce);
 #undef ALLOC
   if (cudaMallocHost((void**)&p->resid_host, (kNPart + 2) * sizeof(double)) != cudaSuccess) {
     cip_plan_destroy(p);
@@ -510,7 +600,7 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->lam64, p->tw, p->tw64,
+  void* bufs[] = {p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -717,9 +807,10 @@ cip_status cip_get_launches(cip_plan* p, unsigned long long* n) {
   return CIP_OK;
 }
 
-cip_status cip_get_config(cip_plan* p, int* rows, int* cc, int* blocksA, int* blocksB) {
+cip_status cip_get_config(cip_plan* p, int* rows, int* cc, int* blocksA, int* blocksB, int* column_pass) {
   if (!p) return CIP_ERR_INVALID_ARG;
   if (rows) *rows = p->rowsA;
+  if (column_pass) *column_pass = p->colmode;
   if (cc) *cc = p->cc;
   if (blocksA) *blocksA = p->blocksA;
   if (blocksB) *blocksB = p->blocksB;

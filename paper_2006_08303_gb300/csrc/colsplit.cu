@@ -1,0 +1,168 @@
+// Split form of the column pass (the x-update of Eq. solx_Trans_DFT, three
+// kernels instead of one): a forward column DFT that writes the spectra
+// column-contiguous ([k2][m][k1]), an element-wise per-frequency solve
+// X = xb + Psi^{-1}/N^2 Q over that layout, and an inverse column DFT back to
+// row-domain half spectra.  It moves 16 more bytes per voxel than the fused
+// cluster kernel but every launch is fully parallel and every access is
+// coalesced; the plan's autotuner chooses between the two per shape.
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace cip {
+
+namespace {
+
+template <typename T> constexpr int cs_cc() { return sizeof(T) == 4 ? 4 : 2; }  // 32-byte row segments
+template <typename T> constexpr int cs_e(int N) { return (sizeof(T) == 4 && N <= 1024) ? 8 : 16; }
+
+// SIGN < 0: rows [M][N][P] -> FFT over k1 -> colbuf [H][M][N]
+// SIGN > 0: colbuf [H][M][N] -> inverse FFT -> rows [M][N][P]
+template <typename T, int LOGN, int SIGN>
+__global__ void __launch_bounds__((1 << LOGN) * cs_cc<T>() / cs_e<T>(1 << LOGN))
+    colfft_split_kernel(const typename CT<T>::type* __restrict__ src, typename CT<T>::type* __restrict__ dst,
+                        const typename CT<T>::type* __restrict__ tw, int M) {
+  using C = typename CT<T>::type;
+  constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N);
+  constexpr int CC = cs_cc<T>(), E = cs_e<T>(N), NT = N * CC / E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * CC;
+  const int m = blockIdx.y;
+  if (SIGN < 0) {
+    const C* rows = src + (size_t)m * N * P;
+    for (int idx = tid; idx < N * CC; idx += NT) {
+      const int n1 = idx / CC, c = idx - n1 * CC;
+      buf[spad(idx)] = (c0 + c < H) ? rows[(size_t)n1 * P + c0 + c] : mk<C>(0.0, 0.0);
+    }
+  } else {
+    for (int idx = tid; idx < N * CC; idx += NT) {
+      const int c = idx / N, k1 = idx - c * N;
+      buf[spad(k1 * CC + c)] = (c0 + c < H) ? src[((size_t)(c0 + c) * M + m) * N + k1] : mk<C>(0.0, 0.0);
+    }
+  }
+  TeamSync ts;
+  ts.bar_id = 0;
+  ts.nthreads = NT;
+  ts.mask = 0xffffffffu;
+  __syncthreads();
+  fft_team<C, LOGN, CC, E, SIGN>(buf, tid, tw, ts);
+  __syncthreads();
+  if (SIGN < 0) {
+    for (int idx = tid; idx < N * CC; idx += NT) {
+      const int c = idx / N, k1 = idx - c * N;
+      if (c0 + c < H) dst[((size_t)(c0 + c) * M + m) * N + k1] = buf[spad(k1 * CC + c)];
+    }
+  } else {
+    C* rows = dst + (size_t)m * N * P;
+    for (int idx = tid; idx < N * CC; idx += NT) {
+      const int n1 = idx / CC, c = idx - n1 * CC;
+      if (c0 + c < H) rows[(size_t)n1 * P + c0 + c] = buf[spad(idx)];
+    }
+  }
+}
+
+// X = xb + Pinv Q at every bin, in place on colbuf; thread = (k2, k1), k1 fastest.
+template <typename T, int MMAX>
+__global__ void __launch_bounds__(256, 3) solve_split_kernel(typename CT<T>::type* __restrict__ colbuf,
+                                                               const typename CT<T>::type* __restrict__ pinv,
+                                                               const typename CT<T>::type* __restrict__ xb, int N,
+                                                               int M) {
+  using C = typename CT<T>::type;
+  const int k1 = blockIdx.x * 256 + threadIdx.x;
+  const int k2 = blockIdx.y;
+  if (k1 >= N) return;
+  const int npk = M * (M + 1) / 2;
+  C* col = colbuf + (size_t)k2 * M * N + k1;
+  const C* xcol = xb + (size_t)k2 * M * N + k1;
+  const C* pcol = pinv + (size_t)k2 * npk * N + k1;
+  C r[MMAX], x[MMAX];
+#pragma unroll
+  for (int i = 0; i < MMAX; ++i) {
+    if (i < M) {
+      r[i] = col[(size_t)i * N];
+      x[i] = xcol[(size_t)i * N];
+    }
+  }
+  int pk = 0;
+#pragma unroll
+  for (int i = 0; i < MMAX; ++i) {
+    if (i < M) {
+#pragma unroll
+      for (int j = i; j < MMAX; ++j) {
+        if (j < M) {
+          const C pij = pcol[(size_t)pk * N];
+          ++pk;
+          cfma(x[i], pij, r[j]);
+          if (j != i) cfmac(x[j], pij, r[i]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < MMAX; ++i)
+    if (i < M) col[(size_t)i * N] = x[i];
+}
+
+template <typename T, int LOGN, int SIGN>
+cudaError_t launch_colfft(const typename CT<T>::type* src, typename CT<T>::type* dst,
+                          const typename CT<T>::type* tw, int M, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  constexpr int N = 1 << LOGN, CC = cs_cc<T>(), NT = N * CC / cs_e<T>(N);
+  const size_t sm = (size_t)spad(N * CC) * sizeof(C);
+  auto k = colfft_split_kernel<T, LOGN, SIGN>;
+  static bool done = false;
+  if (!done && sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  done = true;
+  dim3 grid((N / 2 + 1 + CC - 1) / CC, M);
+  k<<<grid, NT, sm, s>>>(src, dst, tw, M);
+  return cudaGetLastError();
+}
+
+template <typename T, int SIGN>
+cudaError_t colfft_n(const typename CT<T>::type* src, typename CT<T>::type* dst, const typename CT<T>::type* tw,
+                     int N, int M, cudaStream_t s) {
+  switch (N) {
+    case 64: return launch_colfft<T, 6, SIGN>(src, dst, tw, M, s);
+    case 128: return launch_colfft<T, 7, SIGN>(src, dst, tw, M, s);
+    case 256: return launch_colfft<T, 8, SIGN>(src, dst, tw, M, s);
+    case 512: return launch_colfft<T, 9, SIGN>(src, dst, tw, M, s);
+    case 1024: return launch_colfft<T, 10, SIGN>(src, dst, tw, M, s);
+    case 2048: return launch_colfft<T, 11, SIGN>(src, dst, tw, M, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t solve_m(typename CT<T>::type* colbuf, const typename CT<T>::type* pinv, const typename CT<T>::type* xb,
+                    int N, int M, cudaStream_t s) {
+  dim3 grid((N + 255) / 256, N / 2 + 1);
+  if (M <= 4) solve_split_kernel<T, 4><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M);
+  else if (M <= 8) solve_split_kernel<T, 8><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M);
+  else if (M <= 12) solve_split_kernel<T, 12><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M);
+  else if (M <= 16) solve_split_kernel<T, 16><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colbuf, int N, cudaStream_t s,
+                               int* launches) {
+  cudaError_t e = colfft_n<T, -1>(a.qh, colbuf, a.tw, N, a.M, s);
+  if (e != cudaSuccess) return e;
+  e = solve_m<T>(colbuf, a.pinv, a.bhat, N, a.M, s);
+  if (e != cudaSuccess) return e;
+  e = colfft_n<T, +1>(colbuf, a.xh, a.tw, N, a.M, s);
+  if (launches) *launches += 3;
+  return e;
+}
+
+template cudaError_t launch_passB_split<float>(const PassBArgs<float>&, float2*, int, cudaStream_t, int*);
+template cudaError_t launch_passB_split<double>(const PassBArgs<double>&, double2*, int, cudaStream_t, int*);
+
+}  // namespace cip

@@ -61,6 +61,17 @@ __host__ __device__ __forceinline__ constexpr int spad(int i) { return i + (i >>
 // that every row starts on a 32-byte boundary.
 __host__ __device__ __forceinline__ constexpr int half_pitch(int N) { return N / 2 + 4; }
 
+// Bulk prefetch of [p, p + bytes) into L2 (TMA unit, no shared memory, no
+// completion to wait for).  The range is widened to 16-byte boundaries; the
+// caller guarantees that the widened range lies inside one allocation.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(15);
+  const uintptr_t a1 = (reinterpret_cast<uintptr_t>(p) + bytes + 15) & ~uintptr_t(15);
+  if (a1 > a0) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((unsigned)(a1 - a0)) : "memory");
+  }
+}
+
 // soft(w, tau) = sign(w) max(|w| - tau, 0) with sign(0) = -1 (Eq. solt_trans);
 // the result is identical to the sign convention's for w = 0 (both give 0).
 template <typename T> __device__ __forceinline__ T soft(T w, T tau) {

@@ -53,6 +53,10 @@ template <typename T> cudaError_t launch_passA(const PassAArgs<T>& a, int N, int
 template <typename T> int passB_cols(int N, int M);
 template <typename T> size_t passB_smem(int N, int M, int cc);
 template <typename T> cudaError_t launch_passB(const PassBArgs<T>& a, int N, int cc, cudaStream_t s);
+// split form: column FFT to [N/2+1][M][N] in colbuf, per-bin solve in place, inverse column FFT
+template <typename T>
+cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colbuf, int N, cudaStream_t s,
+                               int* launches);
 
 // Setup / read-back FFTs (not fused).
 // rows: nrows real rows of length N -> half spectra with pitch P (unnormalised forward DFT)

@@ -162,6 +162,16 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
 
   auto grow = [&](int j) { return (r0 - HALO + j) & (N - 1); };
 
+  // L2 prefetch of the u rows (and t_prev rows) read after the inverse FFT
+  if (tid < 2 * NCOMP) {
+    const T* src = (tid & 1) ? tprev_rd : u_in;
+    if (src) {
+      const size_t comp = (size_t)(tid >> 1) * plane;
+      prefetch_l2(src + comp + (size_t)r0 * N, (size_t)R * N * sizeof(T));
+      if (HALO) prefetch_l2(src + comp + (size_t)grow(0) * N, (size_t)N * sizeof(T));
+    }
+  }
+
   if (!import_mode) {
     // 1. load row half-spectra (two rows per complex FFT) and invert the row DFT
     const C* xh = a.xh + (size_t)m * N * P;

@@ -63,6 +63,26 @@ __global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
   const size_t mplane = (size_t)N * P;
   const C* qh = a.qh + (size_t)m * mplane;
 
+  // this CTA's share of the tile's bins, and an L2 prefetch of the factor and
+  // data-term columns it will read in the solve (overlaps the forward FFT)
+  const int nbins = N * CC;
+  const int per = (nbins + M - 1) / M;
+  const int b0 = m * per;
+  const int b1 = min(nbins, b0 + per);
+  const int npk = M * (M + 1) / 2;
+  if (b1 > b0) {
+    const int k1lo = b0 / CC, k1hi = (b1 - 1) / CC + 1;
+    const size_t len = (size_t)(k1hi - k1lo) * sizeof(C);
+    for (int s = tid; s < CC * (npk + M); s += NT) {
+      const int c = s % CC, j = s / CC;
+      const int k2 = c0 + c;
+      if (k2 >= H) continue;
+      const C* base = (j < npk) ? a.pinv + ((size_t)k2 * npk + j) * N + k1lo
+                                : a.bhat + ((size_t)k2 * M + (j - npk)) * N + k1lo;
+      prefetch_l2(base, len);
+    }
+  }
+
   for (int idx = tid; idx < N * CC; idx += NT) {
     const int n1 = idx / CC, c = idx - n1 * CC;
     const int k2 = c0 + c;
@@ -77,11 +97,6 @@ __global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
   cluster.sync();
 
   // per-frequency solve over this CTA's share of the tile's bins
-  const int nbins = N * CC;
-  const int per = (nbins + M - 1) / M;
-  const int b0 = m * per;
-  const int b1 = min(nbins, b0 + per);
-  const int npk = M * (M + 1) / 2;
   for (int b = b0 + tid; b < b1; b += NT) {
     const int k1 = b / CC, c = b - k1 * CC;
     const int k2 = c0 + c;

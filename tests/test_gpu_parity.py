@@ -111,6 +111,24 @@ def test_step_parity_on_oracle_states(torch, prior, N, K, M, dtype, lam, rho, ki
     P.close()
 
 
+@pytest.mark.parametrize("column_pass", [1, 2])
+@pytest.mark.parametrize("prior,N,K,M,kind", [("tv", 128, 3, 3, "gauss"), ("dct8", 256, 10, 10, "disk"),
+                                               ("tv", 64, 2, 16, "gauss")])
+def test_column_pass_forms(torch, column_pass, prior, N, K, M, kind):
+    """The fused (cluster) and split column passes both give Alg. 1's iterates: one step from oracle
+    states within 1e-5 (f32), for M up to the 16-channel limit."""
+    rng, h, y = problem(300 + N + M, N, K, M, kind)
+    lam, rho = (1e-2, 1.0) if prior == "tv" else (1e-3, 1e-2)
+    P = make_plan(torch, h, y, prior, lam, rho, 1.0, "f32", column_pass=column_pass)
+    assert P.config()["column_pass"] == {1: "fused", 2: "split"}[column_pass]
+    for l, t, u, x1, u1 in oracle_states(h, y, prior, lam, rho, (0, 5), naive=(N <= 64)):
+        P.state_import(tdev(torch, t, "f32"), tdev(torch, u, "f32"))
+        P.iterate(1)
+        assert rel(P.get_x().double().cpu().numpy(), x1) <= 1e-5
+        assert u_err(P.get_u().double().cpu().numpy(), u1, x1, prior) <= 1e-5
+    P.close()
+
+
 @pytest.mark.parametrize("prior,N,rho", [("tv", 64, 1.0), ("dct8", 64, 0.3), ("l1", 128, 0.5)])
 def test_step_random_state(torch, prior, N, rho):
     """Property at white-noise (t, u): the complex64 step stays within 1e-4 of the FP64 oracle."""
