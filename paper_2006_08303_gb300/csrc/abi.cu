@@ -111,6 +111,10 @@ bool valid_n(int N) { return N >= 64 && N <= 2048 && (N & (N - 1)) == 0; }
 
 // sizes in elements
 size_t half_elems(const cip_plan* p, int maps) { return (size_t)maps * p->N * p->P; }
+// column-contiguous per-bin planes [N/2+1][planes][col_pitch(N)] (+ slack for 16-byte prefetch widening)
+size_t col_elems(const cip_plan* p, int planes) {
+  return (size_t)(p->N / 2 + 1) * planes * col_pitch(p->N) + 16;
+}
 size_t real_elems(const cip_plan* p, int maps) { return (size_t)maps * p->N * p->N; }
 
 template <typename T> void fill_dct(T* d) {
@@ -151,7 +155,7 @@ template <typename T> cip_status alloc_state(cip_plan* p) {
   CIP_CUDA(p, cudaMalloc(&p->tprev, real_elems(p, p->M) * nc * sizeof(T)));
   if (p->pinv) cudaFree(p->pinv);
   p->pinv = nullptr;
-  CIP_CUDA(p, cudaMalloc(&p->pinv, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(C)));
+  CIP_CUDA(p, cudaMalloc(&p->pinv, col_elems(p, p->M * (p->M + 1) / 2) * sizeof(C)));
   if (p->pinv64) cudaFree(p->pinv64);
   p->pinv64 = nullptr;
   CIP_CUDA(p, cudaMalloc((void**)&p->pinv64, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(double2)));
@@ -310,11 +314,11 @@ template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
       p->colmode = it->second.first;
       p->cc = it->second.second;
       // a cached choice of the split form still needs this plan's own column buffer
-      if (p->colmode == 2 && !p->colbuf) CIP_CUDA(p, cudaMalloc(&p->colbuf, half_elems(p, p->M) * sizeof(C)));
+      if (p->colmode == 2 && !p->colbuf) CIP_CUDA(p, cudaMalloc(&p->colbuf, col_elems(p, p->M) * sizeof(C)));
       return CIP_OK;
     }
   }
-  if (!p->colbuf) CIP_CUDA(p, cudaMalloc(&p->colbuf, half_elems(p, p->M) * sizeof(C)));
+  if (!p->colbuf) CIP_CUDA(p, cudaMalloc(&p->colbuf, col_elems(p, p->M) * sizeof(C)));
   std::vector<std::pair<int, int>> cands = {{1, 1}, {1, 2}, {1, 4}, {2, 0}};
   cudaEvent_t e0, e1;
   CIP_CUDA(p, cudaEventCreate(&e0));
@@ -556,7 +560,7 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
   } while (0)
   ALLOC(p->xh, half_elems(p, M) * ce);
   ALLOC(p->qh, half_elems(p, M) * ce);
-  ALLOC(p->bhat, half_elems(p, M) * ce);
+  ALLOC(p->bhat, col_elems(p, M) * ce);
   ALLOC(p->lam64, half_elems(p, K * M) * sizeof(double2));
   ALLOC(p->tw, (size_t)kTwN * ce);
   ALLOC(p->tw64, (size_t)kTwN * sizeof(double2));
@@ -564,7 +568,7 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
   ALLOC(p->resid, (kNPart + 2) * sizeof(double));
   ALLOC(p->conv, sizeof(int));
   ALLOC(p->pinv_list, (1 + kPinvListCap) * sizeof(int));
-  if (p->colmode == 2) ALLOC(p->colbuf, half_elems(p, M) * ce);
+  if (p->colmode == 2) ALLOC(p->colbuf, col_elems(p, M) * ce);
 #undef ALLOC
   if (cudaMallocHost((void**)&p->resid_host, (kNPart + 2) * sizeof(double)) != cudaSuccess) {
     cip_plan_destroy(p);

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__((1 << LOGN) * cs_cc<T>() / cs_e<T>(1 << LOGN))
   using C = typename CT<T>::type;
   constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N);
   constexpr int CC = cs_cc<T>(), E = cs_e<T>(N), NT = N * CC / E;
+  constexpr int CP = col_pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int tid = threadIdx.x;
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__((1 << LOGN) * cs_cc<T>() / cs_e<T>(1 << LOGN))
   } else {
     for (int idx = tid; idx < N * CC; idx += NT) {
       const int c = idx / N, k1 = idx - c * N;
-      buf[spad(k1 * CC + c)] = (c0 + c < H) ? src[((size_t)(c0 + c) * M + m) * N + k1] : mk<C>(0.0, 0.0);
+      buf[spad(k1 * CC + c)] = (c0 + c < H) ? src[((size_t)(c0 + c) * M + m) * CP + k1] : mk<C>(0.0, 0.0);
     }
   }
   TeamSync ts;
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__((1 << LOGN) * cs_cc<T>() / cs_e<T>(1 << LOGN))
   if (SIGN < 0) {
     for (int idx = tid; idx < N * CC; idx += NT) {
       const int c = idx / N, k1 = idx - c * N;
-      if (c0 + c < H) dst[((size_t)(c0 + c) * M + m) * N + k1] = buf[spad(k1 * CC + c)];
+      if (c0 + c < H) dst[((size_t)(c0 + c) * M + m) * CP + k1] = buf[spad(k1 * CC + c)];
     }
   } else {
     C* rows = dst + (size_t)m * N * P;
@@ -73,15 +74,16 @@ __global__ void __launch_bounds__(256, 3) solve_split_kernel(typename CT<T>::typ
   const int k2 = blockIdx.y;
   if (k1 >= N) return;
   const int npk = M * (M + 1) / 2;
-  C* col = colbuf + (size_t)k2 * M * N + k1;
-  const C* xcol = xb + (size_t)k2 * M * N + k1;
-  const C* pcol = pinv + (size_t)k2 * npk * N + k1;
+  const int CP = col_pitch(N);
+  C* col = colbuf + (size_t)k2 * M * CP + k1;
+  const C* xcol = xb + (size_t)k2 * M * CP + k1;
+  const C* pcol = pinv + (size_t)k2 * npk * CP + k1;
   C r[MMAX], x[MMAX];
 #pragma unroll
   for (int i = 0; i < MMAX; ++i) {
     if (i < M) {
-      r[i] = col[(size_t)i * N];
-      x[i] = xcol[(size_t)i * N];
+      r[i] = col[(size_t)i * CP];
+      x[i] = xcol[(size_t)i * CP];
     }
   }
   int pk = 0;
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(256, 3) solve_split_kernel(typename CT<T>::typ
 #pragma unroll
       for (int j = i; j < MMAX; ++j) {
         if (j < M) {
-          const C pij = pcol[(size_t)pk * N];
+          const C pij = pcol[(size_t)pk * CP];
           ++pk;
           cfma(x[i], pij, r[j]);
           if (j != i) cfmac(x[j], pij, r[i]);
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(256, 3) solve_split_kernel(typename CT<T>::typ
   }
 #pragma unroll
   for (int i = 0; i < MMAX; ++i)
-    if (i < M) col[(size_t)i * N] = x[i];
+    if (i < M) col[(size_t)i * CP] = x[i];
 }
 
 template <typename T, int LOGN, int SIGN>

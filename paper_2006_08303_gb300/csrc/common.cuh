@@ -61,6 +61,11 @@ __host__ __device__ __forceinline__ constexpr int spad(int i) { return i + (i >>
 // that every row starts on a 32-byte boundary.
 __host__ __device__ __forceinline__ constexpr int half_pitch(int N) { return N / 2 + 4; }
 
+// Column-contiguous per-bin planes ([k2][plane][k1], used by the factor, the
+// data term and the split column buffer): N bins plus 32 elements of padding
+// so that consecutive planes are not a power-of-two stride apart.
+__host__ __device__ __forceinline__ constexpr int col_pitch(int N) { return N + 32; }
+
 // Bulk prefetch of [p, p + bytes) into L2 (TMA unit, no shared memory, no
 // completion to wait for).  The range is widened to 16-byte boundaries; the
 // caller guarantees that the widened range lies inside one allocation.

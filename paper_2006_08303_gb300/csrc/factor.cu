@@ -101,14 +101,14 @@ __global__ void __launch_bounds__(128) factor_kernel(const double2* __restrict__
   // Psi^{-1} = W^H W, packed upper, scaled by 1/N^2; the plan-precision copy is
   // stored [k2][pk][k1] (contiguous bins along a column), the FP64 copy [pk][k1][P]
   const double sc = 1.0 / ((double)N * (double)N);
-  const size_t colbase = (size_t)k2 * (M * (M + 1) / 2) * N + k1;
+  const size_t colbase = (size_t)k2 * (M * (M + 1) / 2) * col_pitch(N) + k1;
   int pk = 0;
   for (int i = 0; i < M; ++i) {
     for (int j = i; j < M; ++j) {
       double2 s = make_double2(0.0, 0.0);
       for (int k = j; k < M; ++k) cfmac(s, W[k][i], W[k][j]);
       if (i == j) s.y = 0.0;
-      pinv[colbase + (size_t)pk * N] = mk<C>(s.x * sc, s.y * sc);
+      pinv[colbase + (size_t)pk * col_pitch(N)] = mk<C>(s.x * sc, s.y * sc);
       if (pinv64) pinv64[(size_t)pk * mplane + off] = make_double2(s.x * sc, s.y * sc);
       ++pk;
     }
@@ -190,7 +190,7 @@ __global__ void factor_pinv_kernel(const double2* __restrict__ lam, const double
         }
       }
       if (i == j) im = 0.0;
-      pinv[((size_t)k2 * (M * (M + 1) / 2) + pk) * N + k1] = mk<C>(re * sc, im * sc);
+      pinv[((size_t)k2 * (M * (M + 1) / 2) + pk) * col_pitch(N) + k1] = mk<C>(re * sc, im * sc);
       if (pinv64) pinv64[(size_t)pk * mplane + off] = make_double2(re * sc, im * sc);
       ++pk;
     }
@@ -229,7 +229,7 @@ __global__ void rhs_kernel(const double2* __restrict__ lam, const double2* __res
     }
   }
   // stored [k2][m][k1]: the bins of one column are contiguous for the column pass
-  for (int m = 0; m < M; ++m) xb[((size_t)k2 * M + m) * N + k1] = mk<C>(x[m].x, x[m].y);
+  for (int m = 0; m < M; ++m) xb[((size_t)k2 * M + m) * col_pitch(N) + k1] = mk<C>(x[m].x, x[m].y);
 }
 
 template <typename Tout>

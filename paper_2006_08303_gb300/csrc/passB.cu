@@ -53,6 +53,7 @@ __global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
   constexpr int P = half_pitch(N);
   constexpr int E = elems_for<T>();
   constexpr int NT = N * CC / E;  // threads = one team
+  constexpr int CP = col_pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   cg::cluster_group cluster = cg::this_cluster();
@@ -77,8 +78,8 @@ __global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
       const int c = s % CC, j = s / CC;
       const int k2 = c0 + c;
       if (k2 >= H) continue;
-      const C* base = (j < npk) ? a.pinv + ((size_t)k2 * npk + j) * N + k1lo
-                                : a.bhat + ((size_t)k2 * M + (j - npk)) * N + k1lo;
+      const C* base = (j < npk) ? a.pinv + ((size_t)k2 * npk + j) * CP + k1lo
+                                : a.bhat + ((size_t)k2 * M + (j - npk)) * CP + k1lo;
       prefetch_l2(base, len);
     }
   }
@@ -101,15 +102,15 @@ __global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
     const int k1 = b / CC, c = b - k1 * CC;
     const int k2 = c0 + c;
     if (k2 >= H) continue;
-    const C* pcol = a.pinv + ((size_t)k2 * npk) * N + k1;  // plane stride N
-    const C* xcol = a.bhat + ((size_t)k2 * M) * N + k1;
+    const C* pcol = a.pinv + ((size_t)k2 * npk) * CP + k1;  // plane stride CP
+    const C* xcol = a.bhat + ((size_t)k2 * M) * CP + k1;
     C r[MMAX], x[MMAX];
 #pragma unroll
     for (int i = 0; i < MMAX; ++i) {
       if (i < M) {
         const C* peer = cluster.map_shared_rank(buf, i);
         r[i] = peer[spad(b)];
-        x[i] = xcol[(size_t)i * N];
+        x[i] = xcol[(size_t)i * CP];
       }
     }
     int pk = 0;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
 #pragma unroll
         for (int j = i; j < MMAX; ++j) {
           if (j < M) {
-            const C pij = pcol[(size_t)pk * N];
+            const C pij = pcol[(size_t)pk * CP];
             ++pk;
             cfma(x[i], pij, r[j]);
             if (j != i) cfmac(x[j], pij, r[i]);
