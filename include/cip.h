@@ -59,7 +59,9 @@ typedef enum cip_dtype { CIP_F32 = 0, CIP_F64 = 1 } cip_dtype;
 typedef enum cip_prior {
   CIP_PRIOR_TV = 0,   /* anisotropic TV: T = [D_h; D_v], circular forward differences (2 components) */
   CIP_PRIOR_DCT8 = 1, /* orthonormal DCT-II on 8x8 blocks aligned at (0,0) (1 component) */
-  CIP_PRIOR_L1 = 2    /* T = I (1 component) */
+  CIP_PRIOR_L1 = 2,   /* T = I (1 component) */
+  CIP_PRIOR_CONVDICT = 3 /* synthesis prior with a 2D convolutional dictionary shared by all channels
+                            (Alg. 2): x ~ sum_l d_l (*) z_{l,m}, l1 on the coefficient maps z */
 } cip_prior;
 
 typedef struct cip_options {
@@ -101,6 +103,23 @@ cip_status cip_set_psfs(cip_plan* plan, const void* h, void* stream);
  * Psi^{-1} beta Lambda^H F y (Alg. 1 line 2), formed in FP64 and rounded
  * once to the plan's precision.  Resets the ADMM state (t = u = 0). */
 cip_status cip_set_measurements(cip_plan* plan, const void* y, void* stream);
+
+/* Convolutional dictionary (prior CIP_PRIOR_CONVDICT; Section III-B "Convolutional
+ * Dictionary", Alg. 2): filters d[L][P][P] (plan dtype, centre at index P/2, 1 <= L <= 32),
+ * embedded on the N x N torus with their centre at (0,0).  Call after
+ * cip_set_prior(CIP_PRIOR_CONVDICT, lambda, rho, beta) and before cip_set_psfs.  Alg. 2 then
+ * runs with x-update factor (I + beta Lambda^H Lambda)^{-1} (Eq. solx_synt_DFT, t = 1), the
+ * per-frequency Sherman-Morrison z-update (Eq. solz_DFT_SM), t = soft(z + u, lambda/rho)
+ * (Eq. softADMM) and u += z - t (Eq. subu_dic), from z = t = u = 0.  The ADMM variables
+ * t, u and the coefficient maps z have shape [M][L][N][N] (channel-major). */
+cip_status cip_set_dictionary(cip_plan* plan, const void* filters, int L, int P, void* stream);
+
+/* Coefficient maps z[M][L][N][N] of the last z-update (CIP_PRIOR_CONVDICT only). */
+cip_status cip_get_coefficients(cip_plan* plan, void* z, void* stream);
+
+/* Set the dictionary ADMM state from z, t, u [M][L][N][N] (as after Alg. 2 line 7). */
+cip_status cip_state_import_coefficients(cip_plan* plan, const void* z, const void* t, const void* u,
+                                         void* stream);
 
 /* t = u = 0 (Alg. 1 line 1 with zero initial values). */
 cip_status cip_reset_state(cip_plan* plan, void* stream);

@@ -47,6 +47,9 @@ SIGNATURES = {
     "cip_get_timing": (c_int, [c_void_p, P_double, P_int, P_double, P_int]),
     "cip_get_config": (c_int, [c_void_p, P_int, P_int, P_int, P_int, P_int]),
     "cip_get_launches": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "cip_set_dictionary": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "cip_get_coefficients": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "cip_state_import_coefficients": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "cip_shrink_dual_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_double, c_double, c_void_p, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
 }

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib
 
-PRIORS = {"tv": 0, "dct8": 1, "l1": 2}
+PRIORS = {"tv": 0, "dct8": 1, "l1": 2, "convdict": 3}
 DTYPES = {"f32": 0, "f64": 1}
 NP_DTYPE = {"f32": np.float32, "f64": np.float64}
 
@@ -99,6 +99,37 @@ class Plan:
     def ncomp(self) -> int:
         return 2 if self.prior == "tv" else 1
 
+    @property
+    def state_shape(self):
+        """Shape of t and u: [M][ncomp][N][N], or [M][L][N][N] for the convolutional dictionary."""
+        if self.prior == "convdict":
+            return (self.M, self.L, self.N, self.N)
+        return (self.M, self.ncomp, self.N, self.N)
+
+    def set_dictionary(self, filters, stream=None):
+        """Filters [L][P][P] of the convolutional dictionary (after set_prior('convdict', ...))."""
+        L, P = int(filters.shape[0]), int(filters.shape[-1])
+        p, keep = _ptr_and_check(filters, self.dtype, (L, P, P))
+        self._check(self._L.cip_set_dictionary(self._h, ctypes.c_void_p(p), L, P, _stream_ptr(stream)))
+        self.L = L
+
+    def get_coefficients(self, out=None, stream=None):
+        shape = (self.M, self.L, self.N, self.N)
+        if out is None:
+            torch = _torch()
+            out = torch.empty(shape, device="cuda", dtype=torch.float32 if self.dtype == "f32" else torch.float64)
+        p, keep = _ptr_and_check(out, self.dtype, shape)
+        self._check(self._L.cip_get_coefficients(self._h, ctypes.c_void_p(p), _stream_ptr(stream)))
+        return out
+
+    def state_import_coefficients(self, z, t, u, stream=None):
+        shape = (self.M, self.L, self.N, self.N)
+        pz, k0 = _ptr_and_check(z, self.dtype, shape)
+        pt, k1 = _ptr_and_check(t, self.dtype, shape)
+        pu, k2 = _ptr_and_check(u, self.dtype, shape)
+        self._check(self._L.cip_state_import_coefficients(self._h, ctypes.c_void_p(pz), ctypes.c_void_p(pt),
+                                                          ctypes.c_void_p(pu), _stream_ptr(stream)))
+
     def close(self):
         if getattr(self, "_h", None):
             self._L.cip_plan_destroy(self._h)
@@ -147,7 +178,7 @@ class Plan:
         return out
 
     def get_u(self, out=None, stream=None):
-        shape = (self.M, self.ncomp, self.N, self.N)
+        shape = self.state_shape
         if out is None:
             torch = _torch()
             out = torch.empty(shape, device="cuda", dtype=torch.float32 if self.dtype == "f32" else torch.float64)
@@ -166,7 +197,7 @@ class Plan:
         return v.value
 
     def state_import(self, t, u, stream=None):
-        shape = (self.M, self.ncomp, self.N, self.N)
+        shape = self.state_shape
         pt, k1 = _ptr_and_check(t, self.dtype, shape)
         pu, k2 = _ptr_and_check(u, self.dtype, shape)
         self._check(self._L.cip_state_import(self._h, ctypes.c_void_p(pt), ctypes.c_void_p(pu), _stream_ptr(stream)))

@@ -27,6 +27,7 @@ UNITS = [
     ("factor.cu", [], "factor.o"),
     ("noalloc.cu", [], "noalloc.o"),
     ("colsplit.cu", [], "colsplit.o"),
+    ("convdict.cu", [], "convdict.o"),
 ]
 
 

@@ -54,6 +54,12 @@ struct cip_plan {
   size_t esz = 4;
   int rowsA = 8, cc = 1, blocksA = 0, blocksB = 0;
   int colmode = 1;  // column pass: 1 fused cluster kernel, 2 split (FFT / solve / FFT)
+  // convolutional dictionary (prior CIP_PRIOR_CONVDICT): L filters of P x P
+  int L = 0, Pf = 0;
+  void* theta = nullptr;                // [H][L][CP] DFT of the embedded filters
+  void* pbuf[2] = {nullptr, nullptr};   // [H][M][CP] p = sum_l theta_l v_l (ping-pong)
+  int pcur = 0;
+  void* xcol = nullptr;                 // [H][M][CP] x-hat of the last x-update
   // device buffers
   void* xh = nullptr;
   void* qh = nullptr;
@@ -107,6 +113,12 @@ cip_status fail(cip_plan* p, cip_status s, const std::string& msg) {
 
 size_t ncomp_of(int prior) { return prior == CIP_PRIOR_TV ? 2 : 1; }
 
+bool is_cd(const cip_plan* p) { return p->prior == CIP_PRIOR_CONVDICT; }
+// kind of prior pass: the dictionary's shrinkage acts on the coefficient maps with T = I
+int prior_pass_kind(const cip_plan* p) { return is_cd(p) ? (int)PRIOR_L1 : p->prior; }
+// maps the prior pass works on: image channels, or the L*M coefficient maps of the dictionary
+int smaps(const cip_plan* p) { return is_cd(p) ? p->M * p->L : p->M; }
+
 bool valid_n(int N) { return N >= 64 && N <= 2048 && (N & (N - 1)) == 0; }
 
 // sizes in elements
@@ -142,17 +154,38 @@ void twiddles(std::vector<double>& re, std::vector<double>& im) {
   }
 }
 
+void free_ptr(void*& q) {
+  if (q) cudaFree(q);
+  q = nullptr;
+}
+
 template <typename T> cip_status alloc_state(cip_plan* p) {
   using C = typename CT<T>::type;
   const size_t nc = ncomp_of(p->prior);
+  const int S = smaps(p);
   for (int i = 0; i < 2; ++i) {
-    if (p->u[i]) cudaFree(p->u[i]);
-    p->u[i] = nullptr;
-    CIP_CUDA(p, cudaMalloc(&p->u[i], real_elems(p, p->M) * nc * sizeof(T)));
+    free_ptr(p->u[i]);
+    CIP_CUDA(p, cudaMalloc(&p->u[i], real_elems(p, S) * nc * sizeof(T)));
   }
-  if (p->tprev) cudaFree(p->tprev);
-  p->tprev = nullptr;
-  CIP_CUDA(p, cudaMalloc(&p->tprev, real_elems(p, p->M) * nc * sizeof(T)));
+  free_ptr(p->tprev);
+  CIP_CUDA(p, cudaMalloc(&p->tprev, real_elems(p, S) * nc * sizeof(T)));
+  if (is_cd(p)) {
+    // row spectra of v and of rho (t - u) over the coefficient maps, the column buffer and p, x
+    free_ptr(p->xh);
+    free_ptr(p->qh);
+    CIP_CUDA(p, cudaMalloc(&p->xh, half_elems(p, S) * sizeof(C)));
+    CIP_CUDA(p, cudaMalloc(&p->qh, half_elems(p, S) * sizeof(C)));
+    free_ptr(p->colbuf);
+    CIP_CUDA(p, cudaMalloc(&p->colbuf, col_elems(p, S) * sizeof(C)));
+    for (int i = 0; i < 2; ++i) {
+      free_ptr(p->pbuf[i]);
+      CIP_CUDA(p, cudaMalloc(&p->pbuf[i], col_elems(p, p->M) * sizeof(C)));
+    }
+    free_ptr(p->xcol);
+    CIP_CUDA(p, cudaMalloc(&p->xcol, col_elems(p, p->M) * sizeof(C)));
+    free_ptr(p->theta);
+    CIP_CUDA(p, cudaMalloc(&p->theta, col_elems(p, p->L) * sizeof(C)));
+  }
   if (p->pinv) cudaFree(p->pinv);
   p->pinv = nullptr;
   CIP_CUDA(p, cudaMalloc(&p->pinv, col_elems(p, p->M * (p->M + 1) / 2) * sizeof(C)));
@@ -162,7 +195,7 @@ template <typename T> cip_status alloc_state(cip_plan* p) {
   if (p->partials) cudaFree(p->partials);
   p->partials = nullptr;
   p->rowsA = passA_rows<T>(p->N, p->prior);
-  p->blocksA = (p->N / p->rowsA) * p->M;
+  p->blocksA = (p->N / p->rowsA) * smaps(p);
   CIP_CUDA(p, cudaMalloc(&p->partials, (size_t)p->blocksA * kNPart * sizeof(double)));
   return CIP_OK;
 }
@@ -170,11 +203,17 @@ template <typename T> cip_status alloc_state(cip_plan* p) {
 template <typename T> cip_status reset_state(cip_plan* p, cudaStream_t s) {
   using C = typename CT<T>::type;
   const size_t nc = ncomp_of(p->prior);
-  CIP_CUDA(p, cudaMemsetAsync(p->xh, 0, half_elems(p, p->M) * sizeof(C), s));
-  CIP_CUDA(p, cudaMemsetAsync(p->qh, 0, half_elems(p, p->M) * sizeof(C), s));
-  CIP_CUDA(p, cudaMemsetAsync(p->u[0], 0, real_elems(p, p->M) * nc * sizeof(T), s));
-  CIP_CUDA(p, cudaMemsetAsync(p->u[1], 0, real_elems(p, p->M) * nc * sizeof(T), s));
-  CIP_CUDA(p, cudaMemsetAsync(p->tprev, 0, real_elems(p, p->M) * nc * sizeof(T), s));
+  const int S = smaps(p);
+  CIP_CUDA(p, cudaMemsetAsync(p->xh, 0, half_elems(p, S) * sizeof(C), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->qh, 0, half_elems(p, S) * sizeof(C), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->u[0], 0, real_elems(p, S) * nc * sizeof(T), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->u[1], 0, real_elems(p, S) * nc * sizeof(T), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->tprev, 0, real_elems(p, S) * nc * sizeof(T), s));
+  if (is_cd(p)) {
+    for (int i = 0; i < 2; ++i) CIP_CUDA(p, cudaMemsetAsync(p->pbuf[i], 0, col_elems(p, p->M) * sizeof(C), s));
+    CIP_CUDA(p, cudaMemsetAsync(p->xcol, 0, col_elems(p, p->M) * sizeof(C), s));
+    p->pcur = 0;
+  }
   p->cur = 0;
   p->iteration = 0;
   p->resid_valid = false;
@@ -198,9 +237,12 @@ template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
   using C = typename CT<T>::type;
   CIP_CUDA(p, cudaMemsetAsync(p->pinv_list, 0, sizeof(int), s));
   const int use_g = p->prior == CIP_PRIOR_TV ? 1 : 0;
-  CIP_LAUNCH(p, launch_factor<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, p->rho, p->beta,
+  // analysis: Psi = rho g I + beta Lambda^H Lambda; dictionary: t I + beta Lambda^H Lambda with t = 1
+  // (P^H P = I for a convolutional dictionary, Eq. solx_synt_DFT)
+  const double diag = is_cd(p) ? 1.0 : p->rho;
+  CIP_LAUNCH(p, launch_factor<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
                                  static_cast<C*>(p->pinv), p->pinv64, p->pinv_list, kPinvListCap, s));
-  CIP_LAUNCH(p, launch_factor_pinv<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, p->rho, p->beta,
+  CIP_LAUNCH(p, launch_factor_pinv<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
                                       static_cast<C*>(p->pinv), p->pinv64, p->pinv_list, kPinvListCap, s));
   int nlist = 0;
   CIP_CUDA(p, cudaMemcpyAsync(&nlist, p->pinv_list, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -210,7 +252,38 @@ template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
   return CIP_OK;
 }
 
+// Filters d[L][P][P] (plan dtype): embedded on the N x N torus with their centre at (0,0),
+// DFT in FP64, kept as theta in the plan's precision (Section IV-B, Theta_m of the dictionary).
+template <typename T> cip_status do_set_dictionary(cip_plan* p, const void* d, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  cip_status st = alloc_state<T>(p);
+  if (st != CIP_OK) return st;
+  Staging sg;
+  const void* dd = nullptr;
+  st = stage_in(p, d, (size_t)p->L * p->Pf * p->Pf * sizeof(T), s, sg, &dd);
+  if (st != CIP_OK) return st;
+  double* emb = nullptr;
+  double2* th64 = nullptr;
+  CIP_CUDA(p, cudaMallocAsync((void**)&emb, real_elems(p, p->L) * sizeof(double), s));
+  CIP_CUDA(p, cudaMallocAsync((void**)&th64, half_elems(p, p->L) * sizeof(double2), s));
+  cudaError_t e = cudaMemsetAsync(emb, 0, real_elems(p, p->L) * sizeof(double), s);
+  if (e == cudaSuccess) e = launch_embed_filters<T>(static_cast<const T*>(dd), emb, p->L, p->Pf, p->N, s);
+  if (e == cudaSuccess) e = launch_row_r2c<double, double>(emb, th64, p->N, p->L * p->N, 1.0, p->tw64, s);
+  if (e == cudaSuccess) e = launch_col_c2c<double>(th64, p->N, p->L, -1, p->tw64, s);
+  if (e == cudaSuccess) e = launch_theta_store<T>(th64, static_cast<C*>(p->theta), p->L, p->N, s);
+  if (e == cudaSuccess) p->launches += 4;
+  cudaFreeAsync(emb, s);
+  cudaFreeAsync(th64, s);
+  CIP_CUDA(p, e);
+  if (p->have_psfs) {
+    st = form_factor<T>(p, s);
+    if (st != CIP_OK) return st;
+  }
+  return reset_state<T>(p, s);
+}
+
 template <typename T> cip_status do_set_prior(cip_plan* p, cudaStream_t s) {
+  if (is_cd(p)) return CIP_OK;  // buffers follow the dictionary (cip_set_dictionary)
   cip_status st = alloc_state<T>(p);
   if (st != CIP_OK) return st;
   if (p->have_psfs) {
@@ -254,7 +327,7 @@ template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream
   cudaFreeAsync(yhat, s);
   CIP_CUDA(p, e);
   p->have_y = true;
-  if (p->opt.column_pass == 0 && p->opt.col_tile == 0) {
+  if (!is_cd(p) && p->opt.column_pass == 0 && p->opt.col_tile == 0) {
     r = autotune<T>(p, s);
     if (r != CIP_OK) return r;
   }
@@ -272,9 +345,10 @@ template <typename T> PassAArgs<T> passA_args(cip_plan* p, int flags) {
   a.t_imp = nullptr;
   a.partials = p->partials;
   a.tw = static_cast<const C*>(p->tw);
-  a.M = p->M;
+  a.M = smaps(p);
   a.tau = (T)(p->lam / p->rho);
-  a.qscale = (T)(0.5 * p->rho);
+  // the dictionary's column solve works on spectra scaled by 1/N^2 (see convdict.cu)
+  a.qscale = is_cd(p) ? (T)(0.5 * p->rho / ((double)p->N * p->N)) : (T)(0.5 * p->rho);
   a.flags = flags;
   fill_dct<T>(a.dct);
   return a;
@@ -285,6 +359,31 @@ template <typename T> PassBArgs<T> passB_args(cip_plan* p);
 // the column pass in the plan's chosen form
 template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mode, int cc) {
   using C = typename CT<T>::type;
+  if (is_cd(p)) {
+    // dictionary: column DFT of rho (t - u) over the L*M coefficient maps, the per-(bin, channel)
+    // x- and z-update, inverse column DFT of v
+    const int S = smaps(p);
+    CIP_LAUNCH(p, launch_colfft_fwd<T>(static_cast<const C*>(p->qh), static_cast<C*>(p->colbuf),
+                                       static_cast<const C*>(p->tw), p->N, S, s));
+    CDArgs<T> a;
+    a.colbuf = static_cast<C*>(p->colbuf);
+    a.theta = static_cast<const C*>(p->theta);
+    a.p_in = static_cast<const C*>(p->pbuf[p->pcur]);
+    a.p_out = static_cast<C*>(p->pbuf[p->pcur ^ 1]);
+    a.xb = static_cast<const C*>(p->bhat);
+    a.pinv = static_cast<const C*>(p->pinv);
+    a.xcol = static_cast<C*>(p->xcol);
+    a.N = p->N;
+    a.M = p->M;
+    a.L = p->L;
+    a.rho = (T)p->rho;
+    a.n2 = (T)((double)p->N * p->N);
+    CIP_LAUNCH(p, launch_cd_solve<T>(a, s));
+    CIP_LAUNCH(p, launch_colfft_inv<T>(static_cast<const C*>(p->colbuf), static_cast<C*>(p->xh),
+                                       static_cast<const C*>(p->tw), p->N, S, s));
+    p->pcur ^= 1;
+    return CIP_OK;
+  }
   PassBArgs<T> b = passB_args<T>(p);
   if (mode == 2) {
     if (!p->colbuf) return fail(p, CIP_ERR_STATE, "split column pass selected without its column buffer");
@@ -395,7 +494,7 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
     PassAArgs<T> a = passA_args<T>(p, flags);
     const bool timeA = p->timing && p->nA < kMaxTimed;
     if (timeA) cudaEventRecord(p->evA[2 * p->nA], s);
-    CIP_LAUNCH(p, launch_passA<T>(a, p->N, p->prior, s));
+    CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
     if (timeA) cudaEventRecord(p->evA[2 * p->nA++ + 1], s);
     p->cur ^= 1;
     p->iteration++;
@@ -420,23 +519,61 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
   return CIP_OK;
 }
 
-template <typename T> cip_status get_x_impl(cip_plan* p, void* x, cudaStream_t s) {
+// inverse row DFT of `maps` row-domain half spectra into a caller array (host or device)
+template <typename T>
+cip_status rows_out(cip_plan* p, const void* rows, int maps, void* out, cudaStream_t s) {
   using C = typename CT<T>::type;
-  const size_t bytes = real_elems(p, p->M) * sizeof(T);
-  if (is_device_ptr(x)) {
-    CIP_LAUNCH(p, (launch_row_c2r<T, T>(static_cast<const C*>(p->xh), static_cast<T*>(x), p->N, p->M * p->N,
-                                      static_cast<const C*>(p->tw), s)));
+  const size_t bytes = real_elems(p, maps) * sizeof(T);
+  if (is_device_ptr(out)) {
+    CIP_LAUNCH(p, (launch_row_c2r<T, T>(static_cast<const C*>(rows), static_cast<T*>(out), p->N, maps * p->N,
+                                        static_cast<const C*>(p->tw), s)));
     return CIP_OK;
   }
   void* tmp = nullptr;
   CIP_CUDA(p, cudaMallocAsync(&tmp, bytes, s));
-  cudaError_t e = launch_row_c2r<T, T>(static_cast<const C*>(p->xh), static_cast<T*>(tmp), p->N, p->M * p->N,
+  cudaError_t e = launch_row_c2r<T, T>(static_cast<const C*>(rows), static_cast<T*>(tmp), p->N, maps * p->N,
                                        static_cast<const C*>(p->tw), s);
   if (e == cudaSuccess) p->launches++;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(x, tmp, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(tmp, s);
   CIP_CUDA(p, e);
   CIP_CUDA(p, cudaStreamSynchronize(s));
+  return CIP_OK;
+}
+
+template <typename T> cip_status get_x_impl(cip_plan* p, void* x, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  if (!is_cd(p)) return rows_out<T>(p, p->xh, p->M, x, s);
+  // dictionary: x-hat is kept column-contiguous; inverse column DFT to row spectra first
+  void* rows = nullptr;
+  CIP_CUDA(p, cudaMallocAsync(&rows, half_elems(p, p->M) * sizeof(C), s));
+  cudaError_t e = launch_colfft_inv<T>(static_cast<const C*>(p->xcol), static_cast<C*>(rows),
+                                       static_cast<const C*>(p->tw), p->N, p->M, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(rows, s);
+    CIP_CUDA(p, e);
+  }
+  p->launches++;
+  cip_status st = rows_out<T>(p, rows, p->M, x, s);
+  cudaFreeAsync(rows, s);
+  return st;
+}
+
+// dictionary state import: p = sum_l theta_l F z_l / N^2 from coefficient maps z [M][L][N][N]
+template <typename T> cip_status import_z(cip_plan* p, const void* z, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const int S = smaps(p);
+  Staging sz;
+  const void* dz = nullptr;
+  cip_status r = stage_in(p, z, real_elems(p, S) * sizeof(T), s, sz, &dz);
+  if (r != CIP_OK) return r;
+  // row DFT into xh (overwritten by the next column pass), column DFT into colbuf
+  CIP_LAUNCH(p, (launch_row_r2c<T, T>(static_cast<const T*>(dz), static_cast<C*>(p->xh), p->N, S * p->N, (T)1,
+                                      static_cast<const C*>(p->tw), s)));
+  CIP_LAUNCH(p, launch_colfft_fwd<T>(static_cast<const C*>(p->xh), static_cast<C*>(p->colbuf),
+                                     static_cast<const C*>(p->tw), p->N, S, s));
+  CIP_LAUNCH(p, launch_p_from_z<T>(static_cast<const C*>(p->colbuf), static_cast<const C*>(p->theta),
+                                   static_cast<C*>(p->pbuf[p->pcur]), p->N, p->M, p->L, s));
   return CIP_OK;
 }
 
@@ -448,7 +585,7 @@ cip_status copy_out(cip_plan* p, void* dst, const void* src, size_t bytes, cudaS
 }
 
 template <typename T> cip_status import_impl(cip_plan* p, const void* t, const void* u, cudaStream_t s) {
-  const size_t bytes = real_elems(p, p->M) * ncomp_of(p->prior) * sizeof(T);
+  const size_t bytes = real_elems(p, smaps(p)) * ncomp_of(p->prior) * sizeof(T);
   Staging st1, st2;
   const void *dt = nullptr, *du = nullptr;
   cip_status r = stage_in(p, t, bytes, s, st1, &dt);
@@ -459,7 +596,7 @@ template <typename T> cip_status import_impl(cip_plan* p, const void* t, const v
   CIP_CUDA(p, cudaMemcpyAsync(p->tprev, dt, bytes, cudaMemcpyDeviceToDevice, s));
   PassAArgs<T> a = passA_args<T>(p, PA_IMPORT);
   a.t_imp = static_cast<const T*>(dt);
-  CIP_LAUNCH(p, launch_passA<T>(a, p->N, p->prior, s));
+  CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
   p->cur ^= 1;
   p->iteration = 0;
   p->resid_valid = false;
@@ -471,6 +608,7 @@ template <typename T> cip_status import_impl(cip_plan* p, const void* t, const v
 cip_status check_ready(cip_plan* p, bool need_y) {
   if (!p) return CIP_ERR_INVALID_ARG;
   if (p->prior < 0) return fail(p, CIP_ERR_STATE, "cip_set_prior has not been called");
+  if (is_cd(p) && !p->theta) return fail(p, CIP_ERR_STATE, "cip_set_dictionary has not been called");
   if (!p->have_psfs) return fail(p, CIP_ERR_STATE, "cip_set_psfs has not been called");
   if (need_y && !p->have_y) return fail(p, CIP_ERR_STATE, "cip_set_measurements has not been called");
   return CIP_OK;
@@ -604,7 +742,8 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
+  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol,
+                  p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -617,12 +756,13 @@ cip_status cip_plan_destroy(cip_plan* p) {
 
 cip_status cip_set_prior(cip_plan* p, cip_prior prior, double lambda, double rho, double beta, void* stream) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  if (prior != CIP_PRIOR_TV && prior != CIP_PRIOR_DCT8 && prior != CIP_PRIOR_L1)
+  if (prior != CIP_PRIOR_TV && prior != CIP_PRIOR_DCT8 && prior != CIP_PRIOR_L1 && prior != CIP_PRIOR_CONVDICT)
     return fail(p, CIP_ERR_INVALID_ARG, "unknown prior");
   if (!(lambda > 0) || !(rho > 0) || !(beta > 0)) return fail(p, CIP_ERR_INVALID_ARG, "lambda, rho, beta must be > 0");
-  const int rows = p->dtype == CIP_F64 ? passA_rows<double>(p->N, prior) : passA_rows<float>(p->N, prior);
+  const int kind = prior == CIP_PRIOR_CONVDICT ? (int)CIP_PRIOR_L1 : (int)prior;
+  const int rows = p->dtype == CIP_F64 ? passA_rows<double>(p->N, kind) : passA_rows<float>(p->N, kind);
   if (p->N % rows != 0) return fail(p, CIP_ERR_UNSUPPORTED, "image size not a multiple of the row tile");
-  const size_t smA = p->dtype == CIP_F64 ? passA_smem<double>(p->N, prior) : passA_smem<float>(p->N, prior);
+  const size_t smA = p->dtype == CIP_F64 ? passA_smem<double>(p->N, kind) : passA_smem<float>(p->N, kind);
   int dev = 0, smem_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -682,8 +822,40 @@ cip_status cip_get_u(cip_plan* p, void* u, void* stream) {
   if (!p || !u) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
   cip_status r = check_ready(p, false);
   if (r != CIP_OK) return r;
-  return copy_out(p, u, p->u[p->cur], real_elems(p, p->M) * ncomp_of(p->prior) * p->esz,
+  return copy_out(p, u, p->u[p->cur], real_elems(p, smaps(p)) * ncomp_of(p->prior) * p->esz,
                   static_cast<cudaStream_t>(stream));
+}
+
+cip_status cip_set_dictionary(cip_plan* p, const void* filters, int L, int P, void* stream) {
+  if (!p || !filters) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "cip_set_prior(CIP_PRIOR_CONVDICT) must precede cip_set_dictionary");
+  if (L < 1 || L > 32) return fail(p, CIP_ERR_UNSUPPORTED, "L must be in [1, 32]");
+  if (P < 1 || P > p->N) return fail(p, CIP_ERR_INVALID_ARG, "filter size must be in [1, N]");
+  p->L = L;
+  p->Pf = P;
+  p->have_y = false;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return DISPATCH_T(p, do_set_dictionary<float>(p, filters, s), do_set_dictionary<double>(p, filters, s));
+}
+
+cip_status cip_get_coefficients(cip_plan* p, void* z, void* stream) {
+  if (!p || !z) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  cip_status r = check_ready(p, false);
+  if (r != CIP_OK) return r;
+  if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "coefficient maps exist only for CIP_PRIOR_CONVDICT");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return DISPATCH_T(p, rows_out<float>(p, p->xh, smaps(p), z, s), rows_out<double>(p, p->xh, smaps(p), z, s));
+}
+
+cip_status cip_state_import_coefficients(cip_plan* p, const void* z, const void* t, const void* u, void* stream) {
+  if (!p || !z || !t || !u) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  cip_status r = check_ready(p, false);
+  if (r != CIP_OK) return r;
+  if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "coefficient maps exist only for CIP_PRIOR_CONVDICT");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  r = DISPATCH_T(p, import_z<float>(p, z, s), import_z<double>(p, z, s));
+  if (r != CIP_OK) return r;
+  return DISPATCH_T(p, import_impl<float>(p, t, u, s), import_impl<double>(p, t, u, s));
 }
 
 cip_status cip_get_residuals(cip_plan* p, double* r_rel, double* s_rel) {
@@ -710,10 +882,26 @@ cip_status cip_state_import(cip_plan* p, const void* t, const void* u, void* str
   return DISPATCH_T(p, import_impl<float>(p, t, u, s), import_impl<double>(p, t, u, s));
 }
 
+// device buffers that make up the ADMM state, in checkpoint order
+static std::vector<std::pair<void*, size_t>> state_segments(cip_plan* p) {
+  const int S = smaps(p);
+  const size_t hb = half_elems(p, S) * 2 * p->esz;
+  const size_t ub = real_elems(p, S) * ncomp_of(p->prior) * p->esz;
+  std::vector<std::pair<void*, size_t>> seg = {{p->xh, hb}, {p->qh, hb}, {p->u[p->cur], ub}, {p->tprev, ub}};
+  if (is_cd(p)) {
+    seg.push_back({p->pbuf[p->pcur], col_elems(p, p->M) * 2 * p->esz});
+    seg.push_back({p->xcol, col_elems(p, p->M) * 2 * p->esz});
+  }
+  return seg;
+}
+
 cip_status cip_state_size(cip_plan* p, size_t* bytes) {
   if (!p || !bytes) return CIP_ERR_INVALID_ARG;
   if (p->prior < 0) return fail(p, CIP_ERR_STATE, "cip_set_prior has not been called");
-  *bytes = 2 * sizeof(int) + half_elems(p, p->M) * 2 * p->esz * 2 + 2 * real_elems(p, p->M) * ncomp_of(p->prior) * p->esz;
+  if (is_cd(p) && !p->theta) return fail(p, CIP_ERR_STATE, "cip_set_dictionary has not been called");
+  size_t n = 2 * sizeof(int);
+  for (auto& sgm : state_segments(p)) n += sgm.second;
+  *bytes = n;
   return CIP_OK;
 }
 
@@ -730,15 +918,10 @@ cip_status cip_state_export(cip_plan* p, void* buf, void* stream) {
   if (dev) CIP_CUDA(p, cudaMemcpyAsync(b, hdr, sizeof(hdr), cudaMemcpyHostToDevice, s));
   else std::memcpy(b, hdr, sizeof(hdr));
   size_t off = sizeof(hdr);
-  const size_t hb = half_elems(p, p->M) * 2 * p->esz;
-  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->xh, hb, k, s));
-  off += hb;
-  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->qh, hb, k, s));
-  off += hb;
-  const size_t ub = real_elems(p, p->M) * ncomp_of(p->prior) * p->esz;
-  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->u[p->cur], ub, k, s));
-  off += ub;
-  CIP_CUDA(p, cudaMemcpyAsync(b + off, p->tprev, ub, k, s));
+  for (auto& sgm : state_segments(p)) {
+    CIP_CUDA(p, cudaMemcpyAsync(b + off, sgm.first, sgm.second, k, s));
+    off += sgm.second;
+  }
   CIP_CUDA(p, cudaStreamSynchronize(s));
   return CIP_OK;
 }
@@ -760,15 +943,10 @@ cip_status cip_state_restore(cip_plan* p, const void* buf, void* stream) {
     std::memcpy(hdr, b, sizeof(hdr));
   }
   size_t off = sizeof(hdr);
-  const size_t hb = half_elems(p, p->M) * 2 * p->esz;
-  CIP_CUDA(p, cudaMemcpyAsync(p->xh, b + off, hb, k, s));
-  off += hb;
-  CIP_CUDA(p, cudaMemcpyAsync(p->qh, b + off, hb, k, s));
-  off += hb;
-  const size_t ub = real_elems(p, p->M) * ncomp_of(p->prior) * p->esz;
-  CIP_CUDA(p, cudaMemcpyAsync(p->u[p->cur], b + off, ub, k, s));
-  off += ub;
-  CIP_CUDA(p, cudaMemcpyAsync(p->tprev, b + off, ub, k, s));
+  for (auto& sgm : state_segments(p)) {
+    CIP_CUDA(p, cudaMemcpyAsync(sgm.first, b + off, sgm.second, k, s));
+    off += sgm.second;
+  }
   CIP_CUDA(p, cudaStreamSynchronize(s));
   p->iteration = hdr[0];
   p->resid_valid = false;

@@ -164,6 +164,21 @@ cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colb
   return e;
 }
 
+template <typename T>
+cudaError_t launch_colfft_fwd(const typename CT<T>::type* rows, typename CT<T>::type* cols,
+                              const typename CT<T>::type* tw, int N, int maps, cudaStream_t s) {
+  return colfft_n<T, -1>(rows, cols, tw, N, maps, s);
+}
+template <typename T>
+cudaError_t launch_colfft_inv(const typename CT<T>::type* cols, typename CT<T>::type* rows,
+                              const typename CT<T>::type* tw, int N, int maps, cudaStream_t s) {
+  return colfft_n<T, +1>(cols, rows, tw, N, maps, s);
+}
+template cudaError_t launch_colfft_fwd<float>(const float2*, float2*, const float2*, int, int, cudaStream_t);
+template cudaError_t launch_colfft_fwd<double>(const double2*, double2*, const double2*, int, int, cudaStream_t);
+template cudaError_t launch_colfft_inv<float>(const float2*, float2*, const float2*, int, int, cudaStream_t);
+template cudaError_t launch_colfft_inv<double>(const double2*, double2*, const double2*, int, int, cudaStream_t);
+
 template cudaError_t launch_passB_split<float>(const PassBArgs<float>&, float2*, int, cudaStream_t, int*);
 template cudaError_t launch_passB_split<double>(const PassBArgs<double>&, double2*, int, cudaStream_t, int*);
 

@@ -46,6 +46,36 @@ template <typename T> struct PassBArgs {
   int M;
 };
 
+// Convolutional-dictionary column solve (Eqs. solx_synt_DFT, solz_DFT, solz_DFT_SM), one
+// thread per (frequency, channel).  Column layout [k2][plane][col_pitch(N)].
+template <typename T> struct CDArgs {
+  using C = typename CT<T>::type;
+  C* colbuf;       // [H][M*L]: in G = col-DFT of rho (t - u) / N^2, out v (channel-major, m*L + l)
+  const C* theta;  // [H][L]: DFT of the embedded filters
+  const C* p_in;   // [H][M]: p = sum_l theta_l v_l of the previous iteration (scaled 1/N^2)
+  C* p_out;        // [H][M]
+  const C* xb;     // [H][M]: Psi^{-1} beta Lambda^H F y / N^2
+  const C* pinv;   // [H][M(M+1)/2]: packed (I + beta Lambda^H Lambda)^{-1} / N^2
+  C* xcol;         // [H][M]: x-hat / N^2 (for read-back)
+  int N, M, L;
+  T rho;
+  T n2;            // N^2
+};
+template <typename T> cudaError_t launch_cd_solve(const CDArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_p_from_z(const typename CT<T>::type* zcol, const typename CT<T>::type* th,
+                            typename CT<T>::type* p, int N, int M, int L, cudaStream_t s);
+template <typename Tin> cudaError_t launch_embed_filters(const Tin* d, double* out, int L, int P, int N, cudaStream_t s);
+template <typename T>
+cudaError_t launch_theta_store(const double2* th64, typename CT<T>::type* th, int L, int N, cudaStream_t s);
+// column DFTs between the row layout [maps][N][P] and the column layout [H][maps][CP]
+template <typename T>
+cudaError_t launch_colfft_fwd(const typename CT<T>::type* rows, typename CT<T>::type* cols,
+                              const typename CT<T>::type* tw, int N, int maps, cudaStream_t s);
+template <typename T>
+cudaError_t launch_colfft_inv(const typename CT<T>::type* cols, typename CT<T>::type* rows,
+                              const typename CT<T>::type* tw, int N, int maps, cudaStream_t s);
+
 template <typename T> int passA_rows(int N, int prior);
 template <typename T> size_t passA_smem(int N, int prior);
 template <typename T> cudaError_t launch_passA(const PassAArgs<T>& a, int N, int prior, cudaStream_t s);
