@@ -69,7 +69,11 @@ typedef struct cip_options {
   int check_every;  /* residual check period for cip_iterate with tol > 0; 0 = 10 */
   int column_pass;  /* 0 = autotuned at cip_set_measurements (fused vs split, tile width; cached per
                        N, M, dtype), 1 = fused cluster kernel, 2 = split (column FFT / solve / FFT) */
-  int reserved[13];
+  int precision;    /* CIP_F32 plans: 0 = mixed (factor and data term Psi^{-1} beta Lambda^H F y formed
+                       in FP64, rounded once; the default), 1 = plain FP32 method (factor formed and
+                       inverted in FP32, x = Psi^{-1} (beta Lambda^H F y + rho F T^H (t - u)) applied in
+                       FP32 every iteration; analysis priors only) */
+  int reserved[12];
 } cip_options;
 
 typedef struct cip_plan cip_plan;
@@ -166,6 +170,20 @@ cip_status cip_get_launches(cip_plan* plan, unsigned long long* launches);
 /* Launch configuration the plan uses (for reporting). */
 cip_status cip_get_config(cip_plan* plan, int* rows_per_tile, int* col_tile, int* prior_pass_blocks,
                           int* column_pass_blocks, int* column_pass);
+
+/* Batched launch of many independent plans (uneven N, M and prior allowed; every plan
+ * set up and ready to iterate).  cip_batch_iterate runs `iters` iterations of every plan:
+ * the iterations are recorded once into a CUDA graph with one branch per plan (spread
+ * over `nstreams` capture streams, 0 = 8) and the graph is replayed, so the kernels of
+ * small instances run side by side; the last two iterations run outside the graph and
+ * compute each plan's residuals.  The batch does not own the plans; destroy it before
+ * them.  Plans of a batch must not be iterated concurrently on other streams.  The graph
+ * is re-recorded when a plan's buffers changed side since the last recording. */
+typedef struct cip_batch cip_batch;
+cip_status cip_batch_create(cip_batch** out, cip_plan* const* plans, int n, int nstreams);
+cip_status cip_batch_iterate(cip_batch* batch, int iters, void* stream);
+const char* cip_batch_last_error(const cip_batch* batch);
+cip_status cip_batch_destroy(cip_batch* batch);
 
 /* Shrinkage, dual update and residual norms of one ADMM iteration without any
  * device allocation.  The paper has no counterpart: this exists for callers

@@ -19,7 +19,8 @@ P_size = ctypes.POINTER(ctypes.c_size_t)
 
 
 class cip_options(ctypes.Structure):
-    _fields_ = [("col_tile", c_int), ("check_every", c_int), ("column_pass", c_int), ("reserved", c_int * 13)]
+    _fields_ = [("col_tile", c_int), ("check_every", c_int), ("column_pass", c_int), ("precision", c_int),
+                ("reserved", c_int * 12)]
 
 
 # name -> (restype, argtypes)
@@ -47,6 +48,10 @@ SIGNATURES = {
     "cip_get_timing": (c_int, [c_void_p, P_double, P_int, P_double, P_int]),
     "cip_get_config": (c_int, [c_void_p, P_int, P_int, P_int, P_int, P_int]),
     "cip_get_launches": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "cip_batch_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_int, c_int]),
+    "cip_batch_iterate": (c_int, [c_void_p, c_int, c_void_p]),
+    "cip_batch_last_error": (c_char_p, [c_void_p]),
+    "cip_batch_destroy": (c_int, [c_void_p]),
     "cip_set_dictionary": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "cip_get_coefficients": (c_int, [c_void_p, c_void_p, c_void_p]),
     "cip_state_import_coefficients": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

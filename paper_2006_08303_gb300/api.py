@@ -76,7 +76,7 @@ class Plan:
     """One reconstruction instance held on the device (cip_plan)."""
 
     def __init__(self, N: int, K: int, M: int, dtype: str = "f32", col_tile: int = 0, check_every: int = 0,
-                 column_pass: int = 0):
+                 column_pass: int = 0, plain_fp32: bool = False):
         self._L = _lib.load()
         self.N, self.K, self.M, self.dtype = N, K, M, dtype
         self.prior: Optional[str] = None
@@ -84,6 +84,7 @@ class Plan:
         opt.col_tile = col_tile
         opt.check_every = check_every
         opt.column_pass = column_pass
+        opt.precision = 1 if plain_fp32 else 0
         h = ctypes.c_void_p()
         st = self._L.cip_plan_create(ctypes.byref(h), N, K, M, DTYPES[dtype], ctypes.byref(opt))
         if st != 0:
@@ -238,6 +239,36 @@ class Plan:
         self._check(self._L.cip_get_config(self._h, *[ctypes.byref(x) for x in v]))
         return {"rows_per_tile": v[0].value, "col_tile": v[1].value, "prior_pass_blocks": v[2].value,
                 "column_pass_blocks": v[3].value, "column_pass": {1: "fused", 2: "split"}.get(v[4].value, "?")}
+
+
+class Batch:
+    """cip_batch: iterate many plans together through one CUDA graph (one branch per plan)."""
+
+    def __init__(self, plans, nstreams: int = 0):
+        self._L = _lib.load()
+        self.plans = list(plans)  # keeps the plans alive while the batch exists
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        st = self._L.cip_batch_create(ctypes.byref(h), arr, len(self.plans), nstreams)
+        if st != 0:
+            raise CipError(st, "cip_batch_create failed")
+        self._h = h
+
+    def iterate(self, n: int, stream=None):
+        st = self._L.cip_batch_iterate(self._h, n, _stream_ptr(stream))
+        if st != 0:
+            raise CipError(st, self._L.cip_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.cip_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def shrink_dual_noalloc(prior: str, lam: float, rho: float, x, u_in, t_prev, u_out, resid_out, t_out=None,

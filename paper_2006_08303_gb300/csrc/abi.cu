@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/cip.h): plan lifetime, setup
 // (Alg. 1 lines 1-2), the iteration loop (Alg. 1 lines 3-8), read-back,
 // state import/export and per-kernel timing.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -240,8 +241,13 @@ template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
   // analysis: Psi = rho g I + beta Lambda^H Lambda; dictionary: t I + beta Lambda^H Lambda with t = 1
   // (P^H P = I for a convolutional dictionary, Eq. solx_synt_DFT)
   const double diag = is_cd(p) ? 1.0 : p->rho;
-  CIP_LAUNCH(p, launch_factor<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
-                                 static_cast<C*>(p->pinv), p->pinv64, p->pinv_list, kPinvListCap, s));
+  if (p->opt.precision == 1) {
+    CIP_LAUNCH(p, launch_factor_fp32(p->lam64, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
+                                     reinterpret_cast<float2*>(p->pinv), p->pinv_list, kPinvListCap, s));
+  } else {
+    CIP_LAUNCH(p, launch_factor<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
+                                   static_cast<C*>(p->pinv), p->pinv64, p->pinv_list, kPinvListCap, s));
+  }
   CIP_LAUNCH(p, launch_factor_pinv<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
                                       static_cast<C*>(p->pinv), p->pinv64, p->pinv_list, kPinvListCap, s));
   int nlist = 0;
@@ -321,8 +327,12 @@ template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream
   CIP_CUDA(p, cudaMallocAsync((void**)&yhat, half_elems(p, p->K) * sizeof(double2), s));
   cudaError_t e = launch_row_r2c<double, T>(static_cast<const T*>(dy), yhat, p->N, p->K * p->N, 1.0, p->tw64, s);
   if (e == cudaSuccess) e = launch_col_c2c<double>(yhat, p->N, p->K, -1, p->tw64, s);
-  if (e == cudaSuccess)
-    e = launch_rhs<T>(p->lam64, yhat, p->pinv64, p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
+  if (e == cudaSuccess) {
+    if (p->opt.precision == 1)
+      e = launch_rhs_fp32(p->lam64, yhat, p->K, p->M, p->N, p->beta, reinterpret_cast<float2*>(p->bhat), s);
+    else
+      e = launch_rhs<T>(p->lam64, yhat, p->pinv64, p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
+  }
   if (e == cudaSuccess) p->launches += 3;
   cudaFreeAsync(yhat, s);
   CIP_CUDA(p, e);
@@ -461,6 +471,7 @@ template <typename T> PassBArgs<T> passB_args(cip_plan* p) {
   b.bhat = static_cast<const C*>(p->bhat);
   b.tw = static_cast<const C*>(p->tw);
   b.M = p->M;
+  b.plain = p->opt.precision == 1 ? 1 : 0;
   return b;
 }
 
@@ -516,6 +527,22 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
     }
   }
   if (done) *done = it;
+  return CIP_OK;
+}
+
+// One iteration (column pass, prior pass) enqueued with no host synchronisation and no timing
+// events, so that it can be recorded into a CUDA graph.
+template <typename T> cip_status enqueue_iteration(cip_plan* p, cudaStream_t s, int flags) {
+  cip_status cst = column_pass<T>(p, s, p->colmode, p->cc);
+  if (cst != CIP_OK) return cst;
+  PassAArgs<T> a = passA_args<T>(p, flags);
+  CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
+  p->cur ^= 1;
+  p->iteration++;
+  if (flags & PA_RESID) {
+    CIP_LAUNCH(p, launch_reduce_partials(p->partials, p->blocksA, p->rho, 0.0, p->resid, p->conv, s));
+    p->resid_valid = true;
+  }
   return CIP_OK;
 }
 
@@ -683,6 +710,10 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
     return fail(nullptr, CIP_ERR_UNSUPPORTED, "column tile does not fit in shared memory for this N, M and dtype");
   }
   p->blocksB = (N / 2 + 1 + cc - 1) / cc;
+  if (p->opt.precision != 0 && (p->opt.precision != 1 || dtype != CIP_F32)) {
+    delete p;
+    return fail(nullptr, CIP_ERR_INVALID_ARG, "precision must be 0, or 1 (plain FP32) for CIP_F32 plans");
+  }
   p->colmode = p->opt.column_pass == 2 ? 2 : 1;
   if (p->opt.column_pass < 0 || p->opt.column_pass > 2) {
     delete p;
@@ -829,6 +860,7 @@ cip_status cip_get_u(cip_plan* p, void* u, void* stream) {
 cip_status cip_set_dictionary(cip_plan* p, const void* filters, int L, int P, void* stream) {
   if (!p || !filters) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
   if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "cip_set_prior(CIP_PRIOR_CONVDICT) must precede cip_set_dictionary");
+  if (p->opt.precision != 0) return fail(p, CIP_ERR_UNSUPPORTED, "the plain FP32 method covers analysis priors only");
   if (L < 1 || L > 32) return fail(p, CIP_ERR_UNSUPPORTED, "L must be in [1, 32]");
   if (P < 1 || P > p->N) return fail(p, CIP_ERR_INVALID_ARG, "filter size must be in [1, N]");
   p->L = L;
@@ -996,6 +1028,184 @@ cip_status cip_get_config(cip_plan* p, int* rows, int* cc, int* blocksA, int* bl
   if (cc) *cc = p->cc;
   if (blocksA) *blocksA = p->blocksA;
   if (blocksB) *blocksB = p->blocksB;
+  return CIP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched launch: many independent plans (uneven N, M, prior) iterated
+// together.  Their iterations are recorded once into a CUDA graph in which
+// every plan is its own branch (fork/join over a few capture streams), so the
+// hardware scheduler packs the small instances' kernels side by side, and the
+// graph (two iterations, which returns every ping-pong buffer to its starting
+// side) is replayed.  The last two iterations run outside the graph with the
+// residual flags so that cip_get_residuals stays valid for every plan.
+// ---------------------------------------------------------------------------
+struct cip_batch {
+  std::vector<cip_plan*> plans;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t cap = nullptr;  // capture stream (recording cannot start on the legacy default stream)
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<std::pair<int, int>> parity;  // (cur, pcur) of every plan when the graph was recorded
+  std::vector<unsigned long long> graph_launches;
+  std::string err;
+};
+
+namespace {
+
+cip_status bfail(cip_batch* b, cip_status s, const std::string& m) {
+  b->err = m;
+  return s;
+}
+
+#define BATCH_CUDA(b, call)                                                                 \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return bfail(b, CIP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+cip_status plan_enqueue(cip_plan* p, cudaStream_t s, int flags) {
+  return DISPATCH_T(p, enqueue_iteration<float>(p, s, flags), enqueue_iteration<double>(p, s, flags));
+}
+
+// one round over all plans: plan i on capture stream i % S, joined back into `s`
+cip_status batch_round(cip_batch* b, cudaStream_t s, int iters, int last_flags) {
+  BATCH_CUDA(b, cudaEventRecord(b->fork, s));
+  for (auto st : b->streams) BATCH_CUDA(b, cudaStreamWaitEvent(st, b->fork, 0));
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    cudaStream_t st = b->streams[i % b->streams.size()];
+    for (int k = 0; k < iters; ++k) {
+      const int flags = (k == iters - 1) ? last_flags : (k == iters - 2 && last_flags ? PA_STORE_T : 0);
+      cip_status r = plan_enqueue(b->plans[i], st, flags);
+      if (r != CIP_OK) return bfail(b, r, std::string("plan ") + std::to_string(i) + ": " + b->plans[i]->err);
+    }
+  }
+  for (size_t j = 0; j < b->streams.size(); ++j) {
+    BATCH_CUDA(b, cudaEventRecord(b->joins[j], b->streams[j]));
+    BATCH_CUDA(b, cudaStreamWaitEvent(s, b->joins[j], 0));
+  }
+  return CIP_OK;
+}
+
+cip_status batch_record(cip_batch* b) {
+  cudaStream_t s = b->cap;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->parity.clear();
+  b->graph_launches.clear();
+  std::vector<unsigned long long> l0;
+  for (auto* p : b->plans) {
+    b->parity.push_back({p->cur, p->pcur});
+    l0.push_back(p->launches);
+  }
+  BATCH_CUDA(b, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cip_status r = batch_round(b, s, 2, 0);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (r != CIP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  BATCH_CUDA(b, e);
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  BATCH_CUDA(b, e);
+  // recording advanced the host-side bookkeeping by two iterations without running them: undo
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    cip_plan* p = b->plans[i];
+    p->iteration -= 2;
+    b->graph_launches.push_back(p->launches - l0[i]);
+    p->launches = l0[i];
+    p->cur = b->parity[i].first;
+    p->pcur = b->parity[i].second;
+  }
+  return CIP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cip_status cip_batch_create(cip_batch** out, cip_plan* const* plans, int n, int nstreams) {
+  if (!out || !plans || n < 1) return CIP_ERR_INVALID_ARG;
+  *out = nullptr;
+  cip_batch* b = new cip_batch();
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i]) {
+      delete b;
+      return CIP_ERR_INVALID_ARG;
+    }
+    b->plans.push_back(plans[i]);
+  }
+  const int ns = std::max(1, std::min(nstreams > 0 ? nstreams : 8, n));
+  b->streams.resize(ns);
+  b->joins.resize(ns);
+  for (int j = 0; j < ns; ++j) {
+    cudaStreamCreateWithFlags(&b->streams[j], cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&b->joins[j], cudaEventDisableTiming);
+  }
+  cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  *out = b;
+  return CIP_OK;
+}
+
+cip_status cip_batch_iterate(cip_batch* b, int iters, void* stream) {
+  if (!b) return CIP_ERR_INVALID_ARG;
+  if (iters < 0) return bfail(b, CIP_ERR_INVALID_ARG, "iters < 0");
+  for (auto* p : b->plans) {
+    cip_status r = check_ready(p, true);
+    if (r != CIP_OK) return bfail(b, r, p->err);
+  }
+  if (iters == 0) return CIP_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the last two iterations (or the only one) run eagerly with the residual flags
+  const int tail = iters >= 2 ? 2 : 1;
+  int body = iters - tail;
+  if (body % 2) {
+    cip_status r = batch_round(b, s, 1, 0);
+    if (r != CIP_OK) return r;
+    --body;
+  }
+  if (body > 0 && !b->exec) {
+    // first use: two eager iterations (every kernel's one-time attribute setup happens outside capture)
+    cip_status r = batch_round(b, s, 2, 0);
+    if (r != CIP_OK) return r;
+    body -= 2;
+  }
+  if (body > 0) {
+    bool ok = b->exec != nullptr && b->parity.size() == b->plans.size();
+    for (size_t i = 0; ok && i < b->plans.size(); ++i)
+      ok = b->parity[i].first == b->plans[i]->cur && b->parity[i].second == b->plans[i]->pcur;
+    if (!ok) {
+      BATCH_CUDA(b, cudaStreamSynchronize(s));  // recording reads no data; order it after queued work
+      cip_status r = batch_record(b);
+      if (r != CIP_OK) return r;
+    }
+    for (int k = 0; k < body / 2; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->exec, s));
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+      b->plans[i]->iteration += body;
+      b->plans[i]->launches += b->graph_launches[i] * (unsigned long long)(body / 2);
+    }
+  }
+  return batch_round(b, s, tail, PA_STORE_T | PA_RESID);
+}
+
+const char* cip_batch_last_error(const cip_batch* b) { return b ? b->err.c_str() : ""; }
+
+cip_status cip_batch_destroy(cip_batch* b) {
+  if (!b) return CIP_ERR_INVALID_ARG;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto st : b->streams) cudaStreamDestroy(st);
+  for (auto ev : b->joins) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
   return CIP_OK;
 }
 

@@ -68,7 +68,7 @@ template <typename T, int MMAX>
 __global__ void __launch_bounds__(256, 3) solve_split_kernel(typename CT<T>::type* __restrict__ colbuf,
                                                                const typename CT<T>::type* __restrict__ pinv,
                                                                const typename CT<T>::type* __restrict__ xb, int N,
-                                                               int M) {
+                                                               int M, int plain) {
   using C = typename CT<T>::type;
   const int k1 = blockIdx.x * 256 + threadIdx.x;
   const int k2 = blockIdx.y;
@@ -84,6 +84,10 @@ __global__ void __launch_bounds__(256, 3) solve_split_kernel(typename CT<T>::typ
     if (i < M) {
       r[i] = col[(size_t)i * CP];
       x[i] = xcol[(size_t)i * CP];
+      if (plain) {  // plain FP32 method: X = Pinv (b + Q)
+        r[i] = cadd(r[i], x[i]);
+        x[i] = mk<C>(0.0, 0.0);
+      }
     }
   }
   int pk = 0;
@@ -140,12 +144,12 @@ cudaError_t colfft_n(const typename CT<T>::type* src, typename CT<T>::type* dst,
 
 template <typename T>
 cudaError_t solve_m(typename CT<T>::type* colbuf, const typename CT<T>::type* pinv, const typename CT<T>::type* xb,
-                    int N, int M, cudaStream_t s) {
+                    int N, int M, int plain, cudaStream_t s) {
   dim3 grid((N + 255) / 256, N / 2 + 1);
-  if (M <= 4) solve_split_kernel<T, 4><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M);
-  else if (M <= 8) solve_split_kernel<T, 8><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M);
-  else if (M <= 12) solve_split_kernel<T, 12><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M);
-  else if (M <= 16) solve_split_kernel<T, 16><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M);
+  if (M <= 4) solve_split_kernel<T, 4><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M, plain);
+  else if (M <= 8) solve_split_kernel<T, 8><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M, plain);
+  else if (M <= 12) solve_split_kernel<T, 12><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M, plain);
+  else if (M <= 16) solve_split_kernel<T, 16><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M, plain);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
@@ -157,7 +161,7 @@ cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colb
                                int* launches) {
   cudaError_t e = colfft_n<T, -1>(a.qh, colbuf, a.tw, N, a.M, s);
   if (e != cudaSuccess) return e;
-  e = solve_m<T>(colbuf, a.pinv, a.bhat, N, a.M, s);
+  e = solve_m<T>(colbuf, a.pinv, a.bhat, N, a.M, a.plain, s);
   if (e != cudaSuccess) return e;
   e = colfft_n<T, +1>(colbuf, a.xh, a.tw, N, a.M, s);
   if (launches) *launches += 3;

@@ -325,3 +325,120 @@ template cudaError_t launch_spectra_store<float>(const double2*, float2*, size_t
 template cudaError_t launch_spectra_store<double>(const double2*, double2*, size_t, cudaStream_t);
 
 }  // namespace cip
+
+// ---------------------------------------------------------------------------
+// The plain FP32 method (comparison baseline for the mixed-precision path):
+// Psi formed and inverted in FP32 (complex64 Cholesky) from the PSF spectra
+// rounded to complex64, and b = beta Lambda^H yhat in FP32; the column pass
+// then applies x = Psi^{-1} (b + Q) every iteration.
+// ---------------------------------------------------------------------------
+namespace cip {
+namespace {
+
+__global__ void __launch_bounds__(128) factor_fp32_kernel(const double2* __restrict__ lam, const double* __restrict__ gs,
+                                                          int use_g, int K, int M, int N, float rho, float beta,
+                                                          float2* __restrict__ pinv, int* list, int cap) {
+  const int H = N / 2 + 1, P = half_pitch(N);
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= N * H) return;
+  const int k1 = bin / H, k2 = bin - k1 * H;
+  const size_t off = (size_t)k1 * P + k2, mplane = (size_t)N * P;
+  const float g = use_g ? (float)(gs[k1] + gs[k2]) : 1.0f;
+  if (g == 0.0f) {
+    push_bin(list, cap, bin);
+    return;
+  }
+  float2 L[kMaxM][kMaxM];
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j <= i; ++j) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int k = 0; k < K; ++k) {
+        const double2 a = lam[(size_t)(k * M + i) * mplane + off], b = lam[(size_t)(k * M + j) * mplane + off];
+        cfmac(acc, make_float2((float)a.x, (float)a.y), make_float2((float)b.x, (float)b.y));
+      }
+      acc.x *= beta;
+      acc.y *= beta;
+      if (i == j) {
+        acc.x += rho * g;
+        acc.y = 0.f;
+      }
+      L[i][j] = acc;
+    }
+  for (int j = 0; j < M; ++j) {
+    float d = L[j][j].x;
+    for (int k = 0; k < j; ++k) d -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
+    if (!(d > 0.f)) {
+      push_bin(list, cap, bin);
+      return;
+    }
+    const float ljj = sqrtf(d), inv = 1.0f / ljj;
+    L[j][j] = make_float2(ljj, 0.f);
+    for (int i = j + 1; i < M; ++i) {
+      float2 s = L[i][j];
+      for (int k = 0; k < j; ++k) {
+        const float2 a = L[i][k], b = L[j][k];
+        s.x -= a.x * b.x + a.y * b.y;
+        s.y -= a.y * b.x - a.x * b.y;
+      }
+      L[i][j] = make_float2(s.x * inv, s.y * inv);
+    }
+  }
+  float2 W[kMaxM][kMaxM];
+  for (int i = 0; i < M; ++i) {
+    const float inv = 1.0f / L[i][i].x;
+    W[i][i] = make_float2(inv, 0.f);
+    for (int j = 0; j < i; ++j) {
+      float2 s = make_float2(0.f, 0.f);
+      for (int k = j; k < i; ++k) cfma(s, L[i][k], W[k][j]);
+      W[i][j] = make_float2(-s.x * inv, -s.y * inv);
+    }
+  }
+  const float sc = 1.0f / ((float)N * (float)N);
+  const size_t colbase = (size_t)k2 * (M * (M + 1) / 2) * col_pitch(N) + k1;
+  int pk = 0;
+  for (int i = 0; i < M; ++i)
+    for (int j = i; j < M; ++j) {
+      float2 s = make_float2(0.f, 0.f);
+      for (int k = j; k < M; ++k) cfmac(s, W[k][i], W[k][j]);
+      if (i == j) s.y = 0.f;
+      pinv[colbase + (size_t)pk * col_pitch(N)] = make_float2(s.x * sc, s.y * sc);
+      ++pk;
+    }
+}
+
+__global__ void rhs_fp32_kernel(const double2* __restrict__ lam, const double2* __restrict__ yhat, int K, int M,
+                                int N, float beta, float2* __restrict__ b) {
+  const int H = N / 2 + 1, P = half_pitch(N);
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= N * H) return;
+  const int k1 = bin / H, k2 = bin - k1 * H;
+  const size_t off = (size_t)k1 * P + k2, mplane = (size_t)N * P;
+  for (int m = 0; m < M; ++m) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) {
+      const double2 l = lam[(size_t)(k * M + m) * mplane + off], y = yhat[(size_t)k * mplane + off];
+      cfmac(acc, make_float2((float)l.x, (float)l.y), make_float2((float)y.x, (float)y.y));
+    }
+    b[((size_t)k2 * M + m) * col_pitch(N) + k1] = make_float2(beta * acc.x, beta * acc.y);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_factor_fp32(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
+                               double beta, float2* pinv, int* pinv_list, int list_cap, cudaStream_t s) {
+  if (M > kMaxM) return cudaErrorInvalidValue;
+  const int nb = N * (N / 2 + 1);
+  factor_fp32_kernel<<<(nb + 127) / 128, 128, 0, s>>>(lam, gs, use_g, K, M, N, (float)rho, (float)beta, pinv,
+                                                     pinv_list, list_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_fp32(const double2* lam, const double2* yhat, int K, int M, int N, double beta, float2* b,
+                            cudaStream_t s) {
+  const int nb = N * (N / 2 + 1);
+  rhs_fp32_kernel<<<(nb + 255) / 256, 256, 0, s>>>(lam, yhat, K, M, N, (float)beta, b);
+  return cudaGetLastError();
+}
+
+}  // namespace cip

@@ -44,7 +44,14 @@ template <typename T> struct PassBArgs {
   const C* bhat;    // [N/2+1][M][N]: xb = Psi^{-1} beta Lambda^H F y / N^2 (FP64-formed)
   const C* tw;
   int M;
+  int plain;        // 1: plain FP32 method, bhat holds b = beta Lambda^H F y and X = Pinv (b + Q)
 };
+
+// plain FP32 method: factor formed and inverted in FP32, b = beta Lambda^H F y in FP32
+cudaError_t launch_factor_fp32(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
+                               double beta, float2* pinv, int* pinv_list, int list_cap, cudaStream_t s);
+cudaError_t launch_rhs_fp32(const double2* lam, const double2* yhat, int K, int M, int N, double beta, float2* b,
+                            cudaStream_t s);
 
 // Convolutional-dictionary column solve (Eqs. solx_synt_DFT, solz_DFT, solz_DFT_SM), one
 // thread per (frequency, channel).  Column layout [k2][plane][col_pitch(N)].

@@ -111,6 +111,10 @@ __global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
         const C* peer = cluster.map_shared_rank(buf, i);
         r[i] = peer[spad(b)];
         x[i] = xcol[(size_t)i * CP];
+        if (a.plain) {  // plain FP32 method: X = Pinv (b + Q)
+          r[i] = cadd(r[i], x[i]);
+          x[i] = mk<C>(0.0, 0.0);
+        }
       }
     }
     int pk = 0;

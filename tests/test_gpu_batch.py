@@ -1,0 +1,105 @@
+"""Batched launch (cip_batch: one CUDA graph, one branch per plan) and the plain FP32
+comparison mode.  GPU only."""
+import numpy as np
+import pytest
+
+from oracle import fast
+from paper_2006_08303_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+MIX = [("tv", 64, 3, 3), ("dct8", 128, 5, 5), ("l1", 256, 1, 1), ("tv", 256, 2, 3), ("dct8", 64, 3, 2),
+       ("tv", 128, 10, 10)]
+
+
+def build(torch, prior, N, K, M, seed, **kw):
+    from paper_2006_08303_gb300 import api
+    rng = np.random.default_rng(seed)
+    x = inputs.rectangles_image(rng, N, M, n_rect=5)
+    h = inputs.gaussian_psf_bank(N, K, M)
+    y, _ = inputs.measure(rng, x, h, 30.0)
+    lam, rho = (1e-2, 1.0) if prior != "dct8" else (1e-3, 0.1)
+    P = api.Plan(N, K, M, "f32", **kw)
+    P.set_prior(prior, lam, rho, 1.0)
+    P.set_psfs(torch.as_tensor(h, dtype=torch.float32).cuda())
+    P.set_measurements(torch.as_tensor(y, dtype=torch.float32).cuda())
+    return P, (h, y, prior, lam, rho)
+
+
+def test_batch_equals_separate_plans(torch):
+    """Every plan of a mixed batch ends bitwise where it would alone, through the eager head, the
+    graph replays and the residual tail, and again after re-using the recorded graph."""
+    from paper_2006_08303_gb300 import api
+    solo = [build(torch, *c, seed=i)[0] for i, c in enumerate(MIX)]
+    batch_plans = [build(torch, *c, seed=i)[0] for i, c in enumerate(MIX)]
+    B = api.Batch(batch_plans, nstreams=3)
+    B.iterate(23)
+    for P in solo:
+        P.iterate(23)
+    torch.cuda.synchronize()
+    for a, b in zip(solo, batch_plans):
+        assert np.array_equal(a.get_x().cpu().numpy(), b.get_x().cpu().numpy())
+        assert a.residuals() == b.residuals()
+        assert b.iteration() == 23
+    B.iterate(10)
+    for P in solo:
+        P.iterate(10)
+    for a, b in zip(solo, batch_plans):
+        assert np.array_equal(a.get_x().cpu().numpy(), b.get_x().cpu().numpy())
+        assert np.array_equal(a.get_u().cpu().numpy(), b.get_u().cpu().numpy())
+    B.close()
+    for P in solo + batch_plans:
+        P.close()
+
+
+def test_batch_matches_oracle(torch):
+    from paper_2006_08303_gb300 import api
+    P, (h, y, prior, lam, rho) = build(torch, "tv", 128, 3, 3, seed=7)
+    Q, _ = build(torch, "dct8", 64, 2, 2, seed=8)
+    B = api.Batch([P, Q])
+    B.iterate(30)
+    S = fast.analysis_setup(h, y, prior, lam, rho, 1.0)
+    x_or, _, _, _, _ = fast.run_analysis(S, 30)
+    assert rel(P.get_x().double().cpu().numpy(), x_or) <= 1e-4
+    B.close()
+    P.close()
+    Q.close()
+
+
+def test_plain_fp32_method_is_less_accurate_on_ill_conditioned_bins(torch):
+    """The plain FP32 method (factor formed and applied in FP32) versus the mixed path on the
+    spectral DCT instance (rho = 1e-2, kappa(Psi) ~ 1e4): both run, the mixed path stays within the
+    per-step bound and is several times more accurate."""
+    from paper_2006_08303_gb300 import api
+    Pr = inputs.spectral_dct(N=256, M=10)
+    S = fast.analysis_setup(Pr.h, Pr.y, Pr.prior, Pr.lam, Pr.rho, Pr.beta)
+    t = np.zeros((Pr.M, 1, Pr.N, Pr.N))
+    u = np.zeros_like(t)
+    for _ in range(10):
+        _, t, u, _ = fast.analysis_step(S, t, u)
+    x1, _, _, _ = fast.analysis_step(S, t, u)
+    errs = {}
+    for plain in (False, True):
+        P = api.Plan(Pr.N, Pr.K, Pr.M, "f32", plain_fp32=plain)
+        P.set_prior(Pr.prior, Pr.lam, Pr.rho, Pr.beta)
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+        P.set_psfs(f(Pr.h))
+        P.set_measurements(f(Pr.y))
+        P.state_import(f(t), f(u))
+        P.iterate(1)
+        errs[plain] = rel(P.get_x().double().cpu().numpy(), x1)
+        P.close()
+    assert errs[False] <= 1e-5
+    assert errs[True] > 3 * errs[False], errs
