@@ -87,6 +87,11 @@ const char* cip_last_error(const cip_plan* plan); /* plan may be NULL: last erro
  * N a power of two in [64, 2048]).  Allocates all device buffers on the
  * current device.  opt may be NULL. */
 cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype, const cip_options* opt);
+/* Same, with the plan's buffers allocated in stream order on `stream` (the stream-ordered
+ * allocator); every later call allocates and frees on its own stream and cip_plan_destroy frees
+ * on the stream of the plan's last call, so no call synchronises the whole device. */
+cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dtype dtype, const cip_options* opt,
+                                     void* stream);
 cip_status cip_plan_destroy(cip_plan* plan);
 
 /* Device bytes a plan with these sizes holds (for admission by HBM budget). */
@@ -184,6 +189,46 @@ cip_status cip_batch_create(cip_batch** out, cip_plan* const* plans, int n, int 
 cip_status cip_batch_iterate(cip_batch* batch, int iters, void* stream);
 const char* cip_batch_last_error(const cip_batch* batch);
 cip_status cip_batch_destroy(cip_batch* batch);
+
+/* Request server: continuous batching of reconstructions on the current device.
+ * Requests (analysis priors, float32) are queued at submit; a worker thread
+ * admits them in arrival order whenever fewer than max_active are running and
+ * their device memory fits hbm_budget (cached factors are evicted least recently
+ * used to make room), runs each on its own stream in chunks of check_every
+ * iterations ending with the relative-residual test of cip_iterate (tol), and
+ * retires it when it converges or reaches max_iter: x is written to x_out and its
+ * memory is released for the next request.  Running requests' kernels overlap on
+ * the device.  Requests with the same nonzero psf_key and the same (N, K, M, prior,
+ * rho, beta) share one factor (formed once, then copied).  h and y are copied at
+ * submit; x_out must stay valid until the request is done. */
+typedef struct cip_server cip_server;
+typedef struct cip_request {
+  int N, K, M;
+  int prior;                      /* CIP_PRIOR_TV, CIP_PRIOR_DCT8 or CIP_PRIOR_L1 */
+  double lambda, rho, beta;
+  const float* h;                 /* host [K][M][N][N] */
+  const float* y;                 /* host [K][N][N] */
+  float* x_out;                   /* host [M][N][N], written when the request is done */
+  double tol;                     /* relative primal/dual residual stop; <= 0: run max_iter */
+  int max_iter;
+  unsigned long long psf_key;     /* 0 = no factor sharing */
+} cip_request;
+typedef struct cip_result {
+  int state;                      /* 0 queued, 1 running, 2 done, 3 failed, 4 cancelled */
+  int status;                     /* cip_status of a failed request */
+  int iterations;
+  double r_rel, s_rel;            /* relative residuals at the last check */
+  double t_submit, t_admit, t_done; /* seconds since the server was created */
+} cip_result;
+cip_status cip_server_create(cip_server** out, size_t hbm_budget, int max_active, int check_every);
+cip_status cip_server_submit(cip_server* srv, const cip_request* req, unsigned long long* id);
+cip_status cip_server_poll(cip_server* srv, unsigned long long id, cip_result* res);
+/* Blocks until the request is done, failed or cancelled (CIP_ERR_TIMEOUT after timeout_s). */
+cip_status cip_server_wait(cip_server* srv, unsigned long long id, cip_result* res, double timeout_s);
+cip_status cip_server_cancel(cip_server* srv, unsigned long long id);
+cip_status cip_server_stats(cip_server* srv, double* voxel_iters, int* running, int* queued, size_t* bytes_in_use,
+                            int* cache_hits, int* cache_misses);
+cip_status cip_server_destroy(cip_server* srv);
 
 /* Shrinkage, dual update and residual norms of one ADMM iteration without any
  * device allocation.  The paper has no counterpart: this exists for callers

@@ -23,8 +23,30 @@ class cip_options(ctypes.Structure):
                 ("reserved", c_int * 12)]
 
 
+class cip_request(ctypes.Structure):
+    _fields_ = [("N", c_int), ("K", c_int), ("M", c_int), ("prior", c_int), ("lam", c_double), ("rho", c_double),
+                ("beta", c_double), ("h", c_void_p), ("y", c_void_p), ("x_out", c_void_p), ("tol", c_double),
+                ("max_iter", c_int), ("psf_key", ctypes.c_ulonglong)]
+
+
+class cip_result(ctypes.Structure):
+    _fields_ = [("state", c_int), ("status", c_int), ("iterations", c_int), ("r_rel", c_double),
+                ("s_rel", c_double), ("t_submit", c_double), ("t_admit", c_double), ("t_done", c_double)]
+
+
+P_ull = ctypes.POINTER(ctypes.c_ulonglong)
+
 # name -> (restype, argtypes)
 SIGNATURES = {
+    "cip_plan_create_on_stream": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int,
+                                          ctypes.POINTER(cip_options), c_void_p]),
+    "cip_server_create": (c_int, [ctypes.POINTER(c_void_p), c_size_t, c_int, c_int]),
+    "cip_server_submit": (c_int, [c_void_p, ctypes.POINTER(cip_request), P_ull]),
+    "cip_server_poll": (c_int, [c_void_p, ctypes.c_ulonglong, ctypes.POINTER(cip_result)]),
+    "cip_server_wait": (c_int, [c_void_p, ctypes.c_ulonglong, ctypes.POINTER(cip_result), c_double]),
+    "cip_server_cancel": (c_int, [c_void_p, ctypes.c_ulonglong]),
+    "cip_server_stats": (c_int, [c_void_p, P_double, P_int, P_int, P_size, P_int, P_int]),
+    "cip_server_destroy": (c_int, [c_void_p]),
     "cip_version": (c_char_p, []),
     "cip_status_string": (c_char_p, [c_int]),
     "cip_last_error": (c_char_p, [c_void_p]),

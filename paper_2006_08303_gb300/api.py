@@ -271,6 +271,78 @@ class Batch:
             pass
 
 
+RESULT_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
+
+
+class Server:
+    """cip_server: continuous batching of reconstructions with admission by device-memory budget."""
+
+    def __init__(self, hbm_budget: int, max_active: int = 16, check_every: int = 10):
+        self._L = _lib.load()
+        h = ctypes.c_void_p()
+        st = self._L.cip_server_create(ctypes.byref(h), int(hbm_budget), max_active, check_every)
+        if st != 0:
+            raise CipError(st, "cip_server_create failed")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, h, y, prior: str, lam: float, rho: float, beta: float = 1.0, tol: float = 0.0,
+               max_iter: int = 300, psf_key: int = 0):
+        """Queue one reconstruction (float32 host arrays h [K][M][N][N], y [K][N][N]); returns (id, x_out)."""
+        h = np.ascontiguousarray(h, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        K, M, N = h.shape[0], h.shape[1], h.shape[-1]
+        x_out = np.zeros((M, N, N), dtype=np.float32)
+        req = _lib.cip_request(N, K, M, PRIORS[prior], lam, rho, beta, h.ctypes.data, y.ctypes.data,
+                               x_out.ctypes.data, tol, max_iter, psf_key)
+        rid = ctypes.c_ulonglong()
+        st = self._L.cip_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid))
+        if st != 0:
+            raise CipError(st, "cip_server_submit failed")
+        self._keep[rid.value] = x_out
+        return rid.value, x_out
+
+    @staticmethod
+    def _res(r):
+        return {"state": RESULT_STATES.get(r.state, "?"), "status": r.status, "iterations": r.iterations,
+                "r_rel": r.r_rel, "s_rel": r.s_rel, "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done}
+
+    def poll(self, rid: int):
+        r = _lib.cip_result()
+        st = self._L.cip_server_poll(self._h, rid, ctypes.byref(r))
+        if st != 0:
+            raise CipError(st, "cip_server_poll failed")
+        return self._res(r)
+
+    def wait(self, rid: int, timeout: float = 600.0):
+        r = _lib.cip_result()
+        st = self._L.cip_server_wait(self._h, rid, ctypes.byref(r), timeout)
+        if st not in (0, 6):
+            raise CipError(st, "cip_server_wait failed")
+        return self._res(r)
+
+    def cancel(self, rid: int):
+        self._L.cip_server_cancel(self._h, rid)
+
+    def stats(self):
+        v, run, q, b, hit, miss = (ctypes.c_double(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int(),
+                                   ctypes.c_int())
+        self._L.cip_server_stats(self._h, *[ctypes.byref(x) for x in (v, run, q, b, hit, miss)])
+        return {"voxel_iters": v.value, "running": run.value, "queued": q.value, "bytes_in_use": b.value,
+                "cache_hits": hit.value, "cache_misses": miss.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.cip_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def shrink_dual_noalloc(prior: str, lam: float, rho: float, x, u_in, t_prev, u_out, resid_out, t_out=None,
                         stream=None):
     """cip_shrink_dual_noalloc: t/u update and relative residuals from device tensors the caller owns,

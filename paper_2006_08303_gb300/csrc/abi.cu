@@ -61,6 +61,7 @@ struct cip_plan {
   void* pbuf[2] = {nullptr, nullptr};   // [H][M][CP] p = sum_l theta_l v_l (ping-pong)
   int pcur = 0;
   void* xcol = nullptr;                 // [H][M][CP] x-hat of the last x-update
+  const cip_plan* factor_src = nullptr;  // plan whose factor this plan adopted (serving factor cache)
   // device buffers
   void* xh = nullptr;
   void* qh = nullptr;
@@ -85,6 +86,7 @@ struct cip_plan {
   std::vector<cudaEvent_t> evA, evB;
   int nA = 0, nB = 0;
   unsigned long long launches = 0;  // kernels launched by this plan
+  cudaStream_t ast = nullptr;        // stream of the current call: buffers are allocated and freed on it
   std::string err;
 };
 
@@ -155,49 +157,52 @@ void twiddles(std::vector<double>& re, std::vector<double>& im) {
   }
 }
 
-void free_ptr(void*& q) {
-  if (q) cudaFree(q);
+// Plan buffers use the stream-ordered allocator on the stream of the call that creates or frees
+// them, so that no call implicitly synchronises the device (the request server relies on it).
+void free_ptr(cip_plan* p, void*& q) {
+  if (q) cudaFreeAsync(q, p->ast);
   q = nullptr;
 }
+cudaError_t dmalloc(cip_plan* p, void** q, size_t bytes) { return cudaMallocAsync(q, bytes, p->ast); }
 
 template <typename T> cip_status alloc_state(cip_plan* p) {
   using C = typename CT<T>::type;
   const size_t nc = ncomp_of(p->prior);
   const int S = smaps(p);
   for (int i = 0; i < 2; ++i) {
-    free_ptr(p->u[i]);
-    CIP_CUDA(p, cudaMalloc(&p->u[i], real_elems(p, S) * nc * sizeof(T)));
+    free_ptr(p, p->u[i]);
+    CIP_CUDA(p, dmalloc(p, &p->u[i], real_elems(p, S) * nc * sizeof(T)));
   }
-  free_ptr(p->tprev);
-  CIP_CUDA(p, cudaMalloc(&p->tprev, real_elems(p, S) * nc * sizeof(T)));
+  free_ptr(p, p->tprev);
+  CIP_CUDA(p, dmalloc(p, &p->tprev, real_elems(p, S) * nc * sizeof(T)));
   if (is_cd(p)) {
     // row spectra of v and of rho (t - u) over the coefficient maps, the column buffer and p, x
-    free_ptr(p->xh);
-    free_ptr(p->qh);
-    CIP_CUDA(p, cudaMalloc(&p->xh, half_elems(p, S) * sizeof(C)));
-    CIP_CUDA(p, cudaMalloc(&p->qh, half_elems(p, S) * sizeof(C)));
-    free_ptr(p->colbuf);
-    CIP_CUDA(p, cudaMalloc(&p->colbuf, col_elems(p, S) * sizeof(C)));
+    free_ptr(p, p->xh);
+    free_ptr(p, p->qh);
+    CIP_CUDA(p, dmalloc(p, &p->xh, half_elems(p, S) * sizeof(C)));
+    CIP_CUDA(p, dmalloc(p, &p->qh, half_elems(p, S) * sizeof(C)));
+    free_ptr(p, p->colbuf);
+    CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, S) * sizeof(C)));
     for (int i = 0; i < 2; ++i) {
-      free_ptr(p->pbuf[i]);
-      CIP_CUDA(p, cudaMalloc(&p->pbuf[i], col_elems(p, p->M) * sizeof(C)));
+      free_ptr(p, p->pbuf[i]);
+      CIP_CUDA(p, dmalloc(p, &p->pbuf[i], col_elems(p, p->M) * sizeof(C)));
     }
-    free_ptr(p->xcol);
-    CIP_CUDA(p, cudaMalloc(&p->xcol, col_elems(p, p->M) * sizeof(C)));
-    free_ptr(p->theta);
-    CIP_CUDA(p, cudaMalloc(&p->theta, col_elems(p, p->L) * sizeof(C)));
+    free_ptr(p, p->xcol);
+    CIP_CUDA(p, dmalloc(p, &p->xcol, col_elems(p, p->M) * sizeof(C)));
+    free_ptr(p, p->theta);
+    CIP_CUDA(p, dmalloc(p, &p->theta, col_elems(p, p->L) * sizeof(C)));
   }
-  if (p->pinv) cudaFree(p->pinv);
+  free_ptr(p, p->pinv);
   p->pinv = nullptr;
-  CIP_CUDA(p, cudaMalloc(&p->pinv, col_elems(p, p->M * (p->M + 1) / 2) * sizeof(C)));
-  if (p->pinv64) cudaFree(p->pinv64);
-  p->pinv64 = nullptr;
-  CIP_CUDA(p, cudaMalloc((void**)&p->pinv64, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(double2)));
-  if (p->partials) cudaFree(p->partials);
-  p->partials = nullptr;
+  CIP_CUDA(p, dmalloc(p, &p->pinv, col_elems(p, p->M * (p->M + 1) / 2) * sizeof(C)));
+  {
+    void* q = p->partials;
+    free_ptr(p, q);
+    p->partials = nullptr;
+  }
   p->rowsA = passA_rows<T>(p->N, p->prior);
   p->blocksA = (p->N / p->rowsA) * smaps(p);
-  CIP_CUDA(p, cudaMalloc(&p->partials, (size_t)p->blocksA * kNPart * sizeof(double)));
+  CIP_CUDA(p, dmalloc(p, (void**)&p->partials, (size_t)p->blocksA * kNPart * sizeof(double)));
   return CIP_OK;
 }
 
@@ -236,6 +241,9 @@ cip_status stage_in(cip_plan* p, const void* src, size_t bytes, cudaStream_t s, 
 
 template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
   using C = typename CT<T>::type;
+  if (!p->lam64) return fail(p, CIP_ERR_STATE, "the PSF spectra were released (cip_set_psfs again)");
+  if (!p->pinv64)
+    CIP_CUDA(p, dmalloc(p, (void**)&p->pinv64, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(double2)));
   CIP_CUDA(p, cudaMemsetAsync(p->pinv_list, 0, sizeof(int), s));
   const int use_g = p->prior == CIP_PRIOR_TV ? 1 : 0;
   // analysis: Psi = rho g I + beta Lambda^H Lambda; dictionary: t I + beta Lambda^H Lambda with t = 1
@@ -305,6 +313,8 @@ template <typename T> cip_status do_set_psfs(cip_plan* p, const void* h, cudaStr
   const void* dh = nullptr;
   cip_status r = stage_in(p, h, bytes, s, st, &dh);
   if (r != CIP_OK) return r;
+  if (!p->lam64) CIP_CUDA(p, dmalloc(p, (void**)&p->lam64, half_elems(p, p->K * p->M) * sizeof(double2)));
+  p->factor_src = nullptr;
   const int nrows = p->K * p->M * p->N;
   CIP_LAUNCH(p, (launch_row_r2c<double, T>(static_cast<const T*>(dh), p->lam64, p->N, nrows, 1.0, p->tw64, s)));
   CIP_LAUNCH(p, launch_col_c2c<double>(p->lam64, p->N, p->K * p->M, -1, p->tw64, s));
@@ -324,14 +334,17 @@ template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream
   cip_status r = stage_in(p, y, bytes, s, st, &dy);
   if (r != CIP_OK) return r;
   double2* yhat = nullptr;
+  // spectra and FP64 factor: the plan's own, or those of the plan its factor was adopted from
+  const cip_plan* fs = p->factor_src ? p->factor_src : p;
+  if (!fs->lam64 || !fs->pinv64) return fail(p, CIP_ERR_STATE, "the PSF spectra were released (cip_set_psfs again)");
   CIP_CUDA(p, cudaMallocAsync((void**)&yhat, half_elems(p, p->K) * sizeof(double2), s));
   cudaError_t e = launch_row_r2c<double, T>(static_cast<const T*>(dy), yhat, p->N, p->K * p->N, 1.0, p->tw64, s);
   if (e == cudaSuccess) e = launch_col_c2c<double>(yhat, p->N, p->K, -1, p->tw64, s);
   if (e == cudaSuccess) {
     if (p->opt.precision == 1)
-      e = launch_rhs_fp32(p->lam64, yhat, p->K, p->M, p->N, p->beta, reinterpret_cast<float2*>(p->bhat), s);
+      e = launch_rhs_fp32(fs->lam64, yhat, p->K, p->M, p->N, p->beta, reinterpret_cast<float2*>(p->bhat), s);
     else
-      e = launch_rhs<T>(p->lam64, yhat, p->pinv64, p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
+      e = launch_rhs<T>(fs->lam64, yhat, fs->pinv64, p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
   }
   if (e == cudaSuccess) p->launches += 3;
   cudaFreeAsync(yhat, s);
@@ -423,11 +436,11 @@ template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
       p->colmode = it->second.first;
       p->cc = it->second.second;
       // a cached choice of the split form still needs this plan's own column buffer
-      if (p->colmode == 2 && !p->colbuf) CIP_CUDA(p, cudaMalloc(&p->colbuf, col_elems(p, p->M) * sizeof(C)));
+      if (p->colmode == 2 && !p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
       return CIP_OK;
     }
   }
-  if (!p->colbuf) CIP_CUDA(p, cudaMalloc(&p->colbuf, col_elems(p, p->M) * sizeof(C)));
+  if (!p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
   std::vector<std::pair<int, int>> cands = {{1, 1}, {1, 2}, {1, 4}, {2, 0}};
   cudaEvent_t e0, e1;
   CIP_CUDA(p, cudaEventCreate(&e0));
@@ -484,6 +497,8 @@ void ensure_events(cip_plan* p) {
 }
 
 template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double tol, int* done, cudaStream_t s) {
+  if (tol > 0 && !p->resid_host)
+    CIP_CUDA(p, cudaMallocHost((void**)&p->resid_host, (kNPart + 2) * sizeof(double)));
   const int ce = p->opt.check_every > 0 ? p->opt.check_every : 10;
   int it = 0;
   bool stop = false;
@@ -680,12 +695,18 @@ size_t cip_plan_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior) {
 }
 
 cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype, const cip_options* opt) {
+  return cip_plan_create_on_stream(out, N, K, M, dtype, opt, nullptr);
+}
+
+cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dtype dtype, const cip_options* opt,
+                                     void* stream) {
   if (!out) return fail(nullptr, CIP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!valid_n(N)) return fail(nullptr, CIP_ERR_UNSUPPORTED, "N must be a power of two in [64, 2048]");
   if (K < 1 || K > 16 || M < 1 || M > 16) return fail(nullptr, CIP_ERR_UNSUPPORTED, "K and M must be in [1, 16]");
   if (dtype != CIP_F32 && dtype != CIP_F64) return fail(nullptr, CIP_ERR_INVALID_ARG, "bad dtype");
   cip_plan* p = new cip_plan();
+  p->ast = static_cast<cudaStream_t>(stream);
   p->N = N;
   p->K = K;
   p->M = M;
@@ -721,7 +742,7 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
   }
 #define ALLOC(ptr, bytes)                                                                       \
   do {                                                                                          \
-    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                                       \
+    cudaError_t e_ = cudaMallocAsync((void**)&(ptr), (bytes), p->ast);                          \
     if (e_ != cudaSuccess) {                                                                    \
       cip_plan_destroy(p);                                                                      \
       return fail(nullptr, CIP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e_)); \
@@ -730,7 +751,6 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
   ALLOC(p->xh, half_elems(p, M) * ce);
   ALLOC(p->qh, half_elems(p, M) * ce);
   ALLOC(p->bhat, col_elems(p, M) * ce);
-  ALLOC(p->lam64, half_elems(p, K * M) * sizeof(double2));
   ALLOC(p->tw, (size_t)kTwN * ce);
   ALLOC(p->tw64, (size_t)kTwN * sizeof(double2));
   ALLOC(p->gs, (size_t)N * sizeof(double));
@@ -739,10 +759,6 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
   ALLOC(p->pinv_list, (1 + kPinvListCap) * sizeof(int));
   if (p->colmode == 2) ALLOC(p->colbuf, col_elems(p, M) * ce);
 #undef ALLOC
-  if (cudaMallocHost((void**)&p->resid_host, (kNPart + 2) * sizeof(double)) != cudaSuccess) {
-    cip_plan_destroy(p);
-    return fail(nullptr, CIP_ERR_OOM, "cudaMallocHost failed");
-  }
   std::vector<double> re, im;
   twiddles(re, im);
   std::vector<double2> t64(kTwN);
@@ -758,7 +774,8 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
     gs[k] = 4.0 * sn * sn;
   }
   gs[0] = 0.0;
-  cudaError_t e = cudaMemcpy(p->tw64, t64.data(), kTwN * sizeof(double2), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaStreamSynchronize(p->ast);  // buffers valid on every stream from here on
+  if (e == cudaSuccess) e = cudaMemcpy(p->tw64, t64.data(), kTwN * sizeof(double2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = dtype == CIP_F64 ? cudaMemcpy(p->tw, t64.data(), kTwN * sizeof(double2), cudaMemcpyHostToDevice)
                          : cudaMemcpy(p->tw, t32.data(), kTwN * sizeof(float2), cudaMemcpyHostToDevice);
@@ -777,7 +794,7 @@ cip_status cip_plan_destroy(cip_plan* p) {
                   p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
-    if (b) cudaFree(b);
+    if (b) cudaFreeAsync(b, p->ast);
   if (p->resid_host) cudaFreeHost(p->resid_host);
   for (auto& ev : p->evA) cudaEventDestroy(ev);
   for (auto& ev : p->evB) cudaEventDestroy(ev);
@@ -803,6 +820,7 @@ cip_status cip_set_prior(cip_plan* p, cip_prior prior, double lambda, double rho
   p->rho = rho;
   p->beta = beta;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   p->have_y = false;  // the data term depends on the factor: set_measurements again
   return DISPATCH_T(p, do_set_prior<float>(p, s), do_set_prior<double>(p, s));
 }
@@ -811,6 +829,7 @@ cip_status cip_set_psfs(cip_plan* p, const void* h, void* stream) {
   if (!p || !h) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
   if (p->prior < 0) return fail(p, CIP_ERR_STATE, "cip_set_prior must precede cip_set_psfs");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   cip_status r = DISPATCH_T(p, do_set_psfs<float>(p, h, s), do_set_psfs<double>(p, h, s));
   if (r == CIP_OK) p->have_y = false;
   return r;
@@ -821,6 +840,7 @@ cip_status cip_set_measurements(cip_plan* p, const void* y, void* stream) {
   cip_status r = check_ready(p, false);
   if (r != CIP_OK) return r;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   return DISPATCH_T(p, do_set_y<float>(p, y, s), do_set_y<double>(p, y, s));
 }
 
@@ -828,6 +848,7 @@ cip_status cip_reset_state(cip_plan* p, void* stream) {
   cip_status r = check_ready(p, false);
   if (r != CIP_OK) return r;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   return DISPATCH_T(p, reset_state<float>(p, s), reset_state<double>(p, s));
 }
 
@@ -837,6 +858,7 @@ cip_status cip_iterate(cip_plan* p, int max_iter, double tol, int* iters_done, v
   if (max_iter < 0) return fail(p, CIP_ERR_INVALID_ARG, "max_iter < 0");
   if (p->timing) ensure_events(p);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   return DISPATCH_T(p, iterate_impl<float>(p, max_iter, tol, iters_done, s),
                     iterate_impl<double>(p, max_iter, tol, iters_done, s));
 }
@@ -846,6 +868,7 @@ cip_status cip_get_x(cip_plan* p, void* x, void* stream) {
   cip_status r = check_ready(p, false);
   if (r != CIP_OK) return r;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   return DISPATCH_T(p, get_x_impl<float>(p, x, s), get_x_impl<double>(p, x, s));
 }
 
@@ -853,8 +876,8 @@ cip_status cip_get_u(cip_plan* p, void* u, void* stream) {
   if (!p || !u) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
   cip_status r = check_ready(p, false);
   if (r != CIP_OK) return r;
-  return copy_out(p, u, p->u[p->cur], real_elems(p, smaps(p)) * ncomp_of(p->prior) * p->esz,
-                  static_cast<cudaStream_t>(stream));
+  p->ast = static_cast<cudaStream_t>(stream);
+  return copy_out(p, u, p->u[p->cur], real_elems(p, smaps(p)) * ncomp_of(p->prior) * p->esz, p->ast);
 }
 
 cip_status cip_set_dictionary(cip_plan* p, const void* filters, int L, int P, void* stream) {
@@ -867,6 +890,7 @@ cip_status cip_set_dictionary(cip_plan* p, const void* filters, int L, int P, vo
   p->Pf = P;
   p->have_y = false;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   return DISPATCH_T(p, do_set_dictionary<float>(p, filters, s), do_set_dictionary<double>(p, filters, s));
 }
 
@@ -876,6 +900,7 @@ cip_status cip_get_coefficients(cip_plan* p, void* z, void* stream) {
   if (r != CIP_OK) return r;
   if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "coefficient maps exist only for CIP_PRIOR_CONVDICT");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   return DISPATCH_T(p, rows_out<float>(p, p->xh, smaps(p), z, s), rows_out<double>(p, p->xh, smaps(p), z, s));
 }
 
@@ -885,6 +910,7 @@ cip_status cip_state_import_coefficients(cip_plan* p, const void* z, const void*
   if (r != CIP_OK) return r;
   if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "coefficient maps exist only for CIP_PRIOR_CONVDICT");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   r = DISPATCH_T(p, import_z<float>(p, z, s), import_z<double>(p, z, s));
   if (r != CIP_OK) return r;
   return DISPATCH_T(p, import_impl<float>(p, t, u, s), import_impl<double>(p, t, u, s));
@@ -911,6 +937,7 @@ cip_status cip_state_import(cip_plan* p, const void* t, const void* u, void* str
   cip_status r = check_ready(p, false);
   if (r != CIP_OK) return r;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   return DISPATCH_T(p, import_impl<float>(p, t, u, s), import_impl<double>(p, t, u, s));
 }
 
@@ -943,6 +970,7 @@ cip_status cip_state_export(cip_plan* p, void* buf, void* stream) {
   if (r != CIP_OK) return r;
   if (!buf) return fail(p, CIP_ERR_INVALID_ARG, "null buffer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   const bool dev = is_device_ptr(buf);
   const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   char* b = static_cast<char*>(buf);
@@ -964,6 +992,7 @@ cip_status cip_state_restore(cip_plan* p, const void* buf, void* stream) {
   if (r != CIP_OK) return r;
   if (!buf) return fail(p, CIP_ERR_INVALID_ARG, "null buffer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
   const bool dev = is_device_ptr(buf);
   const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const char* b = static_cast<const char*>(buf);
@@ -1210,3 +1239,67 @@ cip_status cip_batch_destroy(cip_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal operations for the request server (plan_internal.h)
+// ---------------------------------------------------------------------------
+#include "plan_internal.h"
+
+namespace cip {
+
+cip_status plan_iterate_async(cip_plan* p, int k, cudaStream_t s, double* host_resid, cudaEvent_t ev) {
+  cip_status r = check_ready(p, true);
+  if (r != CIP_OK) return r;
+  if (k < 1) return fail(p, CIP_ERR_INVALID_ARG, "k < 1");
+  for (int i = 0; i < k; ++i) {
+    const int flags = (i == k - 1) ? (PA_STORE_T | PA_RESID) : (i == k - 2 ? PA_STORE_T : 0);
+    r = plan_enqueue(p, s, flags);
+    if (r != CIP_OK) return r;
+  }
+  CIP_CUDA(p, cudaMemcpyAsync(host_resid, p->resid + kNPart, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CIP_CUDA(p, cudaEventRecord(ev, s));
+  return CIP_OK;
+}
+
+cip_status plan_adopt_factor(cip_plan* dst, const cip_plan* src, cudaStream_t s) {
+  if (!dst || !src) return CIP_ERR_INVALID_ARG;
+  dst->ast = s;
+  if (dst->N != src->N || dst->K != src->K || dst->M != src->M || dst->dtype != src->dtype ||
+      dst->prior != src->prior || dst->rho != src->rho || dst->beta != src->beta ||
+      dst->opt.precision != src->opt.precision || is_cd(dst))
+    return fail(dst, CIP_ERR_INVALID_ARG, "factor source has a different shape or parameters");
+  if (!src->have_psfs || !src->lam64 || !src->pinv64) return fail(dst, CIP_ERR_STATE, "factor source has no factor");
+  const size_t bytes = col_elems(dst, dst->M * (dst->M + 1) / 2) * 2 * dst->esz;
+  CIP_CUDA(dst, cudaMemcpyAsync(dst->pinv, src->pinv, bytes, cudaMemcpyDeviceToDevice, s));
+  dst->factor_src = src;
+  dst->have_psfs = true;
+  dst->have_y = false;
+  return DISPATCH_T(dst, reset_state<float>(dst, s), reset_state<double>(dst, s));
+}
+
+cip_status plan_trim(cip_plan* p) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  if (p->lam64) cudaFreeAsync(p->lam64, p->ast);
+  if (p->pinv64) cudaFreeAsync(p->pinv64, p->ast);
+  p->lam64 = nullptr;
+  p->pinv64 = nullptr;
+  p->factor_src = nullptr;
+  return CIP_OK;
+}
+
+size_t plan_resident_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior) {
+  (void)K;
+  const size_t e = dtype == CIP_F64 ? 8 : 4, c = 2 * e;
+  const size_t H = N / 2 + 1, P = half_pitch(N), CP = col_pitch(N);
+  const size_t nc = prior == CIP_PRIOR_TV ? 2 : 1;
+  const size_t npk = (size_t)M * (M + 1) / 2;
+  size_t b = 2 * (size_t)M * N * P * c;       // xh, qh
+  b += (size_t)M * H * CP * c;                // data term
+  b += npk * H * CP * c;                      // factor
+  b += (size_t)M * H * CP * c;                // column buffer of the split form
+  b += 3 * nc * (size_t)M * N * N * e;        // u (two), t_prev
+  b += (size_t)kTwN * (16 + c) + N * 8 + (size_t)(N / 2) * M * kNPart * 8 + 8192;
+  return b;
+}
+
+}  // namespace cip
