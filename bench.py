@@ -149,6 +149,203 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (not the default line): --workload convdict | batch | serve | precision
+# ---------------------------------------------------------------------------
+def _ev_time(torch, fn, reps=1):
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / 1e3
+
+
+def workload_convdict(args, torch, api, inputs):
+    """256 x 256 x 5, 32 Gabor 11 x 11 filters, 300 iterations of Alg. 2 (setup + iterations + read-back)."""
+    pr = inputs.convdict_problem()
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+    h, y, d = f(pr.h), f(pr.y), f(pr.filters)
+    x = torch.empty((pr.M, pr.N, pr.N), device="cuda")
+    plan = api.Plan(pr.N, pr.K, pr.M, "f32")
+    plan.set_prior("convdict", pr.lam, pr.rho, pr.beta)
+    plan.set_dictionary(d)
+
+    def step():
+        plan.set_psfs(h)
+        plan.set_measurements(y)
+        plan.iterate(pr.iters)
+        plan.get_x(x)
+
+    for _ in range(args.warmup):
+        step()
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")
+    ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        ts.append(_ev_time(torch, step))
+    plan.set_timing(True)
+    step()
+    kt = plan.get_timing()
+    plan.close()
+    L = pr.filters.shape[0]
+    S, H, bins = L * pr.M, pr.N // 2 + 1, pr.N * (pr.N // 2 + 1)
+    col_bytes = (4 * S + 2 * L + 5 * pr.M + pr.M * (pr.M + 1) // 2) * bins * 8   # split column pass as built
+    pri_bytes = 2 * S * bins * 8 + 2 * S * pr.N * pr.N * 4
+    avgB = kt["column_pass_ms"] / max(kt["column_pass_n"], 1)
+    avgA = kt["prior_pass_ms"] / max(kt["prior_pass_n"], 1)
+    t = sum(ts) / len(ts)
+    return {"metric": METRIC, "value": pr.voxels * pr.iters / t, "unit": "voxel-iter/s", "ms_per_step": 1e3 * t,
+            "config": {"workload": f"convdict_{pr.N}x{pr.N}x{pr.M}_L{L} (11x11 Gabor, 25 dB, lambda=0.15, beta=4, "
+                                   f"rho=8, {pr.iters} iterations)", "step": "setup + iterations + read-back"},
+            "kernels": {"column_pass_us": 1e3 * avgB, "column_pass_GBps": col_bytes / avgB / 1e6,
+                        "prior_pass_us": 1e3 * avgA, "prior_pass_GBps": pri_bytes / avgA / 1e6,
+                        "algorithmic_bytes": {"column_pass": col_bytes, "prior_pass": pri_bytes}}}
+
+
+def workload_batch(args, torch, api, inputs):
+    """64 instances, N in {128..1024}, M = K in {3, 5, 10}, TV, 100 iterations each: plain per-instance
+    FP32 method (one plan after another, no graph) against the batched mixed-precision form."""
+    probs = inputs.mixed_batch()
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+    vox = sum(p.voxels for p in probs) * 100
+
+    def plans(plain):
+        out = []
+        for p in probs:
+            P = api.Plan(p.N, p.K, p.M, "f32", plain_fp32=plain)
+            P.set_prior(p.prior, p.lam, p.rho, p.beta)
+            P.set_psfs(f(p.h))
+            P.set_measurements(f(p.y))
+            out.append(P)
+        return out
+
+    res = {}
+    ps = plans(True)
+    for P in ps:
+        P.iterate(2)
+        P.reset_state()
+    t_plain = _ev_time(torch, lambda: [P.iterate(100) for P in ps])
+    x_plain = ps[0].get_x().double().cpu().numpy()
+    for P in ps:
+        P.close()
+    pb = plans(False)
+    B = api.Batch(pb, nstreams=8)
+    B.iterate(10)  # records the graph (after two eager iterations, so every plan is back on side 0)
+    for P in pb:
+        P.reset_state()
+    t_batch = _ev_time(torch, lambda: B.iterate(100))
+    x_mixed = pb[0].get_x().double().cpu().numpy()
+    B.close()
+    for P in pb:
+        P.close()
+    # accuracy of both against the FP64 oracle on the first instance
+    from oracle import fast
+    p0 = probs[0]
+    S = fast.analysis_setup(p0.h, p0.y, p0.prior, p0.lam, p0.rho, p0.beta)
+    x_or, _, _, _, _ = fast.run_analysis(S, 100)
+    err = lambda a: float(np.linalg.norm(a - x_or) / np.linalg.norm(x_or))
+    res.update({"metric": METRIC, "value": vox / t_batch, "unit": "voxel-iter/s", "ms_per_step": 1e3 * t_batch,
+                "config": {"workload": "mixed_batch_64 (N 128..1024, M=K 3/5/10, TV, 100 iterations each)",
+                           "voxel_iters": vox, "step": "100 iterations of all 64 instances (setup excluded)"},
+                "plain_per_instance_fp32": {"value": vox / t_plain, "ms": 1e3 * t_plain,
+                                            "rel_err_instance0": err(x_plain)},
+                "batched_mixed": {"value": vox / t_batch, "ms": 1e3 * t_batch, "rel_err_instance0": err(x_mixed)},
+                "speedup": t_plain / t_batch})
+    return res
+
+
+def workload_serve(args, torch, api, inputs):
+    """Poisson stream of reconstructions (N in {256..2048}, M = K in {3,5,10}, TV or DCT, tol 1e-4,
+    max 300 iterations) served with continuous batching; p50/p99 latency and voxel-iter/s."""
+    reqs = inputs.request_stream(n=args.requests, rate_hz=args.rate)
+    banks, ffts = {}, {}
+    jobs = []
+    for r in reqs:
+        key = (r.N, r.M, r.psf_id)
+        if key not in banks:
+            brng = np.random.default_rng(hash(key) & 0xFFFFFFFF)
+            if r.M == 3:
+                h = inputs.gaussian_psf_bank(r.N, r.M, r.M)
+            else:
+                h = inputs.disk_gaussian_psf_bank(r.N, r.M, r.M, rmax=6.0 + 6.0 * brng.random())
+            banks[key] = h.astype(np.float32)
+            ffts[key] = np.fft.rfft2(h)
+        rng = np.random.default_rng(r.seed)
+        x = inputs.rectangles_image(rng, r.N, r.M) if r.M == 3 else inputs.spectral_image(rng, r.N, r.M)
+        clean = np.fft.irfft2(np.einsum("kmab,mab->kab", ffts[key], np.fft.rfft2(x)), s=(r.N, r.N))
+        sig = np.sqrt(np.mean(clean * clean) / 1e3)
+        y = (clean + sig * rng.standard_normal(clean.shape)).astype(np.float32)
+        lam, rho = (1e-2, 1.0) if r.prior == "tv" else (1e-3, 1e-2)
+        jobs.append((r, key, y, lam, rho))
+    free, total = torch.cuda.mem_get_info()
+    S = api.Server(hbm_budget=int(0.8 * free), max_active=args.max_active, check_every=10)
+    t0 = time.perf_counter()
+    ids = []
+    for r, key, y, lam, rho in jobs:
+        dt = r.arrival_s - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        psf_key = (hash(key) & 0xFFFFFFFFFFFF) + 1
+        ids.append((S.submit(banks[key], y, r.prior, lam, rho, tol=1e-4, max_iter=300, psf_key=psf_key), r))
+    res = [(S.wait(rid), r) for (rid, _), r in ids]
+    makespan = max(x["t_done"] for x, _ in res) - min(x["t_submit"] for x, _ in res)
+    st = S.stats()
+    S.close()
+    lat = np.array([x["t_done"] - x["t_submit"] for x, _ in res])
+    done = [x for x, _ in res if x["state"] == "done"]
+    vi = sum(r.N * r.N * r.M * x["iterations"] for x, r in res)
+    span_arrivals = reqs[-1].arrival_s - reqs[0].arrival_s
+    return {"metric": "serve voxel-iter/s, p50/p99 latency", "value": vi / makespan, "unit": "voxel-iter/s",
+            "config": {"workload": f"poisson_{args.rate:g}hz_{args.requests}req (N 256..2048, M=K 3/5/10, TV/DCT, "
+                                   "tol 1e-4, max 300 iterations)", "max_active": args.max_active},
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "mean": float(lat.mean() * 1e3)},
+            "requests": len(res), "done": len(done), "offered_req_per_s": len(reqs) / max(span_arrivals, 1e-9),
+            "achieved_req_per_s": len(done) / makespan, "voxel_iters": vi, "makespan_s": makespan,
+            "iterations_mean": float(np.mean([x["iterations"] for x, _ in res])), "server": st}
+
+
+def workload_precision(args, torch, api, inputs):
+    """512 x 512 x 10 DCT workload, 200 iterations: the mixed path against the plain FP32 method,
+    throughput and final error against the FP64 oracle."""
+    from oracle import fast
+    pr = inputs.spectral_dct()
+    S = fast.analysis_setup(pr.h, pr.y, pr.prior, pr.lam, pr.rho, pr.beta)
+    x_or, _, _, _, _ = fast.run_analysis(S, pr.iters)
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+    out = {}
+    for plain in (False, True):
+        P = api.Plan(pr.N, pr.K, pr.M, "f32", plain_fp32=plain)
+        P.set_prior(pr.prior, pr.lam, pr.rho, pr.beta)
+        P.set_psfs(f(pr.h))
+        P.set_measurements(f(pr.y))
+        P.iterate(5)
+        P.reset_state()
+        t = _ev_time(torch, lambda: P.iterate(pr.iters))
+        x = P.get_x().double().cpu().numpy()
+        P.close()
+        out["plain_fp32" if plain else "mixed"] = {
+            "value": pr.voxels * pr.iters / t, "ms": 1e3 * t,
+            "rel_err_final": float(np.linalg.norm(x - x_or) / np.linalg.norm(x_or))}
+    return {"metric": METRIC, "value": out["mixed"]["value"], "unit": "voxel-iter/s",
+            "config": {"workload": WORKLOAD, "step": "200 iterations (setup excluded)"}, **out}
+
+
+def run_workload(args):
+    import torch
+    from paper_2006_08303_gb300 import api, inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    fn = {"convdict": workload_convdict, "batch": workload_batch, "serve": workload_serve,
+          "precision": workload_precision}[args.workload]
+    line = fn(args, torch, api, inputs)
+    line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                 "dtype": "f32", "data": "synthetic"})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -157,6 +354,11 @@ def main():
     ap.add_argument("--impl", default="cip", choices=["cip", "reference"])
     ap.add_argument("--ref-iters", type=int, default=10, help="iterations per oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="spectral_dct",
+                    choices=["spectral_dct", "convdict", "batch", "serve", "precision"])
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (req/s)")
+    ap.add_argument("--requests", type=int, default=80, help="serve: number of requests")
+    ap.add_argument("--max-active", type=int, default=16, help="serve: execution slots")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -164,6 +366,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "spectral_dct":
+        if rank == 0:
+            run_workload(args)
         return
 
     import torch

@@ -92,6 +92,8 @@ cip_status cip_plan_create(cip_plan** out, int N, int K, int M, cip_dtype dtype,
  * on the stream of the plan's last call, so no call synchronises the whole device. */
 cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dtype dtype, const cip_options* opt,
                                      void* stream);
+/* Frees the plan's buffers in stream order on the stream of its last call (which must still
+ * exist); work already queued on that stream completes first. */
 cip_status cip_plan_destroy(cip_plan* plan);
 
 /* Device bytes a plan with these sizes holds (for admission by HBM budget). */

@@ -86,6 +86,8 @@ struct cip_server {
   std::thread worker;
   // pinned host slots (2 doubles each) for the residuals of running requests
   double* pinned = nullptr;
+  // stream of the cached factor plans (they outlive the requests and their streams)
+  cudaStream_t cache_stream = nullptr;
   std::vector<int> free_slots;
   // statistics
   double voxel_iters = 0;
@@ -160,10 +162,12 @@ cip_status setup(cip_server* s, Request& q) {
   }
   if (q.r.psf_key && !src) {
     // form the factor once in a cached plan
+    // (set_psfs waits for the factor, so the request's stream may read it right after)
     cip_plan* cp = nullptr;
-    r = cip_plan_create_on_stream(&cp, q.r.N, q.r.K, q.r.M, CIP_F32, nullptr, st);
-    if (r == CIP_OK) r = cip_set_prior(cp, (cip_prior)q.r.prior, q.r.lambda, q.r.rho, q.r.beta, st);
-    if (r == CIP_OK) r = cip_set_psfs(cp, q.h.data(), st);
+    cudaStream_t cs = s->cache_stream;
+    r = cip_plan_create_on_stream(&cp, q.r.N, q.r.K, q.r.M, CIP_F32, nullptr, cs);
+    if (r == CIP_OK) r = cip_set_prior(cp, (cip_prior)q.r.prior, q.r.lambda, q.r.rho, q.r.beta, cs);
+    if (r == CIP_OK) r = cip_set_psfs(cp, q.h.data(), cs);
     if (r != CIP_OK) {
       if (cp) cip_plan_destroy(cp);
       return r;
@@ -314,6 +318,7 @@ cip_status cip_server_create(cip_server** out, size_t hbm_budget, int max_active
     return CIP_ERR_OOM;
   }
   for (int i = s->max_active - 1; i >= 0; --i) s->free_slots.push_back(i);
+  cudaStreamCreateWithFlags(&s->cache_stream, cudaStreamNonBlocking);
   s->t0 = Clock::now();
   s->worker = std::thread(worker_main, s);
   *out = s;
@@ -415,6 +420,7 @@ cip_status cip_server_destroy(cip_server* s) {
   }
   for (auto& c : s->cache) cip_plan_destroy(c.second.plan);
   cudaDeviceSynchronize();
+  if (s->cache_stream) cudaStreamDestroy(s->cache_stream);
   if (s->pinned) cudaFreeHost(s->pinned);
   delete s;
   return CIP_OK;
