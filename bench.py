@@ -334,12 +334,41 @@ def workload_precision(args, torch, api, inputs):
             "config": {"workload": WORKLOAD, "step": "200 iterations (setup excluded)"}, **out}
 
 
+def workload_single(args, torch, api, inputs):
+    """One instance of any shape (N, M = K, prior), setup then `iters` iterations; per-kernel times.
+    Also the small driver used for ncu captures."""
+    if args.prior == "tv":
+        pr = inputs.tiny_tv(N=args.N, M=args.M, iters=args.iters, dtype="f32")
+    else:
+        pr = inputs.spectral_dct(N=args.N, M=args.M, iters=args.iters)
+        pr.prior = args.prior
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+    P = api.Plan(pr.N, pr.K, pr.M, "f32", column_pass=args.column_pass)
+    P.set_prior(pr.prior, pr.lam, pr.rho, pr.beta)
+    P.set_psfs(f(pr.h))
+    P.set_measurements(f(pr.y))
+    P.iterate(2)
+    P.set_timing(True)
+    t = _ev_time(torch, lambda: P.iterate(args.iters))
+    kt = P.get_timing()
+    cfg = P.config()
+    P.close()
+    ab = algorithmic_bytes(pr.N, pr.M, pr.prior)
+    avgA = kt["prior_pass_ms"] / max(kt["prior_pass_n"], 1)
+    avgB = kt["column_pass_ms"] / max(kt["column_pass_n"], 1)
+    return {"metric": METRIC, "value": pr.voxels * args.iters / t, "unit": "voxel-iter/s",
+            "ms_per_step": 1e3 * t,
+            "config": {"workload": f"single_{pr.N}x{pr.N}x{pr.M}_{pr.prior}", "iters": args.iters, "launch": cfg},
+            "kernels": {"prior_pass_us": 1e3 * avgA, "prior_pass_GBps": ab["prior_pass"] / avgA / 1e6,
+                        "column_pass_us": 1e3 * avgB, "column_pass_GBps": ab["column_pass"] / avgB / 1e6}}
+
+
 def run_workload(args):
     import torch
     from paper_2006_08303_gb300 import api, inputs
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     fn = {"convdict": workload_convdict, "batch": workload_batch, "serve": workload_serve,
-          "precision": workload_precision}[args.workload]
+          "precision": workload_precision, "single": workload_single}[args.workload]
     line = fn(args, torch, api, inputs)
     line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                  "dtype": "f32", "data": "synthetic"})
@@ -355,7 +384,12 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=10, help="iterations per oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="spectral_dct",
-                    choices=["spectral_dct", "convdict", "batch", "serve", "precision"])
+                    choices=["spectral_dct", "convdict", "batch", "serve", "precision", "single"])
+    ap.add_argument("--N", type=int, default=1024, help="single: image side")
+    ap.add_argument("--M", type=int, default=10, help="single: channels (= measurements)")
+    ap.add_argument("--prior", default="tv", choices=["tv", "dct8", "l1"], help="single: prior")
+    ap.add_argument("--iters", type=int, default=20, help="single: iterations")
+    ap.add_argument("--column-pass", type=int, default=0, help="single: 0 autotuned, 1 fused, 2 split")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (req/s)")
     ap.add_argument("--requests", type=int, default=80, help="serve: number of requests")
     ap.add_argument("--max-active", type=int, default=16, help="serve: execution slots")
