@@ -343,7 +343,7 @@ def workload_single(args, torch, api, inputs):
         pr = inputs.spectral_dct(N=args.N, M=args.M, iters=args.iters)
         pr.prior = args.prior
     f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
-    P = api.Plan(pr.N, pr.K, pr.M, "f32", column_pass=args.column_pass)
+    P = api.Plan(pr.N, pr.K, pr.M, "f32", column_pass=args.column_pass, col_tile=args.col_tile)
     P.set_prior(pr.prior, pr.lam, pr.rho, pr.beta)
     P.set_psfs(f(pr.h))
     P.set_measurements(f(pr.y))
@@ -390,6 +390,7 @@ def main():
     ap.add_argument("--prior", default="tv", choices=["tv", "dct8", "l1"], help="single: prior")
     ap.add_argument("--iters", type=int, default=20, help="single: iterations")
     ap.add_argument("--column-pass", type=int, default=0, help="single: 0 autotuned, 1 fused, 2 split")
+    ap.add_argument("--col-tile", type=int, default=0, help="single: columns per fused cluster (0 = default)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (req/s)")
     ap.add_argument("--requests", type=int, default=80, help="serve: number of requests")
     ap.add_argument("--max-active", type=int, default=16, help="serve: execution slots")

@@ -46,9 +46,15 @@ def _flags(extra_ptxas: bool = False):
     return f
 
 
+def _tuning_defines():
+    # optional register-budget overrides, e.g. CIP_NVCC_DEFINES="-DPASSA_RT32=64 -DPASSB_RT=80"
+    return [d for d in os.environ.get("CIP_NVCC_DEFINES", "").split() if d.startswith("-D")]
+
+
 def _compile(unit, verbose: bool):
     src, defs, obj = unit
-    cmd = [nvcc(), *_flags(verbose), *defs, "-c", os.path.join(CSRC, src), "-o", os.path.join(BUILD, obj)]
+    cmd = [nvcc(), *_flags(verbose), *defs, *_tuning_defines(), "-c", os.path.join(CSRC, src),
+           "-o", os.path.join(BUILD, obj)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     return unit, r.returncode, r.stdout + r.stderr
 

@@ -19,7 +19,7 @@ using namespace cip;
 namespace {
 
 constexpr int kPinvListCap = 64;
-constexpr int kMaxTimed = 8192;
+constexpr int kMaxTimed = 4096;
 
 std::string g_create_error;
 
@@ -1018,6 +1018,7 @@ cip_status cip_set_timing(cip_plan* p, int on) {
   if (!p) return CIP_ERR_INVALID_ARG;
   p->timing = on != 0;
   p->nA = p->nB = 0;
+  if (p->timing) ensure_events(p);  // created here, outside any timed sequence of iterations
   return CIP_OK;
 }
 

@@ -30,6 +30,8 @@ __global__ void __launch_bounds__((1 << LOGN) * cs_cc<T>() / cs_e<T>(1 << LOGN))
   const int tid = threadIdx.x;
   const int c0 = blockIdx.x * CC;
   const int m = blockIdx.y;
+  grid_dep_wait();  // the source spectra of the preceding kernel are complete from here on
+  grid_dep_launch();
   if (SIGN < 0) {
     const C* rows = src + (size_t)m * N * P;
     for (int idx = tid; idx < N * CC; idx += NT) {
@@ -72,6 +74,8 @@ __global__ void __launch_bounds__(256, 3) solve_split_kernel(typename CT<T>::typ
   using C = typename CT<T>::type;
   const int k1 = blockIdx.x * 256 + threadIdx.x;
   const int k2 = blockIdx.y;
+  grid_dep_wait();  // the forward column DFTs are complete from here on
+  grid_dep_launch();
   if (k1 >= N) return;
   const int npk = M * (M + 1) / 2;
   const int CP = col_pitch(N);
@@ -123,9 +127,7 @@ cudaError_t launch_colfft(const typename CT<T>::type* src, typename CT<T>::type*
     if (e != cudaSuccess) return e;
   }
   done = true;
-  dim3 grid((N / 2 + 1 + CC - 1) / CC, M);
-  k<<<grid, NT, sm, s>>>(src, dst, tw, M);
-  return cudaGetLastError();
+  return launch_pdl(k, dim3((N / 2 + 1 + CC - 1) / CC, M), dim3(NT), sm, s, 0, src, dst, tw, M);
 }
 
 template <typename T, int SIGN>
@@ -145,13 +147,13 @@ cudaError_t colfft_n(const typename CT<T>::type* src, typename CT<T>::type* dst,
 template <typename T>
 cudaError_t solve_m(typename CT<T>::type* colbuf, const typename CT<T>::type* pinv, const typename CT<T>::type* xb,
                     int N, int M, int plain, cudaStream_t s) {
-  dim3 grid((N + 255) / 256, N / 2 + 1);
-  if (M <= 4) solve_split_kernel<T, 4><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M, plain);
-  else if (M <= 8) solve_split_kernel<T, 8><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M, plain);
-  else if (M <= 12) solve_split_kernel<T, 12><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M, plain);
-  else if (M <= 16) solve_split_kernel<T, 16><<<grid, 256, 0, s>>>(colbuf, pinv, xb, N, M, plain);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  const dim3 grid((N + 255) / 256, N / 2 + 1), block(256);
+  if (M <= 4) return launch_pdl(solve_split_kernel<T, 4>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
+  if (M <= 8) return launch_pdl(solve_split_kernel<T, 8>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
+  if (M <= 10) return launch_pdl(solve_split_kernel<T, 10>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
+  if (M <= 12) return launch_pdl(solve_split_kernel<T, 12>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
+  if (M <= 16) return launch_pdl(solve_split_kernel<T, 16>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace

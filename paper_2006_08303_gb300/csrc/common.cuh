@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace cip {
 
 constexpr int kTwN = 2048;  // twiddle table length (max FFT length)
@@ -75,6 +77,43 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
   if (a1 > a0) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((unsigned)(a1 - a0)) : "memory");
   }
+}
+
+// Programmatic dependent launch.  The iteration's kernels are launched with
+// programmatic stream serialisation: a kernel may start while its predecessor
+// drains, runs only independent work (L2 prefetches of constant operands)
+// before grid_dep_wait(), which returns once the predecessor grid has
+// completed and its writes are visible, and then lets its own successor be
+// scheduled (grid_dep_launch()).  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch `kern` with programmatic stream serialisation (plus a cluster of
+// cluster_x CTAs along x when cluster_x > 0).  The kernel must call grid_dep_wait() before it touches any
+// memory that an earlier kernel of the stream writes or reads.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              unsigned cluster_x, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  unsigned n = 0;
+  attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[n].val.programmaticStreamSerializationAllowed = 1;
+  ++n;
+  if (cluster_x > 0) {
+    attr[n].id = cudaLaunchAttributeClusterDimension;
+    attr[n].val.clusterDim.x = cluster_x;
+    attr[n].val.clusterDim.y = 1;
+    attr[n].val.clusterDim.z = 1;
+    ++n;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = n;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 // soft(w, tau) = sign(w) max(|w| - tau, 0) with sign(0) = -1 (Eq. solt_trans);

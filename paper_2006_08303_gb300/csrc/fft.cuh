@@ -107,6 +107,17 @@ __device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* _
   constexpr int TT = N / E;
   static_assert(E % R == 0, "E must be a multiple of the radix");
   C a[E];
+  // twiddles first: they do not depend on the data, so their load latency
+  // overlaps the shared-memory reads and the team barrier
+  C w[LS > 1 ? B * (R - 1) : 1];
+  if constexpr (LS > 1) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = (tt + TT * b) & (LS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = __ldg(&tw[r * j * (kTwN / (LS * R))]);
+    }
+  }
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const int t = tt + TT * b;
@@ -121,9 +132,9 @@ __device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* _
     if constexpr (LS > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        C w = __ldg(&tw[r * j * (kTwN / (LS * R))]);
-        if (SIGN > 0) w.y = -w.y;
-        a[b * R + r] = cmul(a[b * R + r], w);
+        C wr = w[b * (R - 1) + r - 1];
+        if (SIGN > 0) wr.y = -wr.y;
+        a[b * R + r] = cmul(a[b * R + r], wr);
       }
     }
     dft_r<R, SIGN>(&a[b * R]);

@@ -33,21 +33,23 @@ std::mutex g_mu;
 double* g_scratch_dev[64] = {nullptr};  // per device ordinal, device address of g_scratch
 
 template <typename T>
-__device__ __forceinline__ void accumulate(double (&p)[kNPart], T w, T t, T un, T tp) {
-  p[0] += (double)(w - t) * (double)(w - t);
-  p[1] += (double)w * w;
-  p[2] += (double)t * t;
-  p[3] += (double)un * un;
-  p[4] += (double)(t - tp) * (double)(t - tp);
+__device__ __forceinline__ void accumulate(T (&p)[kNPart], T w, T t, T un, T tp) {
+  // per-thread sums (at most 64 terms) in the working precision; block and grid sums in double
+  const T r = w - t, d = t - tp;
+  p[0] = fma(r, r, p[0]);
+  p[1] = fma(w, w, p[1]);
+  p[2] = fma(t, t, p[2]);
+  p[3] = fma(un, un, p[3]);
+  p[4] = fma(d, d, p[4]);
 }
 
 template <typename T>
-__device__ void block_store(const double (&v)[kNPart], double* out) {
+__device__ void block_store(const T (&v)[kNPart], double* out) {
   __shared__ double red[kThreads / 32][kNPart];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < kNPart; ++i) {
-    double x = v[i];
+    double x = (double)v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if (lane == 0) red[warp][i] = x;
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) shrink_dual_px(const T* __restrict__
   constexpr int NC = PRIOR == PRIOR_TV ? 2 : 1;
   const size_t plane = (size_t)N * N;
   const size_t total = (size_t)M * plane;
-  double part[kNPart] = {0, 0, 0, 0, 0};
+  T part[kNPart] = {T(0), T(0), T(0), T(0), T(0)};
   for (int e = 0; e < kPixPerBlock / kThreads; ++e) {
     const size_t idx = (size_t)blockIdx.x * kPixPerBlock + (size_t)e * kThreads + threadIdx.x;
     if (idx >= total) break;
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) shrink_dual_dct(const T* __restrict_
   const int nb = N / 8;
   const size_t nblocks = (size_t)M * nb * nb;
   const size_t b = (size_t)blockIdx.x * kThreads + threadIdx.x;
-  double part[kNPart] = {0, 0, 0, 0, 0};
+  T part[kNPart] = {T(0), T(0), T(0), T(0), T(0)};
   if (b < nblocks) {
     const size_t m = b / ((size_t)nb * nb);
     const int rem = (int)(b - m * nb * nb);

@@ -22,14 +22,18 @@ namespace cip {
 
 namespace {
 
+#ifndef PASSA_RT32
+#define PASSA_RT32 48
+#endif
+
 template <typename T>
-__device__ __forceinline__ void block_reduce_store(const double (&v)[kNPart], double* out) {
+__device__ __forceinline__ void block_reduce_store(const T (&v)[kNPart], double* out) {
   __shared__ double red[32][kNPart];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double s[kNPart];
 #pragma unroll
   for (int i = 0; i < kNPart; ++i) {
-    double x = v[i];
+    double x = (double)v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     s[i] = x;
@@ -79,7 +83,18 @@ template <typename T> constexpr int threads_for(int N, int prior, int R) {
   return ((n + 31) / 32) * 32;
 }
 
-template <typename T> constexpr int minblocks_for(int nth) { return nth >= 1024 ? 1 : 1024 / nth; }
+// CTAs per SM the register budget is cut for: as many as shared memory and the
+// thread limit allow, at <= ~48 registers per thread for complex64 (so that a
+// 10-channel 512 x 512 prior pass runs as one wave) and <= ~168 for complex128
+// (whose 16-element FFT registers would otherwise spill).
+template <typename T> constexpr int minblocks_for(int nth, size_t smem) {
+  const int by_regs = 65536 / (nth * (sizeof(T) == 4 ? PASSA_RT32 : 168));
+  const int by_smem = (int)((227 * 1024) / (smem + 1024));
+  const int by_thr = 2048 / nth;
+  int b = by_regs < by_smem ? by_regs : by_smem;
+  b = b < by_thr ? b : by_thr;
+  return b < 1 ? 1 : b;
+}
 
 // 8-point orthonormal DCT-II (FWD) or its inverse on the two rows of a pair
 template <typename T, bool FWD, typename C>
@@ -112,20 +127,24 @@ __device__ __forceinline__ void shrink(T w, T u, T tau, T& t, T& un) {
 }
 
 template <typename T>
-__device__ __forceinline__ void acc_resid(double (&part)[kNPart], T w, T t, T un, const T* tprev, size_t g) {
-  part[0] += (double)(w - t) * (double)(w - t);
-  part[1] += (double)w * w;
-  part[2] += (double)t * t;
-  part[3] += (double)un * un;
+__device__ __forceinline__ void acc_resid(T (&part)[kNPart], T w, T t, T un, const T* tprev, size_t g) {
+  // a thread sums a few dozen terms at most, so the plan's precision suffices here; the
+  // block and grid reductions run in double (FP64 issue is scarce on this part)
+  const T r = w - t;
+  part[0] = fma(r, r, part[0]);
+  part[1] = fma(w, w, part[1]);
+  part[2] = fma(t, t, part[2]);
+  part[3] = fma(un, un, part[3]);
   if (tprev) {
     const T dt = t - tprev[g];
-    part[4] += (double)dt * dt;
+    part[4] = fma(dt, dt, part[4]);
   }
 }
 
 template <typename T, int LOGN, int PRIOR, int R>
 __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
-                                  minblocks_for<T>(threads_for<T>(1 << LOGN, PRIOR, R)))
+                                  minblocks_for<T>(threads_for<T>(1 << LOGN, PRIOR, R),
+                                                   smem_for<T>(1 << LOGN, PRIOR, R)))
     passA_kernel(const PassAArgs<T> a) {
   using C = typename CT<T>::type;
   constexpr int N = 1 << LOGN;
@@ -158,7 +177,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   T* tprev = a.tprev ? a.tprev + (size_t)m * NCOMP * plane : nullptr;
   const T* timp = a.t_imp ? a.t_imp + (size_t)m * NCOMP * plane : nullptr;
   const T* tprev_rd = resid ? tprev : nullptr;
-  double part[kNPart] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  T part[kNPart] = {T(0), T(0), T(0), T(0), T(0)};
 
   auto grow = [&](int j) { return (r0 - HALO + j) & (N - 1); };
 
@@ -172,6 +191,8 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
     }
   }
 
+  grid_dep_wait();  // x (and u, t) of the previous kernels are complete from here on
+  grid_dep_launch();
   if (!import_mode) {
     // 1. load row half-spectra (two rows per complex FFT) and invert the row DFT
     const C* xh = a.xh + (size_t)m * N * P;
@@ -362,14 +383,18 @@ cudaError_t launchA(const PassAArgs<T>& a, cudaStream_t s) {
   constexpr size_t sm = smem_for<T>(N, PRIOR, R);
   auto kern = passA_kernel<T, LOGN, PRIOR, R>;
   static bool attr_done = false;
-  if (!attr_done && sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (!attr_done) {
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    // the largest shared-memory carveout, so that the register-bound CTA count is reached
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
+    attr_done = true;
   }
-  attr_done = true;
-  dim3 grid(N / R, a.M);
-  kern<<<grid, nth, sm, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(N / R, a.M), dim3(nth), sm, s, 0, a);
 }
 
 template <typename T, int PRIOR>

@@ -37,9 +37,13 @@ template <typename T> int cols_for(int N, int M) {
   return sizeof(T) == 4 ? 4 : 2;
 }
 
-// register budget: at most ~80 registers per thread so that several CTAs share an SM
+#ifndef PASSB_RT
+#define PASSB_RT 80
+#endif
+
+// register budget: at most ~PASSB_RT registers per thread so that several CTAs share an SM
 constexpr int minblocks_b(int nt) {
-  const int b = 65536 / (nt * 80);
+  const int b = 65536 / (nt * PASSB_RT);
   return b < 1 ? 1 : (b > 32 ? 32 : b);
 }
 
@@ -84,6 +88,8 @@ __global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
     }
   }
 
+  grid_dep_wait();  // q of the preceding prior pass is complete from here on
+  grid_dep_launch();
   for (int idx = tid; idx < N * CC; idx += NT) {
     const int n1 = idx / CC, c = idx - n1 * CC;
     const int k2 = c0 + c;
@@ -168,19 +174,7 @@ cudaError_t launchB(const PassBArgs<T>& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(a.M, (N / 2 + 1 + CC - 1) / CC, 1);
-  cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = a.M;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, a);
+  return launch_pdl(kern, dim3(a.M, (N / 2 + 1 + CC - 1) / CC, 1), dim3(NT), sm, s, (unsigned)a.M, a);
 }
 
 template <typename T, int LOGN, int CC>
@@ -188,6 +182,7 @@ cudaError_t dispatchB_m(const PassBArgs<T>& a, cudaStream_t s) {
   if (a.M <= 4) return launchB<T, LOGN, CC, 4>(a, s);
   if (sizeof(T) == 4) {
     if (a.M <= 8) return launchB<T, LOGN, CC, 8>(a, s);
+    if (a.M <= 10) return launchB<T, LOGN, CC, 10>(a, s);
     if (a.M <= 12) return launchB<T, LOGN, CC, 12>(a, s);
   }
   if (a.M <= 16) return launchB<T, LOGN, CC, 16>(a, s);
