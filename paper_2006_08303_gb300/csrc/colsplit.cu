@@ -48,6 +48,7 @@ __global__ void __launch_bounds__((1 << LOGN) * cs_cc<T>() / cs_e<T>(1 << LOGN))
   ts.bar_id = 0;
   ts.nthreads = NT;
   ts.mask = 0xffffffffu;
+  ts.cta = false;
   __syncthreads();
   fft_team<C, LOGN, CC, E, SIGN>(buf, tid, tw, ts);
   __syncthreads();

@@ -18,14 +18,21 @@ namespace cip {
 
 
 
-// Synchronisation of one team: a named barrier for teams wider than a warp,
-// a masked __syncwarp for teams inside one warp.
+// Synchronisation of one team: the CTA-wide barrier (cta: every thread of the
+// CTA runs the FFT, idle ones with active = false), a named barrier for teams
+// wider than a warp, or a masked __syncwarp for teams inside one warp.
+// Named barriers are a per-SM resource: a CTA that uses ids 0..k limits how
+// many CTAs share an SM, so kernels with several teams per CTA use the
+// CTA-wide form.
 struct TeamSync {
   int bar_id;
   int nthreads;
   unsigned mask;
+  bool cta;
   __device__ __forceinline__ void sync() const {
-    if (nthreads > 32) {
+    if (cta) {
+      __syncthreads();
+    } else if (nthreads > 32) {
       asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
     } else {
       __syncwarp(mask);
@@ -37,6 +44,7 @@ struct TeamSync {
 // starts at thread 0).  Barrier ids 1..15 are used for multi-warp teams.
 __device__ __forceinline__ TeamSync make_team_sync(int team, int team_threads) {
   TeamSync s;
+  s.cta = false;
   s.nthreads = team_threads;
   s.bar_id = 1 + team;
   if (team_threads >= 32) {
@@ -45,6 +53,16 @@ __device__ __forceinline__ TeamSync make_team_sync(int team, int team_threads) {
     int lane0 = (team * team_threads) & 31;
     s.mask = ((team_threads == 32) ? 0xffffffffu : ((1u << team_threads) - 1u)) << lane0;
   }
+  return s;
+}
+
+// As make_team_sync, but teams wider than a warp synchronise on the CTA-wide
+// barrier; then every thread of the CTA must call fft_team (idle threads with
+// active = false).  Teams inside one warp keep their masked __syncwarp and
+// their idle threads skip the call.
+__device__ __forceinline__ TeamSync make_block_team_sync(int team, int team_threads) {
+  TeamSync s = make_team_sync(team, team_threads);
+  s.cta = team_threads > 32;
   return s;
 }
 
@@ -101,7 +119,8 @@ template <int R, int SIGN, typename C> __device__ __forceinline__ void dft_r(C* 
 }
 
 template <typename C, int LOGN, int NF, int E, int SIGN, int R, int LS>
-__device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* __restrict__ tw, const TeamSync& ts) {
+__device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* __restrict__ tw, const TeamSync& ts,
+                                               bool active) {
   constexpr int N = 1 << LOGN;
   constexpr int B = E / R;
   constexpr int TT = N / E;
@@ -110,7 +129,7 @@ __device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* _
   // twiddles first: they do not depend on the data, so their load latency
   // overlaps the shared-memory reads and the team barrier
   C w[LS > 1 ? B * (R - 1) : 1];
-  if constexpr (LS > 1) {
+  if (LS > 1 && active) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int j = (tt + TT * b) & (LS - 1);
@@ -118,46 +137,53 @@ __device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* _
       for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = __ldg(&tw[r * j * (kTwN / (LS * R))]);
     }
   }
+  if (active) {
 #pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int t = tt + TT * b;
+    for (int b = 0; b < B; ++b) {
+      const int t = tt + TT * b;
 #pragma unroll
-    for (int r = 0; r < R; ++r) a[b * R + r] = buf[spad((t + r * (N / R)) * NF + f)];
+      for (int r = 0; r < R; ++r) a[b * R + r] = buf[spad((t + r * (N / R)) * NF + f)];
+    }
   }
   ts.sync();
+  if (active) {
 #pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int t = tt + TT * b;
-    const int j = t & (LS - 1);
-    if constexpr (LS > 1) {
+    for (int b = 0; b < B; ++b) {
+      const int t = tt + TT * b;
+      const int j = t & (LS - 1);
+      if constexpr (LS > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        C wr = w[b * (R - 1) + r - 1];
-        if (SIGN > 0) wr.y = -wr.y;
-        a[b * R + r] = cmul(a[b * R + r], wr);
+        for (int r = 1; r < R; ++r) {
+          C wr = w[b * (R - 1) + r - 1];
+          if (SIGN > 0) wr.y = -wr.y;
+          a[b * R + r] = cmul(a[b * R + r], wr);
+        }
       }
-    }
-    dft_r<R, SIGN>(&a[b * R]);
-    const int base = (t / LS) * LS * R + j;
+      dft_r<R, SIGN>(&a[b * R]);
+      const int base = (t / LS) * LS * R + j;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[spad((base + r * LS) * NF + f)] = a[b * R + r];
+      for (int r = 0; r < R; ++r) buf[spad((base + r * LS) * NF + f)] = a[b * R + r];
+    }
   }
   ts.sync();
 }
 
 // NF interleaved length-2^LOGN FFTs executed by the team's NTH = N*NF/E threads;
 // `tid` is the thread's index inside the team.
+// With a CTA-wide TeamSync, threads outside every team call this with
+// active = false: they take part in the barriers only.
 template <typename C, int LOGN, int NF, int E, int SIGN>
-__device__ __forceinline__ void fft_team(C* buf, int tid, const C* __restrict__ tw, const TeamSync& ts) {
+__device__ __forceinline__ void fft_team(C* buf, int tid, const C* __restrict__ tw, const TeamSync& ts,
+                                         bool active = true) {
   constexpr int S8 = LOGN / 3;
   constexpr int REM = LOGN % 3;
   const int f = tid % NF;
   const int tt = tid / NF;
-  if constexpr (S8 >= 1) stockham_stage<C, LOGN, NF, E, SIGN, 8, 1>(buf, f, tt, tw, ts);
-  if constexpr (S8 >= 2) stockham_stage<C, LOGN, NF, E, SIGN, 8, 8>(buf, f, tt, tw, ts);
-  if constexpr (S8 >= 3) stockham_stage<C, LOGN, NF, E, SIGN, 8, 64>(buf, f, tt, tw, ts);
-  if constexpr (REM == 1) stockham_stage<C, LOGN, NF, E, SIGN, 2, (1 << (3 * S8))>(buf, f, tt, tw, ts);
-  if constexpr (REM == 2) stockham_stage<C, LOGN, NF, E, SIGN, 4, (1 << (3 * S8))>(buf, f, tt, tw, ts);
+  if constexpr (S8 >= 1) stockham_stage<C, LOGN, NF, E, SIGN, 8, 1>(buf, f, tt, tw, ts, active);
+  if constexpr (S8 >= 2) stockham_stage<C, LOGN, NF, E, SIGN, 8, 8>(buf, f, tt, tw, ts, active);
+  if constexpr (S8 >= 3) stockham_stage<C, LOGN, NF, E, SIGN, 8, 64>(buf, f, tt, tw, ts, active);
+  if constexpr (REM == 1) stockham_stage<C, LOGN, NF, E, SIGN, 2, (1 << (3 * S8))>(buf, f, tt, tw, ts, active);
+  if constexpr (REM == 2) stockham_stage<C, LOGN, NF, E, SIGN, 4, (1 << (3 * S8))>(buf, f, tt, tw, ts, active);
 }
 
 // ---- two real rows through one complex FFT ---------------------------------

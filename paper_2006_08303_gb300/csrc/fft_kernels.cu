@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kRowThreads) row_r2c_kernel(const Tin* __restr
   }
   __syncthreads();
   const int team = tid / TEAM;
-  fft_team<C, LOGN, 1, 16, -1>(zb + team * ZS, tid % TEAM, tw, make_team_sync(team, TEAM));
+  fft_team<C, LOGN, 1, 16, -1>(zb + team * ZS, tid % TEAM, tw, make_block_team_sync(team, TEAM));
   __syncthreads();
   for (int idx = tid; idx < PAIRS * H; idx += kRowThreads) {
     const int p = idx / H, k = idx - p * H;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kRowThreads) row_c2r_kernel(const typename CT<
   }
   __syncthreads();
   const int team = tid / TEAM;
-  fft_team<C, LOGN, 1, 16, +1>(zb + team * ZS, tid % TEAM, tw, make_team_sync(team, TEAM));
+  fft_team<C, LOGN, 1, 16, +1>(zb + team * ZS, tid % TEAM, tw, make_block_team_sync(team, TEAM));
   __syncthreads();
   for (int idx = tid; idx < PAIRS * N; idx += kRowThreads) {
     const int p = idx / N, n = idx - p * N;
@@ -93,6 +93,7 @@ __global__ void col_c2c_kernel(typename CT<Tc>::type* data, const typename CT<Tc
   ts.bar_id = 0;
   ts.nthreads = TEAM;
   ts.mask = TEAM >= 32 ? 0xffffffffu : ((1u << TEAM) - 1u);
+  ts.cta = false;
   fft_team<C, LOGN, CC, 16, SIGN>(zb, tid, tw, ts);
   __syncthreads();
   for (int idx = tid; idx < N * CC; idx += TEAM) {

@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
     __syncthreads();
     {
       const int team = tid / TEAM;
-      if (team < NPIN) fft_team<C, LOGN, 1, E, +1>(zb + team * ZS, tid % TEAM, a.tw, make_team_sync(team, TEAM));
+      const TeamSync ts = make_block_team_sync(team, TEAM);
+      if (ts.cta || team < NPIN)
+        fft_team<C, LOGN, 1, E, +1>(zb + (team < NPIN ? team : 0) * ZS, tid % TEAM, a.tw, ts, team < NPIN);
     }
     __syncthreads();
   }
@@ -361,7 +363,9 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   // 4. forward row DFT of q (two rows per FFT), 5. store row half-spectra
   {
     const int team = tid / TEAM;
-    if (team < NPOUT) fft_team<C, LOGN, 1, E, -1>(zb + team * ZS, tid % TEAM, a.tw, make_team_sync(team, TEAM));
+    const TeamSync ts = make_block_team_sync(team, TEAM);
+    if (ts.cta || team < NPOUT)
+      fft_team<C, LOGN, 1, E, -1>(zb + (team < NPOUT ? team : 0) * ZS, tid % TEAM, a.tw, ts, team < NPOUT);
   }
   __syncthreads();
   C* qh = a.qh + (size_t)m * N * P;

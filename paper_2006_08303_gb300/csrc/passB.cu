@@ -99,6 +99,7 @@ __global__ void __launch_bounds__((1 << LOGN) * CC / elems_for<T>(),
   ts.bar_id = 0;
   ts.nthreads = NT;
   ts.mask = 0xffffffffu;
+  ts.cta = false;
   __syncthreads();
   fft_team<C, LOGN, CC, E, -1>(buf, tid, a.tw, ts);
   cluster.sync();
