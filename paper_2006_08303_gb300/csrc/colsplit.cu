@@ -32,16 +32,39 @@ __global__ void __launch_bounds__((1 << LOGN) * cs_cc<T>() / cs_e<T>(1 << LOGN))
   const int m = blockIdx.y;
   grid_dep_wait();  // the source spectra of the preceding kernel are complete from here on
   grid_dep_launch();
+  constexpr bool VEC = sizeof(C) == 8;  // complex64: two bins per 16-byte global access
+  const C zero = mk<C>(0.0, 0.0);
   if (SIGN < 0) {
     const C* rows = src + (size_t)m * N * P;
-    for (int idx = tid; idx < N * CC; idx += NT) {
-      const int n1 = idx / CC, c = idx - n1 * CC;
-      buf[spad(idx)] = (c0 + c < H) ? rows[(size_t)n1 * P + c0 + c] : mk<C>(0.0, 0.0);
+    if constexpr (VEC) {
+      // row n1, columns c, c+1 of the tile (P and c0 even: 16-byte aligned, inside the row pitch)
+      for (int i = tid; i < N * CC / 2; i += NT) {
+        const int n1 = i / (CC / 2), c = 2 * (i - n1 * (CC / 2));
+        const float4 v = *reinterpret_cast<const float4*>(rows + (size_t)n1 * P + c0 + c);
+        buf[spad(n1 * CC + c)] = (c0 + c < H) ? mk<C>(v.x, v.y) : zero;
+        buf[spad(n1 * CC + c + 1)] = (c0 + c + 1 < H) ? mk<C>(v.z, v.w) : zero;
+      }
+    } else {
+      for (int idx = tid; idx < N * CC; idx += NT) {
+        const int n1 = idx / CC, c = idx - n1 * CC;
+        buf[spad(idx)] = (c0 + c < H) ? rows[(size_t)n1 * P + c0 + c] : zero;
+      }
     }
   } else {
-    for (int idx = tid; idx < N * CC; idx += NT) {
-      const int c = idx / N, k1 = idx - c * N;
-      buf[spad(k1 * CC + c)] = (c0 + c < H) ? src[((size_t)(c0 + c) * M + m) * CP + k1] : mk<C>(0.0, 0.0);
+    if constexpr (VEC) {
+      // column c, bins k1, k1+1 (CP even: 16-byte aligned)
+      for (int i = tid; i < N * CC / 2; i += NT) {
+        const int c = i / (N / 2), k1 = 2 * (i - c * (N / 2));
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + c < H) v = *reinterpret_cast<const float4*>(src + ((size_t)(c0 + c) * M + m) * CP + k1);
+        buf[spad(k1 * CC + c)] = mk<C>(v.x, v.y);
+        buf[spad((k1 + 1) * CC + c)] = mk<C>(v.z, v.w);
+      }
+    } else {
+      for (int idx = tid; idx < N * CC; idx += NT) {
+        const int c = idx / N, k1 = idx - c * N;
+        buf[spad(k1 * CC + c)] = (c0 + c < H) ? src[((size_t)(c0 + c) * M + m) * CP + k1] : zero;
+      }
     }
   }
   TeamSync ts;
@@ -53,28 +76,70 @@ __global__ void __launch_bounds__((1 << LOGN) * cs_cc<T>() / cs_e<T>(1 << LOGN))
   fft_team<C, LOGN, CC, E, SIGN>(buf, tid, tw, ts);
   __syncthreads();
   if (SIGN < 0) {
-    for (int idx = tid; idx < N * CC; idx += NT) {
-      const int c = idx / N, k1 = idx - c * N;
-      if (c0 + c < H) dst[((size_t)(c0 + c) * M + m) * CP + k1] = buf[spad(k1 * CC + c)];
+    if constexpr (VEC) {
+      for (int i = tid; i < N * CC / 2; i += NT) {
+        const int c = i / (N / 2), k1 = 2 * (i - c * (N / 2));
+        if (c0 + c < H) {
+          const C a = buf[spad(k1 * CC + c)], b = buf[spad((k1 + 1) * CC + c)];
+          *reinterpret_cast<float4*>(dst + ((size_t)(c0 + c) * M + m) * CP + k1) = make_float4(a.x, a.y, b.x, b.y);
+        }
+      }
+    } else {
+      for (int idx = tid; idx < N * CC; idx += NT) {
+        const int c = idx / N, k1 = idx - c * N;
+        if (c0 + c < H) dst[((size_t)(c0 + c) * M + m) * CP + k1] = buf[spad(k1 * CC + c)];
+      }
     }
   } else {
     C* rows = dst + (size_t)m * N * P;
-    for (int idx = tid; idx < N * CC; idx += NT) {
-      const int n1 = idx / CC, c = idx - n1 * CC;
-      if (c0 + c < H) rows[(size_t)n1 * P + c0 + c] = buf[spad(idx)];
+    if constexpr (VEC) {
+      for (int i = tid; i < N * CC / 2; i += NT) {
+        const int n1 = i / (CC / 2), c = 2 * (i - n1 * (CC / 2));
+        const C a = buf[spad(n1 * CC + c)], b = buf[spad(n1 * CC + c + 1)];
+        C* q = rows + (size_t)n1 * P + c0 + c;
+        if (c0 + c + 1 < H) {
+          *reinterpret_cast<float4*>(q) = make_float4(a.x, a.y, b.x, b.y);
+        } else if (c0 + c < H) {
+          *q = a;
+        }
+      }
+    } else {
+      for (int idx = tid; idx < N * CC; idx += NT) {
+        const int n1 = idx / CC, c = idx - n1 * CC;
+        if (c0 + c < H) rows[(size_t)n1 * P + c0 + c] = buf[spad(idx)];
+      }
     }
   }
 }
-
 // X = xb + Pinv Q at every bin, in place on colbuf; thread = (k2, k1), k1 fastest.
+// 128-thread CTAs at <= ~72 registers (complex64) keep every bin of a
+// 512 x 512 x 10 problem resident in one wave; before waiting for the forward
+// column DFTs, each CTA prefetches its slab of the factor and the data term
+// (independent of them) into L2.
+constexpr int kSolveThreads = 128;
+template <typename T, int MMAX> constexpr int solve_minblocks() {
+  return sizeof(T) == 4 ? (MMAX <= 12 ? 7 : 5) : 3;
+}
+
 template <typename T, int MMAX>
-__global__ void __launch_bounds__(256, 3) solve_split_kernel(typename CT<T>::type* __restrict__ colbuf,
-                                                               const typename CT<T>::type* __restrict__ pinv,
-                                                               const typename CT<T>::type* __restrict__ xb, int N,
-                                                               int M, int plain) {
+__global__ void __launch_bounds__(kSolveThreads, solve_minblocks<T, MMAX>())
+    solve_split_kernel(typename CT<T>::type* __restrict__ colbuf, const typename CT<T>::type* __restrict__ pinv,
+                       const typename CT<T>::type* __restrict__ xb, int N, int M, int plain) {
   using C = typename CT<T>::type;
-  const int k1 = blockIdx.x * 256 + threadIdx.x;
+  const int k1 = blockIdx.x * kSolveThreads + threadIdx.x;
   const int k2 = blockIdx.y;
+  {
+    const int npk = M * (M + 1) / 2;
+    const int CP = col_pitch(N);
+    const int k1lo = blockIdx.x * kSolveThreads;
+    const int cnt = min(kSolveThreads, N - k1lo);
+    const int j = threadIdx.x;
+    if (j < npk + M) {
+      const C* base = (j < npk) ? pinv + ((size_t)k2 * npk + j) * CP + k1lo
+                                : xb + ((size_t)k2 * M + (j - npk)) * CP + k1lo;
+      prefetch_l2(base, (size_t)cnt * sizeof(C));
+    }
+  }
   grid_dep_wait();  // the forward column DFTs are complete from here on
   grid_dep_launch();
   if (k1 >= N) return;
@@ -148,7 +213,7 @@ cudaError_t colfft_n(const typename CT<T>::type* src, typename CT<T>::type* dst,
 template <typename T>
 cudaError_t solve_m(typename CT<T>::type* colbuf, const typename CT<T>::type* pinv, const typename CT<T>::type* xb,
                     int N, int M, int plain, cudaStream_t s) {
-  const dim3 grid((N + 255) / 256, N / 2 + 1), block(256);
+  const dim3 grid((N + kSolveThreads - 1) / kSolveThreads, N / 2 + 1), block(kSolveThreads);
   if (M <= 4) return launch_pdl(solve_split_kernel<T, 4>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
   if (M <= 8) return launch_pdl(solve_split_kernel<T, 8>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
   if (M <= 10) return launch_pdl(solve_split_kernel<T, 10>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
