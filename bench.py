@@ -465,10 +465,21 @@ def main():
     # launching stream, over the same steps (kept out of the timed region above: ~400 event
     # records per step would add to its time)
     plan.set_timing(True)
+    ph = {"setup": 0.0, "iterations": 0.0, "readback": 0.0}
     for _ in range(args.steps):
         flush.zero_()
-        step(h_dev, y_dev, x_dev)
-    torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        plan.set_psfs(h_dev)
+        plan.set_measurements(y_dev)
+        ev[1].record(stream)
+        plan.iterate(ITERS)
+        ev[2].record(stream)
+        plan.get_x(x_dev)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        for i, k in enumerate(ph):
+            ph[k] += ev[i].elapsed_time(ev[i + 1]) / args.steps
     kt = plan.get_timing()
     plan.set_timing(False)
     total_ms = sum(ms)
@@ -517,7 +528,8 @@ def main():
             "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
             "peak_source": "measured" if pk else "fallback",
             "avg_launch_us": {"column_pass": round(avgB * 1e3, 2), "prior_pass": round(avgA * 1e3, 2)},
-            "algorithmic_bytes": ab}
+            "algorithmic_bytes": ab,
+            "phases_ms": {k: round(v, 3) for k, v in ph.items()}}
 
     line = {"metric": METRIC, "value": value, "unit": "voxel-iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

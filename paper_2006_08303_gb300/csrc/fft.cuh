@@ -137,12 +137,20 @@ __device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* _
       for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = __ldg(&tw[r * j * (kTwN / (LS * R))]);
     }
   }
+  // Padded addresses as base + constant: with q = (N/R)*NF, the unpadded
+  // read index is i0 + r*q with i0 = t*NF + f, and (i0 & 15) + r*q never
+  // crosses a multiple of 16 beyond r*q itself (q >= 16, or i0 < q <= 16
+  // with q | 16), so spad(i0 + r*q) = spad(i0) + r*q + (r*q)/16; likewise
+  // for the writes with u = LS*NF.
+  constexpr int Q = (N / R) * NF;
+  constexpr int U = LS * NF;
   if (active) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int t = tt + TT * b;
+      const int p0 = spad(t * NF + f);
 #pragma unroll
-      for (int r = 0; r < R; ++r) a[b * R + r] = buf[spad((t + r * (N / R)) * NF + f)];
+      for (int r = 0; r < R; ++r) a[b * R + r] = buf[p0 + r * Q + (r * Q) / 16];
     }
   }
   ts.sync();
@@ -161,8 +169,9 @@ __device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* _
       }
       dft_r<R, SIGN>(&a[b * R]);
       const int base = (t / LS) * LS * R + j;
+      const int p0 = spad(base * NF + f);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[spad((base + r * LS) * NF + f)] = a[b * R + r];
+      for (int r = 0; r < R; ++r) buf[p0 + r * U + (r * U) / 16] = a[b * R + r];
     }
   }
   ts.sync();
