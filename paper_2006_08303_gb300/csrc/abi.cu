@@ -70,10 +70,10 @@ struct cip_plan {
   void* pinv = nullptr;
   void* bhat = nullptr;       // data term xb = Psi^{-1} beta Lambda^H F y / N^2
   void* colbuf = nullptr;     // split column pass: column-contiguous spectra [N/2+1][M][N]
-  double2* pinv64 = nullptr;  // FP64 copy of the packed factor
-  double2* lam64 = nullptr;  // FP64 PSF spectra [K*M][N][P]
+  void* pinv64 = nullptr;     // setup-precision copy of the packed factor (SetupC<T>)
+  void* lam64 = nullptr;      // setup-precision PSF spectra [K*M][N][P] (SetupC<T>)
   void* tw = nullptr;        // plan-precision twiddles
-  double2* tw64 = nullptr;   // FP64 twiddles for setup FFTs
+  void* tw64 = nullptr;       // setup-precision twiddles (SetupC<T>)
   double* gs = nullptr;      // 4 sin^2(pi k / N)
   double* partials = nullptr;
   double* resid = nullptr;   // [kNPart + 2]
@@ -239,25 +239,34 @@ cip_status stage_in(cip_plan* p, const void* src, size_t bytes, cudaStream_t s, 
   return CIP_OK;
 }
 
+// the setup-precision buffers of a plan of real type T
+template <typename T> SetupC<T>* setup_buf(void* b) { return static_cast<SetupC<T>*>(b); }
+
 template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
   using C = typename CT<T>::type;
   if (!p->lam64) return fail(p, CIP_ERR_STATE, "the PSF spectra were released (cip_set_psfs again)");
   if (!p->pinv64)
-    CIP_CUDA(p, dmalloc(p, (void**)&p->pinv64, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(double2)));
+    CIP_CUDA(p, dmalloc(p, &p->pinv64, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(SetupC<T>)));
   CIP_CUDA(p, cudaMemsetAsync(p->pinv_list, 0, sizeof(int), s));
   const int use_g = p->prior == CIP_PRIOR_TV ? 1 : 0;
   // analysis: Psi = rho g I + beta Lambda^H Lambda; dictionary: t I + beta Lambda^H Lambda with t = 1
   // (P^H P = I for a convolutional dictionary, Eq. solx_synt_DFT)
   const double diag = is_cd(p) ? 1.0 : p->rho;
-  if (p->opt.precision == 1) {
-    CIP_LAUNCH(p, launch_factor_fp32(p->lam64, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
-                                     reinterpret_cast<float2*>(p->pinv), p->pinv_list, kPinvListCap, s));
-  } else {
-    CIP_LAUNCH(p, launch_factor<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
-                                   static_cast<C*>(p->pinv), p->pinv64, p->pinv_list, kPinvListCap, s));
+  const SetupC<T>* lam = setup_buf<T>(p->lam64);
+  bool plain = false;
+  if constexpr (sizeof(T) == 4) {
+    if (p->opt.precision == 1) {
+      plain = true;
+      CIP_LAUNCH(p, launch_factor_fp32(lam, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
+                                       reinterpret_cast<float2*>(p->pinv), p->pinv_list, kPinvListCap, s));
+    }
   }
-  CIP_LAUNCH(p, launch_factor_pinv<T>(p->lam64, p->gs, use_g, p->K, p->M, p->N, diag, p->beta,
-                                      static_cast<C*>(p->pinv), p->pinv64, p->pinv_list, kPinvListCap, s));
+  if (!plain) {
+    CIP_LAUNCH(p, launch_factor<T>(lam, p->gs, use_g, p->K, p->M, p->N, diag, p->beta, static_cast<C*>(p->pinv),
+                                   setup_buf<T>(p->pinv64), p->pinv_list, kPinvListCap, s));
+  }
+  CIP_LAUNCH(p, launch_factor_pinv<T>(lam, p->gs, use_g, p->K, p->M, p->N, diag, p->beta, static_cast<C*>(p->pinv),
+                                      setup_buf<T>(p->pinv64), p->pinv_list, kPinvListCap, s));
   int nlist = 0;
   CIP_CUDA(p, cudaMemcpyAsync(&nlist, p->pinv_list, sizeof(int), cudaMemcpyDeviceToHost, s));
   CIP_CUDA(p, cudaStreamSynchronize(s));
@@ -277,13 +286,14 @@ template <typename T> cip_status do_set_dictionary(cip_plan* p, const void* d, c
   st = stage_in(p, d, (size_t)p->L * p->Pf * p->Pf * sizeof(T), s, sg, &dd);
   if (st != CIP_OK) return st;
   double* emb = nullptr;
-  double2* th64 = nullptr;
+  using R = typename SetupReal<T>::type;
+  SetupC<T>* th64 = nullptr;
   CIP_CUDA(p, cudaMallocAsync((void**)&emb, real_elems(p, p->L) * sizeof(double), s));
-  CIP_CUDA(p, cudaMallocAsync((void**)&th64, half_elems(p, p->L) * sizeof(double2), s));
+  CIP_CUDA(p, cudaMallocAsync((void**)&th64, half_elems(p, p->L) * sizeof(SetupC<T>), s));
   cudaError_t e = cudaMemsetAsync(emb, 0, real_elems(p, p->L) * sizeof(double), s);
   if (e == cudaSuccess) e = launch_embed_filters<T>(static_cast<const T*>(dd), emb, p->L, p->Pf, p->N, s);
-  if (e == cudaSuccess) e = launch_row_r2c<double, double>(emb, th64, p->N, p->L * p->N, 1.0, p->tw64, s);
-  if (e == cudaSuccess) e = launch_col_c2c<double>(th64, p->N, p->L, -1, p->tw64, s);
+  if (e == cudaSuccess) e = launch_row_r2c<R, double>(emb, th64, p->N, p->L * p->N, R(1.0f), setup_buf<T>(p->tw64), s);
+  if (e == cudaSuccess) e = launch_col_c2c<R>(th64, p->N, p->L, -1, setup_buf<T>(p->tw64), s);
   if (e == cudaSuccess) e = launch_theta_store<T>(th64, static_cast<C*>(p->theta), p->L, p->N, s);
   if (e == cudaSuccess) p->launches += 4;
   cudaFreeAsync(emb, s);
@@ -313,11 +323,14 @@ template <typename T> cip_status do_set_psfs(cip_plan* p, const void* h, cudaStr
   const void* dh = nullptr;
   cip_status r = stage_in(p, h, bytes, s, st, &dh);
   if (r != CIP_OK) return r;
-  if (!p->lam64) CIP_CUDA(p, dmalloc(p, (void**)&p->lam64, half_elems(p, p->K * p->M) * sizeof(double2)));
+  using R = typename SetupReal<T>::type;
+  if (!p->lam64) CIP_CUDA(p, dmalloc(p, &p->lam64, half_elems(p, p->K * p->M) * sizeof(SetupC<T>)));
   p->factor_src = nullptr;
   const int nrows = p->K * p->M * p->N;
-  CIP_LAUNCH(p, (launch_row_r2c<double, T>(static_cast<const T*>(dh), p->lam64, p->N, nrows, 1.0, p->tw64, s)));
-  CIP_LAUNCH(p, launch_col_c2c<double>(p->lam64, p->N, p->K * p->M, -1, p->tw64, s));
+  SetupC<T>* lam = setup_buf<T>(p->lam64);
+  const SetupC<T>* tw = setup_buf<T>(p->tw64);
+  CIP_LAUNCH(p, (launch_row_r2c<R, T>(static_cast<const T*>(dh), lam, p->N, nrows, R(1.0f), tw, s)));
+  CIP_LAUNCH(p, launch_col_c2c<R>(lam, p->N, p->K * p->M, -1, tw, s));
   p->have_psfs = true;
   r = form_factor<T>(p, s);
   if (r != CIP_OK) return r;
@@ -333,18 +346,26 @@ template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream
   const void* dy = nullptr;
   cip_status r = stage_in(p, y, bytes, s, st, &dy);
   if (r != CIP_OK) return r;
-  double2* yhat = nullptr;
+  using R = typename SetupReal<T>::type;
+  SetupC<T>* yhat = nullptr;
   // spectra and FP64 factor: the plan's own, or those of the plan its factor was adopted from
   const cip_plan* fs = p->factor_src ? p->factor_src : p;
   if (!fs->lam64 || !fs->pinv64) return fail(p, CIP_ERR_STATE, "the PSF spectra were released (cip_set_psfs again)");
-  CIP_CUDA(p, cudaMallocAsync((void**)&yhat, half_elems(p, p->K) * sizeof(double2), s));
-  cudaError_t e = launch_row_r2c<double, T>(static_cast<const T*>(dy), yhat, p->N, p->K * p->N, 1.0, p->tw64, s);
-  if (e == cudaSuccess) e = launch_col_c2c<double>(yhat, p->N, p->K, -1, p->tw64, s);
+  CIP_CUDA(p, cudaMallocAsync((void**)&yhat, half_elems(p, p->K) * sizeof(SetupC<T>), s));
+  const SetupC<T>* tw = setup_buf<T>(p->tw64);
+  cudaError_t e = launch_row_r2c<R, T>(static_cast<const T*>(dy), yhat, p->N, p->K * p->N, R(1.0f), tw, s);
+  if (e == cudaSuccess) e = launch_col_c2c<R>(yhat, p->N, p->K, -1, tw, s);
   if (e == cudaSuccess) {
-    if (p->opt.precision == 1)
-      e = launch_rhs_fp32(fs->lam64, yhat, p->K, p->M, p->N, p->beta, reinterpret_cast<float2*>(p->bhat), s);
-    else
-      e = launch_rhs<T>(fs->lam64, yhat, fs->pinv64, p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
+    const SetupC<T>* lam = setup_buf<T>(fs->lam64);
+    bool plain = false;
+    if constexpr (sizeof(T) == 4) {
+      if (p->opt.precision == 1) {
+        plain = true;
+        e = launch_rhs_fp32(lam, yhat, p->K, p->M, p->N, p->beta, reinterpret_cast<float2*>(p->bhat), s);
+      }
+    }
+    if (!plain)
+      e = launch_rhs<T>(lam, yhat, setup_buf<T>(fs->pinv64), p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
   }
   if (e == cudaSuccess) p->launches += 3;
   cudaFreeAsync(yhat, s);
@@ -752,7 +773,7 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
   ALLOC(p->qh, half_elems(p, M) * ce);
   ALLOC(p->bhat, col_elems(p, M) * ce);
   ALLOC(p->tw, (size_t)kTwN * ce);
-  ALLOC(p->tw64, (size_t)kTwN * sizeof(double2));
+  ALLOC(p->tw64, (size_t)kTwN * 16);  // complex double-float (complex64 plans) or complex128
   ALLOC(p->gs, (size_t)N * sizeof(double));
   ALLOC(p->resid, (kNPart + 2) * sizeof(double));
   ALLOC(p->conv, sizeof(int));
@@ -763,8 +784,11 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
   twiddles(re, im);
   std::vector<double2> t64(kTwN);
   std::vector<float2> t32(kTwN);
+  std::vector<cdf> tdf(kTwN);
   for (int k = 0; k < kTwN; ++k) {
     t64[k] = make_double2(re[k], im[k]);
+    tdf[k].x = df64_from_host(re[k]);
+    tdf[k].y = df64_from_host(im[k]);
     t32[k] = make_float2((float)re[k], (float)im[k]);
   }
   std::vector<double> gs(N);
@@ -775,7 +799,9 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
   }
   gs[0] = 0.0;
   cudaError_t e = cudaStreamSynchronize(p->ast);  // buffers valid on every stream from here on
-  if (e == cudaSuccess) e = cudaMemcpy(p->tw64, t64.data(), kTwN * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = dtype == CIP_F64 ? cudaMemcpy(p->tw64, t64.data(), kTwN * sizeof(double2), cudaMemcpyHostToDevice)
+                         : cudaMemcpy(p->tw64, tdf.data(), kTwN * sizeof(cdf), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = dtype == CIP_F64 ? cudaMemcpy(p->tw, t64.data(), kTwN * sizeof(double2), cudaMemcpyHostToDevice)
                          : cudaMemcpy(p->tw, t32.data(), kTwN * sizeof(float2), cudaMemcpyHostToDevice);

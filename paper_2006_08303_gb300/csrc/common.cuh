@@ -53,6 +53,16 @@ __device__ __forceinline__ void cfmac(double2& acc, double2 a, double2 b) {
   acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+// complex value from computed parts of the complex type's own real type
+template <typename C, typename R> __device__ __forceinline__ C cpack(R re, R im) {
+  C c;
+  c.x = re;
+  c.y = im;
+  return c;
+}
+// read-only cached load of a table entry (twiddles)
+__device__ __forceinline__ float2 ldg_tw(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_tw(const double2* p) { return __ldg(p); }
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(a.x) s) { a.x *= s; a.y *= s; return a; }
 
 // Shared-memory padding: one complex slot per 16 keeps every Stockham read

@@ -99,7 +99,7 @@ __global__ void embed_kernel(const Tin* __restrict__ d, double* __restrict__ out
 
 // theta from the half-pitch layout [L][N][P] (FP64) to the column layout [k2][L][CP]
 template <typename T>
-__global__ void theta_store_kernel(const double2* __restrict__ th64, typename CT<T>::type* __restrict__ th, int L,
+__global__ void theta_store_kernel(const SetupC<T>* __restrict__ th64, typename CT<T>::type* __restrict__ th, int L,
                                    int N) {
   using C = typename CT<T>::type;
   const int H = N / 2 + 1, P = half_pitch(N), CP = col_pitch(N);
@@ -109,8 +109,7 @@ __global__ void theta_store_kernel(const double2* __restrict__ th64, typename CT
     const size_t r = i / N;
     const int l = (int)(r % L);
     const int k2 = (int)(r / L);
-    const double2 v = th64[((size_t)l * N + k1) * P + k2];
-    th[((size_t)k2 * L + l) * CP + k1] = mk<C>(v.x, v.y);
+    th[((size_t)k2 * L + l) * CP + k1] = cconv<C>(th64[((size_t)l * N + k1) * P + k2]);
   }
 }
 
@@ -165,7 +164,7 @@ cudaError_t launch_embed_filters(const Tin* d, double* out, int L, int P, int N,
 }
 
 template <typename T>
-cudaError_t launch_theta_store(const double2* th64, typename CT<T>::type* th, int L, int N, cudaStream_t s) {
+cudaError_t launch_theta_store(const SetupC<T>* th64, typename CT<T>::type* th, int L, int N, cudaStream_t s) {
   theta_store_kernel<T><<<512, 256, 0, s>>>(th64, th, L, N);
   return cudaGetLastError();
 }
@@ -174,7 +173,7 @@ template cudaError_t launch_cd_solve<float>(const CDArgs<float>&, cudaStream_t);
 template cudaError_t launch_cd_solve<double>(const CDArgs<double>&, cudaStream_t);
 template cudaError_t launch_embed_filters<float>(const float*, double*, int, int, int, cudaStream_t);
 template cudaError_t launch_embed_filters<double>(const double*, double*, int, int, int, cudaStream_t);
-template cudaError_t launch_theta_store<float>(const double2*, float2*, int, int, cudaStream_t);
+template cudaError_t launch_theta_store<float>(const cdf*, float2*, int, int, cudaStream_t);
 template cudaError_t launch_theta_store<double>(const double2*, double2*, int, int, cudaStream_t);
 
 }  // namespace cip

@@ -1,16 +1,22 @@
-// Setup kernels, all arithmetic in FP64:
+// Setup kernels:
 //   * Psi(w) = rho g(w) I + beta Lambda(w)^H Lambda(w) at every half-spectrum
 //     bin and its inverse (Alg. 1 line 2; Section IV-A, the inverse of Psi is
 //     "computed only once").  Positive-definite bins use a Cholesky
-//     factorisation L L^H and Psi^{-1} = L^{-H} L^{-1}; bins where g(w) = 0
-//     (the DC bin of TV, singular when the PSFs have unit sum) or where the
-//     factorisation fails get the min-norm pseudo-inverse from a cyclic
-//     Jacobi eigendecomposition of the real 2M x 2M embedding of Psi
+//     factorisation L L^H and Psi^{-1} = L^{-H} L^{-1}, in the setup precision
+//     (double-float, about 44 bits, for complex64 plans; FP64 for complex128
+//     plans; square roots and reciprocals of the M pivots in FP64), with the
+//     packed triangle of each bin in shared memory.  Bins where g(w) = 0 (the
+//     DC bin of TV, singular when the PSFs have unit sum) or where the
+//     factorisation fails get the min-norm pseudo-inverse from a cyclic Jacobi
+//     eigendecomposition of the real 2M x 2M embedding of Psi in FP64
 //     (eigenvalues below 1e-10 of the largest dropped).  Results are scaled by
 //     1/N^2 (the inverse-DFT normalisation) and rounded once to the plan's
-//     precision, packed as the upper triangle row by row.
-//   * xb(w) = Psi^{-1}(w) beta Lambda(w)^H yhat(w) in FP64 (the constant data term).
+//     precision, packed as the upper triangle row by row; a setup-precision
+//     copy is kept for the data term.
+//   * xb(w) = Psi^{-1}(w) beta Lambda(w)^H yhat(w) in the setup precision (the constant data term).
 //   * the deterministic reduction of the prior pass's residual partial sums.
+// The PSF and measurement spectra arrive in the setup precision: complex
+// double-float (cdf) for complex64 plans, complex FP64 for complex128 plans.
 #include "kernels.h"
 
 namespace cip {
@@ -28,13 +34,14 @@ __device__ __forceinline__ double bin_g(const double* gs, int use_g, int k1, int
   return use_g ? gs[k1] + gs[k2] : 1.0;
 }
 
-// Psi_ij (i >= j) = rho g delta_ij + beta sum_k conj(Lam_{k,i}) Lam_{k,j}
-__device__ __forceinline__ double2 psi_entry(const double2* lam, size_t off, size_t mplane, int K, int M, int i, int j,
+// Psi_ij (i >= j) = rho g delta_ij + beta sum_k conj(Lam_{k,i}) Lam_{k,j}, in FP64
+template <typename S>
+__device__ __forceinline__ double2 psi_entry(const S* lam, size_t off, size_t mplane, int K, int M, int i, int j,
                                              double rho_g, double beta) {
   double2 acc = make_double2(0.0, 0.0);
   for (int k = 0; k < K; ++k) {
-    const double2 a = lam[(size_t)(k * M + i) * mplane + off];
-    const double2 b = lam[(size_t)(k * M + j) * mplane + off];
+    const double2 a = cconv<double2>(lam[(size_t)(k * M + i) * mplane + off]);
+    const double2 b = cconv<double2>(lam[(size_t)(k * M + j) * mplane + off]);
     cfmac(acc, a, b);
   }
   acc.x *= beta;
@@ -46,14 +53,25 @@ __device__ __forceinline__ double2 psi_entry(const double2* lam, size_t off, siz
   return acc;
 }
 
-template <typename Tout>
-__global__ void __launch_bounds__(128) factor_kernel(const double2* __restrict__ lam, const double* __restrict__ gs,
-                                                     int use_g, int K, int M, int N, double rho, double beta,
-                                                     typename CT<Tout>::type* __restrict__ pinv,
-                                                     double2* __restrict__ pinv64, int* list, int cap) {
+constexpr int kFacThreads = 64;
+constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // packed lower triangle, i >= j
+
+// One thread per bin; its packed triangle lives in shared memory as
+// [entry][thread] (consecutive threads, consecutive 16-byte slots), so the
+// factorisation keeps no matrix in registers or local memory.
+template <typename Tout, int MMAX>
+__global__ void __launch_bounds__(kFacThreads) factor_kernel(const SetupC<Tout>* __restrict__ lam,
+                                                             const double* __restrict__ gs, int use_g, int K, int M,
+                                                             int N, double rho, double beta,
+                                                             typename CT<Tout>::type* __restrict__ pinv,
+                                                             SetupC<Tout>* __restrict__ pinv64, int* list, int cap) {
   using C = typename CT<Tout>::type;
+  using R = typename SetupReal<Tout>::type;
+  using S = SetupC<Tout>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* sm = reinterpret_cast<S*>(smem_raw);
   const int H = N / 2 + 1, P = half_pitch(N);
-  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  const int bin = blockIdx.x * kFacThreads + threadIdx.x;
   if (bin >= N * H) return;
   const int k1 = bin / H, k2 = bin - k1 * H;
   const size_t off = (size_t)k1 * P + k2, mplane = (size_t)N * P;
@@ -62,54 +80,98 @@ __global__ void __launch_bounds__(128) factor_kernel(const double2* __restrict__
     push_bin(list, cap, bin);
     return;
   }
-  double2 L[kMaxM][kMaxM];
-  for (int i = 0; i < M; ++i)
-    for (int j = 0; j <= i; ++j) L[i][j] = psi_entry(lam, off, mplane, K, M, i, j, rho * g, beta);
-  // Cholesky, lower, in place
+  auto A = [&](int e) -> S& { return sm[e * kFacThreads + threadIdx.x]; };
+  const S zero = mk<S>(0.0, 0.0);
+  // Gram matrix, accumulated over the K measurement rows of Lambda
+#pragma unroll
+  for (int i = 0; i < MMAX; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j)
+      if (i < M) A(tri(i, j)) = zero;
+  for (int k = 0; k < K; ++k) {
+    S l[MMAX];
+#pragma unroll
+    for (int i = 0; i < MMAX; ++i)
+      if (i < M) l[i] = lam[(size_t)(k * M + i) * mplane + off];
+#pragma unroll
+    for (int i = 0; i < MMAX; ++i) {
+      if (i < M) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+          S a = A(tri(i, j));
+          cfmac(a, l[i], l[j]);
+          A(tri(i, j)) = a;
+        }
+      }
+    }
+  }
+  const R bd(beta), rg(rho * g);
+#pragma unroll
+  for (int i = 0; i < MMAX; ++i) {
+    if (i < M) {
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        S a = A(tri(i, j));
+        a.x = a.x * bd;
+        a.y = a.y * bd;
+        if (i == j) {
+          a.x = a.x + rg;
+          a.y = R(0.0f);
+        }
+        A(tri(i, j)) = a;
+      }
+    }
+  }
+  // Cholesky L L^H, lower, in place; square roots and reciprocals of the pivots in FP64.
+  // The diagonal slot keeps 1/L_jj, which is also the diagonal of W = L^{-1}.
   for (int j = 0; j < M; ++j) {
-    double d = L[j][j].x;
-    for (int k = 0; k < j; ++k) d -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
-    if (!(d > 0.0)) {
+    R d = A(tri(j, j)).x;
+    for (int k = 0; k < j; ++k) {
+      const S a = A(tri(j, k));
+      d = d - dfma(a.x, a.x, a.y * a.y);
+    }
+    const double dd = to_double(d);
+    if (!(dd > 0.0)) {
       push_bin(list, cap, bin);
       return;
     }
-    const double ljj = sqrt(d);
-    L[j][j] = make_double2(ljj, 0.0);
-    const double inv = 1.0 / ljj;
+    const R inv(1.0 / sqrt(dd));
+    A(tri(j, j)) = cmk(inv, R(0.0f));
     for (int i = j + 1; i < M; ++i) {
-      double2 s = L[i][j];
+      S t = A(tri(i, j));
       for (int k = 0; k < j; ++k) {
-        // s -= L[i][k] conj(L[j][k])
-        const double2 a = L[i][k], b = L[j][k];
-        s.x -= a.x * b.x + a.y * b.y;
-        s.y -= a.y * b.x - a.x * b.y;
+        // t -= L_ik conj(L_jk)
+        const S a = A(tri(i, k)), b = A(tri(j, k));
+        t.x = t.x - dfma(a.x, b.x, a.y * b.y);
+        t.y = t.y - dfma(a.y, b.x, -(a.x * b.y));
       }
-      L[i][j] = make_double2(s.x * inv, s.y * inv);
+      A(tri(i, j)) = cmk(t.x * inv, t.y * inv);
     }
   }
-  // W = L^{-1} (lower)
-  double2 W[kMaxM][kMaxM];
-  for (int i = 0; i < M; ++i) {
-    const double inv = 1.0 / L[i][i].x;
-    W[i][i] = make_double2(inv, 0.0);
+  // W = L^{-1} in place, row by row: W_ij = -W_ii sum_{k=j}^{i-1} L_ik W_kj, for ascending j
+  // (reads L_ik with k >= j of the row being rewritten and the finished rows above it)
+  for (int i = 1; i < M; ++i) {
+    const R wii = A(tri(i, i)).x;
     for (int j = 0; j < i; ++j) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int k = j; k < i; ++k) cfma(s, L[i][k], W[k][j]);
-      W[i][j] = make_double2(-s.x * inv, -s.y * inv);
+      S t = zero;
+      for (int k = j; k < i; ++k) cfma(t, A(tri(i, k)), A(tri(k, j)));
+      A(tri(i, j)) = cmk(-(t.x * wii), -(t.y * wii));
     }
   }
-  // Psi^{-1} = W^H W, packed upper, scaled by 1/N^2; the plan-precision copy is
-  // stored [k2][pk][k1] (contiguous bins along a column), the FP64 copy [pk][k1][P]
-  const double sc = 1.0 / ((double)N * (double)N);
+  // Psi^{-1} = W^H W, packed upper, scaled by 1/N^2 (exact: N is a power of two); the
+  // plan-precision copy is stored [k2][pk][k1] (contiguous bins along a column), the
+  // setup-precision copy [pk][k1][P]
+  const float sc = 1.0f / ((float)N * (float)N);
   const size_t colbase = (size_t)k2 * (M * (M + 1) / 2) * col_pitch(N) + k1;
   int pk = 0;
   for (int i = 0; i < M; ++i) {
     for (int j = i; j < M; ++j) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int k = j; k < M; ++k) cfmac(s, W[k][i], W[k][j]);
-      if (i == j) s.y = 0.0;
-      pinv[colbase + (size_t)pk * col_pitch(N)] = mk<C>(s.x * sc, s.y * sc);
-      if (pinv64) pinv64[(size_t)pk * mplane + off] = make_double2(s.x * sc, s.y * sc);
+      S t = zero;
+      for (int k = j; k < M; ++k) cfmac(t, A(tri(k, i)), A(tri(k, j)));
+      if (i == j) t.y = R(0.0f);
+      t = cscale_pow2(t, sc);
+      pinv[colbase + (size_t)pk * col_pitch(N)] = cconv<C>(t);
+      if (pinv64) pinv64[(size_t)pk * mplane + off] = t;
       ++pk;
     }
   }
@@ -117,9 +179,10 @@ __global__ void __launch_bounds__(128) factor_kernel(const double2* __restrict__
 
 // Min-norm pseudo-inverse at the listed bins (one thread per bin).
 template <typename Tout>
-__global__ void factor_pinv_kernel(const double2* __restrict__ lam, const double* __restrict__ gs, int use_g, int K,
-                                   int M, int N, double rho, double beta, typename CT<Tout>::type* __restrict__ pinv,
-                                   double2* __restrict__ pinv64, const int* list, int cap) {
+__global__ void factor_pinv_kernel(const SetupC<Tout>* __restrict__ lam, const double* __restrict__ gs, int use_g,
+                                   int K, int M, int N, double rho, double beta,
+                                   typename CT<Tout>::type* __restrict__ pinv, SetupC<Tout>* __restrict__ pinv64,
+                                   const int* list, int cap) {
   using C = typename CT<Tout>::type;
   const int n = min(list[0], cap);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,52 +254,76 @@ __global__ void factor_pinv_kernel(const double2* __restrict__ lam, const double
       }
       if (i == j) im = 0.0;
       pinv[((size_t)k2 * (M * (M + 1) / 2) + pk) * col_pitch(N) + k1] = mk<C>(re * sc, im * sc);
-      if (pinv64) pinv64[(size_t)pk * mplane + off] = make_double2(re * sc, im * sc);
+      if (pinv64) pinv64[(size_t)pk * mplane + off] = cconv<SetupC<Tout>>(make_double2(re * sc, im * sc));
       ++pk;
     }
   }
 }
 
-// xb(w) = Psi^{-1}(w) / N^2 * beta Lambda(w)^H yhat(w), all in FP64, rounded once.
-// This is the data term of Eq. solx_Trans_DFT; it does not change across
+// xb(w) = Psi^{-1}(w) / N^2 * beta Lambda(w)^H yhat(w) in the setup precision, rounded
+// once.  This is the data term of Eq. solx_Trans_DFT; it does not change across
 // iterations, so the ill-conditioned product with Psi^{-1} (cancellation at
-// bins where the PSFs are nearly dependent) is taken once in FP64 and the
-// per-iteration column pass only adds Psi^{-1} rho F T^H (t - u).
-template <typename Tout>
-__global__ void rhs_kernel(const double2* __restrict__ lam, const double2* __restrict__ yhat,
-                           const double2* __restrict__ pinv64, int K, int M, int N, double beta,
-                           typename CT<Tout>::type* __restrict__ xb) {
+// bins where the PSFs are nearly dependent) is taken once at high precision and
+// the per-iteration column pass only adds Psi^{-1} rho F T^H (t - u).
+template <typename Tout, int MMAX>
+__global__ void __launch_bounds__(128) rhs_kernel(const SetupC<Tout>* __restrict__ lam,
+                                                  const SetupC<Tout>* __restrict__ yhat,
+                                                  const SetupC<Tout>* __restrict__ pinv64, int K, int M, int N,
+                                                  double beta, typename CT<Tout>::type* __restrict__ xb) {
   using C = typename CT<Tout>::type;
+  using R = typename SetupReal<Tout>::type;
+  using S = SetupC<Tout>;
   const int H = N / 2 + 1, P = half_pitch(N);
   const int bin = blockIdx.x * blockDim.x + threadIdx.x;
   if (bin >= N * H) return;
   const int k1 = bin / H, k2 = bin - k1 * H;
   const size_t off = (size_t)k1 * P + k2, mplane = (size_t)N * P;
-  double2 b[kMaxM], x[kMaxM];
-  for (int m = 0; m < M; ++m) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k < K; ++k) cfmac(acc, lam[(size_t)(k * M + m) * mplane + off], yhat[(size_t)k * mplane + off]);
-    b[m] = make_double2(beta * acc.x, beta * acc.y);
-    x[m] = make_double2(0.0, 0.0);
+  const R bd(beta);
+  const S zero = mk<S>(0.0, 0.0);
+  S b[MMAX], x[MMAX];
+#pragma unroll
+  for (int m = 0; m < MMAX; ++m) {
+    b[m] = zero;
+    x[m] = zero;
+  }
+  for (int k = 0; k < K; ++k) {
+    const S yk = yhat[(size_t)k * mplane + off];
+#pragma unroll
+    for (int m = 0; m < MMAX; ++m)
+      if (m < M) cfmac(b[m], lam[(size_t)(k * M + m) * mplane + off], yk);
+  }
+#pragma unroll
+  for (int m = 0; m < MMAX; ++m) {
+    b[m].x = b[m].x * bd;
+    b[m].y = b[m].y * bd;
   }
   int pk = 0;
-  for (int i = 0; i < M; ++i) {
-    for (int j = i; j < M; ++j) {
-      const double2 pij = pinv64[(size_t)pk * mplane + off];
-      ++pk;
-      cfma(x[i], pij, b[j]);
-      if (j != i) cfmac(x[j], pij, b[i]);
+#pragma unroll
+  for (int i = 0; i < MMAX; ++i) {
+    if (i < M) {
+#pragma unroll
+      for (int j = i; j < MMAX; ++j) {
+        if (j < M) {
+          const S pij = pinv64[(size_t)pk * mplane + off];
+          ++pk;
+          cfma(x[i], pij, b[j]);
+          if (j != i) cfmac(x[j], pij, b[i]);
+        }
+      }
     }
   }
   // stored [k2][m][k1]: the bins of one column are contiguous for the column pass
-  for (int m = 0; m < M; ++m) xb[((size_t)k2 * M + m) * col_pitch(N) + k1] = mk<C>(x[m].x, x[m].y);
+#pragma unroll
+  for (int m = 0; m < MMAX; ++m)
+    if (m < M) xb[((size_t)k2 * M + m) * col_pitch(N) + k1] = cconv<C>(x[m]);
 }
 
 template <typename Tout>
-__global__ void store_kernel(const double2* __restrict__ src, typename CT<Tout>::type* __restrict__ dst, size_t n) {
+__global__ void store_kernel(const SetupC<Tout>* __restrict__ src, typename CT<Tout>::type* __restrict__ dst,
+                             size_t n) {
   using C = typename CT<Tout>::type;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = mk<C>(src[i].x, src[i].y);
+    dst[i] = cconv<C>(src[i]);
 }
 
 __global__ void reduce_kernel(const double* __restrict__ partials, int nblocks, double rho, double tol,
@@ -267,20 +354,41 @@ __global__ void reduce_kernel(const double* __restrict__ partials, int nblocks, 
 
 }  // namespace
 
-template <typename Tout>
-cudaError_t launch_factor(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
-                          double beta, typename CT<Tout>::type* pinv, double2* pinv64, int* pinv_list, int list_cap,
-                          cudaStream_t s) {
-  if (M > kMaxM) return cudaErrorInvalidValue;
+template <typename Tout, int MMAX>
+cudaError_t launch_factor_m(const SetupC<Tout>* lam, const double* gs, int use_g, int K, int M, int N, double rho,
+                            double beta, typename CT<Tout>::type* pinv, SetupC<Tout>* pinv64, int* pinv_list,
+                            int list_cap, cudaStream_t s) {
   const int nb = N * (N / 2 + 1);
-  factor_kernel<Tout><<<(nb + 127) / 128, 128, 0, s>>>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64, pinv_list,
-                                                       list_cap);
+  const size_t sm = (size_t)(M * (M + 1) / 2) * kFacThreads * sizeof(SetupC<Tout>);
+  auto k = factor_kernel<Tout, MMAX>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    const int most = MMAX * (MMAX + 1) / 2 * kFacThreads * (int)sizeof(SetupC<Tout>);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  k<<<(nb + kFacThreads - 1) / kFacThreads, kFacThreads, sm, s>>>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64,
+                                                                  pinv_list, list_cap);
   return cudaGetLastError();
 }
 
 template <typename Tout>
-cudaError_t launch_factor_pinv(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
-                               double beta, typename CT<Tout>::type* pinv, double2* pinv64, const int* pinv_list,
+cudaError_t launch_factor(const SetupC<Tout>* lam, const double* gs, int use_g, int K, int M, int N, double rho,
+                          double beta, typename CT<Tout>::type* pinv, SetupC<Tout>* pinv64, int* pinv_list,
+                          int list_cap, cudaStream_t s) {
+  if (M <= 4) return launch_factor_m<Tout, 4>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64, pinv_list, list_cap, s);
+  if (M <= 8) return launch_factor_m<Tout, 8>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64, pinv_list, list_cap, s);
+  if (M <= 12)
+    return launch_factor_m<Tout, 12>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64, pinv_list, list_cap, s);
+  if (M <= kMaxM)
+    return launch_factor_m<Tout, 16>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64, pinv_list, list_cap, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename Tout>
+cudaError_t launch_factor_pinv(const SetupC<Tout>* lam, const double* gs, int use_g, int K, int M, int N, double rho,
+                               double beta, typename CT<Tout>::type* pinv, SetupC<Tout>* pinv64, const int* pinv_list,
                                int list_cap, cudaStream_t s) {
   if (M > kMaxM) return cudaErrorInvalidValue;
   factor_pinv_kernel<Tout><<<(list_cap + 31) / 32, 32, 0, s>>>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64,
@@ -289,16 +397,21 @@ cudaError_t launch_factor_pinv(const double2* lam, const double* gs, int use_g, 
 }
 
 template <typename Tout>
-cudaError_t launch_rhs(const double2* lam, const double2* yhat, const double2* pinv64, int K, int M, int N,
-                       double beta, typename CT<Tout>::type* xb, cudaStream_t s) {
-  if (M > kMaxM) return cudaErrorInvalidValue;
+cudaError_t launch_rhs(const SetupC<Tout>* lam, const SetupC<Tout>* yhat, const SetupC<Tout>* pinv64, int K, int M,
+                       int N, double beta, typename CT<Tout>::type* xb, cudaStream_t s) {
   const int nb = N * (N / 2 + 1);
-  rhs_kernel<Tout><<<(nb + 127) / 128, 128, 0, s>>>(lam, yhat, pinv64, K, M, N, beta, xb);
+  const dim3 grid((nb + 127) / 128), block(128);
+  if (M <= 4) rhs_kernel<Tout, 4><<<grid, block, 0, s>>>(lam, yhat, pinv64, K, M, N, beta, xb);
+  else if (M <= 8) rhs_kernel<Tout, 8><<<grid, block, 0, s>>>(lam, yhat, pinv64, K, M, N, beta, xb);
+  else if (M <= 10) rhs_kernel<Tout, 10><<<grid, block, 0, s>>>(lam, yhat, pinv64, K, M, N, beta, xb);
+  else if (M <= 12) rhs_kernel<Tout, 12><<<grid, block, 0, s>>>(lam, yhat, pinv64, K, M, N, beta, xb);
+  else if (M <= kMaxM) rhs_kernel<Tout, 16><<<grid, block, 0, s>>>(lam, yhat, pinv64, K, M, N, beta, xb);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 template <typename Tout>
-cudaError_t launch_spectra_store(const double2* src, typename CT<Tout>::type* dst, size_t n, cudaStream_t s) {
+cudaError_t launch_spectra_store(const SetupC<Tout>* src, typename CT<Tout>::type* dst, size_t n, cudaStream_t s) {
   store_kernel<Tout><<<1024, 256, 0, s>>>(src, dst, n);
   return cudaGetLastError();
 }
@@ -309,19 +422,19 @@ cudaError_t launch_reduce_partials(const double* partials, int nblocks, double r
   return cudaGetLastError();
 }
 
-template cudaError_t launch_factor<float>(const double2*, const double*, int, int, int, int, double, double, float2*,
-                                          double2*, int*, int, cudaStream_t);
+template cudaError_t launch_factor<float>(const cdf*, const double*, int, int, int, int, double, double, float2*,
+                                          cdf*, int*, int, cudaStream_t);
 template cudaError_t launch_factor<double>(const double2*, const double*, int, int, int, int, double, double,
                                            double2*, double2*, int*, int, cudaStream_t);
-template cudaError_t launch_factor_pinv<float>(const double2*, const double*, int, int, int, int, double, double,
-                                               float2*, double2*, const int*, int, cudaStream_t);
+template cudaError_t launch_factor_pinv<float>(const cdf*, const double*, int, int, int, int, double, double, float2*,
+                                               cdf*, const int*, int, cudaStream_t);
 template cudaError_t launch_factor_pinv<double>(const double2*, const double*, int, int, int, int, double, double,
                                                 double2*, double2*, const int*, int, cudaStream_t);
-template cudaError_t launch_rhs<float>(const double2*, const double2*, const double2*, int, int, int, double,
-                                       float2*, cudaStream_t);
+template cudaError_t launch_rhs<float>(const cdf*, const cdf*, const cdf*, int, int, int, double, float2*,
+                                       cudaStream_t);
 template cudaError_t launch_rhs<double>(const double2*, const double2*, const double2*, int, int, int, double,
                                         double2*, cudaStream_t);
-template cudaError_t launch_spectra_store<float>(const double2*, float2*, size_t, cudaStream_t);
+template cudaError_t launch_spectra_store<float>(const cdf*, float2*, size_t, cudaStream_t);
 template cudaError_t launch_spectra_store<double>(const double2*, double2*, size_t, cudaStream_t);
 
 }  // namespace cip
@@ -335,7 +448,7 @@ template cudaError_t launch_spectra_store<double>(const double2*, double2*, size
 namespace cip {
 namespace {
 
-__global__ void __launch_bounds__(128) factor_fp32_kernel(const double2* __restrict__ lam, const double* __restrict__ gs,
+__global__ void __launch_bounds__(128) factor_fp32_kernel(const cdf* __restrict__ lam, const double* __restrict__ gs,
                                                           int use_g, int K, int M, int N, float rho, float beta,
                                                           float2* __restrict__ pinv, int* list, int cap) {
   const int H = N / 2 + 1, P = half_pitch(N);
@@ -353,8 +466,8 @@ __global__ void __launch_bounds__(128) factor_fp32_kernel(const double2* __restr
     for (int j = 0; j <= i; ++j) {
       float2 acc = make_float2(0.f, 0.f);
       for (int k = 0; k < K; ++k) {
-        const double2 a = lam[(size_t)(k * M + i) * mplane + off], b = lam[(size_t)(k * M + j) * mplane + off];
-        cfmac(acc, make_float2((float)a.x, (float)a.y), make_float2((float)b.x, (float)b.y));
+        cfmac(acc, cconv<float2>(lam[(size_t)(k * M + i) * mplane + off]),
+              cconv<float2>(lam[(size_t)(k * M + j) * mplane + off]));
       }
       acc.x *= beta;
       acc.y *= beta;
@@ -406,7 +519,7 @@ __global__ void __launch_bounds__(128) factor_fp32_kernel(const double2* __restr
     }
 }
 
-__global__ void rhs_fp32_kernel(const double2* __restrict__ lam, const double2* __restrict__ yhat, int K, int M,
+__global__ void rhs_fp32_kernel(const cdf* __restrict__ lam, const cdf* __restrict__ yhat, int K, int M,
                                 int N, float beta, float2* __restrict__ b) {
   const int H = N / 2 + 1, P = half_pitch(N);
   const int bin = blockIdx.x * blockDim.x + threadIdx.x;
@@ -416,8 +529,7 @@ __global__ void rhs_fp32_kernel(const double2* __restrict__ lam, const double2* 
   for (int m = 0; m < M; ++m) {
     float2 acc = make_float2(0.f, 0.f);
     for (int k = 0; k < K; ++k) {
-      const double2 l = lam[(size_t)(k * M + m) * mplane + off], y = yhat[(size_t)k * mplane + off];
-      cfmac(acc, make_float2((float)l.x, (float)l.y), make_float2((float)y.x, (float)y.y));
+      cfmac(acc, cconv<float2>(lam[(size_t)(k * M + m) * mplane + off]), cconv<float2>(yhat[(size_t)k * mplane + off]));
     }
     b[((size_t)k2 * M + m) * col_pitch(N) + k1] = make_float2(beta * acc.x, beta * acc.y);
   }
@@ -425,7 +537,7 @@ __global__ void rhs_fp32_kernel(const double2* __restrict__ lam, const double2* 
 
 }  // namespace
 
-cudaError_t launch_factor_fp32(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
+cudaError_t launch_factor_fp32(const cdf* lam, const double* gs, int use_g, int K, int M, int N, double rho,
                                double beta, float2* pinv, int* pinv_list, int list_cap, cudaStream_t s) {
   if (M > kMaxM) return cudaErrorInvalidValue;
   const int nb = N * (N / 2 + 1);
@@ -434,7 +546,7 @@ cudaError_t launch_factor_fp32(const double2* lam, const double* gs, int use_g, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_rhs_fp32(const double2* lam, const double2* yhat, int K, int M, int N, double beta, float2* b,
+cudaError_t launch_rhs_fp32(const cdf* lam, const cdf* yhat, int K, int M, int N, double beta, float2* b,
                             cudaStream_t s) {
   const int nb = N * (N / 2 + 1);
   rhs_fp32_kernel<<<(nb + 255) / 256, 256, 0, s>>>(lam, yhat, K, M, N, (float)beta, b);

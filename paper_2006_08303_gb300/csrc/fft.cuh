@@ -97,15 +97,20 @@ template <int SIGN, typename C> __device__ __forceinline__ void dft8(C* a) {
   C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
   dft4<SIGN>(e0, e1, e2, e3);
   dft4<SIGN>(o0, o1, o2, o3);
-  // w^k = exp(SIGN i pi k / 4)
+  // w^k = exp(SIGN i pi k / 4): w^1 = (1 + SIGN i)/sqrt2, w^3 = (-1 + SIGN i)/sqrt2
   C w1o, w2o, w3o;
-  // w^1 = (1 + SIGN i)/sqrt2
-  w1o.x = h * (o1.x - R(SIGN) * o1.y);
-  w1o.y = h * (o1.y + R(SIGN) * o1.x);
+  if constexpr (SIGN < 0) {
+    w1o.x = h * (o1.x + o1.y);
+    w1o.y = h * (o1.y - o1.x);
+    w3o.x = h * (o3.y - o3.x);
+    w3o.y = -(h * (o3.y + o3.x));
+  } else {
+    w1o.x = h * (o1.x - o1.y);
+    w1o.y = h * (o1.y + o1.x);
+    w3o.x = -(h * (o3.x + o3.y));
+    w3o.y = h * (o3.x - o3.y);
+  }
   w2o = mul_si<SIGN>(o2);
-  // w^3 = (-1 + SIGN i)/sqrt2
-  w3o.x = h * (-o3.x - R(SIGN) * o3.y);
-  w3o.y = h * (-o3.y + R(SIGN) * o3.x);
   a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
   a[1] = cadd(e1, w1o); a[5] = csub(e1, w1o);
   a[2] = cadd(e2, w2o); a[6] = csub(e2, w2o);
@@ -134,7 +139,7 @@ __device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* _
     for (int b = 0; b < B; ++b) {
       const int j = (tt + TT * b) & (LS - 1);
 #pragma unroll
-      for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = __ldg(&tw[r * j * (kTwN / (LS * R))]);
+      for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = ldg_tw(&tw[r * j * (kTwN / (LS * R))]);
     }
   }
   // Padded addresses as base + constant: with q = (N/R)*NF, the unpadded
@@ -202,10 +207,10 @@ __device__ __forceinline__ void fft_team(C* buf, int tid, const C* __restrict__ 
 template <typename C>
 __device__ __forceinline__ void pair_spectrum_put(C* z, int N, int k, C xa, C xb) {
   if (k == 0 || k == N / 2) {
-    z[spad(k)] = mk<C>(xa.x, xb.x);
+    z[spad(k)] = cpack<C>(xa.x, xb.x);
   } else {
-    z[spad(k)] = mk<C>(xa.x - xb.y, xa.y + xb.x);
-    z[spad(N - k)] = mk<C>(xa.x + xb.y, xb.x - xa.y);
+    z[spad(k)] = cpack<C>(xa.x - xb.y, xa.y + xb.x);
+    z[spad(N - k)] = cpack<C>(xa.x + xb.y, xb.x - xa.y);
   }
 }
 

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kRowThreads) row_r2c_kernel(const Tin* __restr
     const int ra = row0 + 2 * p, rb = ra + 1;
     const Tc xa = ra < nrows ? (Tc)in[(size_t)ra * N + n] : Tc(0);
     const Tc xb = rb < nrows ? (Tc)in[(size_t)rb * N + n] : Tc(0);
-    zb[p * ZS + spad(n)] = mk<C>(xa * scale * Tc(0.5), xb * scale * Tc(0.5));
+    zb[p * ZS + spad(n)] = cpack<C>(xa * scale * Tc(0.5f), xb * scale * Tc(0.5f));
   }
   __syncthreads();
   const int team = tid / TEAM;
@@ -177,8 +177,8 @@ cudaError_t launch_col_c2c(typename CT<Tc>::type* data, int N, int nmaps, int si
   CIP_SWITCH_N(N, (cc2c<Tc, L>(data, nmaps, sign, tw, s)))
 }
 
-template cudaError_t launch_row_r2c<double, float>(const float*, double2*, int, int, double, const double2*,
-                                                   cudaStream_t);
+template cudaError_t launch_row_r2c<df64, float>(const float*, cdf*, int, int, df64, const cdf*, cudaStream_t);
+template cudaError_t launch_row_r2c<df64, double>(const double*, cdf*, int, int, df64, const cdf*, cudaStream_t);
 template cudaError_t launch_row_r2c<double, double>(const double*, double2*, int, int, double, const double2*,
                                                     cudaStream_t);
 template cudaError_t launch_row_r2c<float, float>(const float*, float2*, int, int, float, const float2*,
@@ -188,5 +188,6 @@ template cudaError_t launch_row_c2r<double, double>(const double2*, double*, int
                                                     cudaStream_t);
 template cudaError_t launch_col_c2c<float>(float2*, int, int, int, const float2*, cudaStream_t);
 template cudaError_t launch_col_c2c<double>(double2*, int, int, int, const double2*, cudaStream_t);
+template cudaError_t launch_col_c2c<df64>(cdf*, int, int, int, const cdf*, cudaStream_t);
 
 }  // namespace cip

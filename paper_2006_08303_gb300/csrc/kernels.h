@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace cip {
 
@@ -48,9 +49,9 @@ template <typename T> struct PassBArgs {
 };
 
 // plain FP32 method: factor formed and inverted in FP32, b = beta Lambda^H F y in FP32
-cudaError_t launch_factor_fp32(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
+cudaError_t launch_factor_fp32(const cdf* lam, const double* gs, int use_g, int K, int M, int N, double rho,
                                double beta, float2* pinv, int* pinv_list, int list_cap, cudaStream_t s);
-cudaError_t launch_rhs_fp32(const double2* lam, const double2* yhat, int K, int M, int N, double beta, float2* b,
+cudaError_t launch_rhs_fp32(const cdf* lam, const cdf* yhat, int K, int M, int N, double beta, float2* b,
                             cudaStream_t s);
 
 // Convolutional-dictionary column solve (Eqs. solx_synt_DFT, solz_DFT, solz_DFT_SM), one
@@ -74,7 +75,7 @@ cudaError_t launch_p_from_z(const typename CT<T>::type* zcol, const typename CT<
                             typename CT<T>::type* p, int N, int M, int L, cudaStream_t s);
 template <typename Tin> cudaError_t launch_embed_filters(const Tin* d, double* out, int L, int P, int N, cudaStream_t s);
 template <typename T>
-cudaError_t launch_theta_store(const double2* th64, typename CT<T>::type* th, int L, int N, cudaStream_t s);
+cudaError_t launch_theta_store(const SetupC<T>* th64, typename CT<T>::type* th, int L, int N, cudaStream_t s);
 // column DFTs between the row layout [maps][N][P] and the column layout [H][maps][CP]
 template <typename T>
 cudaError_t launch_colfft_fwd(const typename CT<T>::type* rows, typename CT<T>::type* cols,
@@ -109,25 +110,28 @@ template <typename Tc>
 cudaError_t launch_col_c2c(typename CT<Tc>::type* data, int N, int nmaps, int sign,
                            const typename CT<Tc>::type* tw, cudaStream_t s);
 
-// Factor formation in FP64: Psi = rho g I + beta Lam^H Lam per bin; writes
+// Factor formation in the setup precision (double-float for complex64 plans, FP64 for
+// complex128 plans): Psi = rho g I + beta Lam^H Lam per bin; writes
 // Psi^{-1} / N^2 packed into `pinv`.  Bins needing a pseudo-inverse are
 // appended to `pinv_list` (count in pinv_list[0]).
-// The FP64 copy `pinv64` (same layout) is written too when non-null.
+// The setup-precision copy `pinv64` (same layout) is written too when non-null.
 template <typename Tout>
-cudaError_t launch_factor(const double2* lam, const double* gs, int use_g, int K, int M, int N, double rho,
-                          double beta, typename CT<Tout>::type* pinv, double2* pinv64, int* pinv_list, int list_cap,
+cudaError_t launch_factor(const SetupC<Tout>* lam, const double* gs, int use_g, int K, int M, int N, double rho,
+                          double beta, typename CT<Tout>::type* pinv, SetupC<Tout>* pinv64, int* pinv_list,
+                          int list_cap,
                           cudaStream_t s);
 template <typename Tout>
-cudaError_t launch_factor_pinv(const double2* lam, const double* gs, int use_g, int K, int M, int N,
-                               double rho, double beta, typename CT<Tout>::type* pinv, double2* pinv64,
+cudaError_t launch_factor_pinv(const SetupC<Tout>* lam, const double* gs, int use_g, int K, int M, int N,
+                               double rho, double beta, typename CT<Tout>::type* pinv, SetupC<Tout>* pinv64,
                                const int* pinv_list, int list_cap, cudaStream_t s);
-// xb = Pinv64 (beta Lam^H yhat), all FP64, rounded once to the plan precision
+// xb = Pinv64 (beta Lam^H yhat) in the setup precision, rounded once to the plan precision
 template <typename Tout>
-cudaError_t launch_rhs(const double2* lam, const double2* yhat, const double2* pinv64, int K, int M, int N,
+cudaError_t launch_rhs(const SetupC<Tout>* lam, const SetupC<Tout>* yhat, const SetupC<Tout>* pinv64, int K, int M,
+                       int N,
                        double beta, typename CT<Tout>::type* xb, cudaStream_t s);
-// copy FP64 spectra to the plan precision
+// copy setup-precision spectra to the plan precision
 template <typename Tout>
-cudaError_t launch_spectra_store(const double2* src, typename CT<Tout>::type* dst, size_t n, cudaStream_t s);
+cudaError_t launch_spectra_store(const SetupC<Tout>* src, typename CT<Tout>::type* dst, size_t n, cudaStream_t s);
 
 // deterministic reduction of pass-A partials: out[0..kNPart) sums, out[5]=r_rel, out[6]=s_rel,
 // conv[0] set to 1 when both relative residuals < tol (tol > 0)
