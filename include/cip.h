@@ -68,9 +68,12 @@ typedef struct cip_options {
   int col_tile;     /* columns per CTA of the column pass (1, 2 or 4); 0 = automatic */
   int check_every;  /* residual check period for cip_iterate with tol > 0; 0 = 10 */
   int column_pass;  /* 0 = autotuned at cip_set_measurements (fused vs split, tile width; cached per
-                       N, M, dtype), 1 = fused cluster kernel, 2 = split (column FFT / solve / FFT) */
+                       N, M, dtype for the process, and in the file named by the environment variable
+                       CIP_TUNE_CACHE when set, one "N M dtype mode cc" line per decision, read on
+                       first use), 1 = fused cluster kernel, 2 = split (column FFT / solve / FFT) */
   int precision;    /* CIP_F32 plans: 0 = mixed (factor and data term Psi^{-1} beta Lambda^H F y formed
-                       in FP64, rounded once; the default), 1 = plain FP32 method (factor formed and
+                       in double-float, about 44 bits, rounded once; the default), 1 = plain FP32
+                       method (factor formed and
                        inverted in FP32, x = Psi^{-1} (beta Lambda^H F y + rho F T^H (t - u)) applied in
                        FP32 every iteration; analysis priors only) */
   int reserved[12];
@@ -101,17 +104,19 @@ size_t cip_plan_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior);
 
 /* Prior and ADMM weights (Alg. 1 line 1): lambda > 0, rho > 0, beta > 0.
  * Must precede cip_set_psfs; calling it again afterwards re-forms the factor
- * from the kept FP64 PSF spectra and requires cip_set_measurements again
+ * from the kept PSF spectra and requires cip_set_measurements again
  * (the precomputed data term depends on the factor). */
 cip_status cip_set_prior(cip_plan* plan, cip_prior prior, double lambda, double rho, double beta, void* stream);
 
-/* PSFs h[K][M][N][N] (plan dtype).  Forms Lambda = DFT2(h) in FP64 and the
- * per-frequency factor Psi^{-1} in FP64 (Alg. 1 line 2; Section IV-A), kept
- * in the plan's precision.  Resets the ADMM state. */
+/* PSFs h[K][M][N][N] (plan dtype).  Forms Lambda = DFT2(h) and the
+ * per-frequency factor Psi^{-1} (Alg. 1 line 2; Section IV-A) in the setup
+ * precision -- double-float (about 44 bits, on the FP32 pipes) for CIP_F32
+ * plans, FP64 for CIP_F64 plans -- kept in the plan's precision.  Resets the
+ * ADMM state. */
 cip_status cip_set_psfs(cip_plan* plan, const void* h, void* stream);
 
 /* Measurements y[K][N][N] (plan dtype): the data term of the x-update,
- * Psi^{-1} beta Lambda^H F y (Alg. 1 line 2), formed in FP64 and rounded
+ * Psi^{-1} beta Lambda^H F y (Alg. 1 line 2), formed in the setup precision and rounded
  * once to the plan's precision.  Resets the ADMM state (t = u = 0). */
 cip_status cip_set_measurements(cip_plan* plan, const void* y, void* stream);
 

@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -442,6 +444,28 @@ template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mo
 
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;  // (N, M, dtype) -> (mode, cc)
+bool g_tune_loaded = false;
+
+// Optional persistent tuning table: when CIP_TUNE_CACHE names a file, its lines
+// "N M dtype mode cc" seed the table on first use and every new decision is
+// appended, so that later processes (a profiler run, a service restart) reuse a
+// choice instead of timing again under different conditions.  Caller holds g_tune_mu.
+void tune_cache_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("CIP_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::ifstream in(path);
+  int n, m, dt, mode, cc;
+  while (in >> n >> m >> dt >> mode >> cc) g_tune[std::make_tuple(n, m, dt)] = {mode, cc};
+}
+void tune_cache_store(const std::tuple<int, int, int>& key, std::pair<int, int> v) {
+  const char* path = std::getenv("CIP_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::ofstream out(path, std::ios::app);
+  out << std::get<0>(key) << ' ' << std::get<1>(key) << ' ' << std::get<2>(key) << ' ' << v.first << ' ' << v.second
+      << '\n';
+}
 
 // Autotuner: times the fused column pass at each tile width and the split
 // form on this plan's buffers (the column pass only rewrites x-hat from q-hat,
@@ -452,10 +476,12 @@ template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
   const auto key = std::make_tuple(p->N, p->M, (int)p->dtype);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       p->colmode = it->second.first;
-      p->cc = it->second.second;
+      if (p->colmode == 1) p->cc = it->second.second;
+      p->blocksB = p->M * ((p->N / 2 + 1 + p->cc - 1) / p->cc);
       // a cached choice of the split form still needs this plan's own column buffer
       if (p->colmode == 2 && !p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
       return CIP_OK;
@@ -493,6 +519,7 @@ template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
   p->blocksB = p->M * ((p->N / 2 + 1 + p->cc - 1) / p->cc);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = {p->colmode, p->cc};
+  tune_cache_store(key, g_tune[key]);
   return CIP_OK;
 }
 
