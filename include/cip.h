@@ -155,7 +155,10 @@ cip_status cip_get_x(cip_plan* plan, void* x, void* stream);
 /* Scaled dual u[M][ncomp][N][N] (ncomp = 2 for TV, else 1). */
 cip_status cip_get_u(cip_plan* plan, void* u, void* stream);
 
-/* Relative residuals of the last iteration that computed them (synchronises). */
+/* Relative residuals of the last iteration that computed them (synchronises).
+ * Returns CIP_ERR_TIMEOUT if a kernel of the plan gave up a bounded wait for one of
+ * its asynchronous copies since the last state reset (the iterate is then invalid);
+ * cip_iterate with tol > 0 checks the same flag at each residual check. */
 cip_status cip_get_residuals(cip_plan* plan, double* r_rel, double* s_rel);
 
 /* Iterations run since the last reset/import. */

@@ -214,6 +214,7 @@ template <typename T> cip_status reset_state(cip_plan* p, cudaStream_t s) {
   const int S = smaps(p);
   CIP_CUDA(p, cudaMemsetAsync(p->xh, 0, half_elems(p, S) * sizeof(C), s));
   CIP_CUDA(p, cudaMemsetAsync(p->qh, 0, half_elems(p, S) * sizeof(C), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->conv, 0, 2 * sizeof(int), s));
   CIP_CUDA(p, cudaMemsetAsync(p->u[0], 0, real_elems(p, S) * nc * sizeof(T), s));
   CIP_CUDA(p, cudaMemsetAsync(p->u[1], 0, real_elems(p, S) * nc * sizeof(T), s));
   CIP_CUDA(p, cudaMemsetAsync(p->tprev, 0, real_elems(p, S) * nc * sizeof(T), s));
@@ -390,6 +391,7 @@ template <typename T> PassAArgs<T> passA_args(cip_plan* p, int flags) {
   a.tprev = static_cast<T*>(p->tprev);
   a.t_imp = nullptr;
   a.partials = p->partials;
+  a.err = p->conv + 1;
   a.tw = static_cast<const C*>(p->tw);
   a.M = smaps(p);
   a.tau = (T)(p->lam / p->rho);
@@ -579,7 +581,10 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
       if (tol > 0 && !last) {
         CIP_CUDA(p, cudaMemcpyAsync(p->resid_host, p->resid, (kNPart + 2) * sizeof(double),
                                     cudaMemcpyDeviceToHost, s));
+        int kerr = 0;
+        CIP_CUDA(p, cudaMemcpyAsync(&kerr, p->conv + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         CIP_CUDA(p, cudaStreamSynchronize(s));
+        if (kerr) return fail(p, CIP_ERR_TIMEOUT, "a device wait for an asynchronous copy timed out");
         const double r = p->resid_host[kNPart], sr = p->resid_host[kNPart + 1];
         if (!std::isfinite(r) || !std::isfinite(sr)) {
           if (done) *done = it + 1;
@@ -803,7 +808,7 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
   ALLOC(p->tw64, (size_t)kTwN * 16);  // complex double-float (complex64 plans) or complex128
   ALLOC(p->gs, (size_t)N * sizeof(double));
   ALLOC(p->resid, (kNPart + 2) * sizeof(double));
-  ALLOC(p->conv, sizeof(int));
+  ALLOC(p->conv, 2 * sizeof(int));  // [0] converged, [1] a kernel's bounded wait gave up
   ALLOC(p->pinv_list, (1 + kPinvListCap) * sizeof(int));
   if (p->colmode == 2) ALLOC(p->colbuf, col_elems(p, M) * ce);
 #undef ALLOC
@@ -973,7 +978,10 @@ cip_status cip_get_residuals(cip_plan* p, double* r_rel, double* s_rel) {
   if (!p) return CIP_ERR_INVALID_ARG;
   if (!p->resid_valid) return fail(p, CIP_ERR_STATE, "no residuals computed since the last reset");
   double h[kNPart + 2];
+  int kerr = 0;
   CIP_CUDA(p, cudaMemcpy(h, p->resid, sizeof(h), cudaMemcpyDeviceToHost));
+  CIP_CUDA(p, cudaMemcpy(&kerr, p->conv + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (kerr) return fail(p, CIP_ERR_TIMEOUT, "a device wait for an asynchronous copy timed out");
   if (r_rel) *r_rel = h[kNPart];
   if (s_rel) *s_rel = h[kNPart + 1];
   return CIP_OK;

@@ -27,6 +27,7 @@ template <typename T> struct PassAArgs {
   T* tprev;         // [M][ncomp][N][N] (STORE_T writes t, RESID reads t_prev)
   const T* t_imp;   // [M][ncomp][N][N] (IMPORT)
   double* partials; // [gridDim.y * gridDim.x][kNPart] (RESID)
+  int* err;         // set to 1 when a bounded wait on an asynchronous copy gives up
   const C* tw;      // twiddle table, kTwN entries
   int M;
   T tau;            // lambda / rho

@@ -69,11 +69,20 @@ template <typename T> constexpr int rows_for(int N, int prior) {
   return 2;
 }
 
+// DCT and l1 tiles stage their R rows of u in shared memory with one TMA bulk
+// copy issued before the grid dependency (u does not depend on the preceding
+// column pass), when the staging area keeps the CTA within ~100 KB
+template <typename T> constexpr bool u_staged(int N, int prior, int R) {
+  using C = typename CT<T>::type;
+  return prior != PRIOR_TV && (size_t)(R / 2) * spad(N) * sizeof(C) + (size_t)R * N * sizeof(T) <= 100 * 1024;
+}
+
 template <typename T> constexpr size_t smem_for(int N, int prior, int R) {
   using C = typename CT<T>::type;
   const int halo = prior == PRIOR_TV ? 1 : 0;
   size_t sm = (size_t)((R + 2 * halo) / 2) * spad(N) * sizeof(C);
   if (prior == PRIOR_TV) sm += (size_t)(2 * R + 1) * N * sizeof(T);
+  if (u_staged<T>(N, prior, R)) sm += (size_t)R * N * sizeof(T);
   return sm;
 }
 
@@ -202,6 +211,9 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   C* zb = reinterpret_cast<C*>(smem_raw);
   T* ah = reinterpret_cast<T*>(zb + NPIN * ZS);  // TV only: [R][N], a_h at tile rows 1..R
   T* av = ah + R * N;                             // TV only: [R+1][N], a_v at tile rows 0..R
+  constexpr bool USTAGE = u_staged<T>(N, PRIOR, R);
+  T* us = reinterpret_cast<T*>(zb + NPIN * ZS);   // DCT / l1 with USTAGE: [R][N] rows r0.. of u_in
+  __shared__ unsigned long long ubar;
 
   const int tid = threadIdx.x;
   const int nth = blockDim.x;
@@ -221,8 +233,19 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
 
   auto grow = [&](int j) { return (r0 - HALO + j) & (N - 1); };
 
+  if constexpr (USTAGE) {
+    // u rows r0 .. r0+R-1 of this channel: one contiguous block (16-byte aligned: r0 is a
+    // multiple of 8 and N >= 64), fetched by the TMA unit while the previous kernel drains
+    if (tid == 0) {
+      constexpr unsigned bytes = (unsigned)(R * N * sizeof(T));
+      mbar_init(&ubar, 1);
+      mbar_arrive_expect_tx(&ubar, bytes);
+      bulk_copy_g2s(us, u_in + (size_t)r0 * N, bytes, &ubar);
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+  }
   // L2 prefetch of the u rows (and t_prev rows) read after the inverse FFT
-  if (tid < 2 * NCOMP) {
+  if (tid < 2 * NCOMP && !(USTAGE && (tid & 1) == 0)) {
     const T* src = (tid & 1) ? tprev_rd : u_in;
     if (src) {
       const size_t comp = (size_t)(tid >> 1) * plane;
@@ -341,6 +364,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
       }
       __syncthreads();
     }
+    if constexpr (USTAGE) mbar_wait_bounded(&ubar, 0, a.err);
     // column DCT -> coefficients w; shrink; dual; inverse column DCT of (t - u')
     for (int idx = tid; idx < (R / 8) * N; idx += nth) {
       const int br = idx / N, c = idx - br * N;
@@ -357,13 +381,14 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const size_t g = (size_t)(r0 + br * 8 + k) * N + c;
+        const T uo = USTAGE ? us[(br * 8 + k) * N + c] : u_in[g];
         T t, un;
         if (import_mode) {
           t = timp[g];
-          un = u_in[g];
+          un = uo;
           w[k] = T(0);
         } else {
-          shrink(w[k], u_in[g], tau, t, un);
+          shrink(w[k], uo, tau, t, un);
         }
         u_out[g] = un;
         d[k] = t - un;
@@ -385,6 +410,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
       for (int n = 0; n < 8; ++n) zb[p * ZS + spad(c0 + n)] = mk<C>(o[n].x * a.qscale, o[n].y * a.qscale);
     }
   } else {  // PRIOR_L1: T = I
+    if constexpr (USTAGE) mbar_wait_bounded(&ubar, 0, a.err);
     for (int idx = tid; idx < NPOUT * N; idx += nth) {
       const int p = idx / N, c = idx - p * N;
       const C z = zb[p * ZS + spad(c)];
@@ -393,12 +419,13 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const size_t g = (size_t)(r0 + 2 * p + s) * N + c;
+        const T uo = USTAGE ? us[(2 * p + s) * N + c] : u_in[g];
         T t, un;
         if (import_mode) {
           t = timp[g];
-          un = u_in[g];
+          un = uo;
         } else {
-          shrink(w[s], u_in[g], tau, t, un);
+          shrink(w[s], uo, tau, t, un);
         }
         u_out[g] = un;
         if (resid) acc_resid(part, import_mode ? T(0) : w[s], t, un, tprev_rd, g);
