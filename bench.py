@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 N, M, K, ITERS = 512, 10, 10, 200
 WORKLOAD = f"spectral_dct_{N}x{N}x{M} (K={K}, 8x8 DCT l1, lambda=1e-3, rho=1e-2, beta=1, {ITERS} iterations)"
 METRIC = "ADMM voxel-iter/s"
+# DRAM bytes (read + write) per launch of each pass on this workload, from one ncu capture of the
+# current kernels (profiles/passes_spectral_dct_512x512x10.md; the column pass is the sum of its
+# three split kernels).  Set an entry to None when its kernels change until they are re-captured.
+TRAFFIC_BYTES = {"column_pass": 102_341_000, "prior_pass": 21_188_000}
 
 
 def peaks():
@@ -525,7 +529,7 @@ def main():
     peak = pk["hbm_gbs"] if pk else 6800.0
     achieved = byts / (avg / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
+            "frac": round(achieved / peak, 4), "traffic": TRAFFIC_BYTES.get(dom), "kernel": dom,
             "peak_source": "measured" if pk else "fallback",
             "avg_launch_us": {"column_pass": round(avgB * 1e3, 2), "prior_pass": round(avgA * 1e3, 2)},
             "algorithmic_bytes": ab,
