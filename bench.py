@@ -2,8 +2,9 @@
 (M = K = 10 channels, 512 x 512, disk-plus-Gaussian defocus PSFs, 8x8
 block-DCT l1 prior, 200 iterations of Alg. 1) on one GB300.
 
-One step = one whole reconstruction: PSF spectra + FP64 factor (setup),
-rhs, 200 fused iterations (column pass + prior pass) and the read-back of x.
+One step = one whole reconstruction: PSF spectra and factor (setup, in
+double-float), data term, 200 iterations (column pass + prior pass) and the
+read-back of x.
 L2 is flushed (256 MiB write) before every timed step, outside its events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -540,7 +541,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "M": M, "K": K, "iters": ITERS,
                        "parallelism": f"replicas{world}", "l2": "flushed before each step (256 MiB write)",
-                       "step": "setup (FP64 factor) + rhs + 200 iterations + read-back",
+                       "step": "setup (double-float spectra, factor and data term) + 200 iterations + read-back",
                        "launch": plan.config()},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "voxel-iter/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
