@@ -369,6 +369,8 @@ class ConvDictSetup:
     theta: np.ndarray   # [L, N, N]  DFT of the embedded filters
     Pinv: np.ndarray    # [N, N, M, M] (I + beta Lambda^H Lambda)^{-1}
     bhat: np.ndarray    # [M, N, N]
+    mu: float = 0.0     # Tikhonov weight on the code gradients (Eq. DL_PriorHP_conv)
+    rho_n: np.ndarray = None  # [N, N] diagonal of the z-update per bin: rho + mu (|r1^|^2 + |r2^|^2)
 
 
 def embed_filters(d: np.ndarray, N: int) -> np.ndarray:
@@ -384,18 +386,26 @@ def embed_filters(d: np.ndarray, N: int) -> np.ndarray:
 
 
 def convdict_setup(h: np.ndarray, y: np.ndarray, d: np.ndarray, lam: float, rho: float,
-                   beta: float) -> ConvDictSetup:
-    """Alg. 2 setup with t = 1 (P = I for the convolutional dictionary, Eq. solx_synt)."""
+                   beta: float, mu: float = 0.0) -> ConvDictSetup:
+    """Alg. 2 setup with t = 1 (P = I for the convolutional dictionary, Eq. solx_synt).
+
+    mu > 0 adds the gradient (Tikhonov) penalty mu/2 sum_m sum_i ||r_i * z_m||^2 on the codes
+    (Eq. DL_PriorHP_conv, 2D: r_1, r_2 the circular differences along the two axes).  Its normal
+    equation gains mu sum_i R_i^H R_i (the note after Eq. solz), diagonalised by the DFT with the
+    eigenvalues of D^T D of the TV operator, so per bin the z-update matrix is
+    (rho + mu g(w)) I + conj(theta) theta^T: still diagonal plus rank one."""
     K, M, N, _ = h.shape
     Lam = psf_spectra(h)
     Psi = form_psi(Lam, np.ones((N, N)), 1.0, beta)
     Pinv = np.linalg.inv(Psi)
     theta = dft2(embed_filters(d, N))
-    return ConvDictSetup(N, M, d.shape[0], lam, rho, beta, Lam, theta, Pinv, rhs_bhat(Lam, y, beta))
+    rho_n = rho + mu * gram_eigenvalues("tv", N)
+    return ConvDictSetup(N, M, d.shape[0], lam, rho, beta, Lam, theta, Pinv, rhs_bhat(Lam, y, beta), mu, rho_n)
 
 
 def sherman_morrison(theta_n: np.ndarray, c_n: np.ndarray, rho: float) -> np.ndarray:
-    """Eq. solz_DFT_SM at one bin (reading R10): solve (rho I + conj(theta) theta^T) v = c."""
+    """Eq. solz_DFT_SM at one bin (reading R10): solve (rho I + conj(theta) theta^T) v = c.
+    With the gradient penalty, rho is the bin's diagonal rho + mu g(w)."""
     a = theta_n.conj()
     return (c_n - a * (theta_n @ c_n) / (rho + np.vdot(theta_n, theta_n).real)) / rho
 
@@ -413,7 +423,7 @@ def convdict_step(C: ConvDictSetup, z: np.ndarray, t: np.ndarray, u: np.ndarray)
         for b in range(C.N):
             th = C.theta[:, a, b]
             for m in range(C.M):
-                v[:, m, a, b] = sherman_morrison(th, c[:, m, a, b], C.rho)
+                v[:, m, a, b] = sherman_morrison(th, c[:, m, a, b], C.rho_n[a, b])
     z_new = idft2(v).real
     t_new = soft(z_new + u, C.lam / C.rho)
     u_new = u + z_new - t_new

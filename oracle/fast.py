@@ -117,9 +117,10 @@ class FastConvDict:
     Pinv: np.ndarray   # [N, H, M, M]
     bhat: np.ndarray   # [N, H, M]
     theta: np.ndarray  # [N, H, L]
+    rho_n: np.ndarray = None  # [N, H] rho + mu g(w) (gradient penalty on the codes)
 
 
-def convdict_setup(h, y, d, lam, rho, beta) -> FastConvDict:
+def convdict_setup(h, y, d, lam, rho, beta, mu: float = 0.0) -> FastConvDict:
     K, M, N, _ = h.shape
     Lam = np.moveaxis(rfft2(h), (0, 1), (2, 3))
     Psi = np.eye(M) + beta * np.einsum("abki,abkj->abij", Lam.conj(), Lam)
@@ -127,7 +128,8 @@ def convdict_setup(h, y, d, lam, rho, beta) -> FastConvDict:
     Y = np.moveaxis(rfft2(y), 0, 2)
     bhat = beta * np.einsum("abkm,abk->abm", Lam.conj(), Y)
     theta = np.moveaxis(rfft2(ref.embed_filters(d, N)), 0, 2)
-    return FastConvDict(N, M, d.shape[0], lam, rho, beta, Pinv, bhat, theta)
+    rho_n = rho + mu * ref.gram_eigenvalues("tv", N)[:, : N // 2 + 1]
+    return FastConvDict(N, M, d.shape[0], lam, rho, beta, Pinv, bhat, theta, rho_n)
 
 
 def convdict_step(C: FastConvDict, z, t, u):
@@ -141,7 +143,8 @@ def convdict_step(C: FastConvDict, z, t, u):
     th = C.theta[..., None]
     dot = np.sum(th * c, axis=2, keepdims=True)                 # theta^T c
     nrm = np.sum(np.abs(C.theta) ** 2, axis=2)[..., None, None]
-    v = (c - th.conj() * dot / (C.rho + nrm)) / C.rho
+    rn = C.rho_n[..., None, None]
+    v = (c - th.conj() * dot / (rn + nrm)) / rn
     z_new = irfft2(np.moveaxis(v, (2, 3), (0, 1)), C.N)
     t_new = ref.soft(z_new + u, C.lam / C.rho)
     return x, z_new, t_new, u + z_new - t_new

@@ -305,21 +305,31 @@ def cd8():
     return dict(rng=rng, N=N, K=K, M=M, L=L, d=d, h=h, y=y, C=C, z=z, t=t, u=u)
 
 
-def test_convdict_x_and_z_update_dense(cd8):
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_convdict_x_and_z_update_dense(cd8, mu):
     """Eq. iterd_ADMM1 and Eq. iterd_ADMM2 solved densely (reading R9: 1/2||Dz - x||^2,
-    rho/2 ||z - t + u||^2) match Eqs. solx_synt_DFT and solz_DFT/solz_DFT_SM of the oracle."""
-    N, M, L, d, h, y, C = cd8["N"], cd8["M"], cd8["L"], cd8["d"], cd8["h"], cd8["y"], cd8["C"]
+    rho/2 ||z - t + u||^2; with mu > 0 also mu/2 sum ||r_i * z_m||^2 of Eq. DL_PriorHP_conv,
+    r_i the circular differences along each axis, built here as an explicit dense operator)
+    match Eqs. solx_synt_DFT and solz_DFT/solz_DFT_SM of the oracle."""
+    N, M, L, d, h, y = cd8["N"], cd8["M"], cd8["L"], cd8["d"], cd8["h"], cd8["y"]
+    C0 = cd8["C"]
+    C = admm.convdict_setup(h, y, d, C0.lam, C0.rho, C0.beta, mu)
     z, t, u = cd8["z"], cd8["t"], cd8["u"]
     de = admm.embed_filters(d, N)
     Dop = lambda zz: np.stack([sum(admm.circconv2(zz[l, m], de[l]) for l in range(L)) for m in range(M)])
     H = dense_operator(lambda v: admm.forward_H(v, h), (M, N, N))
     D = dense_operator(Dop, (L, M, N, N))
+
+    def grad_op(zz):  # [L, M, N, N] -> both axis differences of every code map, by index shifts
+        return np.stack([np.roll(zz, -1, axis=2) - zz, np.roll(zz, -1, axis=3) - zz])
+
+    G = dense_operator(grad_op, (L, M, N, N))
     beta, rho = C.beta, C.rho
     A = np.concatenate([math.sqrt(beta) * H, np.eye(M * N * N)])
     b = np.concatenate([math.sqrt(beta) * y.ravel(), Dop(z).ravel()])
     x_ls = np.linalg.lstsq(A, b, rcond=None)[0].reshape(M, N, N)
-    A2 = np.concatenate([D, math.sqrt(rho) * np.eye(L * M * N * N)])
-    b2 = np.concatenate([x_ls.ravel(), math.sqrt(rho) * (t - u).ravel()])
+    A2 = np.concatenate([D, math.sqrt(rho) * np.eye(L * M * N * N), math.sqrt(mu) * G])
+    b2 = np.concatenate([x_ls.ravel(), math.sqrt(rho) * (t - u).ravel(), np.zeros(G.shape[0])])
     z_ls = np.linalg.lstsq(A2, b2, rcond=None)[0].reshape(L, M, N, N)
     x, z_new, t_new, u_new = admm.convdict_step(C, z, t, u)
     assert rel(x, x_ls) < 1e-10
@@ -343,9 +353,11 @@ def test_fast_oracle_matches_naive(prior):
     assert rel(xf, xs) < 1e-11 and rel(uf, us) < 1e-11
 
 
-def test_fast_convdict_matches_naive(cd8):
-    C = cd8["C"]
-    F = fast.convdict_setup(cd8["h"], cd8["y"], cd8["d"], C.lam, C.rho, C.beta)
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_fast_convdict_matches_naive(cd8, mu):
+    C0 = cd8["C"]
+    C = admm.convdict_setup(cd8["h"], cd8["y"], cd8["d"], C0.lam, C0.rho, C0.beta, mu)
+    F = fast.convdict_setup(cd8["h"], cd8["y"], cd8["d"], C.lam, C.rho, C.beta, mu)
     xs, zs, ts, us, _ = admm.run_convdict(C, 6)
     xf, zf, tf, uf = fast.run_convdict(F, 6)
     assert rel(xf, xs) < 1e-11 and rel(zf, zs) < 1e-11
