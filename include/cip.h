@@ -130,6 +130,16 @@ cip_status cip_set_measurements(cip_plan* plan, const void* y, void* stream);
  * t, u and the coefficient maps z have shape [M][L][N][N] (channel-major). */
 cip_status cip_set_dictionary(cip_plan* plan, const void* filters, int L, int P, void* stream);
 
+/* Gradient (Tikhonov) penalty on the codes of a CIP_PRIOR_CONVDICT plan (Section III-B,
+ * "Convolutional Dictionary with Tikhonov Regularization", Eq. DL_PriorHP_conv in 2D):
+ * adds mu/2 sum_m (||r_1 * z_m||^2 + ||r_2 * z_m||^2), r_1, r_2 the circular differences
+ * along the two image axes.  The z-update of each frequency w then solves
+ * ((rho + mu g(w)) I + conj(theta) theta^T) v = c by Sherman-Morrison, g(w) = 4 sin^2(pi k1/N)
+ * + 4 sin^2(pi k2/N) (the mu sum_i R_i^H R_i term noted after Eq. solz).  mu >= 0, finite;
+ * 0 (the default) is plain Alg. 2.  Takes effect from the next iteration; the factor and the
+ * state are unchanged.  CIP_ERR_STATE for other priors. */
+cip_status cip_set_code_gradient_weight(cip_plan* plan, double mu);
+
 /* Coefficient maps z[M][L][N][N] of the last z-update (CIP_PRIOR_CONVDICT only). */
 cip_status cip_get_coefficients(cip_plan* plan, void* z, void* stream);
 

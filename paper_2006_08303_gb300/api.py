@@ -114,6 +114,10 @@ class Plan:
         self._check(self._L.cip_set_dictionary(self._h, ctypes.c_void_p(p), L, P, _stream_ptr(stream)))
         self.L = L
 
+    def set_code_gradient_weight(self, mu: float):
+        """Gradient (Tikhonov) penalty mu on the dictionary codes (cip_set_code_gradient_weight)."""
+        self._check(self._L.cip_set_code_gradient_weight(self._h, ctypes.c_double(mu)))
+
     def get_coefficients(self, out=None, stream=None):
         shape = (self.M, self.L, self.N, self.N)
         if out is None:

@@ -51,6 +51,7 @@ struct cip_plan {
   cip_options opt{};
   int prior = -1;
   double lam = 0, rho = 0, beta = 0;
+  double mu = 0;  // dictionary: gradient (Tikhonov) weight on the codes
   bool have_psfs = false, have_y = false;
   int iteration = 0;
   int cur = 0;  // index of the u buffer holding the current u
@@ -424,7 +425,9 @@ template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mo
     a.N = p->N;
     a.M = p->M;
     a.L = p->L;
+    a.gs = p->gs;
     a.rho = (T)p->rho;
+    a.mu = (T)p->mu;
     a.n2 = (T)((double)p->N * p->N);
     CIP_LAUNCH(p, launch_cd_solve<T>(a, s));
     CIP_LAUNCH(p, launch_colfft_inv<T>(static_cast<const C*>(p->colbuf), static_cast<C*>(p->xh),
@@ -950,6 +953,14 @@ cip_status cip_set_dictionary(cip_plan* p, const void* filters, int L, int P, vo
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   p->ast = s;
   return DISPATCH_T(p, do_set_dictionary<float>(p, filters, s), do_set_dictionary<double>(p, filters, s));
+}
+
+cip_status cip_set_code_gradient_weight(cip_plan* p, double mu) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "the gradient penalty applies to CIP_PRIOR_CONVDICT plans only");
+  if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(p, CIP_ERR_INVALID_ARG, "mu must be finite and >= 0");
+  p->mu = mu;
+  return CIP_OK;
 }
 
 cip_status cip_get_coefficients(cip_plan* p, void* z, void* stream) {

@@ -2,7 +2,10 @@
 // channels), the per-frequency part of one iteration:
 //   x(w)   = xb(w) + Psi^{-1}(w)/N^2 p(w),  p_m = sum_l theta_l v_{l,m}      (Eq. solx_synt_DFT)
 //   c_l    = conj(theta_l) x_m + rho G_{l,m},  G = F (t - u)                 (Eq. solz_DFT)
-//   v_{.,m} = (c - conj(theta) (theta^T c) / (rho + ||theta||^2)) / rho      (Eq. solz_DFT_SM)
+//   v_{.,m} = (c - conj(theta) (theta^T c) / (rho_w + ||theta||^2)) / rho_w  (Eq. solz_DFT_SM)
+// with rho_w = rho, or rho + mu g(w) when the codes carry the gradient (Tikhonov) penalty of
+// Eq. DL_PriorHP_conv (g = |r1^|^2 + |r2^|^2, the circular differences along both axes: the
+// mu sum_i R_i^H R_i term of the note after Eq. solz keeps each bin's matrix diagonal + rank one)
 // where theta_l is the DFT of filter l, Psi = I + beta Lambda^H Lambda (t = 1
 // in Eq. solx_synt_DFT) and p is carried from the previous iteration's v.  One
 // thread owns one (frequency, channel) pair; the L coefficient spectra of the
@@ -64,8 +67,9 @@ __global__ void __launch_bounds__(128) cd_solve_kernel(CDArgs<T> a) {
       nrm += t.x * t.x + t.y * t.y;
     }
   }
-  const T inv_rho = T(1) / a.rho;
-  const T den = T(1) / (a.rho + nrm);
+  const T rho_w = a.mu == T(0) ? a.rho : a.rho + a.mu * (T)(a.gs[k1] + a.gs[k2]);
+  const T inv_rho = T(1) / rho_w;
+  const T den = T(1) / (rho_w + nrm);
   const C coef = mk<C>(s.x * den, s.y * den);
   C pn = mk<C>(0.0, 0.0);
 #pragma unroll

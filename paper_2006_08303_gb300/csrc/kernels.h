@@ -66,8 +66,10 @@ template <typename T> struct CDArgs {
   const C* xb;     // [H][M]: Psi^{-1} beta Lambda^H F y / N^2
   const C* pinv;   // [H][M(M+1)/2]: packed (I + beta Lambda^H Lambda)^{-1} / N^2
   C* xcol;         // [H][M]: x-hat / N^2 (for read-back)
+  const double* gs;  // [N] 4 sin^2(pi k / N): per-axis eigenvalues of the circular difference
   int N, M, L;
   T rho;
+  T mu;            // gradient (Tikhonov) weight on the codes; z-update diagonal rho + mu (gs[k1] + gs[k2])
   T n2;            // N^2
 };
 template <typename T> cudaError_t launch_cd_solve(const CDArgs<T>& a, cudaStream_t s);

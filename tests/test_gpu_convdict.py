@@ -140,3 +140,54 @@ def test_convdict_checkpoint_resume(torch):
     xb = P.get_x().cpu().numpy()
     P.close()
     assert np.array_equal(xa, xb)
+
+
+@pytest.mark.parametrize("mu", [0.01, 0.5])
+def test_convdict_gradient_penalty_step_parity(torch, mu):
+    """Gradient (Tikhonov) penalty on the codes (Eq. DL_PriorHP_conv): one GPU iteration from the
+    oracle's state vs the oracle's, with mu = 0.01 (the paper's Tikhonov setting) and a larger
+    mu that changes the z-update visibly; per-step tolerance 1e-5 (complex64 path)."""
+    h, y, d = small_problem(seed=23)
+    lam, rho, beta = 0.15, 8.0, 4.0
+    S = fast.convdict_setup(h, y, d, lam, rho, beta, mu)
+    S0 = fast.convdict_setup(h, y, d, lam, rho, beta, 0.0)
+    P, f = plan_for(torch, h, y, d, lam, rho, beta)
+    P.set_code_gradient_weight(mu)
+    L, M, N = d.shape[0], h.shape[1], h.shape[-1]
+    z = np.zeros((L, M, N, N)); t = np.zeros_like(z); u = np.zeros_like(z)
+    for l in range(5):
+        x1, z1, t1, u1 = fast.convdict_step(S, z, t, u)
+        if l in (1, 4):
+            P.state_import_coefficients(f(gl(z)), f(gl(t)), f(gl(u)))
+            P.iterate(1)
+            zg = P.get_coefficients().double().cpu().numpy()
+            xg = P.get_x().double().cpu().numpy()
+            assert rel(xg, x1) <= 1e-5, (l, rel(xg, x1))
+            assert rel(zg, gl(z1)) <= 1e-5, (l, rel(zg, gl(z1)))
+            _, z0, _, _ = fast.convdict_step(S0, z, t, u)
+            assert rel(z0, z1) > 100 * max(rel(zg, gl(z1)), 1e-9)  # the penalty is really applied
+        z, t, u = z1, t1, u1
+    P.close()
+
+
+def test_convdict_gradient_penalty_final(torch):
+    """Free-running 40 iterations with mu = 0.1 from zero state: final x within 1e-4 of the oracle."""
+    h, y, d = small_problem(seed=24)
+    lam, rho, beta, mu = 0.15, 8.0, 4.0, 0.1
+    S = fast.convdict_setup(h, y, d, lam, rho, beta, mu)
+    x_ref, _, _, _ = fast.run_convdict(S, 40)
+    P, f = plan_for(torch, h, y, d, lam, rho, beta)
+    P.set_code_gradient_weight(mu)
+    P.iterate(40)
+    xg = P.get_x().double().cpu().numpy()
+    assert rel(xg, x_ref) <= 1e-4, rel(xg, x_ref)
+    P.close()
+
+
+def test_gradient_weight_rejected_outside_dictionary(torch):
+    from paper_2006_08303_gb300 import api
+    P = api.Plan(64, 2, 2, "f32")
+    P.set_prior("tv", 0.01, 1.0, 1.0)
+    with pytest.raises(Exception):
+        P.set_code_gradient_weight(0.1)
+    P.close()
