@@ -347,6 +347,42 @@ def run_analysis(S: AnalysisSetup, iters: int, t0=None, u0=None, keep_history: b
     return x, t, u, hist
 
 
+def adapt_rho(rho: float, r: float, s: float, tau: float = 2.0, mu: float = 10.0) -> float:
+    """Eq. paramS: tau rho if ||r|| > mu ||s||, rho / tau if ||s|| > mu ||r||, else rho
+    (r the primal residual ||Tx - t||, s the dual residual rho ||t - t_prev||, reading R11)."""
+    if r > mu * s:
+        return rho * tau
+    if s > mu * r:
+        return rho / tau
+    return rho
+
+
+def run_analysis_adaptive(h: np.ndarray, y: np.ndarray, prior: str, lam: float, rho: float, beta: float,
+                          iters: int, check_every: int, tau: float = 2.0, mu: float = 10.0):
+    """Alg. 1 from t = u = 0 with the penalty adapted by Eq. paramS after every check_every-th
+    iteration (reading R17).  When rho changes the scaled dual is rescaled, u <- u rho/rho', so
+    that the unscaled multiplier rho u is unchanged (reading R18), and Psi^{-1} and the data term
+    are formed again for rho'.  Returns (x, t, u, [rho after each iteration])."""
+    S = analysis_setup(h, y, prior, lam, rho, beta)
+    ncomp = 2 if prior == "tv" else 1
+    t = np.zeros((S.M, ncomp, S.N, S.N))
+    u = np.zeros_like(t)
+    rhos = []
+    x = None
+    for it in range(iters):
+        x, t_new, u_new, w = analysis_step(S, t, u)
+        if (it + 1) % check_every == 0:
+            r = float(np.linalg.norm(w - t_new))
+            s = S.rho * float(np.linalg.norm(t_new - t))
+            rho_new = adapt_rho(S.rho, r, s, tau, mu)
+            if rho_new != S.rho:
+                u_new = u_new * (S.rho / rho_new)
+                S = analysis_setup(h, y, prior, lam, rho_new, beta)
+        t, u = t_new, u_new
+        rhos.append(S.rho)
+    return x, t, u, rhos
+
+
 def objective(x: np.ndarray, h: np.ndarray, y: np.ndarray, prior: str, lam: float, beta: float) -> float:
     """Eq. rls with the analysis prior: beta/2 ||y - Hx||^2 + lambda ||Tx||_1 (H spatial)."""
     fwd, _ = PRIORS[prior]

@@ -83,6 +83,40 @@ def analysis_step(S: FastAnalysis, t, u):
     return x, t_new, u + w - t_new, w
 
 
+def run_analysis_adaptive(h, y, prior, lam, rho, beta, iters: int, check_every: int, tau: float = 2.0,
+                          mu: float = 10.0, tol: float = 0.0):
+    """Same schedule as oracle.admm.run_analysis_adaptive (Eq. paramS after every check_every-th
+    iteration, u rescaled, factor formed again); with tol > 0 it also stops at the first check at
+    which both relative residuals are below tol.  Returns (x, t, u, rhos, iterations_done)."""
+    S = analysis_setup(h, y, prior, lam, rho, beta)
+    ncomp = 2 if prior == "tv" else 1
+    t = np.zeros((S.M, ncomp, S.N, S.N))
+    u = np.zeros_like(t)
+    rhos = []
+    x = None
+    done = 0
+    for it in range(iters):
+        x, t_new, u_new, w = analysis_step(S, t, u)
+        done = it + 1
+        stop = False
+        if (it + 1) % check_every == 0:
+            r = float(np.linalg.norm(w - t_new))
+            s = S.rho * float(np.linalg.norm(t_new - t))
+            if tol > 0:
+                r_rel = r / max(np.linalg.norm(w), np.linalg.norm(t_new), 1e-300)
+                s_rel = s / max(S.rho * np.linalg.norm(u_new), 1e-300)
+                stop = r_rel < tol and s_rel < tol
+            rho_new = ref.adapt_rho(S.rho, r, s, tau, mu)
+            if not stop and rho_new != S.rho:
+                u_new = u_new * (S.rho / rho_new)
+                S = analysis_setup(h, y, prior, lam, rho_new, beta)
+        t, u = t_new, u_new
+        rhos.append(S.rho)
+        if stop:
+            break
+    return x, t, u, rhos, done
+
+
 def run_analysis(S: FastAnalysis, iters: int, t0=None, u0=None, tol: float = 0.0):
     """Alg. 1; with tol > 0 stops when both relative residuals (reading R11) fall below tol.
     Returns (x, t, u, iterations_done, (r_rel, s_rel))."""

@@ -373,3 +373,45 @@ def test_fast_oracle_tiny_workload_residuals():
     assert n == 50 and rel(xf, xs) < 1e-11
     assert abs(rr[0] - hist[-1].r_rel) < 1e-9 * hist[-1].r_rel
     assert abs(rr[1] - hist[-1].s_rel) < 1e-9 * hist[-1].s_rel
+
+
+# ----------------------------------------------------------------- adaptive penalty (Eq. paramS)
+def test_adapt_rho_rule():
+    assert admm.adapt_rho(1.0, 11.0, 1.0) == 2.0        # primal residual dominates: rho * tau
+    assert admm.adapt_rho(1.0, 1.0, 11.0) == 0.5        # dual residual dominates: rho / tau
+    assert admm.adapt_rho(1.0, 5.0, 1.0) == 1.0         # balanced within mu
+    assert admm.adapt_rho(3.0, 1.0, 100.0, tau=3.0, mu=5.0) == 1.0
+
+
+def test_adaptive_rho_reaches_the_fixed_rho_minimiser():
+    """The minimiser of Eq. rls does not depend on rho: adaptive-rho ADMM, started from a badly
+    chosen rho, ends at the fixed-rho solution, and it does change rho on the way."""
+    P = inputs.tiny_tv(N=16, M=2, iters=1)
+    S = admm.analysis_setup(P.h, P.y, P.prior, P.lam, 1.0, P.beta)
+    x_fix, _, _, _ = admm.run_analysis(S, 3000)
+    x_ad, _, _, rhos = admm.run_analysis_adaptive(P.h, P.y, P.prior, P.lam, 100.0, P.beta, 600, 10)
+    assert len(set(rhos)) > 1
+    assert rel(x_ad, x_fix) < 1e-6
+
+
+def test_adaptive_rho_keeps_the_unscaled_multiplier():
+    """Reading R18: at a change of rho the scaled dual is rescaled so that rho u is continuous;
+    the first iteration after the change equals one fixed-rho step at the new rho from
+    (t, u rho_old / rho_new)."""
+    P = inputs.tiny_tv(N=16, M=2, iters=1)
+    x10, t10, u10, rhos = admm.run_analysis_adaptive(P.h, P.y, P.prior, P.lam, 100.0, P.beta, 10, 10)
+    assert rhos[-1] != 100.0
+    x11, t11, u11, _ = admm.run_analysis_adaptive(P.h, P.y, P.prior, P.lam, 100.0, P.beta, 11, 10)
+    S_new = admm.analysis_setup(P.h, P.y, P.prior, P.lam, rhos[-1], P.beta)
+    x_step, t_step, u_step, _ = admm.analysis_step(S_new, t10, u10)
+    assert rel(x11, x_step) < 1e-12 and rel(u11, u_step) < 1e-12
+    _, _, u_pre, _ = admm.run_analysis(admm.analysis_setup(P.h, P.y, P.prior, P.lam, 100.0, P.beta), 10)
+    assert rel(rhos[-1] * u10, 100.0 * u_pre) < 1e-12
+
+
+def test_fast_adaptive_matches_naive():
+    P = inputs.tiny_tv(N=16, M=2, iters=1)
+    xn, tn, un, rn = admm.run_analysis_adaptive(P.h, P.y, P.prior, P.lam, 100.0, P.beta, 60, 10)
+    xf, tf, uf, rf, _ = fast.run_analysis_adaptive(P.h, P.y, P.prior, P.lam, 100.0, P.beta, 60, 10)
+    assert rn == rf
+    assert rel(xf, xn) < 1e-10 and rel(uf, un) < 1e-10
