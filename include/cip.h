@@ -150,6 +150,23 @@ cip_status cip_state_import_coefficients(cip_plan* plan, const void* z, const vo
 /* t = u = 0 (Alg. 1 line 1 with zero initial values). */
 cip_status cip_reset_state(cip_plan* plan, void* stream);
 
+/* Adaptive penalty (Section IV-C, Eq. paramS): at each residual check of cip_iterate (every
+ * check_every iterations; the checks synchronise the stream), rho becomes tau rho if the
+ * primal residual ||Tx - t|| exceeds mu times the dual residual rho ||t - t_prev||, rho / tau
+ * if the dual exceeds mu times the primal, and stays otherwise (the paper uses tau = 2,
+ * mu = 10).  On a change the scaled dual u is multiplied by rho_old / rho_new (the multiplier
+ * rho u is unchanged), the factor and the data term are formed again for the new rho, and the
+ * next x-update's right-hand side is formed again.  tau = 0 turns adaptation off (the
+ * default); otherwise tau > 1 and mu > 1.  Analysis priors only (CIP_ERR_UNSUPPORTED for the
+ * dictionary).  Call it before cip_set_measurements, which then keeps the measurement spectra
+ * (K half-spectrum maps, 16 bytes per bin) for re-forming the data term; CIP_ERR_STATE
+ * otherwise.  rho keeps its adapted value until cip_set_prior.  Applies to cip_iterate (not to
+ * batches or the request server). */
+cip_status cip_set_rho_adaptation(cip_plan* plan, double tau, double mu);
+
+/* Current penalty rho of the plan (the adapted value when adaptation is on). */
+cip_status cip_get_rho(cip_plan* plan, double* rho);
+
 /* Run ADMM iterations (Alg. 1 lines 3-8).  tol <= 0: exactly max_iter
  * iterations.  tol > 0: stop after the first check at which both relative
  * residuals r/max(||Tx||,||t||) and s/||rho u|| (r = ||Tx - t||,

@@ -114,6 +114,17 @@ class Plan:
         self._check(self._L.cip_set_dictionary(self._h, ctypes.c_void_p(p), L, P, _stream_ptr(stream)))
         self.L = L
 
+    def set_rho_adaptation(self, tau: float = 2.0, mu: float = 10.0):
+        """Adaptive penalty of Eq. paramS at the residual checks (tau = 0: off); call before
+        set_measurements."""
+        self._check(self._L.cip_set_rho_adaptation(self._h, ctypes.c_double(tau), ctypes.c_double(mu)))
+
+    @property
+    def rho(self) -> float:
+        v = ctypes.c_double()
+        self._check(self._L.cip_get_rho(self._h, ctypes.byref(v)))
+        return v.value
+
     def set_code_gradient_weight(self, mu: float):
         """Gradient (Tikhonov) penalty mu on the dictionary codes (cip_set_code_gradient_weight)."""
         self._check(self._L.cip_set_code_gradient_weight(self._h, ctypes.c_double(mu)))

@@ -52,6 +52,8 @@ struct cip_plan {
   int prior = -1;
   double lam = 0, rho = 0, beta = 0;
   double mu = 0;  // dictionary: gradient (Tikhonov) weight on the codes
+  double adapt_tau = 0, adapt_mu = 0;  // adaptive penalty (Eq. paramS); tau = 0: off
+  void* yhat_keep = nullptr;           // measurement spectra kept for re-forming the data term
   bool have_psfs = false, have_y = false;
   int iteration = 0;
   int cur = 0;  // index of the u buffer holding the current u
@@ -343,6 +345,18 @@ template <typename T> cip_status do_set_psfs(cip_plan* p, const void* h, cudaStr
 
 template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s);
 
+// data term xb (or b for the plain FP32 method) from the measurement spectra yhat
+template <typename T> cudaError_t form_data_term(cip_plan* p, const SetupC<T>* yhat, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const cip_plan* fs = p->factor_src ? p->factor_src : p;
+  const SetupC<T>* lam = setup_buf<T>(fs->lam64);
+  if constexpr (sizeof(T) == 4) {
+    if (p->opt.precision == 1)
+      return launch_rhs_fp32(lam, yhat, p->K, p->M, p->N, p->beta, reinterpret_cast<float2*>(p->bhat), s);
+  }
+  return launch_rhs<T>(lam, yhat, setup_buf<T>(fs->pinv64), p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
+}
+
 template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream_t s) {
   using C = typename CT<T>::type;
   const size_t bytes = real_elems(p, p->K) * sizeof(T);
@@ -359,20 +373,15 @@ template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream
   const SetupC<T>* tw = setup_buf<T>(p->tw64);
   cudaError_t e = launch_row_r2c<R, T>(static_cast<const T*>(dy), yhat, p->N, p->K * p->N, R(1.0f), tw, s);
   if (e == cudaSuccess) e = launch_col_c2c<R>(yhat, p->N, p->K, -1, tw, s);
-  if (e == cudaSuccess) {
-    const SetupC<T>* lam = setup_buf<T>(fs->lam64);
-    bool plain = false;
-    if constexpr (sizeof(T) == 4) {
-      if (p->opt.precision == 1) {
-        plain = true;
-        e = launch_rhs_fp32(lam, yhat, p->K, p->M, p->N, p->beta, reinterpret_cast<float2*>(p->bhat), s);
-      }
-    }
-    if (!plain)
-      e = launch_rhs<T>(lam, yhat, setup_buf<T>(fs->pinv64), p->K, p->M, p->N, p->beta, static_cast<C*>(p->bhat), s);
-  }
+  if (e == cudaSuccess) e = form_data_term<T>(p, yhat, s);
   if (e == cudaSuccess) p->launches += 3;
-  cudaFreeAsync(yhat, s);
+  if (e == cudaSuccess && p->adapt_tau > 0 && !is_cd(p)) {
+    // the data term is formed again whenever the adaptive penalty changes rho
+    if (p->yhat_keep) cudaFreeAsync(p->yhat_keep, s);
+    p->yhat_keep = yhat;
+  } else {
+    cudaFreeAsync(yhat, s);
+  }
   CIP_CUDA(p, e);
   p->have_y = true;
   if (!is_cd(p) && p->opt.column_pass == 0 && p->opt.col_tile == 0) {
@@ -549,8 +558,31 @@ void ensure_events(cip_plan* p) {
   for (auto& e : p->evB) cudaEventCreate(&e);
 }
 
+// Adaptive penalty: rho -> rho_new after a residual check (readings R17, R18).  The scaled
+// dual is rescaled so that rho u is unchanged, the factor and the data term are formed again
+// for rho_new (the dictionary's factor does not depend on rho), and q of the next x-update is
+// formed again from the kept t and the rescaled u by the prior pass in import mode.
+template <typename T> cip_status change_rho(cip_plan* p, double rho_new, cudaStream_t s) {
+  const size_t n = real_elems(p, smaps(p)) * ncomp_of(p->prior);
+  CIP_LAUNCH(p, launch_scale<T>(static_cast<T*>(p->u[p->cur]), n, (T)(p->rho / rho_new), s));
+  p->rho = rho_new;
+  if (!is_cd(p)) {
+    if (!p->yhat_keep) return fail(p, CIP_ERR_STATE, "the adaptive penalty needs cip_set_rho_adaptation before cip_set_measurements");
+    cip_status st = form_factor<T>(p, s);
+    if (st != CIP_OK) return st;
+    CIP_LAUNCH(p, form_data_term<T>(p, setup_buf<T>(p->yhat_keep), s));
+  }
+  PassAArgs<T> a = passA_args<T>(p, PA_IMPORT);
+  a.t_imp = static_cast<const T*>(p->tprev);
+  CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
+  p->cur ^= 1;
+  return CIP_OK;
+}
+
 template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double tol, int* done, cudaStream_t s) {
-  if (tol > 0 && !p->resid_host)
+  const bool adapt = p->adapt_tau > 0;
+  const bool checks = tol > 0 || adapt;
+  if (checks && !p->resid_host)
     CIP_CUDA(p, cudaMallocHost((void**)&p->resid_host, (kNPart + 2) * sizeof(double)));
   const int ce = p->opt.check_every > 0 ? p->opt.check_every : 10;
   int it = 0;
@@ -560,9 +592,10 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
     const int phase = (it + 1) % ce;
     int flags = 0;
     // t is kept on the iteration before a residual check and on the last iteration (so the next
-    // call's first dual residual compares against the right t_prev)
-    if ((tol > 0 && phase == ce - 1) || it == max_iter - 2 || last) flags |= PA_STORE_T;
-    const bool check = (tol > 0 && phase == 0 && it > 0) || last;
+    // call's first dual residual compares against the right t_prev); with the adaptive penalty
+    // also on the check itself (q is formed again from it when rho changes)
+    if ((checks && phase == ce - 1) || (adapt && phase == 0) || it == max_iter - 2 || last) flags |= PA_STORE_T;
+    const bool check = (checks && phase == 0 && it > 0) || last;
     if (check) flags |= PA_RESID;
     // x-update (pass B), then t/u update + next adjoint (pass A)
     const bool timeB = p->timing && p->nB < kMaxTimed;
@@ -581,7 +614,10 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
       // the previous iteration stored t only if it ran; otherwise s is not meaningful
       CIP_LAUNCH(p, launch_reduce_partials(p->partials, p->blocksA, p->rho, tol, p->resid, p->conv, s));
       p->resid_valid = true;
-      if (tol > 0 && !last) {
+      // the penalty adapts at every check, the last iteration of a call included, so that
+      // splitting the iterations over several calls does not change the iterates
+      const bool adapt_now = adapt && phase == 0 && it > 0;
+      if ((tol > 0 && !last) || adapt_now) {
         CIP_CUDA(p, cudaMemcpyAsync(p->resid_host, p->resid, (kNPart + 2) * sizeof(double),
                                     cudaMemcpyDeviceToHost, s));
         int kerr = 0;
@@ -593,7 +629,18 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
           if (done) *done = it + 1;
           return fail(p, CIP_ERR_DIVERGED, "residuals are not finite");
         }
-        if (r < tol && sr < tol) stop = true;
+        if (tol > 0 && !last && r < tol && sr < tol) stop = true;
+        if (adapt_now && !stop) {
+          // Eq. paramS on the absolute residuals r = ||Tx - t||, s = rho ||t - t_prev||
+          const double ra = std::sqrt(p->resid_host[0]), sa = p->rho * std::sqrt(p->resid_host[4]);
+          double rho_new = p->rho;
+          if (ra > p->adapt_mu * sa) rho_new = p->rho * p->adapt_tau;
+          else if (sa > p->adapt_mu * ra) rho_new = p->rho / p->adapt_tau;
+          if (rho_new != p->rho) {
+            cip_status cs = change_rho<T>(p, rho_new, s);
+            if (cs != CIP_OK) return cs;
+          }
+        }
       }
     }
   }
@@ -851,7 +898,7 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol,
+  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep,
                   p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
@@ -960,6 +1007,28 @@ cip_status cip_set_code_gradient_weight(cip_plan* p, double mu) {
   if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "the gradient penalty applies to CIP_PRIOR_CONVDICT plans only");
   if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(p, CIP_ERR_INVALID_ARG, "mu must be finite and >= 0");
   p->mu = mu;
+  return CIP_OK;
+}
+
+cip_status cip_set_rho_adaptation(cip_plan* p, double tau, double mu) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  if (tau == 0.0) {
+    p->adapt_tau = p->adapt_mu = 0.0;
+    return CIP_OK;
+  }
+  if (!(tau > 1.0) || !(mu > 1.0) || !std::isfinite(tau) || !std::isfinite(mu))
+    return fail(p, CIP_ERR_INVALID_ARG, "tau and mu must be finite and > 1 (or tau = 0 to turn adaptation off)");
+  if (is_cd(p)) return fail(p, CIP_ERR_UNSUPPORTED, "the adaptive penalty covers analysis priors");
+  if (p->have_y && !is_cd(p) && !p->yhat_keep)
+    return fail(p, CIP_ERR_STATE, "cip_set_rho_adaptation must precede cip_set_measurements");
+  p->adapt_tau = tau;
+  p->adapt_mu = mu;
+  return CIP_OK;
+}
+
+cip_status cip_get_rho(cip_plan* p, double* rho) {
+  if (!p || !rho) return CIP_ERR_INVALID_ARG;
+  *rho = p->rho;
   return CIP_OK;
 }
 

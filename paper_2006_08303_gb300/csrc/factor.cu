@@ -416,6 +416,18 @@ cudaError_t launch_spectra_store(const SetupC<Tout>* src, typename CT<Tout>::typ
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void scale_kernel(T* __restrict__ a, size_t n, T f) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] *= f;
+}
+
+template <typename T> cudaError_t launch_scale(T* a, size_t n, T f, cudaStream_t s) {
+  scale_kernel<T><<<1216, 256, 0, s>>>(a, n, f);
+  return cudaGetLastError();
+}
+template cudaError_t launch_scale<float>(float*, size_t, float, cudaStream_t);
+template cudaError_t launch_scale<double>(double*, size_t, double, cudaStream_t);
+
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, double rho, double tol, double* out, int* conv,
                                    cudaStream_t s) {
   reduce_kernel<<<1, 256, 0, s>>>(partials, nblocks, rho, tol, out, conv);

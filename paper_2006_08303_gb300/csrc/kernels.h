@@ -136,6 +136,9 @@ cudaError_t launch_rhs(const SetupC<Tout>* lam, const SetupC<Tout>* yhat, const 
 template <typename Tout>
 cudaError_t launch_spectra_store(const SetupC<Tout>* src, typename CT<Tout>::type* dst, size_t n, cudaStream_t s);
 
+// a[i] *= f for i < n (the scaled dual at a change of the penalty)
+template <typename T> cudaError_t launch_scale(T* a, size_t n, T f, cudaStream_t s);
+
 // deterministic reduction of pass-A partials: out[0..kNPart) sums, out[5]=r_rel, out[6]=s_rel,
 // conv[0] set to 1 when both relative residuals < tol (tol > 0)
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, double rho, double tol, double* out,
