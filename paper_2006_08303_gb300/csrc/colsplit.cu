@@ -13,7 +13,10 @@ namespace cip {
 namespace {
 
 template <typename T> constexpr int cs_cc() { return sizeof(T) == 4 ? 4 : 2; }  // 32-byte row segments
-template <typename T> constexpr int cs_e(int N) { return (sizeof(T) == 4 && N <= 1024) ? 8 : 16; }
+#ifndef COLFFT_E32
+#define COLFFT_E32 8
+#endif
+template <typename T> constexpr int cs_e(int N) { return (sizeof(T) == 4 && N <= 1024) ? COLFFT_E32 : 16; }
 
 // SIGN < 0: rows [M][N][P] -> FFT over k1 -> colbuf [H][M][N]
 // SIGN > 0: colbuf [H][M][N] -> inverse FFT -> rows [M][N][P]
