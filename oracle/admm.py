@@ -171,9 +171,14 @@ def l1_adjoint(w: np.ndarray) -> np.ndarray:
 
 PRIORS = {
     "tv": (tv_forward, tv_adjoint),
+    "tv_iso": (tv_forward, tv_adjoint),   # isotropic TV: same T, coupled shrinkage (reading R20)
     "dct8": (dct8_forward, dct8_adjoint),
     "l1": (l1_forward, l1_adjoint),
 }
+
+
+def ncomp_of(prior: str) -> int:
+    return 2 if prior in ("tv", "tv_iso") else 1
 
 
 def gram_eigenvalues(prior: str, N: int) -> np.ndarray:
@@ -188,6 +193,19 @@ def gram_eigenvalues(prior: str, N: int) -> np.ndarray:
     kern = adj(fwd(delta))
     g = dft2(kern)
     return g.real
+
+
+def group_soft(v: np.ndarray, tau: float) -> np.ndarray:
+    """Proximal map of tau ||.||_2 on the two-component axis (-3) of v = [..., 2, N, N]:
+    v max(0, 1 - tau / ||v||), the t-update of isotropic TV (reading R20)."""
+    n = np.sqrt(np.sum(v * v, axis=-3, keepdims=True))
+    f = np.where(n > tau, 1.0 - tau / np.where(n > 0, n, 1.0), 0.0)
+    return v * f
+
+
+def shrink(prior: str, v: np.ndarray, tau: float) -> np.ndarray:
+    """t-update of Eq. solt_trans for the prior: coupled for isotropic TV, elementwise otherwise."""
+    return group_soft(v, tau) if prior == "tv_iso" else soft(v, tau)
 
 
 def soft(w: np.ndarray, tau: float) -> np.ndarray:
@@ -306,7 +324,7 @@ def t_u_update(S: AnalysisSetup, x: np.ndarray, u: np.ndarray):
     """Eq. solt_trans and Eq. subu_trans: t = soft(Tx + u, lambda/rho); u += Tx - t."""
     fwd, _ = PRIORS[S.prior]
     w = fwd(x)
-    t = soft(w + u, S.lam / S.rho)
+    t = shrink(S.prior, w + u, S.lam / S.rho)
     return t, u + w - t, w
 
 
@@ -330,7 +348,7 @@ def analysis_step(S: AnalysisSetup, t: np.ndarray, u: np.ndarray):
 
 def run_analysis(S: AnalysisSetup, iters: int, t0=None, u0=None, keep_history: bool = False):
     """Alg. 1 for a fixed number of iterations from t^0 = u^0 = 0 (reading R5)."""
-    ncomp = 2 if S.prior == "tv" else 1
+    ncomp = ncomp_of(S.prior)
     t = np.zeros((S.M, ncomp, S.N, S.N)) if t0 is None else t0.copy()
     u = np.zeros_like(t) if u0 is None else u0.copy()
     hist: List[IterRecord] = []
@@ -364,7 +382,7 @@ def run_analysis_adaptive(h: np.ndarray, y: np.ndarray, prior: str, lam: float, 
     that the unscaled multiplier rho u is unchanged (reading R18), and Psi^{-1} and the data term
     are formed again for rho'.  Returns (x, t, u, [rho after each iteration])."""
     S = analysis_setup(h, y, prior, lam, rho, beta)
-    ncomp = 2 if prior == "tv" else 1
+    ncomp = ncomp_of(prior)
     t = np.zeros((S.M, ncomp, S.N, S.N))
     u = np.zeros_like(t)
     rhos = []
@@ -387,7 +405,9 @@ def objective(x: np.ndarray, h: np.ndarray, y: np.ndarray, prior: str, lam: floa
     """Eq. rls with the analysis prior: beta/2 ||y - Hx||^2 + lambda ||Tx||_1 (H spatial)."""
     fwd, _ = PRIORS[prior]
     res = y - forward_H(x, h)
-    return 0.5 * beta * float(np.sum(res * res)) + lam * float(np.sum(np.abs(fwd(x))))
+    w = fwd(x)
+    reg = np.sum(np.sqrt(np.sum(w * w, axis=-3))) if prior == "tv_iso" else np.sum(np.abs(w))
+    return 0.5 * beta * float(np.sum(res * res)) + lam * float(reg)
 
 
 # ---------------------------------------------------------------------------

@@ -79,7 +79,7 @@ def analysis_step(S: FastAnalysis, t, u):
     fwd, _ = ref.PRIORS[S.prior]
     x = x_update(S, t, u)
     w = fwd(x)
-    t_new = ref.soft(w + u, S.lam / S.rho)
+    t_new = ref.shrink(S.prior, w + u, S.lam / S.rho)
     return x, t_new, u + w - t_new, w
 
 
@@ -89,7 +89,7 @@ def run_analysis_adaptive(h, y, prior, lam, rho, beta, iters: int, check_every: 
     iteration, u rescaled, factor formed again); with tol > 0 it also stops at the first check at
     which both relative residuals are below tol.  Returns (x, t, u, rhos, iterations_done)."""
     S = analysis_setup(h, y, prior, lam, rho, beta)
-    ncomp = 2 if prior == "tv" else 1
+    ncomp = ref.ncomp_of(prior)
     t = np.zeros((S.M, ncomp, S.N, S.N))
     u = np.zeros_like(t)
     rhos = []
@@ -120,7 +120,7 @@ def run_analysis_adaptive(h, y, prior, lam, rho, beta, iters: int, check_every: 
 def run_analysis(S: FastAnalysis, iters: int, t0=None, u0=None, tol: float = 0.0):
     """Alg. 1; with tol > 0 stops when both relative residuals (reading R11) fall below tol.
     Returns (x, t, u, iterations_done, (r_rel, s_rel))."""
-    ncomp = 2 if S.prior == "tv" else 1
+    ncomp = ref.ncomp_of(S.prior)
     t = np.zeros((S.M, ncomp, S.N, S.N)) if t0 is None else t0.copy()
     u = np.zeros_like(t) if u0 is None else u0.copy()
     x = None

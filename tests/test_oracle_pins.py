@@ -415,3 +415,80 @@ def test_fast_adaptive_matches_naive():
     xf, tf, uf, rf, _ = fast.run_analysis_adaptive(P.h, P.y, P.prior, P.lam, 100.0, P.beta, 60, 10)
     assert rn == rf
     assert rel(xf, xn) < 1e-10 and rel(uf, un) < 1e-10
+
+
+# ----------------------------------------------------------------- isotropic TV (reading R20)
+def test_group_soft_is_the_prox():
+    """t = v max(0, 1 - tau/||v||) minimises 1/2||t - v||^2 + tau ||t||_2 per pixel: checked by the
+    optimality conditions (t - v + tau t/||t|| = 0 where t != 0, ||v|| <= tau where t = 0) and
+    against every point of a fine polar grid around v."""
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal((5, 2, 7, 7))
+    tau = 0.9
+    t = admm.group_soft(v, tau)
+    n_t = np.sqrt(np.sum(t * t, axis=1, keepdims=True))
+    n_v = np.sqrt(np.sum(v * v, axis=1))
+    nz = n_t[:, 0] > 0
+    g = (t - v + tau * t / np.where(n_t > 0, n_t, 1.0))
+    assert np.abs(np.moveaxis(g, 1, -1)[nz]).max() < 1e-12
+    assert np.all(n_v[~nz] <= tau + 1e-12) and np.all(n_v[nz] > tau)
+    f = lambda tt, vv: 0.5 * np.sum((tt - vv) ** 2) + tau * np.sqrt(np.sum(tt * tt))
+    vv = v[0, :, 0, 0]
+    best = f(t[0, :, 0, 0], vv)
+    rr, th = np.meshgrid(np.linspace(0, 3, 301), np.linspace(0, 2 * np.pi, 361))
+    grid = np.stack([rr * np.cos(th), rr * np.sin(th)], -1).reshape(-1, 2)
+    assert best <= min(f(p, vv) for p in grid) + 1e-9
+
+
+@pytest.fixture(scope="module")
+def tviso16():
+    rng = np.random.default_rng(98)
+    N, M = 16, 2
+    x0 = inputs.rectangles_image(rng, N, M, n_rect=3)
+    h = inputs.gaussian_psf_bank(N, 3, M)
+    y, _ = inputs.measure(rng, x0, h, 30.0)
+    lam, rho, beta = 1e-2, 0.5, 1.0
+    S = admm.analysis_setup(h, y, "tv_iso", lam, rho, beta)
+    x, t, u, hist = admm.run_analysis(S, 3000, keep_history=True)
+    return dict(h=h, y=y, lam=lam, rho=rho, beta=beta, S=S, x=x, t=t, u=u, hist=hist)
+
+
+def test_isotropic_dual_in_ball_every_iteration(tviso16):
+    """Isotropic counterpart of the dual invariant: ||u|| <= lam/rho per pixel, and u = t/||t|| lam/rho
+    wherever t != 0."""
+    tau = tviso16["lam"] / tviso16["rho"]
+    for rec in tviso16["hist"][:60]:
+        nu = np.sqrt(np.sum(rec.u ** 2, axis=1))
+        assert nu.max() <= tau * (1 + 1e-12)
+        nt = np.sqrt(np.sum(rec.t ** 2, axis=1, keepdims=True))
+        nz = nt[:, 0] > 0
+        d = np.moveaxis(rec.u - tau * rec.t / np.where(nt > 0, nt, 1.0), 1, -1)[nz]
+        assert np.abs(d).max() < 1e-12
+
+
+def test_isotropic_kkt_and_objective(tviso16):
+    """Stationarity beta H^T(Hx - y) + rho D^T u = 0 and feasibility Dx = t at convergence; the
+    isotropic objective is below the anisotropic solution's value of it (the latter minimises
+    a different problem) and below the first iterate's."""
+    d = tviso16
+    g = d["beta"] * admm.adjoint_H(admm.forward_H(d["x"], d["h"]) - d["y"], d["h"]) + d["rho"] * admm.tv_adjoint(d["u"])
+    assert np.linalg.norm(g) / np.linalg.norm(d["beta"] * admm.adjoint_H(d["y"], d["h"])) < 1e-6
+    w = admm.tv_forward(d["x"])
+    assert np.linalg.norm(w - d["t"]) <= 1e-6 * np.linalg.norm(w)
+    f = lambda x: admm.objective(x, d["h"], d["y"], "tv_iso", d["lam"], d["beta"])
+    S_an = admm.analysis_setup(d["h"], d["y"], "tv", d["lam"], d["rho"], d["beta"])
+    x_an, _, _, _ = admm.run_analysis(S_an, 3000)
+    assert f(d["x"]) < f(x_an)
+    assert f(d["x"]) < f(d["hist"][0].x)
+
+
+def test_fast_oracle_matches_naive_tv_iso():
+    rng = np.random.default_rng(12)
+    N, K, M = 16, 3, 2
+    h = inputs.gaussian_psf_bank(N, K, M)
+    y = rng.standard_normal((K, N, N))
+    S = admm.analysis_setup(h, y, "tv_iso", 0.05, 0.7, 1.2)
+    F = fast.analysis_setup(h, y, "tv_iso", 0.05, 0.7, 1.2)
+    xs, ts, us, _ = admm.run_analysis(S, 20)
+    xf, tf, uf, _, _ = fast.run_analysis(F, 20)
+    assert rel(xf, xs) < 1e-11 and rel(uf, us) < 1e-11
