@@ -98,7 +98,7 @@ def algorithmic_bytes(n, m, prior="dct8", esz=4):
     """HBM bytes one launch must move (complex64 half spectra of N x (N/2+1) bins)."""
     bins = n * (n // 2 + 1)
     cpx = 2 * esz
-    ncomp = 2 if prior == "tv" else 1
+    ncomp = 2 if prior in ("tv", "tv_iso") else 1
     col = (3 * m + m * (m + 1) // 2) * bins * cpx            # read q, bhat, Pinv; write x
     pri = 2 * m * bins * cpx + 2 * ncomp * m * n * n * esz    # read x, write q; read+write u
     return {"column_pass": col, "prior_pass": pri}
@@ -382,8 +382,9 @@ def workload_adaptive(args, torch, api, inputs):
 def workload_single(args, torch, api, inputs):
     """One instance of any shape (N, M = K, prior), setup then `iters` iterations; per-kernel times.
     Also the small driver used for ncu captures."""
-    if args.prior == "tv":
+    if args.prior in ("tv", "tv_iso"):
         pr = inputs.tiny_tv(N=args.N, M=args.M, iters=args.iters, dtype="f32")
+        pr.prior = args.prior
     else:
         pr = inputs.spectral_dct(N=args.N, M=args.M, iters=args.iters)
         pr.prior = args.prior
@@ -433,7 +434,7 @@ def main():
                     choices=["spectral_dct", "convdict", "batch", "serve", "precision", "single", "adaptive"])
     ap.add_argument("--N", type=int, default=1024, help="single: image side")
     ap.add_argument("--M", type=int, default=10, help="single: channels (= measurements)")
-    ap.add_argument("--prior", default="tv", choices=["tv", "dct8", "l1"], help="single: prior")
+    ap.add_argument("--prior", default="tv", choices=["tv", "tv_iso", "dct8", "l1"], help="single: prior")
     ap.add_argument("--iters", type=int, default=20, help="single: iterations")
     ap.add_argument("--column-pass", type=int, default=0, help="single: 0 autotuned, 1 fused, 2 split")
     ap.add_argument("--col-tile", type=int, default=0, help="single: columns per fused cluster (0 = default)")

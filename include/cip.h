@@ -60,8 +60,11 @@ typedef enum cip_prior {
   CIP_PRIOR_TV = 0,   /* anisotropic TV: T = [D_h; D_v], circular forward differences (2 components) */
   CIP_PRIOR_DCT8 = 1, /* orthonormal DCT-II on 8x8 blocks aligned at (0,0) (1 component) */
   CIP_PRIOR_L1 = 2,   /* T = I (1 component) */
-  CIP_PRIOR_CONVDICT = 3 /* synthesis prior with a 2D convolutional dictionary shared by all channels
+  CIP_PRIOR_CONVDICT = 3, /* synthesis prior with a 2D convolutional dictionary shared by all channels
                             (Alg. 2): x ~ sum_l d_l (*) z_{l,m}, l1 on the coefficient maps z */
+  CIP_PRIOR_TV_ISO = 4 /* isotropic TV, lambda sum_pixels ||(D_h x, D_v x)||_2 (Section III-A): the
+                          same T and x-update as CIP_PRIOR_TV, the t-update the per-pixel group
+                          shrinkage (v max(0, 1 - (lambda/rho)/||v||)), 2 components */
 } cip_prior;
 
 typedef struct cip_options {
@@ -241,7 +244,7 @@ cip_status cip_batch_destroy(cip_batch* batch);
 typedef struct cip_server cip_server;
 typedef struct cip_request {
   int N, K, M;
-  int prior;                      /* CIP_PRIOR_TV, CIP_PRIOR_DCT8 or CIP_PRIOR_L1 */
+  int prior;                      /* CIP_PRIOR_TV, CIP_PRIOR_TV_ISO, CIP_PRIOR_DCT8 or CIP_PRIOR_L1 */
   double lambda, rho, beta;
   const float* h;                 /* host [K][M][N][N] */
   const float* y;                 /* host [K][N][N] */

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib
 
-PRIORS = {"tv": 0, "dct8": 1, "l1": 2, "convdict": 3}
+PRIORS = {"tv": 0, "dct8": 1, "l1": 2, "convdict": 3, "tv_iso": 4}
 DTYPES = {"f32": 0, "f64": 1}
 NP_DTYPE = {"f32": np.float32, "f64": np.float64}
 
@@ -98,7 +98,7 @@ class Plan:
 
     @property
     def ncomp(self) -> int:
-        return 2 if self.prior == "tv" else 1
+        return 2 if self.prior in ("tv", "tv_iso") else 1
 
     @property
     def state_shape(self):

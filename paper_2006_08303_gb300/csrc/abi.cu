@@ -119,7 +119,7 @@ cip_status fail(cip_plan* p, cip_status s, const std::string& msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                              \
   } while (0)
 
-size_t ncomp_of(int prior) { return prior == CIP_PRIOR_TV ? 2 : 1; }
+size_t ncomp_of(int prior) { return prior_is_tv(prior) ? 2 : 1; }
 
 bool is_cd(const cip_plan* p) { return p->prior == CIP_PRIOR_CONVDICT; }
 // kind of prior pass: the dictionary's shrinkage acts on the coefficient maps with T = I
@@ -254,7 +254,7 @@ template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
   if (!p->pinv64)
     CIP_CUDA(p, dmalloc(p, &p->pinv64, half_elems(p, p->M * (p->M + 1) / 2) * sizeof(SetupC<T>)));
   CIP_CUDA(p, cudaMemsetAsync(p->pinv_list, 0, sizeof(int), s));
-  const int use_g = p->prior == CIP_PRIOR_TV ? 1 : 0;
+  const int use_g = prior_is_tv(p->prior) ? 1 : 0;
   // analysis: Psi = rho g I + beta Lambda^H Lambda; dictionary: t I + beta Lambda^H Lambda with t = 1
   // (P^H P = I for a convolutional dictionary, Eq. solx_synt_DFT)
   const double diag = is_cd(p) ? 1.0 : p->rho;
@@ -785,7 +785,7 @@ size_t cip_plan_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior) {
   if (!valid_n(N) || K < 1 || M < 1) return 0;
   const size_t e = dtype == CIP_F64 ? 8 : 4;
   const size_t P = (size_t)half_pitch(N), half = (size_t)N * P * 2 * e, real = (size_t)N * N * e;
-  const size_t nc = prior == CIP_PRIOR_TV ? 2 : 1;
+  const size_t nc = prior_is_tv(prior) ? 2 : 1;
   size_t b = 0;
   b += 3 * M * half;                          // xh, qh, bhat
   b += (size_t)M * (M + 1) / 2 * half;        // pinv
@@ -912,7 +912,8 @@ cip_status cip_plan_destroy(cip_plan* p) {
 
 cip_status cip_set_prior(cip_plan* p, cip_prior prior, double lambda, double rho, double beta, void* stream) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  if (prior != CIP_PRIOR_TV && prior != CIP_PRIOR_DCT8 && prior != CIP_PRIOR_L1 && prior != CIP_PRIOR_CONVDICT)
+  if (prior != CIP_PRIOR_TV && prior != CIP_PRIOR_DCT8 && prior != CIP_PRIOR_L1 && prior != CIP_PRIOR_CONVDICT &&
+      prior != CIP_PRIOR_TV_ISO)
     return fail(p, CIP_ERR_INVALID_ARG, "unknown prior");
   if (!(lambda > 0) || !(rho > 0) || !(beta > 0)) return fail(p, CIP_ERR_INVALID_ARG, "lambda, rho, beta must be > 0");
   const int kind = prior == CIP_PRIOR_CONVDICT ? (int)CIP_PRIOR_L1 : (int)prior;
@@ -1433,7 +1434,7 @@ size_t plan_resident_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior
   (void)K;
   const size_t e = dtype == CIP_F64 ? 8 : 4, c = 2 * e;
   const size_t H = N / 2 + 1, P = half_pitch(N), CP = col_pitch(N);
-  const size_t nc = prior == CIP_PRIOR_TV ? 2 : 1;
+  const size_t nc = prior_is_tv(prior) ? 2 : 1;
   const size_t npk = (size_t)M * (M + 1) / 2;
   size_t b = 2 * (size_t)M * N * P * c;       // xh, qh
   b += (size_t)M * H * CP * c;                // data term

@@ -6,13 +6,15 @@
 
 namespace cip {
 
-enum PriorKind { PRIOR_TV = 0, PRIOR_DCT8 = 1, PRIOR_L1 = 2, PRIOR_CONVDICT = 3 };
+enum PriorKind { PRIOR_TV = 0, PRIOR_DCT8 = 1, PRIOR_L1 = 2, PRIOR_CONVDICT = 3, PRIOR_TV_ISO = 4 };
+// the two TV priors share T = [D_h; D_v] (two components, one halo row each side)
+constexpr bool prior_is_tv(int p) { return p == PRIOR_TV || p == PRIOR_TV_ISO; }
 
 // flags of the prior pass
 enum { PA_STORE_T = 1, PA_RESID = 2, PA_IMPORT = 4 };
 constexpr int kNPart = 5;  // sum (w-t)^2, sum w^2, sum t^2, sum u^2, sum (t - t_prev)^2
 
-inline int prior_ncomp(int prior) { return prior == PRIOR_TV ? 2 : 1; }
+inline int prior_ncomp(int prior) { return prior_is_tv(prior) ? 2 : 1; }
 
 // Prior pass (one ADMM t/u update + the adjoint for the next x-update):
 //   x = row-IDFT(xh)  ->  w = T x  ->  t = soft(w + u, tau)  ->  u' = u + w - t

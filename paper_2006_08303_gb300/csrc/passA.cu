@@ -59,7 +59,7 @@ template <typename T> constexpr int elems_a(int N) { return (sizeof(T) == 4 && N
 
 // rows per tile
 template <typename T> constexpr int rows_for(int N, int prior) {
-  if (prior != PRIOR_TV) return 8;
+  if (!prior_is_tv(prior)) return 8;
   using C = typename CT<T>::type;
   for (int R = 8; R >= 2; R /= 2) {
     size_t zs = (size_t)spad(N);
@@ -74,20 +74,20 @@ template <typename T> constexpr int rows_for(int N, int prior) {
 // column pass), when the staging area keeps the CTA within ~100 KB
 template <typename T> constexpr bool u_staged(int N, int prior, int R) {
   using C = typename CT<T>::type;
-  return prior != PRIOR_TV && (size_t)(R / 2) * spad(N) * sizeof(C) + (size_t)R * N * sizeof(T) <= 100 * 1024;
+  return !prior_is_tv(prior) && (size_t)(R / 2) * spad(N) * sizeof(C) + (size_t)R * N * sizeof(T) <= 100 * 1024;
 }
 
 template <typename T> constexpr size_t smem_for(int N, int prior, int R) {
   using C = typename CT<T>::type;
-  const int halo = prior == PRIOR_TV ? 1 : 0;
+  const int halo = prior_is_tv(prior) ? 1 : 0;
   size_t sm = (size_t)((R + 2 * halo) / 2) * spad(N) * sizeof(C);
-  if (prior == PRIOR_TV) sm += (size_t)(2 * R + 1) * N * sizeof(T);
+  if (prior_is_tv(prior)) sm += (size_t)(2 * R + 1) * N * sizeof(T);
   if (u_staged<T>(N, prior, R)) sm += (size_t)R * N * sizeof(T);
   return sm;
 }
 
 template <typename T> constexpr int threads_for(int N, int prior, int R) {
-  const int npin = (R + (prior == PRIOR_TV ? 2 : 0)) / 2;
+  const int npin = (R + (prior_is_tv(prior) ? 2 : 0)) / 2;
   const int n = npin * (N / elems_a<T>(N));
   return ((n + 31) / 32) * 32;
 }
@@ -199,14 +199,14 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   constexpr int N = 1 << LOGN;
   constexpr int H = N / 2 + 1;
   constexpr int P = half_pitch(N);
-  constexpr int HALO = PRIOR == PRIOR_TV ? 1 : 0;
+  constexpr int HALO = prior_is_tv(PRIOR) ? 1 : 0;
   constexpr int ROWS = R + 2 * HALO;
   constexpr int NPIN = ROWS / 2;
   constexpr int NPOUT = R / 2;
   constexpr int ZS = spad(N);
   constexpr int E = elems_a<T>(N);
   constexpr int TEAM = N / E;
-  constexpr int NCOMP = PRIOR == PRIOR_TV ? 2 : 1;
+  constexpr int NCOMP = prior_is_tv(PRIOR) ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* zb = reinterpret_cast<C*>(smem_raw);
   T* ah = reinterpret_cast<T*>(zb + NPIN * ZS);  // TV only: [R][N], a_h at tile rows 1..R
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   }
 
   // 2. analysis operator, shrinkage, dual update; 3. q = qscale T^T (t - u')
-  if constexpr (PRIOR == PRIOR_TV) {
+  if constexpr (prior_is_tv(PRIOR)) {
     // a_v at tile rows 0..R, a_h at tile rows 1..R; thread = (row pair p, column c)
     for (int idx = tid; idx < NPIN * N; idx += nth) {
       const int p = idx / N, c = idx - p * N;
@@ -306,23 +306,31 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
         const int j = 2 * p + s;
         if (j > R) continue;  // row R+1: neither component needed
         const size_t g = (size_t)grow(j) * N + c;
-        T tv, uvn;
+        T tv, uvn, th = T(0), uhn = T(0);
         if (import_mode) {
           tv = timp[plane + g];
           uvn = u_in[plane + g];
+          if (j >= 1) {
+            th = timp[g];
+            uhn = u_in[g];
+          }
+        } else if constexpr (PRIOR == PRIOR_TV_ISO) {
+          // isotropic TV: the pixel's two components shrink together (group soft threshold);
+          // the halo row needs its horizontal component too, for the vertical one
+          const T vh = wh[s] + u_in[g], vv = wv[s] + u_in[plane + g];
+          const T nrm = sqrt(vh * vh + vv * vv);
+          const T f = nrm > tau ? T(1) - tau / nrm : T(0);
+          th = vh * f;
+          tv = vv * f;
+          uhn = vh - th;
+          uvn = vv - tv;
         } else {
           shrink(wv[s], u_in[plane + g], tau, tv, uvn);
+          if (j >= 1) shrink(wh[s], u_in[g], tau, th, uhn);
         }
         av[j * N + c] = tv - uvn;
         if (j >= 1) {
           u_out[plane + g] = uvn;
-          T th, uhn;
-          if (import_mode) {
-            th = timp[g];
-            uhn = u_in[g];
-          } else {
-            shrink(wh[s], u_in[g], tau, th, uhn);
-          }
           ah[(j - 1) * N + c] = th - uhn;
           u_out[g] = uhn;
           if (resid) {
@@ -518,6 +526,7 @@ template <typename T> size_t passA_smem(int N, int prior) { return smem_for<T>(N
 template <typename T> cudaError_t launch_passA(const PassAArgs<T>& a, int N, int prior, cudaStream_t s) {
   switch (prior) {
     case PRIOR_TV: return dispatchA<T, PRIOR_TV>(a, N, s);
+    case PRIOR_TV_ISO: return dispatchA<T, PRIOR_TV_ISO>(a, N, s);
     case PRIOR_DCT8: return dispatchA<T, PRIOR_DCT8>(a, N, s);
     case PRIOR_L1: return dispatchA<T, PRIOR_L1>(a, N, s);
     default: return cudaErrorInvalidValue;

@@ -327,7 +327,9 @@ cip_status cip_server_create(cip_server** out, size_t hbm_budget, int max_active
 
 cip_status cip_server_submit(cip_server* s, const cip_request* r, unsigned long long* id) {
   if (!s || !r || !r->h || !r->y || !r->x_out) return CIP_ERR_INVALID_ARG;
-  if (r->prior != CIP_PRIOR_TV && r->prior != CIP_PRIOR_DCT8 && r->prior != CIP_PRIOR_L1) return CIP_ERR_UNSUPPORTED;
+  if (r->prior != CIP_PRIOR_TV && r->prior != CIP_PRIOR_DCT8 && r->prior != CIP_PRIOR_L1 &&
+      r->prior != CIP_PRIOR_TV_ISO)
+    return CIP_ERR_UNSUPPORTED;
   if (r->N < 64 || r->N > 2048 || (r->N & (r->N - 1)) || r->K < 1 || r->K > 16 || r->M < 1 || r->M > 16)
     return CIP_ERR_UNSUPPORTED;
   if (r->max_iter < 1) return CIP_ERR_INVALID_ARG;

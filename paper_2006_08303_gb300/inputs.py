@@ -336,7 +336,7 @@ def request_problem(req: Request, iters: int = 300) -> Problem:
 def random_state(rng: np.random.Generator, prior: str, M: int, N: int, scale: float = 0.1):
     """Random ADMM auxiliary/dual pair (t, u) in the prior's transform domain
     (TV: 2 components per channel, DCT/l1: 1), for step-level parity tests."""
-    ncomp = 2 if prior == "tv" else 1
+    ncomp = 2 if prior in ("tv", "tv_iso") else 1
     t = scale * rng.standard_normal((M, ncomp, N, N))
     u = scale * rng.standard_normal((M, ncomp, N, N))
     return t, u

@@ -65,7 +65,7 @@ def oracle_states(h, y, prior, lam, rho, ls, naive):
     mod = admm if naive else fast
     S = mod.analysis_setup(h, y, prior, lam, rho, 1.0)
     K, M, N, _ = h.shape
-    nc = 2 if prior == "tv" else 1
+    nc = 2 if prior in ("tv", "tv_iso") else 1
     t = np.zeros((M, nc, N, N))
     u = np.zeros_like(t)
     out = []
@@ -90,6 +90,9 @@ STEP_CASES = [
     ("tv", 128, 5, 2, "f32", 1e-2, 1.0, "gauss", (0, 10)),     # K > M
     ("l1", 2048, 1, 1, "f32", 1e-2, 1.0, "gauss", (0, 5)),     # largest N
     ("tv", 1024, 3, 3, "f32", 1e-2, 1.0, "gauss", (0, 5)),
+    ("tv_iso", 64, 3, 3, "f64", 1e-2, 1.0, "gauss", (0, 1, 10, 49)),   # isotropic TV (reading R20)
+    ("tv_iso", 64, 3, 3, "f32", 1e-2, 1.0, "gauss", (0, 1, 10, 49)),
+    ("tv_iso", 512, 5, 5, "f32", 1e-2, 1.0, "disk", (0, 1, 10)),
 ]
 
 
@@ -300,3 +303,20 @@ def test_errors_are_statuses(torch):
     with pytest.raises(api.CipError):
         P.set_prior("tv", -1.0, 1.0, 1.0)
     P.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_isotropic_tv_full_run(torch, dtype):
+    """Isotropic TV (coupled shrinkage, reading R20): 50 free-running iterations of the tiny
+    instance from t = u = 0 against the FP64 oracle, final x within FINAL_TOL."""
+    P = inputs.tiny_tv(dtype="f64")
+    S = fast.analysis_setup(P.h, P.y, "tv_iso", P.lam, P.rho, P.beta)
+    x_or, _, _, _, _ = fast.run_analysis(S, 50)
+    plan = make_plan(torch, P.h, P.y, "tv_iso", P.lam, P.rho, P.beta, dtype)
+    plan.iterate(50)
+    x = plan.get_x().double().cpu().numpy()
+    S_an = fast.analysis_setup(P.h, P.y, "tv", P.lam, P.rho, P.beta)
+    x_an, _, _, _, _ = fast.run_analysis(S_an, 50)
+    assert rel(x, x_or) <= FINAL_TOL[dtype], rel(x, x_or)
+    assert rel(x_an, x_or) > 100 * FINAL_TOL["f32"]  # the isotropic iterates really differ
+    plan.close()
