@@ -158,12 +158,12 @@ cip_status cip_reset_state(cip_plan* plan, void* stream);
  * primal residual ||Tx - t|| exceeds mu times the dual residual rho ||t - t_prev||, rho / tau
  * if the dual exceeds mu times the primal, and stays otherwise (the paper uses tau = 2,
  * mu = 10).  On a change the scaled dual u is multiplied by rho_old / rho_new (the multiplier
- * rho u is unchanged), the factor and the data term are formed again for the new rho, and the
- * next x-update's right-hand side is formed again.  tau = 0 turns adaptation off (the
- * default); otherwise tau > 1 and mu > 1.  Analysis priors only (CIP_ERR_UNSUPPORTED for the
- * dictionary).  Call it before cip_set_measurements, which then keeps the measurement spectra
- * (K half-spectrum maps, 16 bytes per bin) for re-forming the data term; CIP_ERR_STATE
- * otherwise.  rho keeps its adapted value until cip_set_prior.  Applies to cip_iterate (not to
+ * rho u is unchanged), the factor and the data term are formed again for the new rho (analysis
+ * priors; the dictionary's x-update factor does not depend on rho), and the next update's
+ * right-hand side is formed again.  tau = 0 turns adaptation off (the default); otherwise
+ * tau > 1 and mu > 1.  For analysis priors call it before cip_set_measurements, which then
+ * keeps the measurement spectra (K half-spectrum maps, 16 bytes per bin) for re-forming the data
+ * term; CIP_ERR_STATE otherwise.  rho keeps its adapted value until cip_set_prior.  Applies to cip_iterate (not to
  * batches or the request server). */
 cip_status cip_set_rho_adaptation(cip_plan* plan, double tau, double mu);
 

@@ -184,6 +184,32 @@ def convdict_step(C: FastConvDict, z, t, u):
     return x, z_new, t_new, u + z_new - t_new
 
 
+def run_convdict_adaptive(h, y, d, lam, rho, beta, iters: int, check_every: int, tau: float = 2.0,
+                          mu_bal: float = 10.0, mu: float = 0.0):
+    """Alg. 2 from zero state with the penalty of Eq. paramS adapted after every check_every-th
+    iteration (r = ||z - t||, s = rho ||t - t_prev||; readings R17, R18: u rescaled by
+    rho/rho').  The x-update factor (I + beta Lambda^H Lambda) does not depend on rho; the z-update
+    diagonal and the shrinkage threshold follow the current rho.  Returns (x, z, t, u, rhos)."""
+    C = convdict_setup(h, y, d, lam, rho, beta, mu)
+    z = np.zeros((C.L, C.M, C.N, C.N))
+    t = np.zeros_like(z)
+    u = np.zeros_like(z)
+    rhos = []
+    x = None
+    for it in range(iters):
+        x, z_new, t_new, u_new = convdict_step(C, z, t, u)
+        if (it + 1) % check_every == 0:
+            r = float(np.linalg.norm(z_new - t_new))
+            s = C.rho * float(np.linalg.norm(t_new - t))
+            rho_new = ref.adapt_rho(C.rho, r, s, tau, mu_bal)
+            if rho_new != C.rho:
+                u_new = u_new * (C.rho / rho_new)
+                C = convdict_setup(h, y, d, lam, rho_new, beta, mu)
+        z, t, u = z_new, t_new, u_new
+        rhos.append(C.rho)
+    return x, z, t, u, rhos
+
+
 def run_convdict(C: FastConvDict, iters: int):
     z = np.zeros((C.L, C.M, C.N, C.N))
     t = np.zeros_like(z)

@@ -1019,7 +1019,6 @@ cip_status cip_set_rho_adaptation(cip_plan* p, double tau, double mu) {
   }
   if (!(tau > 1.0) || !(mu > 1.0) || !std::isfinite(tau) || !std::isfinite(mu))
     return fail(p, CIP_ERR_INVALID_ARG, "tau and mu must be finite and > 1 (or tau = 0 to turn adaptation off)");
-  if (is_cd(p)) return fail(p, CIP_ERR_UNSUPPORTED, "the adaptive penalty covers analysis priors");
   if (p->have_y && !is_cd(p) && !p->yhat_keep)
     return fail(p, CIP_ERR_STATE, "cip_set_rho_adaptation must precede cip_set_measurements");
   p->adapt_tau = tau;

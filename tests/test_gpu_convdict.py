@@ -191,3 +191,30 @@ def test_gradient_weight_rejected_outside_dictionary(torch):
     with pytest.raises(Exception):
         P.set_code_gradient_weight(0.1)
     P.close()
+
+
+def test_convdict_adaptive_penalty(torch):
+    """Adaptive penalty (Eq. paramS) on Alg. 2 from rho = 64: the rho trajectory is the oracle's
+    (five halvings in 60 iterations, checks every 10) and the final x within 1e-4."""
+    from paper_2006_08303_gb300 import api
+    rng = np.random.default_rng(25)
+    d = inputs.gabor_filters(rng, 4, 5)
+    z = inputs.bernoulli_gaussian_codes(rng, 4, 3, 64, 0.02)
+    x = inputs.convdict_image(inputs.embed_filters(d, 64), z)
+    h = inputs.gaussian_psf_bank(64, 2, 3)
+    y, _ = inputs.measure(rng, x, h, 25.0)
+    lam, rho, beta = 0.15, 64.0, 4.0
+    x_ref, _, _, _, rhos = fast.run_convdict_adaptive(h, y, d, lam, rho, beta, 60, 10)
+    assert rhos[-1] == 2.0
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+    P = api.Plan(64, 2, 3, "f32", check_every=10)
+    P.set_prior("convdict", lam, rho, beta)
+    P.set_rho_adaptation(2.0, 10.0)
+    P.set_dictionary(f(d))
+    P.set_psfs(f(h))
+    P.set_measurements(f(y))
+    P.iterate(60)
+    assert P.rho == rhos[-1], (P.rho, rhos[-1])
+    xg = P.get_x().double().cpu().numpy()
+    assert rel(xg, x_ref) <= 1e-4, rel(xg, x_ref)
+    P.close()

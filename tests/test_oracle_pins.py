@@ -492,3 +492,18 @@ def test_fast_oracle_matches_naive_tv_iso():
     xs, ts, us, _ = admm.run_analysis(S, 20)
     xf, tf, uf, _, _ = fast.run_analysis(F, 20)
     assert rel(xf, xs) < 1e-11 and rel(uf, us) < 1e-11
+
+
+def test_convdict_adaptive_keeps_the_unscaled_multiplier(cd8):
+    """Adaptive penalty on Alg. 2 (readings R17, R18): the iteration after a change equals one
+    fixed-rho step at the new rho from (z, t, u rho_old/rho_new)."""
+    C0 = cd8["C"]
+    args = (cd8["h"], cd8["y"], cd8["d"], C0.lam, 50.0, C0.beta)
+    x5, z5, t5, u5, rhos = fast.run_convdict_adaptive(*args, 5, 5)
+    assert rhos[-1] != 50.0
+    x6, z6, t6, u6, _ = fast.run_convdict_adaptive(*args, 6, 5)
+    C_new = fast.convdict_setup(cd8["h"], cd8["y"], cd8["d"], C0.lam, rhos[-1], C0.beta)
+    xs, zs, ts, us = fast.convdict_step(C_new, z5, t5, u5)
+    assert rel(x6, xs) < 1e-12 and rel(z6, zs) < 1e-12 and rel(u6, us) < 1e-12
+    _, _, _, u_fix = fast.run_convdict(fast.convdict_setup(cd8["h"], cd8["y"], cd8["d"], C0.lam, 50.0, C0.beta), 5)
+    assert rel(rhos[-1] * u5, 50.0 * u_fix) < 1e-12
