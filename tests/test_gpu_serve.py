@@ -19,10 +19,10 @@ def torch():
     return torch
 
 
-def make_req(seed, N, M, prior):
+def make_req(seed, N, M, prior, K=None):
     rng = np.random.default_rng(seed)
     x = inputs.rectangles_image(rng, N, M, n_rect=5)
-    h = inputs.gaussian_psf_bank(N, M, M)
+    h = inputs.gaussian_psf_bank(N, M if K is None else K, M)
     y, _ = inputs.measure(rng, x, h, 30.0)
     lam, rho = (1e-2, 1.0) if prior != "dct8" else (1e-3, 0.1)
     return h.astype(np.float32), y.astype(np.float32), prior, lam, rho
@@ -127,3 +127,21 @@ def test_oversize_request_is_rejected(torch):
     with pytest.raises(api.CipError):
         S.submit(*make_req(6, 256, 3, "tv"))
     S.close()
+
+
+def test_served_k_differs_from_m(torch):
+    """Requests with K != M (one frame of three channels, four frames of two channels, four
+    frames of one image: multiframe deconvolution) are served alongside K = M ones, each result
+    equal to the plan run alone, and isotropic TV is served like the other analysis priors."""
+    from paper_2006_08303_gb300 import api
+    S = api.Server(hbm_budget=8 << 30, max_active=3, check_every=10)
+    cases = [(128, 3, "tv", 1), (64, 2, "dct8", 4), (128, 1, "tv_iso", 4), (64, 3, "tv", 3)]
+    reqs = [make_req(40 + i, N, M, prior, K) for i, (N, M, prior, K) in enumerate(cases)]
+    ids = [S.submit(h, y, prior, lam, rho, tol=1e-3, max_iter=150) for (h, y, prior, lam, rho) in reqs]
+    results = [S.wait(rid) for rid, _ in ids]
+    S.close()
+    for (rid, x_out), res, (h, y, prior, lam, rho) in zip(ids, results, reqs):
+        assert res["state"] == "done", res
+        x_alone, n_alone = alone(torch, h, y, prior, lam, rho, 1e-3, 150)
+        assert res["iterations"] == n_alone
+        assert np.array_equal(x_out, x_alone)
