@@ -12,7 +12,10 @@ namespace cip {
 
 namespace {
 
-template <typename T> constexpr int cs_cc() { return sizeof(T) == 4 ? 4 : 2; }  // 32-byte row segments
+#ifndef COLFFT_CC32
+#define COLFFT_CC32 4
+#endif
+template <typename T> constexpr int cs_cc() { return sizeof(T) == 4 ? COLFFT_CC32 : 2; }  // 32-byte row segments
 #ifndef COLFFT_E32
 #define COLFFT_E32 8
 #endif

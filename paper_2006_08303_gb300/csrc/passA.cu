@@ -55,7 +55,12 @@ __device__ __forceinline__ void block_reduce_store(const T (&v)[kNPart], double*
 
 // FFT elements per thread: 8 for complex64 up to N = 1024 (more warps per
 // tile), 16 otherwise (keeps the CTA within 1024 threads).
-template <typename T> constexpr int elems_a(int N) { return (sizeof(T) == 4 && N <= 1024) ? 8 : 16; }
+// (complex64 DCT / l1 tiles at N = 512 take 16: one warp per row-pair FFT, whose stage
+// barriers are then warp syncs; measured 6% faster there, while TV, which needs more
+// registers for its halo rows, is faster at 8)
+template <typename T> constexpr int elems_a(int N, int prior) {
+  return (sizeof(T) == 4 && N <= 1024) ? ((N == 512 && !prior_is_tv(prior)) ? 16 : 8) : 16;
+}
 
 // rows per tile
 template <typename T> constexpr int rows_for(int N, int prior) {
@@ -88,7 +93,7 @@ template <typename T> constexpr size_t smem_for(int N, int prior, int R) {
 
 template <typename T> constexpr int threads_for(int N, int prior, int R) {
   const int npin = (R + (prior_is_tv(prior) ? 2 : 0)) / 2;
-  const int n = npin * (N / elems_a<T>(N));
+  const int n = npin * (N / elems_a<T>(N, prior));
   return ((n + 31) / 32) * 32;
 }
 
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   constexpr int NPIN = ROWS / 2;
   constexpr int NPOUT = R / 2;
   constexpr int ZS = spad(N);
-  constexpr int E = elems_a<T>(N);
+  constexpr int E = elems_a<T>(N, PRIOR);
   constexpr int TEAM = N / E;
   constexpr int NCOMP = prior_is_tv(PRIOR) ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
