@@ -9,14 +9,18 @@ namespace cip {
 namespace {
 
 constexpr int kRowThreads = 256;
+#ifndef SETUP_FFT_E
+#define SETUP_FFT_E 8
+#endif
+constexpr int kE = SETUP_FFT_E;  // FFT elements per thread in these kernels (8 measured faster than 16 for the double-float setup)
 
-// Two real rows per complex FFT.  Each team of N/16 threads owns one row pair.
+// Two real rows per complex FFT.  Each team of N/kE threads owns one row pair.
 template <typename Tc, typename Tin, int LOGN>
 __global__ void __launch_bounds__(kRowThreads) row_r2c_kernel(const Tin* __restrict__ in,
                                                                 typename CT<Tc>::type* __restrict__ out, int nrows,
                                                                 Tc scale, const typename CT<Tc>::type* tw) {
   using C = typename CT<Tc>::type;
-  constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N), ZS = spad(N), TEAM = N / 16;
+  constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N), ZS = spad(N), TEAM = N / kE;
   constexpr int PAIRS = kRowThreads / TEAM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* zb = reinterpret_cast<C*>(smem_raw);
@@ -31,7 +35,7 @@ __global__ void __launch_bounds__(kRowThreads) row_r2c_kernel(const Tin* __restr
   }
   __syncthreads();
   const int team = tid / TEAM;
-  fft_team<C, LOGN, 1, 16, -1>(zb + team * ZS, tid % TEAM, tw, make_block_team_sync(team, TEAM));
+  fft_team<C, LOGN, 1, kE, -1>(zb + team * ZS, tid % TEAM, tw, make_block_team_sync(team, TEAM));
   __syncthreads();
   for (int idx = tid; idx < PAIRS * H; idx += kRowThreads) {
     const int p = idx / H, k = idx - p * H;
@@ -48,7 +52,7 @@ __global__ void __launch_bounds__(kRowThreads) row_c2r_kernel(const typename CT<
                                                                 Tout* __restrict__ out, int nrows,
                                                                 const typename CT<Tc>::type* tw) {
   using C = typename CT<Tc>::type;
-  constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N), ZS = spad(N), TEAM = N / 16;
+  constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N), ZS = spad(N), TEAM = N / kE;
   constexpr int PAIRS = kRowThreads / TEAM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* zb = reinterpret_cast<C*>(smem_raw);
@@ -63,7 +67,7 @@ __global__ void __launch_bounds__(kRowThreads) row_c2r_kernel(const typename CT<
   }
   __syncthreads();
   const int team = tid / TEAM;
-  fft_team<C, LOGN, 1, 16, +1>(zb + team * ZS, tid % TEAM, tw, make_block_team_sync(team, TEAM));
+  fft_team<C, LOGN, 1, kE, +1>(zb + team * ZS, tid % TEAM, tw, make_block_team_sync(team, TEAM));
   __syncthreads();
   for (int idx = tid; idx < PAIRS * N; idx += kRowThreads) {
     const int p = idx / N, n = idx - p * N;
@@ -78,7 +82,7 @@ __global__ void __launch_bounds__(kRowThreads) row_c2r_kernel(const typename CT<
 template <typename Tc, int LOGN, int SIGN>
 __global__ void col_c2c_kernel(typename CT<Tc>::type* data, const typename CT<Tc>::type* tw) {
   using C = typename CT<Tc>::type;
-  constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N), CC = 4, TEAM = N * CC / 16;
+  constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N), CC = 4, TEAM = N * CC / kE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* zb = reinterpret_cast<C*>(smem_raw);
   const int tid = threadIdx.x;
@@ -94,7 +98,7 @@ __global__ void col_c2c_kernel(typename CT<Tc>::type* data, const typename CT<Tc
   ts.nthreads = TEAM;
   ts.mask = TEAM >= 32 ? 0xffffffffu : ((1u << TEAM) - 1u);
   ts.cta = false;
-  fft_team<C, LOGN, CC, 16, SIGN>(zb, tid, tw, ts);
+  fft_team<C, LOGN, CC, kE, SIGN>(zb, tid, tw, ts);
   __syncthreads();
   for (int idx = tid; idx < N * CC; idx += TEAM) {
     const int n = idx / CC, c = idx - n * CC;
@@ -106,7 +110,7 @@ template <typename Tc, typename Tin, int LOGN>
 cudaError_t rr2c(const Tin* in, typename CT<Tc>::type* out, int nrows, Tc scale, const typename CT<Tc>::type* tw,
                  cudaStream_t s) {
   using C = typename CT<Tc>::type;
-  constexpr int N = 1 << LOGN, PAIRS = kRowThreads / (N / 16);
+  constexpr int N = 1 << LOGN, PAIRS = kRowThreads / (N / kE);
   const size_t sm = (size_t)PAIRS * spad(N) * sizeof(C);
   auto k = row_r2c_kernel<Tc, Tin, LOGN>;
   if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -119,7 +123,7 @@ template <typename Tc, typename Tout, int LOGN>
 cudaError_t rc2r(const typename CT<Tc>::type* in, Tout* out, int nrows, const typename CT<Tc>::type* tw,
                  cudaStream_t s) {
   using C = typename CT<Tc>::type;
-  constexpr int N = 1 << LOGN, PAIRS = kRowThreads / (N / 16);
+  constexpr int N = 1 << LOGN, PAIRS = kRowThreads / (N / kE);
   const size_t sm = (size_t)PAIRS * spad(N) * sizeof(C);
   auto k = row_c2r_kernel<Tc, Tout, LOGN>;
   if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -131,7 +135,7 @@ cudaError_t rc2r(const typename CT<Tc>::type* in, Tout* out, int nrows, const ty
 template <typename Tc, int LOGN>
 cudaError_t cc2c(typename CT<Tc>::type* data, int nmaps, int sign, const typename CT<Tc>::type* tw, cudaStream_t s) {
   using C = typename CT<Tc>::type;
-  constexpr int N = 1 << LOGN, CC = 4, TEAM = N * CC / 16;
+  constexpr int N = 1 << LOGN, CC = 4, TEAM = N * CC / kE;
   const size_t sm = (size_t)spad(N * CC) * sizeof(C);
   dim3 grid((N / 2 + 1 + CC - 1) / CC, nmaps);
   if (sign < 0) {
