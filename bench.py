@@ -128,6 +128,20 @@ def cpu_oracle_sample(problem, iters_sample: int):
     }
 
 
+def replica_throughput(local_ms: float, units_per_rank: float, dist=None, device: str = "cpu"):
+    """Whole-job figure of independent replicas: the job lasts as long as its slowest rank (maximum
+    of the per-rank times over the process group) and processes the units of all ranks.  Returns
+    (max_ms, units_per_second)."""
+    world = dist.get_world_size() if dist else 1
+    total = float(local_ms)
+    if dist:
+        import torch
+        tt = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+    return total, units_per_rank * world / (total / 1e3)
+
+
 def run_reference(args, rank, world):
     from paper_2006_08303_gb300 import inputs
     if rank != 0:
@@ -529,13 +543,7 @@ def main():
             ph[k] += ev[i].elapsed_time(ev[i + 1]) / args.steps
     kt = plan.get_timing()
     plan.set_timing(False)
-    total_ms = sum(ms)
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    vox_iters = prob.voxels * ITERS * args.steps * world
-    value = vox_iters / (total_ms / 1e3)
+    total_ms, value = replica_throughput(sum(ms), prob.voxels * ITERS * args.steps, dist, "cuda")
 
     # ---- end-to-end through the C ABI with host buffers (H2D/D2H inside the timed region)
     for _ in range(1):
@@ -553,12 +561,7 @@ def main():
         e.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(s.elapsed_time(e))
-    e2e_total = sum(e2e_ms)
-    if dist:
-        tt = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt.item())
-    e2e_value = vox_iters / (e2e_total / 1e3)
+    e2e_total, e2e_value = replica_throughput(sum(e2e_ms), prob.voxels * ITERS * args.steps, dist, "cuda")
     h2d = (prob.h.size + prob.y.size) * 4
     d2h = M * N * N * 4
 
