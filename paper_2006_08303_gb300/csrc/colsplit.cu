@@ -193,12 +193,11 @@ cudaError_t launch_colfft(const typename CT<T>::type* src, typename CT<T>::type*
   constexpr int N = 1 << LOGN, CC = cs_cc<T>(), NT = N * CC / cs_e<T>(N);
   const size_t sm = (size_t)spad(N * CC) * sizeof(C);
   auto k = colfft_split_kernel<T, LOGN, SIGN>;
-  static bool done = false;
-  if (!done && sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static PerDeviceOnce once;
+  if (sm > 48 * 1024) {
+    cudaError_t e = once([&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); });
     if (e != cudaSuccess) return e;
   }
-  done = true;
   return launch_pdl(k, dim3((N / 2 + 1 + CC - 1) / CC, M), dim3(NT), sm, s, 0, src, dst, tw, M);
 }
 

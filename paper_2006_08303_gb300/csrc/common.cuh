@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <utility>
 
 namespace cip {
@@ -129,6 +130,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
   if (err) atomicExch(err, 1);
   return false;
 }
+
+// Kernel attributes (shared-memory size, carveout, cluster size) are per function and per
+// device: PerDeviceOnce runs the setting once for each device a call site meets.
+struct PerDeviceOnce {
+  std::atomic<unsigned long long> done{0};
+  template <typename F> cudaError_t operator()(F&& set) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = set();
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+  }
+};
 
 // Programmatic dependent launch.  The iteration's kernels are launched with
 // programmatic stream serialisation: a kernel may start while its predecessor

@@ -361,13 +361,10 @@ cudaError_t launch_factor_m(const SetupC<Tout>* lam, const double* gs, int use_g
   const int nb = N * (N / 2 + 1);
   const size_t sm = (size_t)(M * (M + 1) / 2) * kFacThreads * sizeof(SetupC<Tout>);
   auto k = factor_kernel<Tout, MMAX>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    const int most = MMAX * (MMAX + 1) / 2 * kFacThreads * (int)sizeof(SetupC<Tout>);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static PerDeviceOnce once;
+  const int most = MMAX * (MMAX + 1) / 2 * kFacThreads * (int)sizeof(SetupC<Tout>);
+  cudaError_t e = once([&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, most); });
+  if (e != cudaSuccess) return e;
   k<<<(nb + kFacThreads - 1) / kFacThreads, kFacThreads, sm, s>>>(lam, gs, use_g, K, M, N, rho, beta, pinv, pinv64,
                                                                   pinv_list, list_cap);
   return cudaGetLastError();

@@ -495,18 +495,17 @@ cudaError_t launchA(const PassAArgs<T>& a, cudaStream_t s) {
   constexpr int nth = threads_for<T>(N, PRIOR, R);
   constexpr size_t sm = smem_for<T>(N, PRIOR, R);
   auto kern = passA_kernel<T, LOGN, PRIOR, R>;
-  static bool attr_done = false;
-  if (!attr_done) {
+  static PerDeviceOnce once;
+  cudaError_t e = once([&] {
     if (sm > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
+      cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (r != cudaSuccess) return r;
     }
     // the largest shared-memory carveout, so that the register-bound CTA count is reached
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+    return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+  });
+  if (e != cudaSuccess) return e;
   return launch_pdl(kern, dim3(N / R, a.M), dim3(nth), sm, s, 0, a);
 }
 

@@ -165,16 +165,15 @@ cudaError_t launchB(const PassBArgs<T>& a, cudaStream_t s) {
   constexpr int NT = N * CC / elems_for<T>();
   const size_t sm = (size_t)spad(N * CC) * sizeof(C);
   auto kern = passB_kernel<T, LOGN, CC, MMAX>;
-  static bool attr_done = false;
-  if (!attr_done) {
+  static PerDeviceOnce once;
+  cudaError_t e = once([&] {
     if (sm > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
+      cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (r != cudaSuccess) return r;
     }
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  });
+  if (e != cudaSuccess) return e;
   return launch_pdl(kern, dim3(a.M, (N / 2 + 1 + CC - 1) / CC, 1), dim3(NT), sm, s, (unsigned)a.M, a);
 }
 
