@@ -413,6 +413,13 @@ def workload_single(args, torch, api, inputs):
     kt = P.get_timing()
     cfg = P.config()
     P.close()
+    # reference point only: cuFFT (through torch.fft) forward + inverse real 2D transform of the
+    # same M x N x N float32 stack, the transform work one iteration contains
+    xs = torch.randn((pr.M, pr.N, pr.N), device="cuda")
+    for _ in range(3):
+        torch.fft.irfft2(torch.fft.rfft2(xs), s=(pr.N, pr.N))
+    reps = 20
+    t_cufft = _ev_time(torch, lambda: torch.fft.irfft2(torch.fft.rfft2(xs), s=(pr.N, pr.N)), reps) / reps
     ab = algorithmic_bytes(pr.N, pr.M, pr.prior)
     avgA = kt["prior_pass_ms"] / max(kt["prior_pass_n"], 1)
     avgB = kt["column_pass_ms"] / max(kt["column_pass_n"], 1)
@@ -420,7 +427,9 @@ def workload_single(args, torch, api, inputs):
             "ms_per_step": 1e3 * t,
             "config": {"workload": f"single_{pr.N}x{pr.N}x{pr.M}_{pr.prior}", "iters": args.iters, "launch": cfg},
             "kernels": {"prior_pass_us": 1e3 * avgA, "prior_pass_GBps": ab["prior_pass"] / avgA / 1e6,
-                        "column_pass_us": 1e3 * avgB, "column_pass_GBps": ab["column_pass"] / avgB / 1e6}}
+                        "column_pass_us": 1e3 * avgB, "column_pass_GBps": ab["column_pass"] / avgB / 1e6},
+            "cufft_reference": {"rfft2_plus_irfft2_us": 1e6 * t_cufft,
+                                "note": "cuFFT via torch.fft on the same M x N x N float32 stack; reference point only"}}
 
 
 def run_workload(args):
