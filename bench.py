@@ -104,6 +104,24 @@ def algorithmic_bytes(n, m, prior="dct8", esz=4):
     return {"column_pass": col, "prior_pass": pri}
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU-baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_oracle_sample(problem, iters_sample: int):
     """Time the fast FP64 oracle (setup + iters_sample iterations) on this host's cores."""
     from oracle import fast
@@ -119,6 +137,7 @@ def cpu_oracle_sample(problem, iters_sample: int):
         "value": problem.voxels * problem.iters / recon_s,
         "unit": "voxel-iter/s",
         "cores": os.cpu_count(),
+        "cpu_model": _cpu_model(),
         "kind": "oracle",
         "sample": f"fast FP64 oracle (scipy.fft, {fast.WORKERS} workers): setup + {iters_sample} of {problem.iters} "
                   f"iterations of the same {problem.N}x{problem.N}x{problem.M} instance, scaled to a full "
@@ -266,6 +285,12 @@ def workload_batch(args, torch, api, inputs):
     S = fast.analysis_setup(p0.h, p0.y, p0.prior, p0.lam, p0.rho, p0.beta)
     x_or, _, _, _, _ = fast.run_analysis(S, 100)
     err = lambda a: float(np.linalg.norm(a - x_or) / np.linalg.norm(x_or))
+    byts = 100 * sum(sum(algorithmic_bytes(p.N, p.M, p.prior).values()) for p in probs)
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    res["roofline"] = {"bound": "hbm", "achieved": round(byts / t_batch / 1e9, 1), "peak": peak, "unit": "GB/s",
+                       "frac": round(byts / t_batch / 1e9 / peak, 4),
+                       "algorithmic_bytes": byts, "note": "both passes of all 64 instances, 100 iterations"}
     res.update({"metric": METRIC, "value": vox / t_batch, "unit": "voxel-iter/s", "ms_per_step": 1e3 * t_batch,
                 "config": {"workload": "mixed_batch_64 (N 128..1024, M=K 3/5/10, TV, 100 iterations each)",
                            "voxel_iters": vox, "step": "100 iterations of all 64 instances (setup excluded)"},
@@ -276,9 +301,8 @@ def workload_batch(args, torch, api, inputs):
     return res
 
 
-def workload_serve(args, torch, api, inputs):
-    """Poisson stream of reconstructions (N in {256..2048}, M = K in {3,5,10}, TV or DCT, tol 1e-4,
-    max 300 iterations) served with continuous batching; p50/p99 latency and voxel-iter/s."""
+def _serve_jobs(args, inputs):
+    """The request stream of the serving workload with its inputs (generated once, outside timing)."""
     reqs = inputs.request_stream(n=args.requests, rate_hz=args.rate)
     banks, ffts = {}, {}
     jobs = []
@@ -299,15 +323,22 @@ def workload_serve(args, torch, api, inputs):
         y = (clean + sig * rng.standard_normal(clean.shape)).astype(np.float32)
         lam, rho = (1e-2, 1.0) if r.prior == "tv" else (1e-3, 1e-2)
         jobs.append((r, key, y, lam, rho))
+    return jobs, banks
+
+
+def _serve_run(args, torch, api, jobs, banks, slow: float = 1.0, cache: bool = True, n: int = None):
+    """Submit the stream (arrival times stretched by `slow`) to a fresh server and wait for all."""
+    jobs = jobs[:n] if n else jobs
     free, total = torch.cuda.mem_get_info()
     S = api.Server(hbm_budget=int(0.8 * free), max_active=args.max_active, check_every=10)
     t0 = time.perf_counter()
     ids = []
+    a0 = jobs[0][0].arrival_s
     for r, key, y, lam, rho in jobs:
-        dt = r.arrival_s - (time.perf_counter() - t0)
+        dt = (r.arrival_s - a0) * slow - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
-        psf_key = (hash(key) & 0xFFFFFFFFFFFF) + 1
+        psf_key = (hash(key) & 0xFFFFFFFFFFFF) + 1 if cache else 0
         ids.append((S.submit(banks[key], y, r.prior, lam, rho, tol=1e-4, max_iter=300, psf_key=psf_key), r))
     res = [(S.wait(rid), r) for (rid, _), r in ids]
     makespan = max(x["t_done"] for x, _ in res) - min(x["t_submit"] for x, _ in res)
@@ -316,15 +347,40 @@ def workload_serve(args, torch, api, inputs):
     lat = np.array([x["t_done"] - x["t_submit"] for x, _ in res])
     done = [x for x, _ in res if x["state"] == "done"]
     vi = sum(r.N * r.N * r.M * x["iterations"] for x, r in res)
-    span_arrivals = reqs[-1].arrival_s - reqs[0].arrival_s
-    return {"metric": "serve voxel-iter/s, p50/p99 latency", "value": vi / makespan, "unit": "voxel-iter/s",
-            "config": {"workload": f"poisson_{args.rate:g}hz_{args.requests}req (N 256..2048, M=K 3/5/10, TV/DCT, "
-                                   "tol 1e-4, max 300 iterations)", "max_active": args.max_active},
-            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
-                           "mean": float(lat.mean() * 1e3)},
-            "requests": len(res), "done": len(done), "offered_req_per_s": len(reqs) / max(span_arrivals, 1e-9),
+    span = (jobs[-1][0].arrival_s - a0) * slow
+    return {"value": vi / makespan, "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
+                                                   "p99": float(np.percentile(lat, 99) * 1e3),
+                                                   "mean": float(lat.mean() * 1e3)},
+            "requests": len(res), "done": len(done), "offered_req_per_s": len(jobs) / max(span, 1e-9),
             "achieved_req_per_s": len(done) / makespan, "voxel_iters": vi, "makespan_s": makespan,
             "iterations_mean": float(np.mean([x["iterations"] for x, _ in res])), "server": st}
+
+
+def workload_serve(args, torch, api, inputs):
+    """Poisson stream of reconstructions (N in {256..2048}, M = K in {3,5,10}, TV or DCT, tol 1e-4,
+    max 300 iterations) served with continuous batching; p50/p99 latency and voxel-iter/s with the
+    PSF-factor cache on and off, and the highest offered rate the server sustains (the same stream,
+    its first 40 requests, stretched to lower rates: sustained when at least 90% of the offered
+    rate is achieved)."""
+    jobs, banks = _serve_jobs(args, inputs)
+    on = _serve_run(args, torch, api, jobs, banks, cache=True)
+    off = _serve_run(args, torch, api, jobs, banks, cache=False)
+    sweep, sustained = [], None
+    for rate in (2.0, 4.0, 8.0, 16.0, 32.0):
+        r = _serve_run(args, torch, api, jobs, banks, slow=args.rate / rate, cache=True, n=40)
+        ok = r["achieved_req_per_s"] >= 0.9 * r["offered_req_per_s"]
+        sweep.append({"offered_req_per_s": r["offered_req_per_s"], "achieved_req_per_s": r["achieved_req_per_s"],
+                      "p50_ms": r["latency_ms"]["p50"], "p99_ms": r["latency_ms"]["p99"], "sustained": ok})
+        if ok:
+            sustained = r["offered_req_per_s"]
+    out = {"metric": "serve voxel-iter/s, p50/p99 latency", "unit": "voxel-iter/s",
+           "config": {"workload": f"poisson_{args.rate:g}hz_{args.requests}req (N 256..2048, M=K 3/5/10, TV/DCT, "
+                                  "tol 1e-4, max 300 iterations)", "max_active": args.max_active}}
+    out.update(on)
+    out["factor_cache_off"] = {k: off[k] for k in ("value", "latency_ms", "achieved_req_per_s", "makespan_s")}
+    out["rate_sweep"] = sweep
+    out["highest_sustained_req_per_s"] = sustained
+    return out
 
 
 def workload_precision(args, torch, api, inputs):
@@ -588,7 +644,8 @@ def main():
             "peak_source": "measured" if pk else "fallback",
             "avg_launch_us": {"column_pass": round(avgB * 1e3, 2), "prior_pass": round(avgA * 1e3, 2)},
             "algorithmic_bytes": ab,
-            "phases_ms": {k: round(v, 3) for k, v in ph.items()}}
+            "phases_ms": {k: round(v, 3) for k, v in ph.items()},
+            "peak_spec_gbs": 7900.0, "frac_of_spec": round(achieved / 7900.0, 4)}
 
     line = {"metric": METRIC, "value": value, "unit": "voxel-iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -600,6 +657,8 @@ def main():
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "voxel-iter/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_total / args.steps},
+            "iterations_only": {"value": prob.voxels * ITERS / (ph["iterations"] / 1e3), "unit": "voxel-iter/s",
+                                "note": "iterations phase alone (setup excluded), from the per-kernel timing pass"},
             "gpu_launches": int(launches) * args.steps,
             "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
