@@ -501,6 +501,69 @@ def run_convdict(C: ConvDictSetup, iters: int, keep_history: bool = False):
     return x, z, t, u, hist
 
 
+# ---------------------------------------------------------------------------
+# Online convolutional dictionary update (Section IV-B "Convolutional dictionary update",
+# Eqs. set, Constrained2, d_admm, g_admm, h_admm, sold_3D; 2D filters shared by the slices)
+# ---------------------------------------------------------------------------
+def crop_filters(v: np.ndarray, P: int) -> np.ndarray:
+    """Q^T: the P x P support (centre at P//2, placed at the origin of the torus) of [L, N, N] maps."""
+    N = v.shape[-1]
+    idx = (np.arange(P) - P // 2) % N
+    return v[:, idx][:, :, idx]
+
+
+def project_filters(v: np.ndarray, P: int) -> np.ndarray:
+    """Solution of Eq. g_admm: Q Q^T v / ||Q^T v|| per filter (support constraint and unit norm)."""
+    L, N, _ = v.shape
+    c = crop_filters(v, P)
+    n = np.sqrt(np.sum(c * c, axis=(1, 2)))
+    return embed_filters(c / n[:, None, None], N)
+
+
+def dict_update(x: np.ndarray, z: np.ndarray, g: np.ndarray, e: np.ndarray, sigma: float, P: int):
+    """One step of the filter ADMM (Eqs. d_admm, g_admm, h_admm): d solves the normal equation of
+    Eq. sold_3D summed over the slices, per frequency
+        (sigma I + sum_s conj(zhat_s) zhat_s^T) dhat = sum_s conj(zhat_s) xhat_s + sigma F(g - e),
+    then g = projection of d + e onto the constraint set (Eq. set) and e <- e + d - g (readings
+    R21-R23).  x [S, N, N], z [L, S, N, N], g, e [L, N, N]."""
+    L, S, N, _ = z.shape
+    Zh = dft2(z)
+    Xh = dft2(x)
+    GE = dft2(g - e)
+    dh = np.empty((L, N, N), dtype=complex)
+    for a in range(N):
+        for b in range(N):
+            zs = Zh[:, :, a, b]                                   # [L, S]
+            A = sigma * np.eye(L) + zs.conj() @ zs.T
+            rhs = zs.conj() @ Xh[:, a, b] + sigma * GE[:, a, b]
+            dh[:, a, b] = np.linalg.solve(A, rhs)
+    d = idft2(dh).real
+    g_new = project_filters(d + e, P)
+    return d, g_new, e + d - g_new
+
+
+def run_convdict_learn(h: np.ndarray, y: np.ndarray, d0: np.ndarray, lam: float, rho: float, beta: float,
+                       sigma: float, iters: int):
+    """Alg. 2 with the online dictionary update after every iteration (reading R21): the x-, z-,
+    t- and u-updates use the current filters g, then one filter-ADMM step updates (d, g, e) from
+    the new x and z.  From z = t = u = 0, g = the given unit-norm filters, e = 0.  Returns
+    (x, z, t, u, filters [L, P, P])."""
+    P = d0.shape[-1]
+    C = convdict_setup(h, y, d0, lam, rho, beta)
+    g = embed_filters(d0, C.N)
+    e = np.zeros_like(g)
+    z = np.zeros((C.L, C.M, C.N, C.N))
+    t = np.zeros_like(z)
+    u = np.zeros_like(z)
+    x = None
+    for _ in range(iters):
+        C.theta = dft2(g)
+        x, z, t_new, u = convdict_step(C, z, t, u)
+        t = t_new
+        _, g, e = dict_update(x, z, g, e, sigma, P)
+    return x, z, t, u, crop_filters(g, P)
+
+
 def convdict_objective(x, z, d, h, y, lam, beta) -> float:
     """beta/2 ||y - Hx||^2 + 1/2 ||sum_l d_l (*) z_l - x||^2 + lambda ||z||_1 (reading R9)."""
     N = x.shape[-1]

@@ -210,6 +210,39 @@ def run_convdict_adaptive(h, y, d, lam, rho, beta, iters: int, check_every: int,
     return x, z, t, u, rhos
 
 
+def dict_update(x, z, g, e, sigma: float, P: int):
+    """Same filter-ADMM step as oracle.admm.dict_update on the half spectrum (batched solves)."""
+    N = x.shape[-1]
+    Zh = np.moveaxis(rfft2(z), (0, 1), (2, 3))                  # [N, H, L, S]
+    Xh = np.moveaxis(rfft2(x), 0, 2)                            # [N, H, S]
+    GE = np.moveaxis(rfft2(g - e), 0, 2)                        # [N, H, L]
+    L = Zh.shape[2]
+    A = sigma * np.eye(L) + np.einsum("abls,abks->ablk", Zh.conj(), Zh)
+    rhs = np.einsum("abls,abs->abl", Zh.conj(), Xh) + sigma * GE
+    dh = np.linalg.solve(A, rhs[..., None])[..., 0]
+    d = irfft2(np.moveaxis(dh, 2, 0), N)
+    g_new = ref.project_filters(d + e, P)
+    return d, g_new, e + d - g_new
+
+
+def run_convdict_learn(h, y, d0, lam, rho, beta, sigma: float, iters: int):
+    """Same schedule as oracle.admm.run_convdict_learn.  Returns (x, z, t, u, filters [L, P, P])."""
+    P = d0.shape[-1]
+    C = convdict_setup(h, y, d0, lam, rho, beta)
+    N = C.N
+    g = ref.embed_filters(d0, N)
+    e = np.zeros_like(g)
+    z = np.zeros((C.L, C.M, N, N))
+    t = np.zeros_like(z)
+    u = np.zeros_like(z)
+    x = None
+    for _ in range(iters):
+        C.theta = np.moveaxis(rfft2(g), 0, 2)
+        x, z, t, u = convdict_step(C, z, t, u)
+        _, g, e = dict_update(x, z, g, e, sigma, P)
+    return x, z, t, u, ref.crop_filters(g, P)
+
+
 def run_convdict(C: FastConvDict, iters: int):
     z = np.zeros((C.L, C.M, C.N, C.N))
     t = np.zeros_like(z)

@@ -507,3 +507,51 @@ def test_convdict_adaptive_keeps_the_unscaled_multiplier(cd8):
     assert rel(x6, xs) < 1e-12 and rel(z6, zs) < 1e-12 and rel(u6, us) < 1e-12
     _, _, _, u_fix = fast.run_convdict(fast.convdict_setup(cd8["h"], cd8["y"], cd8["d"], C0.lam, 50.0, C0.beta), 5)
     assert rel(rhos[-1] * u5, 50.0 * u_fix) < 1e-12
+
+
+# ----------------------------------------------------------------- online dictionary update
+def test_filter_projection_is_the_nearest_feasible_point():
+    """Eq. g_admm: Q Q^T v / ||Q^T v|| has the P x P support, unit norm, and is at least as close to v
+    as any other unit-norm filter on the support (checked against random ones)."""
+    rng = np.random.default_rng(4)
+    N, L, P = 12, 3, 5
+    v = rng.standard_normal((L, N, N))
+    g = admm.project_filters(v, P)
+    mask = admm.embed_filters(np.ones((1, P, P)), N)[0] != 0
+    assert np.all(g[:, ~mask] == 0)
+    assert np.allclose(np.sqrt(np.sum(g * g, axis=(1, 2))), 1.0)
+    for l in range(L):
+        best = np.sum((g[l] - v[l]) ** 2)
+        for _ in range(200):
+            c = rng.standard_normal((P, P))
+            c = admm.embed_filters((c / np.linalg.norm(c))[None], N)[0]
+            assert best <= np.sum((c - v[l]) ** 2) + 1e-12
+
+
+def test_filter_update_equals_dense_least_squares():
+    """Eq. d_admm summed over the slices (Eq. sold_3D in 2D) solved densely: the stacked system
+    [Z; sqrt(sigma) I] d = [x; sqrt(sigma)(g - e)] with Z the explicit convolution operator of the
+    codes matches the oracle's per-frequency solve."""
+    rng = np.random.default_rng(6)
+    N, L, S, P, sigma = 6, 2, 2, 3, 1.7
+    z = rng.standard_normal((L, S, N, N))
+    x = rng.standard_normal((S, N, N))
+    g = rng.standard_normal((L, N, N))
+    e = rng.standard_normal((L, N, N))
+    Zop = lambda dd: np.stack([sum(admm.circconv2(z[l, s], dd[l]) for l in range(L)) for s in range(S)])
+    Zd = dense_operator(Zop, (L, N, N))
+    A = np.concatenate([Zd, math.sqrt(sigma) * np.eye(L * N * N)])
+    b = np.concatenate([x.ravel(), math.sqrt(sigma) * (g - e).ravel()])
+    d_ls = np.linalg.lstsq(A, b, rcond=None)[0].reshape(L, N, N)
+    d, g_new, e_new = admm.dict_update(x, z, g, e, sigma, P)
+    assert rel(d, d_ls) < 1e-10
+    assert np.allclose(e_new, e + d - g_new, atol=0)
+
+
+def test_fast_learning_matches_naive(cd8):
+    C = cd8["C"]
+    args = (cd8["h"], cd8["y"], cd8["d"], C.lam, C.rho, C.beta, 2.0, 5)
+    xn, zn, tn, un, fn = admm.run_convdict_learn(*args)
+    xf, zf, tf, uf, ff = fast.run_convdict_learn(*args)
+    assert rel(xf, xn) < 1e-10 and rel(ff, fn) < 1e-10
+    assert rel(fn, cd8["d"] / np.linalg.norm(cd8["d"].reshape(cd8["L"], -1), axis=1)[:, None, None]) > 1e-3
