@@ -188,7 +188,7 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
-# Other workloads (not the default line): --workload convdict | batch | serve | precision
+# Other workloads (not the default line): --workload convdict | dictlearn | batch | serve | precision
 # ---------------------------------------------------------------------------
 def _ev_time(torch, fn, reps=1):
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -241,6 +241,71 @@ def workload_convdict(args, torch, api, inputs):
             "kernels": {"column_pass_us": 1e3 * avgB, "column_pass_GBps": col_bytes / avgB / 1e6,
                         "prior_pass_us": 1e3 * avgA, "prior_pass_GBps": pri_bytes / avgA / 1e6,
                         "algorithmic_bytes": {"column_pass": col_bytes, "prior_pass": pri_bytes}}}
+
+
+def workload_dictlearn(args, torch, api, inputs):
+    """The convdict workload (256 x 256 x 5, 32 Gabor 11 x 11 filters, 300 iterations) with the
+    online dictionary update on (Section IV-B, sigma = 10): every iteration adds one filter-ADMM
+    step.  The step is setup + iterations + read-back of x and the 32 learnt filters; the same
+    run with the update off is timed beside it, and the difference per iteration is the update's
+    cost.  The CPU leg is the FP64 oracle on 3 iterations of the same problem."""
+    from oracle import fast
+    pr = inputs.convdict_problem()
+    sigma = 10.0
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+    h, y, d = f(pr.h), f(pr.y), f(pr.filters)
+    L, P = pr.filters.shape[0], pr.filters.shape[-1]
+    x = torch.empty((pr.M, pr.N, pr.N), device="cuda")
+    filt = torch.empty((L, P, P), device="cuda")
+
+    def make(learn):
+        plan = api.Plan(pr.N, pr.K, pr.M, "f32")
+        plan.set_prior("convdict", pr.lam, pr.rho, pr.beta)
+        plan.set_dictionary(d)
+        if learn:
+            plan.set_dictionary_learning(sigma)
+        plan.set_psfs(h)
+
+        def step():
+            if learn:
+                plan.set_dictionary(d)  # start every step from the same filters
+                plan.set_dictionary_learning(sigma)
+            plan.set_measurements(y)
+            plan.iterate(pr.iters)
+            plan.get_x(x)
+            if learn:
+                plan.get_dictionary(filt)
+        return plan, step
+
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")
+    out = {}
+    for learn in (True, False):
+        plan, step = make(learn)
+        for _ in range(args.warmup):
+            step()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            ts.append(_ev_time(torch, step))
+        plan.close()
+        out[learn] = sum(ts) / len(ts)
+    t = out[True]
+    upd_s = (out[True] - out[False]) / pr.iters
+    S, bins = L * pr.M, pr.N * (pr.N // 2 + 1)
+    # a fused update's least traffic per iteration: read z-hat, x-hat, g, e; write g, e, theta, p
+    upd_bytes = (S + 2 * pr.M + L) * bins * 8 + 4 * L * pr.N * pr.N * 4
+    t0 = time.perf_counter()
+    fast.run_convdict_learn(pr.h, pr.y, pr.filters, pr.lam, pr.rho, pr.beta, sigma, 3)
+    tc = time.perf_counter() - t0
+    return {"metric": METRIC, "value": pr.voxels * pr.iters / t, "unit": "voxel-iter/s", "ms_per_step": 1e3 * t,
+            "config": {"workload": f"dictlearn_{pr.N}x{pr.N}x{pr.M}_L{L} (11x11 Gabor start, 25 dB, lambda=0.15, "
+                                   f"beta=4, rho=8, sigma={sigma:g}, {pr.iters} iterations)",
+                       "step": "setup + iterations with the filter update + read-back of x and filters"},
+            "without_update_ms_per_step": 1e3 * out[False],
+            "update": {"us_per_iteration": 1e6 * upd_s, "least_bytes": upd_bytes,
+                       "GBps_on_least_bytes": upd_bytes / upd_s / 1e9 if upd_s > 0 else None},
+            "cpu_baseline": {"value": pr.voxels * 3 / tc, "unit": "voxel-iter/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "3 iterations of the same problem, FP64 scipy.fft"}}
 
 
 def workload_batch(args, torch, api, inputs):
@@ -492,7 +557,7 @@ def run_workload(args):
     import torch
     from paper_2006_08303_gb300 import api, inputs
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    fn = {"convdict": workload_convdict, "batch": workload_batch, "serve": workload_serve,
+    fn = {"convdict": workload_convdict, "dictlearn": workload_dictlearn, "batch": workload_batch, "serve": workload_serve,
           "precision": workload_precision, "single": workload_single,
           "adaptive": workload_adaptive}[args.workload]
     line = fn(args, torch, api, inputs)
@@ -510,7 +575,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=10, help="iterations per oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="spectral_dct",
-                    choices=["spectral_dct", "convdict", "batch", "serve", "precision", "single", "adaptive"])
+                    choices=["spectral_dct", "convdict", "dictlearn", "batch", "serve", "precision", "single",
+                             "adaptive"])
     ap.add_argument("--N", type=int, default=1024, help="single: image side")
     ap.add_argument("--M", type=int, default=10, help="single: channels (= measurements)")
     ap.add_argument("--prior", default="tv", choices=["tv", "tv_iso", "dct8", "l1"], help="single: prior")

@@ -143,6 +143,27 @@ cip_status cip_set_dictionary(cip_plan* plan, const void* filters, int L, int P,
  * state are unchanged.  CIP_ERR_STATE for other priors. */
 cip_status cip_set_code_gradient_weight(cip_plan* plan, double mu);
 
+/* Online convolutional dictionary update (Section IV-B, Eqs. d_admm, g_admm, h_admm with the
+ * sum over channels of Eq. sold_3D) for a CIP_PRIOR_CONVDICT plan; call after
+ * cip_set_dictionary.  sigma > 0 turns it on: the filters start as those given to
+ * cip_set_dictionary (g = d, scaled dual e = 0, both N x N planes) and after the z-update of
+ * every iteration one step of the filter ADMM runs on that iteration's x and z:
+ *   d-hat(w) = (sigma I + Z(w)^H Z(w))^{-1} (Z(w)^H x-hat(w) + sigma F(g - e)(w)),
+ *   g = (d + e) restricted to the P x P support, scaled to unit Frobenius norm,
+ *   e <- e + d - g,
+ * Z(w) the M x L matrix of code spectra; the next iteration uses theta = F g.  The filters
+ * persist across cip_set_measurements and cip_reset; cip_set_dictionary starts them again.
+ * sigma = 0 turns the update off (the filters learnt so far stay); a new sigma > 0 while on
+ * keeps g and e.  The learnt g and e are part of cip_state_export's buffer while on.
+ * CIP_ERR_STATE without a dictionary, CIP_ERR_UNSUPPORTED for M > 8, CIP_ERR_INVALID_ARG for
+ * sigma < 0 or not finite.  Enqueued on `stream`. */
+cip_status cip_set_dictionary_learning(cip_plan* plan, double sigma, void* stream);
+
+/* Learnt filters g cropped to filters[L][P][P] (plan dtype, centre at index P/2, host or
+ * device pointer; a host copy synchronises `stream`).  CIP_ERR_STATE unless the dictionary
+ * update is on. */
+cip_status cip_get_dictionary(cip_plan* plan, void* filters, void* stream);
+
 /* Coefficient maps z[M][L][N][N] of the last z-update (CIP_PRIOR_CONVDICT only). */
 cip_status cip_get_coefficients(cip_plan* plan, void* z, void* stream);
 

@@ -76,6 +76,8 @@ SIGNATURES = {
     "cip_batch_destroy": (c_int, [c_void_p]),
     "cip_set_dictionary": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "cip_set_code_gradient_weight": (c_int, [c_void_p, c_double]),
+    "cip_set_dictionary_learning": (c_int, [c_void_p, c_double, c_void_p]),
+    "cip_get_dictionary": (c_int, [c_void_p, c_void_p, c_void_p]),
     "cip_set_rho_adaptation": (c_int, [c_void_p, c_double, c_double]),
     "cip_get_rho": (c_int, [c_void_p, P_double]),
     "cip_get_coefficients": (c_int, [c_void_p, c_void_p, c_void_p]),

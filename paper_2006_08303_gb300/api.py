@@ -113,6 +113,7 @@ class Plan:
         p, keep = _ptr_and_check(filters, self.dtype, (L, P, P))
         self._check(self._L.cip_set_dictionary(self._h, ctypes.c_void_p(p), L, P, _stream_ptr(stream)))
         self.L = L
+        self.filter_size = P
 
     def set_rho_adaptation(self, tau: float = 2.0, mu: float = 10.0):
         """Adaptive penalty of Eq. paramS at the residual checks (tau = 0: off); call before
@@ -128,6 +129,21 @@ class Plan:
     def set_code_gradient_weight(self, mu: float):
         """Gradient (Tikhonov) penalty mu on the dictionary codes (cip_set_code_gradient_weight)."""
         self._check(self._L.cip_set_code_gradient_weight(self._h, ctypes.c_double(mu)))
+
+    def set_dictionary_learning(self, sigma: float, stream=None):
+        """Online dictionary update with filter-ADMM penalty sigma (cip_set_dictionary_learning);
+        0 turns it off."""
+        self._check(self._L.cip_set_dictionary_learning(self._h, ctypes.c_double(sigma), _stream_ptr(stream)))
+
+    def get_dictionary(self, out=None, stream=None):
+        """Learnt filters [L, P, P] (cip_get_dictionary)."""
+        shape = (self.L, self.filter_size, self.filter_size)
+        if out is None:
+            torch = _torch()
+            out = torch.empty(shape, device="cuda", dtype=torch.float32 if self.dtype == "f32" else torch.float64)
+        p, keep = _ptr_and_check(out, self.dtype, shape)
+        self._check(self._L.cip_get_dictionary(self._h, ctypes.c_void_p(p), _stream_ptr(stream)))
+        return out
 
     def get_coefficients(self, out=None, stream=None):
         shape = (self.M, self.L, self.N, self.N)

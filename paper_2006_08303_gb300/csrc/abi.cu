@@ -66,6 +66,17 @@ struct cip_plan {
   void* pbuf[2] = {nullptr, nullptr};   // [H][M][CP] p = sum_l theta_l v_l (ping-pong)
   int pcur = 0;
   void* xcol = nullptr;                 // [H][M][CP] x-hat of the last x-update
+  // online dictionary update (Section IV-B): sigma = 0 off.  While on, theta lives in the first L
+  // planes of dl_spec and F(g - e) in the last L (one forward transform makes both).
+  double dl_sigma = 0;
+  int dl_L = 0;             // L the buffers below were sized for
+  void* dl_sp = nullptr;    // real [2L][N][N]: g (filters on the torus, Eq. g_admm), then g - e
+  void* dl_e = nullptr;     // real [L][N][N]: scaled dual of the filter ADMM (Eq. h_admm)
+  void* dl_d = nullptr;     // real [L][N][N]: d of Eq. d_admm
+  void* dl_rows = nullptr;  // [2L][N][P] row spectra scratch
+  void* dl_spec = nullptr;  // [H][2L][CP]: theta = F g, F(g - e)
+  void* dl_col = nullptr;   // [H][L][CP]: d-hat / N^2
+  void* dl_inv = nullptr;   // [L]: 1 / ||Q^T (d + e)|| of the projection
   const cip_plan* factor_src = nullptr;  // plan whose factor this plan adopted (serving factor cache)
   // device buffers
   void* xh = nullptr;
@@ -281,6 +292,33 @@ template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
   return CIP_OK;
 }
 
+// theta as the column solve reads it: the learnt spectra while the dictionary update is on
+const void* theta_of(const cip_plan* p) { return p->dl_sigma > 0 ? p->dl_spec : p->theta; }
+int theta_planes(const cip_plan* p) { return p->dl_sigma > 0 ? 2 * p->L : p->L; }
+
+// buffers of the dictionary update for the plan's current L (allocated once per L)
+cip_status alloc_dict(cip_plan* p) {
+  if (p->dl_sp && p->dl_L == p->L) return CIP_OK;
+  void** bufs[] = {&p->dl_sp, &p->dl_e, &p->dl_d, &p->dl_rows, &p->dl_spec, &p->dl_col, &p->dl_inv};
+  for (void** b : bufs)
+    if (*b) {
+      cudaFreeAsync(*b, p->ast);
+      *b = nullptr;
+    }
+  const size_t ce = 2 * p->esz;
+  CIP_CUDA(p, dmalloc(p, &p->dl_sp, real_elems(p, 2 * p->L) * p->esz));
+  CIP_CUDA(p, dmalloc(p, &p->dl_e, real_elems(p, p->L) * p->esz));
+  CIP_CUDA(p, dmalloc(p, &p->dl_d, real_elems(p, p->L) * p->esz));
+  CIP_CUDA(p, dmalloc(p, &p->dl_rows, half_elems(p, 2 * p->L) * ce));
+  CIP_CUDA(p, dmalloc(p, &p->dl_spec, col_elems(p, 2 * p->L) * ce));
+  CIP_CUDA(p, dmalloc(p, &p->dl_col, col_elems(p, p->L) * ce));
+  CIP_CUDA(p, dmalloc(p, &p->dl_inv, 32 * p->esz));
+  p->dl_L = p->L;
+  return CIP_OK;
+}
+
+template <typename T> cip_status dict_init(cip_plan* p, cudaStream_t s);
+
 // Filters d[L][P][P] (plan dtype): embedded on the N x N torus with their centre at (0,0),
 // DFT in FP64, kept as theta in the plan's precision (Section IV-B, Theta_m of the dictionary).
 template <typename T> cip_status do_set_dictionary(cip_plan* p, const void* d, cudaStream_t s) {
@@ -305,6 +343,12 @@ template <typename T> cip_status do_set_dictionary(cip_plan* p, const void* d, c
   cudaFreeAsync(emb, s);
   cudaFreeAsync(th64, s);
   CIP_CUDA(p, e);
+  if (p->dl_sigma > 0) {
+    st = alloc_dict(p);
+    if (st != CIP_OK) return st;
+    st = dict_init<T>(p, s);
+    if (st != CIP_OK) return st;
+  }
   if (p->have_psfs) {
     st = form_factor<T>(p, s);
     if (st != CIP_OK) return st;
@@ -425,7 +469,8 @@ template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mo
                                        static_cast<const C*>(p->tw), p->N, S, s));
     CDArgs<T> a;
     a.colbuf = static_cast<C*>(p->colbuf);
-    a.theta = static_cast<const C*>(p->theta);
+    a.theta = static_cast<const C*>(theta_of(p));
+    a.th_planes = theta_planes(p);
     a.p_in = static_cast<const C*>(p->pbuf[p->pcur]);
     a.p_out = static_cast<C*>(p->pbuf[p->pcur ^ 1]);
     a.xb = static_cast<const C*>(p->bhat);
@@ -558,6 +603,57 @@ void ensure_events(cip_plan* p) {
   for (auto& e : p->evB) cudaEventCreate(&e);
 }
 
+// forward transform of [g; g - e] into dl_spec: theta and the filter solve's F(g - e)
+template <typename T> cip_status dict_forward(cip_plan* p, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const C* tw = static_cast<const C*>(p->tw);
+  C* rows = static_cast<C*>(p->dl_rows);
+  CIP_LAUNCH(p, (launch_row_r2c<T, T>(static_cast<const T*>(p->dl_sp), rows, p->N, 2 * p->L * p->N, (T)1, tw, s)));
+  CIP_LAUNCH(p, launch_colfft_fwd<T>(rows, static_cast<C*>(p->dl_spec), tw, p->N, 2 * p->L, s));
+  return CIP_OK;
+}
+
+// Online dictionary update: g = F^-1(theta) (the filters on the torus), e = 0, g - e = g.
+template <typename T> cip_status dict_init(cip_plan* p, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const size_t n = real_elems(p, p->L);
+  T* g = static_cast<T*>(p->dl_sp);
+  CIP_LAUNCH(p, launch_colfft_inv<T>(static_cast<const C*>(p->theta), static_cast<C*>(p->dl_rows),
+                                     static_cast<const C*>(p->tw), p->N, p->L, s));
+  CIP_LAUNCH(p, (launch_row_c2r<T, T>(static_cast<const C*>(p->dl_rows), g, p->N, p->L * p->N,
+                                      static_cast<const C*>(p->tw), s)));
+  CIP_LAUNCH(p, launch_scale<T>(g, n, (T)(1.0 / ((double)p->N * p->N)), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->dl_e, 0, n * sizeof(T), s));
+  CIP_CUDA(p, cudaMemcpyAsync(g + n, g, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  return dict_forward<T>(p, s);
+}
+
+// One step of the filter ADMM (Section IV-B) after the column pass, from the x and z of that
+// pass (x-hat in xcol, z-hat in colbuf, both / N^2): d from Eq. d_admm summed over the channels
+// (Eq. sold_3D), g from Eq. g_admm, e from Eq. h_admm; then theta = F g and p = sum_l theta_l z_l
+// formed again, so that the next x-update sees the updated dictionary (reading R21).
+template <typename T> cip_status dict_step(cip_plan* p, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const C* tw = static_cast<const C*>(p->tw);
+  const C* spec = static_cast<const C*>(p->dl_spec);
+  const size_t cp = (size_t)col_pitch(p->N);
+  C* rows = static_cast<C*>(p->dl_rows);
+  C* col = static_cast<C*>(p->dl_col);
+  T* d = static_cast<T*>(p->dl_d);
+  CIP_LAUNCH(p, launch_dl_solve<T>(static_cast<const C*>(p->colbuf), static_cast<const C*>(p->xcol),
+                                   spec + p->L * cp, 2 * p->L, col, p->N, p->M, p->L, p->dl_sigma, s));
+  CIP_LAUNCH(p, launch_colfft_inv<T>(col, rows, tw, p->N, p->L, s));
+  CIP_LAUNCH(p, (launch_row_c2r<T, T>(rows, d, p->N, p->L * p->N, tw, s)));
+  T* inv = static_cast<T*>(p->dl_inv);
+  CIP_LAUNCH(p, launch_dl_norm<T>(d, static_cast<const T*>(p->dl_e), inv, p->L, p->N, p->Pf, s));
+  CIP_LAUNCH(p, launch_dl_project<T>(d, static_cast<T*>(p->dl_e), static_cast<T*>(p->dl_sp), inv, p->L, p->N, p->Pf, s));
+  cip_status st = dict_forward<T>(p, s);
+  if (st != CIP_OK) return st;
+  CIP_LAUNCH(p, launch_p_from_z<T>(static_cast<const C*>(p->colbuf), spec, static_cast<C*>(p->pbuf[p->pcur]), p->N,
+                                   p->M, p->L, s, 1.0, 2 * p->L));
+  return CIP_OK;
+}
+
 // Adaptive penalty: rho -> rho_new after a residual check (readings R17, R18).  The scaled
 // dual is rescaled so that rho u is unchanged, the factor and the data term are formed again
 // for rho_new (the dictionary's factor does not depend on rho), and q of the next x-update is
@@ -603,6 +699,10 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
     cip_status cst = column_pass<T>(p, s, p->colmode, p->cc);
     if (cst != CIP_OK) return cst;
     if (timeB) cudaEventRecord(p->evB[2 * p->nB++ + 1], s);
+    if (p->dl_sigma > 0) {
+      cst = dict_step<T>(p, s);
+      if (cst != CIP_OK) return cst;
+    }
     PassAArgs<T> a = passA_args<T>(p, flags);
     const bool timeA = p->timing && p->nA < kMaxTimed;
     if (timeA) cudaEventRecord(p->evA[2 * p->nA], s);
@@ -653,6 +753,10 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
 template <typename T> cip_status enqueue_iteration(cip_plan* p, cudaStream_t s, int flags) {
   cip_status cst = column_pass<T>(p, s, p->colmode, p->cc);
   if (cst != CIP_OK) return cst;
+  if (p->dl_sigma > 0) {
+    cst = dict_step<T>(p, s);
+    if (cst != CIP_OK) return cst;
+  }
   PassAArgs<T> a = passA_args<T>(p, flags);
   CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
   p->cur ^= 1;
@@ -717,8 +821,8 @@ template <typename T> cip_status import_z(cip_plan* p, const void* z, cudaStream
                                       static_cast<const C*>(p->tw), s)));
   CIP_LAUNCH(p, launch_colfft_fwd<T>(static_cast<const C*>(p->xh), static_cast<C*>(p->colbuf),
                                      static_cast<const C*>(p->tw), p->N, S, s));
-  CIP_LAUNCH(p, launch_p_from_z<T>(static_cast<const C*>(p->colbuf), static_cast<const C*>(p->theta),
-                                   static_cast<C*>(p->pbuf[p->pcur]), p->N, p->M, p->L, s));
+  CIP_LAUNCH(p, launch_p_from_z<T>(static_cast<const C*>(p->colbuf), static_cast<const C*>(theta_of(p)),
+                                   static_cast<C*>(p->pbuf[p->pcur]), p->N, p->M, p->L, s, 0.0, theta_planes(p)));
   return CIP_OK;
 }
 
@@ -898,7 +1002,7 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep,
+  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv,
                   p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
@@ -1011,6 +1115,57 @@ cip_status cip_set_code_gradient_weight(cip_plan* p, double mu) {
   return CIP_OK;
 }
 
+cip_status cip_set_dictionary_learning(cip_plan* p, double sigma, void* stream) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  cip_status r = CIP_OK;
+  if (!is_cd(p) || !p->theta)
+    return fail(p, CIP_ERR_STATE, "dictionary learning needs a CIP_PRIOR_CONVDICT plan after cip_set_dictionary");
+  if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(p, CIP_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+  if (sigma > 0 && p->M > 8) return fail(p, CIP_ERR_UNSUPPORTED, "dictionary learning supports M <= 8 channels");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
+  const size_t ce = 2 * p->esz;
+  if (sigma == 0.0) {
+    if (p->dl_sigma > 0) {  // the learnt theta becomes the plan's dictionary
+      const size_t w = (size_t)p->L * col_pitch(p->N) * ce;
+      CIP_CUDA(p, cudaMemcpy2DAsync(p->theta, w, p->dl_spec, 2 * w, w, p->N / 2 + 1, cudaMemcpyDeviceToDevice, s));
+    }
+    p->dl_sigma = 0.0;
+    return CIP_OK;
+  }
+  r = alloc_dict(p);
+  if (r != CIP_OK) return r;
+  const bool was_on = p->dl_sigma > 0;
+  p->dl_sigma = sigma;
+  if (was_on) return CIP_OK;  // a new sigma keeps the filters learnt so far
+  return DISPATCH_T(p, dict_init<float>(p, s), dict_init<double>(p, s));
+}
+
+cip_status cip_get_dictionary(cip_plan* p, void* filters, void* stream) {
+  if (!p || !filters) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  if (!is_cd(p) || !(p->dl_sigma > 0))
+    return fail(p, CIP_ERR_STATE, "the filters change only with cip_set_dictionary_learning on");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
+  const size_t bytes = (size_t)p->L * p->Pf * p->Pf * p->esz;
+  const bool dev = is_device_ptr(filters);
+  void* out = filters;
+  if (!dev) CIP_CUDA(p, cudaMallocAsync(&out, bytes, s));
+  cudaError_t e = p->dtype == CIP_F32
+                      ? launch_dl_crop<float>(static_cast<const float*>(p->dl_sp), static_cast<float*>(out), p->L,
+                                              p->N, p->Pf, s)
+                      : launch_dl_crop<double>(static_cast<const double*>(p->dl_sp), static_cast<double*>(out), p->L,
+                                               p->N, p->Pf, s);
+  if (e == cudaSuccess) p->launches++;
+  if (!dev) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(filters, out, bytes, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  CIP_CUDA(p, e);
+  return CIP_OK;
+}
+
 cip_status cip_set_rho_adaptation(cip_plan* p, double tau, double mu) {
   if (!p) return CIP_ERR_INVALID_ARG;
   if (tau == 0.0) {
@@ -1091,6 +1246,11 @@ static std::vector<std::pair<void*, size_t>> state_segments(cip_plan* p) {
   if (is_cd(p)) {
     seg.push_back({p->pbuf[p->pcur], col_elems(p, p->M) * 2 * p->esz});
     seg.push_back({p->xcol, col_elems(p, p->M) * 2 * p->esz});
+  }
+  if (p->dl_sigma > 0) {  // the dictionary being learnt is part of the state
+    seg.push_back({p->dl_spec, col_elems(p, 2 * p->L) * 2 * p->esz});
+    seg.push_back({p->dl_sp, real_elems(p, 2 * p->L) * p->esz});
+    seg.push_back({p->dl_e, real_elems(p, p->L) * p->esz});
   }
   return seg;
 }

@@ -12,6 +12,8 @@
 // channel are contiguous planes in the column layout [k2][m*L + l][k1].  The
 // column DFTs around it and the element-wise shrinkage on the coefficient
 // maps (the l1 prior pass over L*M maps) are the analysis path's kernels.
+#include <algorithm>
+
 #include "fft.cuh"
 #include "kernels.h"
 
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(128) cd_solve_kernel(CDArgs<T> a) {
   a.xcol[((size_t)k2 * M + m) * CP + k1] = x;
   // c_l = conj(theta_l) x + G_l ; s = theta^T c ; nrm = ||theta||^2
   C* g = a.colbuf + ((size_t)k2 * M * L + (size_t)m * L) * CP + k1;
-  const C* th = a.theta + (size_t)k2 * L * CP + k1;
+  const C* th = a.theta + (size_t)k2 * a.th_planes * CP + k1;
   C c[LMAX];
   C s = mk<C>(0.0, 0.0);
   T nrm = T(0);
@@ -120,30 +122,288 @@ __global__ void theta_store_kernel(const SetupC<T>* __restrict__ th64, typename 
 // p_m = sum_l theta_l Z_{m,l} / N^2 from the column spectra Z of imported coefficient maps
 template <typename T>
 __global__ void p_from_z_kernel(const typename CT<T>::type* __restrict__ zcol, const typename CT<T>::type* __restrict__ th,
-                                typename CT<T>::type* __restrict__ p, int N, int M, int L) {
+                                typename CT<T>::type* __restrict__ p, int N, int M, int L, int thp, T s) {
   using C = typename CT<T>::type;
   const int CP = col_pitch(N);
   const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int k2 = blockIdx.y, m = blockIdx.z;
   if (k1 >= N) return;
-  const T s = T(1) / ((T)N * (T)N);
   C acc = mk<C>(0.0, 0.0);
   for (int l = 0; l < L; ++l)
-    cfma(acc, th[((size_t)k2 * L + l) * CP + k1], zcol[((size_t)k2 * M * L + (size_t)m * L + l) * CP + k1]);
+    cfma(acc, th[((size_t)k2 * thp + l) * CP + k1], zcol[((size_t)k2 * M * L + (size_t)m * L + l) * CP + k1]);
   p[((size_t)k2 * M + m) * CP + k1] = mk<C>(acc.x * s, acc.y * s);
+}
+
+// ---- online dictionary update (Section IV-B, Eqs. d_admm, g_admm, h_admm, sold_3D) ----------
+
+// Per frequency, one warp, lane l = filter l: the filter normal equation summed over the S
+// channels,  (sigma I + W W^H) d = b,  W = [conj(zhat_{.,s})]_s (L x S),  b = W xhat + sigma F(g - e),
+// by the Woodbury identity d = (b - W alpha) / sigma with (sigma I_S + W^H W) alpha = W^H b, the
+// S x S system solved by Cholesky on every lane (W^H W and W^H b are warp reductions).  zcol holds
+// the code spectra and xcol the image spectra scaled by 1/N^2 (the column solve's convention);
+// ge holds F(g - e) (plane stride gep per bin); dcol receives d-hat / N^2 (so that an
+// unnormalised inverse gives d).
+template <typename T, int SMAX>
+__global__ void __launch_bounds__(128) dl_solve_kernel(const typename CT<T>::type* __restrict__ zcol,
+                                                       const typename CT<T>::type* __restrict__ xcol,
+                                                       const typename CT<T>::type* __restrict__ gecol, int gep,
+                                                       typename CT<T>::type* __restrict__ dcol, int N, int M, int L,
+                                                       T sigma) {
+  using C = typename CT<T>::type;
+  const int H = N / 2 + 1, CP = col_pitch(N);
+  const int lane = threadIdx.x & 31;
+  const long long bin = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (bin >= (long long)N * H) return;  // whole warps leave together
+  const int k2 = (int)(bin / N), k1 = (int)(bin - (long long)k2 * N);
+  const T n2 = (T)N * (T)N;
+  const bool on = lane < L;
+  C z[SMAX];
+  C b = mk<C>(0.0, 0.0);
+  if (on) {
+    const C ge = gecol[((size_t)k2 * gep + lane) * CP + k1];
+    b = mk<C>(sigma * ge.x, sigma * ge.y);
+  }
+#pragma unroll
+  for (int s = 0; s < SMAX; ++s) {
+    z[s] = mk<C>(0.0, 0.0);
+    if (s < M) {
+      C xs = xcol[((size_t)k2 * M + s) * CP + k1];
+      xs.x *= n2;
+      xs.y *= n2;
+      if (on) {
+        C zz = zcol[((size_t)k2 * M * L + (size_t)s * L + lane) * CP + k1];
+        zz.x *= n2;
+        zz.y *= n2;
+        z[s] = zz;
+        cfmac(b, zz, xs);  // b += conj(z) x
+      }
+    }
+  }
+  // G = W^H W (G_{s s'} = sum_l z_{l s} conj(z_{l s'})), c = W^H b = sum_l z_{l s} b_l
+  C G[SMAX][SMAX], c[SMAX];
+#pragma unroll
+  for (int s = 0; s < SMAX; ++s) {
+    if (s < M) {
+      C v = mk<C>(0.0, 0.0);
+      cfma(v, z[s], b);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      c[s] = v;
+#pragma unroll
+      for (int t = 0; t <= s; ++t) {
+        C w = mk<C>(0.0, 0.0);
+        cfmac(w, z[t], z[s]);  // conj(z_t) z_s summed over l -> G_{s t}
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+          w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+        }
+        G[s][t] = w;
+      }
+      G[s][s].x += sigma;
+      G[s][s].y = T(0);
+    }
+  }
+  // Cholesky G = R R^H (lower), then forward and back substitution for alpha
+#pragma unroll
+  for (int j = 0; j < SMAX; ++j) {
+    if (j < M) {
+      T d = G[j][j].x;
+#pragma unroll
+      for (int k = 0; k < j; ++k) d -= G[j][k].x * G[j][k].x + G[j][k].y * G[j][k].y;
+      const T r = sqrt(d > T(0) ? d : T(0)), inv = r > T(0) ? T(1) / r : T(0);
+      G[j][j] = mk<C>(r, 0.0);
+#pragma unroll
+      for (int i = j + 1; i < SMAX; ++i) {
+        if (i < M) {
+          C acc = G[i][j];
+#pragma unroll
+          for (int k = 0; k < j; ++k) {
+            // acc -= G_ik conj(G_jk)
+            const C a = G[i][k], bb = G[j][k];
+            acc.x -= a.x * bb.x + a.y * bb.y;
+            acc.y -= a.y * bb.x - a.x * bb.y;
+          }
+          G[i][j] = mk<C>(acc.x * inv, acc.y * inv);
+        }
+      }
+    }
+  }
+  C w[SMAX];
+#pragma unroll
+  for (int i = 0; i < SMAX; ++i) {  // R w = c
+    if (i < M) {
+      C acc = c[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) {
+        acc.x -= G[i][k].x * w[k].x - G[i][k].y * w[k].y;
+        acc.y -= G[i][k].x * w[k].y + G[i][k].y * w[k].x;
+      }
+      const T inv = T(1) / G[i][i].x;
+      w[i] = mk<C>(acc.x * inv, acc.y * inv);
+    }
+  }
+  C al[SMAX];
+#pragma unroll
+  for (int i = SMAX - 1; i >= 0; --i) {  // R^H alpha = w
+    if (i < M) {
+      C acc = w[i];
+#pragma unroll
+      for (int k = i + 1; k < SMAX; ++k) {
+        if (k < M) {
+          // acc -= conj(G_ki) alpha_k
+          acc.x -= G[k][i].x * al[k].x + G[k][i].y * al[k].y;
+          acc.y -= G[k][i].x * al[k].y - G[k][i].y * al[k].x;
+        }
+      }
+      const T inv = T(1) / G[i][i].x;
+      al[i] = mk<C>(acc.x * inv, acc.y * inv);
+    }
+  }
+  if (on) {
+    C d = b;
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      if (s < M) {
+        // d -= conj(z_s) alpha_s
+        d.x -= z[s].x * al[s].x + z[s].y * al[s].y;
+        d.y -= z[s].x * al[s].y - z[s].y * al[s].x;
+      }
+    }
+    const T sc = T(1) / (sigma * n2);
+    dcol[((size_t)k2 * L + lane) * CP + k1] = mk<C>(d.x * sc, d.y * sc);
+  }
+}
+
+// 1 / ||Q^T (d + e)|| per filter l = blockIdx.x (0 for a zero filter), formed before any block
+// of the projection writes e.
+template <typename T>
+__global__ void __launch_bounds__(256) dl_norm_kernel(const T* __restrict__ d, const T* __restrict__ e,
+                                                      T* __restrict__ inv, int N, int P) {
+  __shared__ double red[8];
+  const int l = blockIdx.x;
+  const size_t plane = (size_t)N * N;
+  const T* dl = d + (size_t)l * plane;
+  const T* el = e + (size_t)l * plane;
+  const int c = P / 2;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+    const int a = ((i / P - c) % N + N) % N, b = ((i % P - c) % N + N) % N;
+    const size_t k = (size_t)a * N + b;
+    const double v = (double)dl[k] + (double)el[k];
+    acc += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    inv[l] = tot > 0.0 ? (T)(1.0 / sqrt(tot)) : T(0);
+  }
+}
+
+// Eq. g_admm and Eq. h_admm (reading R22) for filter l = blockIdx.x over the chunk blockIdx.y of
+// its N x N plane: g = Q Q^T (d + e) * inv_l, e <- e + d - g, and g - e for the next filter
+// solve.  gs holds [g planes][g - e planes] (L each).
+template <typename T>
+__global__ void __launch_bounds__(256) dl_project_kernel(const T* __restrict__ d, T* __restrict__ e,
+                                                         T* __restrict__ gs, const T* __restrict__ inv, int L, int N,
+                                                         int P) {
+  const int l = blockIdx.x;
+  const size_t plane = (size_t)N * N;
+  const T* dl = d + (size_t)l * plane;
+  T* el = e + (size_t)l * plane;
+  T* gl = gs + (size_t)l * plane;
+  T* ql = gs + ((size_t)L + l) * plane;
+  const int c = P / 2;
+  const T s = inv[l];
+  const size_t chunk = (plane + gridDim.y - 1) / gridDim.y;
+  const size_t k0 = (size_t)blockIdx.y * chunk, k1 = min(plane, k0 + chunk);
+  for (size_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const int a = (int)(k / N), b = (int)(k - (size_t)a * N);
+    const int ia = (a + c) % N, ib = (b + c) % N;  // position inside the P x P support if < P
+    const bool in = ia < P && ib < P;
+    const T v = dl[k] + el[k];
+    const T gn = in ? v * s : T(0);
+    const T en = v - gn;
+    gl[k] = gn;
+    el[k] = en;
+    ql[k] = gn - en;
+  }
+}
+
+// filters [L][P][P] (centre P/2) cropped from the N x N planes g
+template <typename T>
+__global__ void dl_crop_kernel(const T* __restrict__ g, T* __restrict__ out, int L, int N, int P) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L * P * P) return;
+  const int l = idx / (P * P), r = idx - l * P * P;
+  const int i = r / P, j = r - i * P;
+  const int c = P / 2;
+  const int a = ((i - c) % N + N) % N, b = ((j - c) % N + N) % N;
+  out[idx] = g[((size_t)l * N + a) * N + b];
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_p_from_z(const typename CT<T>::type* zcol, const typename CT<T>::type* th,
-                            typename CT<T>::type* p, int N, int M, int L, cudaStream_t s) {
-  dim3 grid((N + 127) / 128, N / 2 + 1, M);
-  p_from_z_kernel<T><<<grid, 128, 0, s>>>(zcol, th, p, N, M, L);
+cudaError_t launch_dl_solve(const typename CT<T>::type* zcol, const typename CT<T>::type* xcol,
+                            const typename CT<T>::type* gecol, int gep, typename CT<T>::type* dcol, int N, int M,
+                            int L, double sigma, cudaStream_t s) {
+  if (L > 32) return cudaErrorInvalidValue;
+  const long long bins = (long long)N * (N / 2 + 1);
+  const dim3 grid((unsigned)((bins + 3) / 4)), block(128);
+  if (M <= 4) dl_solve_kernel<T, 4><<<grid, block, 0, s>>>(zcol, xcol, gecol, gep, dcol, N, M, L, (T)sigma);
+  else if (M <= 8) dl_solve_kernel<T, 8><<<grid, block, 0, s>>>(zcol, xcol, gecol, gep, dcol, N, M, L, (T)sigma);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
-template cudaError_t launch_p_from_z<float>(const float2*, const float2*, float2*, int, int, int, cudaStream_t);
-template cudaError_t launch_p_from_z<double>(const double2*, const double2*, double2*, int, int, int, cudaStream_t);
+template <typename T> cudaError_t launch_dl_norm(const T* d, const T* e, T* inv, int L, int N, int P, cudaStream_t s) {
+  dl_norm_kernel<T><<<L, 256, 0, s>>>(d, e, inv, N, P);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_dl_project(const T* d, T* e, T* gs, const T* inv, int L, int N, int P, cudaStream_t s) {
+  const size_t plane = (size_t)N * N;
+  const unsigned chunks = (unsigned)std::min<size_t>(64, std::max<size_t>(1, plane / 2048));
+  dl_project_kernel<T><<<dim3(L, chunks), 256, 0, s>>>(d, e, gs, inv, L, N, P);
+  return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_dl_crop(const T* g, T* out, int L, int N, int P, cudaStream_t s) {
+  const int n = L * P * P;
+  dl_crop_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(g, out, L, N, P);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dl_solve<float>(const float2*, const float2*, const float2*, int, float2*, int, int, int,
+                                            double, cudaStream_t);
+template cudaError_t launch_dl_solve<double>(const double2*, const double2*, const double2*, int, double2*, int, int,
+                                             int, double, cudaStream_t);
+template cudaError_t launch_dl_norm<float>(const float*, const float*, float*, int, int, int, cudaStream_t);
+template cudaError_t launch_dl_norm<double>(const double*, const double*, double*, int, int, int, cudaStream_t);
+template cudaError_t launch_dl_project<float>(const float*, float*, float*, const float*, int, int, int, cudaStream_t);
+template cudaError_t launch_dl_project<double>(const double*, double*, double*, const double*, int, int, int,
+                                               cudaStream_t);
+template cudaError_t launch_dl_crop<float>(const float*, float*, int, int, int, cudaStream_t);
+template cudaError_t launch_dl_crop<double>(const double*, double*, int, int, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_p_from_z(const typename CT<T>::type* zcol, const typename CT<T>::type* th,
+                            typename CT<T>::type* p, int N, int M, int L, cudaStream_t s, double scale,
+                            int th_planes) {
+  dim3 grid((N + 127) / 128, N / 2 + 1, M);
+  const T sc = scale > 0 ? (T)scale : T(1) / ((T)N * (T)N);
+  p_from_z_kernel<T><<<grid, 128, 0, s>>>(zcol, th, p, N, M, L, th_planes > 0 ? th_planes : L, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_p_from_z<float>(const float2*, const float2*, float2*, int, int, int, cudaStream_t,
+                                            double, int);
+template cudaError_t launch_p_from_z<double>(const double2*, const double2*, double2*, int, int, int, cudaStream_t,
+                                             double, int);
 
 template <typename T> cudaError_t launch_cd_solve(const CDArgs<T>& a, cudaStream_t s) {
   dim3 grid((a.N + 127) / 128, a.N / 2 + 1, a.M);

@@ -62,7 +62,7 @@ cudaError_t launch_rhs_fp32(const cdf* lam, const cdf* yhat, int K, int M, int N
 template <typename T> struct CDArgs {
   using C = typename CT<T>::type;
   C* colbuf;       // [H][M*L]: in G = col-DFT of rho (t - u) / N^2, out v (channel-major, m*L + l)
-  const C* theta;  // [H][L]: DFT of the embedded filters
+  const C* theta;  // [H][th_planes]: DFT of the embedded filters in the first L planes of each bin
   const C* p_in;   // [H][M]: p = sum_l theta_l v_l of the previous iteration (scaled 1/N^2)
   C* p_out;        // [H][M]
   const C* xb;     // [H][M]: Psi^{-1} beta Lambda^H F y / N^2
@@ -70,6 +70,7 @@ template <typename T> struct CDArgs {
   C* xcol;         // [H][M]: x-hat / N^2 (for read-back)
   const double* gs;  // [N] 4 sin^2(pi k / N): per-axis eigenvalues of the circular difference
   int N, M, L;
+  int th_planes;   // planes per bin in theta's buffer (L, or 2L while the dictionary is learnt)
   T rho;
   T mu;            // gradient (Tikhonov) weight on the codes; z-update diagonal rho + mu (gs[k1] + gs[k2])
   T n2;            // N^2
@@ -77,7 +78,18 @@ template <typename T> struct CDArgs {
 template <typename T> cudaError_t launch_cd_solve(const CDArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_p_from_z(const typename CT<T>::type* zcol, const typename CT<T>::type* th,
-                            typename CT<T>::type* p, int N, int M, int L, cudaStream_t s);
+                            typename CT<T>::type* p, int N, int M, int L, cudaStream_t s,
+                            double scale = 0.0, int th_planes = 0);
+// online dictionary update (Section IV-B): per-frequency filter solve; projection and dual;
+// crop of the filters to P x P
+template <typename T>
+cudaError_t launch_dl_solve(const typename CT<T>::type* zcol, const typename CT<T>::type* xcol,
+                            const typename CT<T>::type* gecol, int gep, typename CT<T>::type* dcol, int N, int M,
+                            int L, double sigma, cudaStream_t s);
+template <typename T> cudaError_t launch_dl_norm(const T* d, const T* e, T* inv, int L, int N, int P, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dl_project(const T* d, T* e, T* gs, const T* inv, int L, int N, int P, cudaStream_t s);
+template <typename T> cudaError_t launch_dl_crop(const T* g, T* out, int L, int N, int P, cudaStream_t s);
 template <typename Tin> cudaError_t launch_embed_filters(const Tin* d, double* out, int L, int P, int N, cudaStream_t s);
 template <typename T>
 cudaError_t launch_theta_store(const SetupC<T>* th64, typename CT<T>::type* th, int L, int N, cudaStream_t s);
