@@ -136,145 +136,114 @@ __global__ void p_from_z_kernel(const typename CT<T>::type* __restrict__ zcol, c
 
 // ---- online dictionary update (Section IV-B, Eqs. d_admm, g_admm, h_admm, sold_3D) ----------
 
-// Per frequency, one warp, lane l = filter l: the filter normal equation summed over the S
-// channels,  (sigma I + W W^H) d = b,  W = [conj(zhat_{.,s})]_s (L x S),  b = W xhat + sigma F(g - e),
-// by the Woodbury identity d = (b - W alpha) / sigma with (sigma I_S + W^H W) alpha = W^H b, the
-// S x S system solved by Cholesky on every lane (W^H W and W^H b are warp reductions).  zcol holds
-// the code spectra and xcol the image spectra scaled by 1/N^2 (the column solve's convention);
-// ge holds F(g - e) (plane stride gep per bin); dcol receives d-hat / N^2 (so that an
-// unnormalised inverse gives d).
-template <typename T, int SMAX>
-__global__ void __launch_bounds__(128) dl_solve_kernel(const typename CT<T>::type* __restrict__ zcol,
-                                                       const typename CT<T>::type* __restrict__ xcol,
-                                                       const typename CT<T>::type* __restrict__ gecol, int gep,
-                                                       typename CT<T>::type* __restrict__ dcol, int N, int M, int L,
-                                                       T sigma) {
+// Per frequency, one thread (k1 = threadIdx + block offset, k2 = blockIdx.y, so that the warps
+// read the column layout contiguously): the filter normal equation summed over the M channels,
+// (sigma I + W W^H) d = b with W = [conj(zhat_{l,s})] (L x M) and b = W xhat + sigma F(g - e), by
+// the Woodbury identity d = (b - W alpha) / sigma, (sigma I_M + W^H W) alpha = W^H b.  The L
+// filters are streamed twice: once to accumulate W^H W and W^H b, once to form d; the M x M system
+// is solved by Cholesky in registers.  zcol holds the code spectra and xcol the image spectra
+// scaled by 1/N^2 (the column solve's convention); ge holds F(g - e) (gep planes per bin); dcol
+// receives d-hat / N^2 (so that an unnormalised inverse gives d).
+template <typename T, int M>
+__global__ void __launch_bounds__(64) dl_solve_kernel(const typename CT<T>::type* __restrict__ zcol,
+                                                      const typename CT<T>::type* __restrict__ xcol,
+                                                      const typename CT<T>::type* __restrict__ gecol, int gep,
+                                                      typename CT<T>::type* __restrict__ dcol, int N, int L,
+                                                      T sigma) {
   using C = typename CT<T>::type;
-  const int H = N / 2 + 1, CP = col_pitch(N);
-  const int lane = threadIdx.x & 31;
-  const long long bin = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (bin >= (long long)N * H) return;  // whole warps leave together
-  const int k2 = (int)(bin / N), k1 = (int)(bin - (long long)k2 * N);
+  const int CP = col_pitch(N);
+  const int k1 = blockIdx.x * blockDim.x + threadIdx.x, k2 = blockIdx.y;
+  if (k1 >= N) return;
   const T n2 = (T)N * (T)N;
-  const bool on = lane < L;
-  C z[SMAX];
-  C b = mk<C>(0.0, 0.0);
-  if (on) {
-    const C ge = gecol[((size_t)k2 * gep + lane) * CP + k1];
-    b = mk<C>(sigma * ge.x, sigma * ge.y);
-  }
+  const C* zb = zcol + (size_t)k2 * M * L * CP + k1;  // z_{l,s} at zb[(s L + l) CP]
+  const C* gb = gecol + (size_t)k2 * gep * CP + k1;
+  C x[M], c[M], G[M][M];
 #pragma unroll
-  for (int s = 0; s < SMAX; ++s) {
-    z[s] = mk<C>(0.0, 0.0);
-    if (s < M) {
-      C xs = xcol[((size_t)k2 * M + s) * CP + k1];
-      xs.x *= n2;
-      xs.y *= n2;
-      if (on) {
-        C zz = zcol[((size_t)k2 * M * L + (size_t)s * L + lane) * CP + k1];
-        zz.x *= n2;
-        zz.y *= n2;
-        z[s] = zz;
-        cfmac(b, zz, xs);  // b += conj(z) x
-      }
+  for (int s = 0; s < M; ++s) {
+    const C v = xcol[((size_t)k2 * M + s) * CP + k1];
+    x[s] = mk<C>(v.x * n2, v.y * n2);
+    c[s] = mk<C>(0.0, 0.0);
+#pragma unroll
+    for (int t = 0; t < M; ++t) G[s][t] = mk<C>(0.0, 0.0);
+  }
+  // b_l = sigma ge_l + sum_s conj(z_{l,s}) x_s
+  auto load_b = [&](int l, C (&z)[M]) {
+    const C ge = __ldg(gb + (size_t)l * CP);
+    C b = mk<C>(sigma * ge.x, sigma * ge.y);
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      const C v = __ldg(zb + ((size_t)s * L + l) * CP);
+      z[s] = mk<C>(v.x * n2, v.y * n2);
+      cfmac(b, z[s], x[s]);
+    }
+    return b;
+  };
+#pragma unroll 2
+  for (int l = 0; l < L; ++l) {
+    C z[M];
+    const C b = load_b(l, z);
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      cfma(c[s], z[s], b);  // W^H b
+#pragma unroll
+      for (int t = 0; t <= s; ++t) cfmac(G[s][t], z[t], z[s]);  // z_s conj(z_t)
     }
   }
-  // G = W^H W (G_{s s'} = sum_l z_{l s} conj(z_{l s'})), c = W^H b = sum_l z_{l s} b_l
-  C G[SMAX][SMAX], c[SMAX];
+  // Cholesky of sigma I + G = R R^H (lower, in place), then R w = c and R^H alpha = w
 #pragma unroll
-  for (int s = 0; s < SMAX; ++s) {
-    if (s < M) {
-      C v = mk<C>(0.0, 0.0);
-      cfma(v, z[s], b);
+  for (int j = 0; j < M; ++j) {
+    T d = sigma + G[j][j].x;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    for (int k = 0; k < j; ++k) d -= G[j][k].x * G[j][k].x + G[j][k].y * G[j][k].y;
+    const T r = sqrt(d > T(0) ? d : T(0)), inv = r > T(0) ? T(1) / r : T(0);
+    G[j][j] = mk<C>(r, 0.0);
+#pragma unroll
+    for (int i = j + 1; i < M; ++i) {
+      C acc = G[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) {  // acc -= G_ik conj(G_jk)
+        const C a = G[i][k], bb = G[j][k];
+        acc.x -= a.x * bb.x + a.y * bb.y;
+        acc.y -= a.y * bb.x - a.x * bb.y;
       }
-      c[s] = v;
-#pragma unroll
-      for (int t = 0; t <= s; ++t) {
-        C w = mk<C>(0.0, 0.0);
-        cfmac(w, z[t], z[s]);  // conj(z_t) z_s summed over l -> G_{s t}
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
-          w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
-        }
-        G[s][t] = w;
-      }
-      G[s][s].x += sigma;
-      G[s][s].y = T(0);
+      G[i][j] = mk<C>(acc.x * inv, acc.y * inv);
     }
   }
-  // Cholesky G = R R^H (lower), then forward and back substitution for alpha
+  C w[M], al[M];
 #pragma unroll
-  for (int j = 0; j < SMAX; ++j) {
-    if (j < M) {
-      T d = G[j][j].x;
+  for (int i = 0; i < M; ++i) {
+    C acc = c[i];
 #pragma unroll
-      for (int k = 0; k < j; ++k) d -= G[j][k].x * G[j][k].x + G[j][k].y * G[j][k].y;
-      const T r = sqrt(d > T(0) ? d : T(0)), inv = r > T(0) ? T(1) / r : T(0);
-      G[j][j] = mk<C>(r, 0.0);
-#pragma unroll
-      for (int i = j + 1; i < SMAX; ++i) {
-        if (i < M) {
-          C acc = G[i][j];
-#pragma unroll
-          for (int k = 0; k < j; ++k) {
-            // acc -= G_ik conj(G_jk)
-            const C a = G[i][k], bb = G[j][k];
-            acc.x -= a.x * bb.x + a.y * bb.y;
-            acc.y -= a.y * bb.x - a.x * bb.y;
-          }
-          G[i][j] = mk<C>(acc.x * inv, acc.y * inv);
-        }
-      }
+    for (int k = 0; k < i; ++k) {
+      acc.x -= G[i][k].x * w[k].x - G[i][k].y * w[k].y;
+      acc.y -= G[i][k].x * w[k].y + G[i][k].y * w[k].x;
     }
+    const T inv = T(1) / G[i][i].x;
+    w[i] = mk<C>(acc.x * inv, acc.y * inv);
   }
-  C w[SMAX];
 #pragma unroll
-  for (int i = 0; i < SMAX; ++i) {  // R w = c
-    if (i < M) {
-      C acc = c[i];
+  for (int i = M - 1; i >= 0; --i) {
+    C acc = w[i];
 #pragma unroll
-      for (int k = 0; k < i; ++k) {
-        acc.x -= G[i][k].x * w[k].x - G[i][k].y * w[k].y;
-        acc.y -= G[i][k].x * w[k].y + G[i][k].y * w[k].x;
-      }
-      const T inv = T(1) / G[i][i].x;
-      w[i] = mk<C>(acc.x * inv, acc.y * inv);
+    for (int k = i + 1; k < M; ++k) {  // acc -= conj(G_ki) alpha_k
+      acc.x -= G[k][i].x * al[k].x + G[k][i].y * al[k].y;
+      acc.y -= G[k][i].x * al[k].y - G[k][i].y * al[k].x;
     }
+    const T inv = T(1) / G[i][i].x;
+    al[i] = mk<C>(acc.x * inv, acc.y * inv);
   }
-  C al[SMAX];
+  const T sc = T(1) / (sigma * n2);
+  C* db = dcol + (size_t)k2 * L * CP + k1;
+#pragma unroll 2
+  for (int l = 0; l < L; ++l) {
+    C z[M];
+    C d = load_b(l, z);
 #pragma unroll
-  for (int i = SMAX - 1; i >= 0; --i) {  // R^H alpha = w
-    if (i < M) {
-      C acc = w[i];
-#pragma unroll
-      for (int k = i + 1; k < SMAX; ++k) {
-        if (k < M) {
-          // acc -= conj(G_ki) alpha_k
-          acc.x -= G[k][i].x * al[k].x + G[k][i].y * al[k].y;
-          acc.y -= G[k][i].x * al[k].y - G[k][i].y * al[k].x;
-        }
-      }
-      const T inv = T(1) / G[i][i].x;
-      al[i] = mk<C>(acc.x * inv, acc.y * inv);
+    for (int s = 0; s < M; ++s) {  // d -= conj(z_s) alpha_s
+      d.x -= z[s].x * al[s].x + z[s].y * al[s].y;
+      d.y -= z[s].x * al[s].y - z[s].y * al[s].x;
     }
-  }
-  if (on) {
-    C d = b;
-#pragma unroll
-    for (int s = 0; s < SMAX; ++s) {
-      if (s < M) {
-        // d -= conj(z_s) alpha_s
-        d.x -= z[s].x * al[s].x + z[s].y * al[s].y;
-        d.y -= z[s].x * al[s].y - z[s].y * al[s].x;
-      }
-    }
-    const T sc = T(1) / (sigma * n2);
-    dcol[((size_t)k2 * L + lane) * CP + k1] = mk<C>(d.x * sc, d.y * sc);
+    db[(size_t)l * CP] = mk<C>(d.x * sc, d.y * sc);
   }
 }
 
@@ -355,12 +324,15 @@ template <typename T>
 cudaError_t launch_dl_solve(const typename CT<T>::type* zcol, const typename CT<T>::type* xcol,
                             const typename CT<T>::type* gecol, int gep, typename CT<T>::type* dcol, int N, int M,
                             int L, double sigma, cudaStream_t s) {
-  if (L > 32) return cudaErrorInvalidValue;
-  const long long bins = (long long)N * (N / 2 + 1);
-  const dim3 grid((unsigned)((bins + 3) / 4)), block(128);
-  if (M <= 4) dl_solve_kernel<T, 4><<<grid, block, 0, s>>>(zcol, xcol, gecol, gep, dcol, N, M, L, (T)sigma);
-  else if (M <= 8) dl_solve_kernel<T, 8><<<grid, block, 0, s>>>(zcol, xcol, gecol, gep, dcol, N, M, L, (T)sigma);
-  else return cudaErrorInvalidValue;
+  const dim3 grid((N + 63) / 64, N / 2 + 1), block(64);
+  const T sg = (T)sigma;
+  switch (M) {
+#define DL_CASE(m) \
+  case m: dl_solve_kernel<T, m><<<grid, block, 0, s>>>(zcol, xcol, gecol, gep, dcol, N, L, sg); break;
+    DL_CASE(1) DL_CASE(2) DL_CASE(3) DL_CASE(4) DL_CASE(5) DL_CASE(6) DL_CASE(7) DL_CASE(8)
+#undef DL_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_dl_norm(const T* d, const T* e, T* inv, int L, int N, int P, cudaStream_t s) {

@@ -77,19 +77,21 @@ def test_learning_parity_small(torch, dtype, iters, tol, sigma):
     assert np.allclose(np.linalg.norm(fg.reshape(fg.shape[0], -1), axis=1), 1.0, atol=1e-5)
 
 
-def test_learning_parity_ragged_channels(torch):
-    """M = 5 channels (the M <= 8 solve with a partly filled register tile), L = 7 filters of 7 x 7,
-    N = 128."""
-    h, y, d0 = problem(seed=8, N=128, K=3, M=5, L=7, Pf=7)
+@pytest.mark.parametrize("N,K,M,L,Pf,dtype,tol", [(128, 3, 5, 7, 7, "f32", 1e-4), (64, 2, 8, 3, 3, "f32", 1e-4),
+                                                  (64, 2, 8, 3, 3, "f64", 1e-9), (64, 1, 1, 5, 4, "f32", 1e-4)])
+def test_learning_parity_channel_counts(torch, N, K, M, L, Pf, dtype, tol):
+    """Channel counts 1, 5 and 8 (each its own register-resident M x M solve), odd and even
+    filter sizes, 12 iterations."""
+    h, y, d0 = problem(seed=8, N=N, K=K, M=M, L=L, Pf=Pf)
     sigma, iters = 5.0, 12
     x_or, z_or, _, _, f_or = fast.run_convdict_learn(h, y, d0, LAM, RHO, BETA, sigma, iters)
-    P, _ = learning_plan(torch, h, y, d0, LAM, RHO, BETA, sigma)
+    P, _ = learning_plan(torch, h, y, d0, LAM, RHO, BETA, sigma, dtype)
     P.iterate(iters)
     xg = P.get_x().double().cpu().numpy()
     fg = P.get_dictionary().double().cpu().numpy()
     P.close()
-    assert rel(fg, f_or) <= 1e-4, rel(fg, f_or)
-    assert rel(xg, x_or) <= 1e-4, rel(xg, x_or)
+    assert rel(fg, f_or) <= tol, rel(fg, f_or)
+    assert rel(xg, x_or) <= tol, rel(xg, x_or)
 
 
 def test_learning_full_size(torch):
