@@ -36,6 +36,7 @@ Readings where the paper is silent or garbled (each listed in the design notes):
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 from typing import List, Optional
@@ -169,11 +170,137 @@ def l1_adjoint(w: np.ndarray) -> np.ndarray:
     return w[..., 0, :, :].copy()
 
 
+# ---------------------------------------------------------------------------
+# Kronecker prior T = (2D Symmlet-8 wavelet) (x) (1D DCT along the channels) (Section V,
+# the analysis prior of the spectral experiments; readings R24-R26)
+# ---------------------------------------------------------------------------
+def symlet_lowpass(p: int) -> np.ndarray:
+    """Orthonormal lowpass filter (2p taps, sum sqrt(2)) with p vanishing moments and the most
+    nearly linear phase (Daubechies' least-asymmetric construction, reading R24):
+      |m0(w)|^2 = cos^{2p}(w/2) P(sin^2(w/2)),  P(y) = sum_{k<p} C(p-1+k, k) y^k,
+    each root y of P gives the root pair z, 1/z of z^2 - 2(1 - 2y) z + 1; one of each pair (one
+    conjugate pair of pairs for complex y) is kept, every choice is formed, and the one whose
+    remaining factor Q(e^{iw}) has the smallest least-squares deviation of its unwrapped phase
+    from a straight line on [0, pi] wins; of the two mirror-image winners the one with the
+    smaller energy centroid sum_n n h_n^2 is returned."""
+    coeffs = [math.comb(p - 1 + k, k) for k in range(p)]
+    ys = list(np.roots(coeffs[::-1])) if p > 1 else []
+    groups = []                       # each: the inside-circle z roots of one real y / conjugate pair
+    taken = [False] * len(ys)
+    for i, y in enumerate(ys):
+        if taken[i]:
+            continue
+        taken[i] = True
+        w = 1.0 - 2.0 * y
+        z = w + np.sqrt(w * w - 1.0 + 0j)
+        z_in = z if abs(z) < 1.0 else 1.0 / z
+        if abs(y.imag) <= 1e-9 * max(1.0, abs(y)):
+            groups.append([complex(z_in.real, 0.0)])
+        else:
+            j = min((k for k in range(len(ys)) if not taken[k]), key=lambda k: abs(ys[k] - np.conj(y)))
+            taken[j] = True
+            groups.append([z_in, np.conj(z_in)])
+    omega = math.pi * np.arange(513) / 512.0
+    best = None
+    for pick in range(1 << len(groups)):
+        roots = []
+        for b, g in enumerate(groups):
+            roots += g if not (pick >> b) & 1 else [1.0 / z for z in g]
+        q = np.array([1.0 + 0j])
+        for r in roots:
+            q = np.convolve(q, [1.0, -r])
+        h = q
+        for _ in range(p):
+            h = np.convolve(h, [1.0, 1.0])
+        h = h.real * (math.sqrt(2.0) / h.real.sum())
+        Q = np.ones(omega.shape, dtype=complex)
+        for r in roots:
+            Q *= 1.0 - r * np.exp(-1j * omega)
+        phase = np.unwrap(np.angle(Q))
+        A = np.stack([np.ones_like(omega), omega], axis=1)
+        fit = A @ np.linalg.lstsq(A, phase, rcond=None)[0]
+        dev = float(np.sum((phase - fit) ** 2))
+        centroid = float(np.sum(np.arange(h.size) * h * h))
+        key = (round(dev, 6), centroid)
+        if best is None or key < best[0]:
+            best = (key, h)
+    return best[1]
+
+
+@functools.lru_cache(maxsize=None)
+def _sym8_cached() -> tuple:
+    return tuple(symlet_lowpass(8))
+
+
+def _sym8() -> np.ndarray:
+    return np.array(_sym8_cached())
+
+
+def wavelet_levels(N: int) -> int:
+    """Decomposition depth: down to a 16 x 16 coarse band (reading R25)."""
+    return int(round(math.log2(N))) - 4
+
+
+def dwt_matrix(n: int, h: np.ndarray) -> np.ndarray:
+    """One level of the periodic orthonormal DWT on length n: rows i < n/2 are the lowpass
+    taps h[(j - 2i) mod n], rows n/2 + i the highpass taps g[k] = (-1)^k h[L-1-k]."""
+    L = h.size
+    g = np.array([(-1) ** k * h[L - 1 - k] for k in range(L)])
+    A = np.zeros((n, n))
+    for i in range(n // 2):
+        for k in range(L):
+            A[i, (2 * i + k) % n] += h[k]
+            A[n // 2 + i, (2 * i + k) % n] += g[k]
+    return A
+
+
+def dct_matrix(n: int) -> np.ndarray:
+    """Orthonormal DCT-II, C[k, m] = a_k cos(pi (2m+1) k / (2n)), a_0 = sqrt(1/n), a_k = sqrt(2/n)."""
+    k = np.arange(n)[:, None]
+    m = np.arange(n)[None, :]
+    C = np.cos(math.pi * (2 * m + 1) * k / (2.0 * n))
+    C[0, :] *= math.sqrt(1.0 / n)
+    C[1:, :] *= math.sqrt(2.0 / n)
+    return C
+
+
+def wdct_forward(x: np.ndarray) -> np.ndarray:
+    """T x for T = W (x) C: the J-level periodic 2D Symmlet-8 transform of every channel (Mallat
+    layout: level by level rows then columns of the current coarse band), then the DCT-II along
+    the channel axis.  x [M, N, N] -> [M, 1, N, N]."""
+    M, N, _ = x.shape
+    h = _sym8()
+    w = x.astype(float).copy()
+    n = N
+    for _ in range(wavelet_levels(N)):
+        A = dwt_matrix(n, h)
+        w[:, :n, :n] = w[:, :n, :n] @ A.T     # rows
+        w[:, :n, :n] = A @ w[:, :n, :n]       # columns
+        n //= 2
+    return np.einsum("km,mij->kij", dct_matrix(M), w)[:, None, :, :]
+
+
+def wdct_adjoint(c: np.ndarray) -> np.ndarray:
+    """T^T (= T^-1, T orthonormal): inverse DCT along channels, then the inverse levels from the
+    coarsest.  [M, 1, N, N] -> [M, N, N]."""
+    M, N = c.shape[0], c.shape[-1]
+    h = _sym8()
+    w = np.einsum("km,kij->mij", dct_matrix(M), c[:, 0])
+    J = wavelet_levels(N)
+    for lev in reversed(range(J)):
+        n = N >> lev
+        A = dwt_matrix(n, h)
+        w[:, :n, :n] = A.T @ w[:, :n, :n]     # columns
+        w[:, :n, :n] = w[:, :n, :n] @ A       # rows
+    return w
+
+
 PRIORS = {
     "tv": (tv_forward, tv_adjoint),
     "tv_iso": (tv_forward, tv_adjoint),   # isotropic TV: same T, coupled shrinkage (reading R20)
     "dct8": (dct8_forward, dct8_adjoint),
     "l1": (l1_forward, l1_adjoint),
+    "wdct": (wdct_forward, wdct_adjoint),   # Symmlet-8 (x) channel DCT (readings R24-R26)
 }
 
 
@@ -185,7 +312,7 @@ def gram_eigenvalues(prior: str, N: int) -> np.ndarray:
     """g(w): DFT eigenvalues of the circulant T^T T.  Computed as the DFT of
     the kernel T^T T delta (Eq. solx_Trans with BCCB T^T T).  For an
     orthonormal T (DCT, identity) T^T T = I and g = 1 (Eq. solx_Trans_DFT)."""
-    if prior in ("dct8", "l1"):
+    if prior in ("dct8", "l1", "wdct"):
         return np.ones((N, N))
     fwd, adj = PRIORS[prior]
     delta = np.zeros((N, N))

@@ -32,7 +32,7 @@ def irfft2(X, N):
 
 def gram_eigenvalues_half(prior: str, N: int) -> np.ndarray:
     """g(w) on the half spectrum [N, N/2+1] (DFT of the kernel T^T T delta)."""
-    if prior in ("dct8", "l1"):
+    if prior in ("dct8", "l1", "wdct"):
         return np.ones((N, N // 2 + 1))
     fwd, adj = ref.PRIORS[prior]
     delta = np.zeros((N, N))

@@ -555,3 +555,121 @@ def test_fast_learning_matches_naive(cd8):
     xf, zf, tf, uf, ff = fast.run_convdict_learn(*args)
     assert rel(xf, xn) < 1e-10 and rel(ff, fn) < 1e-10
     assert rel(fn, cd8["d"] / np.linalg.norm(cd8["d"].reshape(cd8["L"], -1), axis=1)[:, None, None]) > 1e-3
+
+
+# ----------------------------------------------------------------- Kronecker wavelet (x) DCT prior
+def test_symlet_construction_textbook_cases():
+    """Daubechies' spectral factorisation: one vanishing moment gives Haar, two give the D4
+    filter (1+sqrt3, 3+sqrt3, 3-sqrt3, 1-sqrt3) / (4 sqrt2)."""
+    assert np.allclose(admm.symlet_lowpass(1), [1 / math.sqrt(2)] * 2, atol=1e-15)
+    s3 = math.sqrt(3.0)
+    d4 = np.array([1 + s3, 3 + s3, 3 - s3, 1 - s3]) / (4 * math.sqrt(2.0))
+    assert np.allclose(admm.symlet_lowpass(2), d4, atol=1e-13)
+
+
+def test_sym8_orthonormal_with_eight_vanishing_moments():
+    """The Symmlet-8 lowpass (Section V): 16 taps, sum sqrt 2, orthonormal to its even shifts,
+    and the highpass g_k = (-1)^k h_{15-k} annihilates polynomials of degree < 8."""
+    h = admm.symlet_lowpass(8)
+    assert h.size == 16 and abs(h.sum() - math.sqrt(2.0)) < 1e-13
+    for k in range(8):
+        assert abs(np.dot(h[2 * k:], h[: 16 - 2 * k]) - (1.0 if k == 0 else 0.0)) < 1e-12
+    g = np.array([(-1) ** k * h[15 - k] for k in range(16)])
+    n = np.arange(16.0)
+    for k in range(8):
+        assert abs(np.dot(g, n ** k)) < 1e-9 * max(1.0, np.abs(n ** k).sum())
+
+
+def test_sym8_is_less_asymmetric_than_the_minimum_phase_filter():
+    """The least-asymmetric choice (reading R24) is not Daubechies' minimum-phase D16, and its
+    energy is far more concentrated around the centre of the support."""
+    h = admm.symlet_lowpass(8)
+    # minimum-phase: every root of P kept inside the unit circle
+    coeffs = [math.comb(7 + k, k) for k in range(8)]
+    q = np.array([1.0 + 0j])
+    for y in np.roots(coeffs[::-1]):
+        w = 1 - 2 * y
+        z = w + np.sqrt(w * w - 1 + 0j)
+        q = np.convolve(q, [1.0, -(z if abs(z) < 1 else 1 / z)])
+    for _ in range(8):
+        q = np.convolve(q, [1.0, 1.0])
+    d16 = q.real * math.sqrt(2.0) / q.real.sum()
+    assert np.abs(np.abs(h) - np.abs(d16)).max() > 1e-2
+    spread = lambda f: np.sum((np.arange(16) - np.sum(np.arange(16) * f * f)) ** 2 * f * f)
+    assert spread(h) < 0.6 * spread(d16)
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_dwt_level_is_periodic_filtering_and_orthogonal(n):
+    """One level equals circular filtering with h and g followed by keeping even samples, and its
+    matrix is orthogonal on any even length at least the filter length."""
+    h = admm.symlet_lowpass(8)
+    g = np.array([(-1) ** k * h[15 - k] for k in range(16)])
+    A = admm.dwt_matrix(n, h)
+    x = RNG.standard_normal(n)
+    xx = np.concatenate([x, x])       # periodic extension
+    lo = np.array([sum(h[k] * xx[2 * i + k] for k in range(16)) for i in range(n // 2)])
+    hi = np.array([sum(g[k] * xx[2 * i + k] for k in range(16)) for i in range(n // 2)])
+    assert np.allclose(A @ x, np.concatenate([lo, hi]), atol=1e-13)
+    assert np.abs(A @ A.T - np.eye(n)).max() < 1e-12
+
+
+def test_channel_dct_matches_library():
+    for n in (1, 3, 10):
+        assert np.allclose(admm.dct_matrix(n), sfft.dct(np.eye(n), axis=0, norm="ortho"), atol=1e-14)
+
+
+def test_wdct_is_the_kronecker_product():
+    """T = W (x) C (Section V): for x_m = a_m B, T x = (C a)_k W(B), with W(B) the 2D wavelet of
+    one channel (the M = 1 transform)."""
+    M, N = 4, 64
+    a = RNG.standard_normal(M)
+    B = RNG.standard_normal((N, N))
+    x = a[:, None, None] * B[None]
+    WB = admm.wdct_forward(B[None])[0, 0]
+    expect = (admm.dct_matrix(M) @ a)[:, None, None] * WB[None]
+    assert rel(admm.wdct_forward(x)[:, 0], expect) < 1e-13
+
+
+def test_wdct_orthonormal_and_constant_image():
+    """T is orthonormal (norm kept, T^T the inverse, adjoint identity); a constant image lands in
+    the DC channel of the coarse 16 x 16 band with value c sqrt(M) 2^J (each level multiplies the
+    constant by 2), every other coefficient zero."""
+    M, N = 3, 64
+    x = RNG.standard_normal((M, N, N))
+    c = RNG.standard_normal((M, 1, N, N))
+    Tx = admm.wdct_forward(x)
+    assert abs(np.linalg.norm(Tx) - np.linalg.norm(x)) < 1e-12 * np.linalg.norm(x)
+    assert np.abs(admm.wdct_adjoint(Tx) - x).max() < 1e-12
+    assert abs(np.sum(Tx * c) - np.sum(x * admm.wdct_adjoint(c))) < 1e-11 * np.linalg.norm(x) * np.linalg.norm(c)
+    J = admm.wavelet_levels(N)
+    w = admm.wdct_forward(np.full((M, N, N), 0.7))[:, 0]
+    expect = np.zeros_like(w)
+    expect[0, :16, :16] = 0.7 * math.sqrt(M) * 2 ** J
+    assert np.abs(w - expect).max() < 1e-10
+
+
+def test_closed_form_wdct_identity():
+    """h = delta per channel (K = M), T orthonormal: x* = T^T soft(T y, lam/beta)."""
+    N, M = 32, 3
+    h = np.zeros((M, M, N, N))
+    for m in range(M):
+        h[m, m, 0, 0] = 1.0
+    y = RNG.standard_normal((M, N, N))
+    lam, beta, rho = 0.3, 2.0, 1.5
+    S = admm.analysis_setup(h, y, "wdct", lam, rho, beta)
+    x, _, _, _ = admm.run_analysis(S, 400)
+    xs = admm.wdct_adjoint(admm.soft(admm.wdct_forward(y), lam / beta))
+    assert np.abs(x - xs).max() < 1e-9
+
+
+def test_fast_wdct_matches_naive():
+    rng = np.random.default_rng(17)
+    N, K, M = 32, 3, 3
+    h = random_psfs(rng, K, M, N)
+    y = rng.standard_normal((K, N, N))
+    S = admm.analysis_setup(h, y, "wdct", 0.05, 0.7, 1.0)
+    F = fast.analysis_setup(h, y, "wdct", 0.05, 0.7, 1.0)
+    xn = admm.run_analysis(S, 6)[0]
+    xf = fast.run_analysis(F, 6)[0]
+    assert rel(xf, xn) < 1e-11
