@@ -579,7 +579,7 @@ def main():
                              "adaptive"])
     ap.add_argument("--N", type=int, default=1024, help="single: image side")
     ap.add_argument("--M", type=int, default=10, help="single: channels (= measurements)")
-    ap.add_argument("--prior", default="tv", choices=["tv", "tv_iso", "dct8", "l1"], help="single: prior")
+    ap.add_argument("--prior", default="tv", choices=["tv", "tv_iso", "dct8", "l1", "wdct"], help="single: prior")
     ap.add_argument("--iters", type=int, default=20, help="single: iterations")
     ap.add_argument("--column-pass", type=int, default=0, help="single: 0 autotuned, 1 fused, 2 split")
     ap.add_argument("--col-tile", type=int, default=0, help="single: columns per fused cluster (0 = default)")

@@ -62,9 +62,16 @@ typedef enum cip_prior {
   CIP_PRIOR_L1 = 2,   /* T = I (1 component) */
   CIP_PRIOR_CONVDICT = 3, /* synthesis prior with a 2D convolutional dictionary shared by all channels
                             (Alg. 2): x ~ sum_l d_l (*) z_{l,m}, l1 on the coefficient maps z */
-  CIP_PRIOR_TV_ISO = 4 /* isotropic TV, lambda sum_pixels ||(D_h x, D_v x)||_2 (Section III-A): the
+  CIP_PRIOR_TV_ISO = 4, /* isotropic TV, lambda sum_pixels ||(D_h x, D_v x)||_2 (Section III-A): the
                           same T and x-update as CIP_PRIOR_TV, the t-update the per-pixel group
                           shrinkage (v max(0, 1 - (lambda/rho)/||v||)), 2 components */
+  CIP_PRIOR_WDCT = 5   /* Kronecker basis T = W (x) C of Section V (1 component): W the periodic 2D
+                          Symmlet-8 wavelet transform of each channel (orthonormal filter with 8
+                          vanishing moments and the least-asymmetric root choice of Daubechies'
+                          factorisation; Mallat levels, rows then columns, down to a 16 x 16 coarse
+                          band), C the orthonormal DCT-II along the M channels; t and u hold the
+                          coefficients [M][1][N][N] (index 0 = DCT frequency along channels, Mallat
+                          layout in the plane) */
 } cip_prior;
 
 typedef struct cip_options {

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib
 
-PRIORS = {"tv": 0, "dct8": 1, "l1": 2, "convdict": 3, "tv_iso": 4}
+PRIORS = {"tv": 0, "dct8": 1, "l1": 2, "convdict": 3, "tv_iso": 4, "wdct": 5}
 DTYPES = {"f32": 0, "f64": 1}
 NP_DTYPE = {"f32": np.float32, "f64": np.float64}
 

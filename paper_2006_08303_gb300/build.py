@@ -28,6 +28,7 @@ UNITS = [
     ("noalloc.cu", [], "noalloc.o"),
     ("colsplit.cu", [], "colsplit.o"),
     ("convdict.cu", [], "convdict.o"),
+    ("wavelet.cu", [], "wavelet.o"),
     ("serve.cu", [], "serve.o"),
 ]
 

@@ -66,6 +66,11 @@ struct cip_plan {
   void* pbuf[2] = {nullptr, nullptr};   // [H][M][CP] p = sum_l theta_l v_l (ping-pong)
   int pcur = 0;
   void* xcol = nullptr;                 // [H][M][CP] x-hat of the last x-update
+  // Kronecker wavelet (x) DCT prior (CIP_PRIOR_WDCT): two [M][N][N] work planes, the channel DCT
+  // matrix [M][M] and the Symmlet-8 lowpass
+  void* wbuf[2] = {nullptr, nullptr};
+  void* wcos = nullptr;
+  double wfilt[16] = {};
   // online dictionary update (Section IV-B): sigma = 0 off.  While on, theta lives in the first L
   // planes of dl_spec and F(g - e) in the last L (one forward transform makes both).
   double dl_sigma = 0;
@@ -135,6 +140,8 @@ size_t ncomp_of(int prior) { return prior_is_tv(prior) ? 2 : 1; }
 bool is_cd(const cip_plan* p) { return p->prior == CIP_PRIOR_CONVDICT; }
 // kind of prior pass: the dictionary's shrinkage acts on the coefficient maps with T = I
 int prior_pass_kind(const cip_plan* p) { return is_cd(p) ? (int)PRIOR_L1 : p->prior; }
+// row tile of the prior pass's work split (the wavelet prior shares the l1 split for its partials)
+int tile_kind(int prior) { return (prior == CIP_PRIOR_CONVDICT || prior == CIP_PRIOR_WDCT) ? (int)PRIOR_L1 : prior; }
 // maps the prior pass works on: image channels, or the L*M coefficient maps of the dictionary
 int smaps(const cip_plan* p) { return is_cd(p) ? p->M * p->L : p->M; }
 
@@ -216,7 +223,23 @@ template <typename T> cip_status alloc_state(cip_plan* p) {
     free_ptr(p, q);
     p->partials = nullptr;
   }
-  p->rowsA = passA_rows<T>(p->N, p->prior);
+  if (p->prior == CIP_PRIOR_WDCT) {
+    for (int i = 0; i < 2; ++i) {
+      free_ptr(p, p->wbuf[i]);
+      CIP_CUDA(p, dmalloc(p, &p->wbuf[i], real_elems(p, p->M) * sizeof(T)));
+    }
+    free_ptr(p, p->wcos);
+    CIP_CUDA(p, dmalloc(p, &p->wcos, (size_t)p->M * p->M * sizeof(T)));
+    // orthonormal DCT-II along the channels, C[k][m] = a_k cos(pi (2m + 1) k / (2M))
+    std::vector<T> c((size_t)p->M * p->M);
+    for (int k = 0; k < p->M; ++k)
+      for (int m = 0; m < p->M; ++m)
+        c[(size_t)k * p->M + m] =
+            (T)(std::sqrt((k == 0 ? 1.0 : 2.0) / p->M) * std::cos(M_PI * (2 * m + 1) * k / (2.0 * p->M)));
+    CIP_CUDA(p, cudaMemcpyAsync(p->wcos, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice, p->ast));
+    CIP_CUDA(p, cudaStreamSynchronize(p->ast));
+  }
+  p->rowsA = passA_rows<T>(p->N, tile_kind(p->prior));
   p->blocksA = (p->N / p->rowsA) * smaps(p);
   CIP_CUDA(p, dmalloc(p, (void**)&p->partials, (size_t)p->blocksA * kNPart * sizeof(double)));
   return CIP_OK;
@@ -458,6 +481,42 @@ template <typename T> PassAArgs<T> passA_args(cip_plan* p, int flags) {
 
 template <typename T> PassBArgs<T> passB_args(cip_plan* p);
 
+// The prior pass: one fused kernel per row tile for TV, DCT and l1; for the wavelet (x) DCT prior
+// (not local to a row tile) the chain x = row IDFT, J wavelet levels, channel DCT + shrinkage +
+// dual + residual partials, J inverse levels, q-hat = rho row DFT(q).  In import mode x is not
+// needed and the chain starts at the shrinkage kernel.
+template <typename T> cip_status prior_pass(cip_plan* p, const PassAArgs<T>& a, cudaStream_t s) {
+  if (p->prior != CIP_PRIOR_WDCT) {
+    CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
+    return CIP_OK;
+  }
+  const int N = p->N, M = p->M;
+  T* A = static_cast<T*>(p->wbuf[0]);
+  T* B = static_cast<T*>(p->wbuf[1]);
+  WaveFilt<T> f;
+  for (int k = 0; k < 16; ++k) {
+    f.h[k] = (T)p->wfilt[k];
+    f.g[k] = (T)((k & 1) ? -p->wfilt[15 - k] : p->wfilt[15 - k]);
+  }
+  int J = 0;
+  while ((N >> (J + 1)) >= 16) ++J;  // levels down to a 16 x 16 coarse band
+  if (!(a.flags & PA_IMPORT)) {
+    CIP_LAUNCH(p, (launch_row_c2r<T, T>(a.xh, A, N, M * N, a.tw, s)));
+    for (int lev = 0; lev < J; ++lev) {
+      CIP_LAUNCH(p, launch_dwt_level<T>(A, B, N, N >> lev, M, false, false, f, s));
+      CIP_LAUNCH(p, launch_dwt_level<T>(B, A, N, N >> lev, M, true, false, f, s));
+    }
+  }
+  CIP_LAUNCH(p, launch_wdct_shrink<T>(A, static_cast<const T*>(p->wcos), a.u_in, a.u_out, a.tprev, a.t_imp,
+                                      a.partials, p->blocksA, N, M, a.tau, a.flags, s));
+  for (int lev = J - 1; lev >= 0; --lev) {
+    CIP_LAUNCH(p, launch_dwt_level<T>(A, B, N, N >> lev, M, true, true, f, s));
+    CIP_LAUNCH(p, launch_dwt_level<T>(B, A, N, N >> lev, M, false, true, f, s));
+  }
+  CIP_LAUNCH(p, (launch_row_r2c<T, T>(A, a.qh, N, M * N, (T)p->rho, a.tw, s)));
+  return CIP_OK;
+}
+
 // the column pass in the plan's chosen form
 template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mode, int cc) {
   using C = typename CT<T>::type;
@@ -670,7 +729,10 @@ template <typename T> cip_status change_rho(cip_plan* p, double rho_new, cudaStr
   }
   PassAArgs<T> a = passA_args<T>(p, PA_IMPORT);
   a.t_imp = static_cast<const T*>(p->tprev);
-  CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
+  {
+    cip_status pst = prior_pass<T>(p, a, s);
+    if (pst != CIP_OK) return pst;
+  }
   p->cur ^= 1;
   return CIP_OK;
 }
@@ -706,7 +768,10 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
     PassAArgs<T> a = passA_args<T>(p, flags);
     const bool timeA = p->timing && p->nA < kMaxTimed;
     if (timeA) cudaEventRecord(p->evA[2 * p->nA], s);
-    CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
+    {
+      cip_status pst = prior_pass<T>(p, a, s);
+      if (pst != CIP_OK) return pst;
+    }
     if (timeA) cudaEventRecord(p->evA[2 * p->nA++ + 1], s);
     p->cur ^= 1;
     p->iteration++;
@@ -758,7 +823,10 @@ template <typename T> cip_status enqueue_iteration(cip_plan* p, cudaStream_t s, 
     if (cst != CIP_OK) return cst;
   }
   PassAArgs<T> a = passA_args<T>(p, flags);
-  CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
+  {
+    cip_status pst = prior_pass<T>(p, a, s);
+    if (pst != CIP_OK) return pst;
+  }
   p->cur ^= 1;
   p->iteration++;
   if (flags & PA_RESID) {
@@ -845,7 +913,10 @@ template <typename T> cip_status import_impl(cip_plan* p, const void* t, const v
   CIP_CUDA(p, cudaMemcpyAsync(p->tprev, dt, bytes, cudaMemcpyDeviceToDevice, s));
   PassAArgs<T> a = passA_args<T>(p, PA_IMPORT);
   a.t_imp = static_cast<const T*>(dt);
-  CIP_LAUNCH(p, launch_passA<T>(a, p->N, prior_pass_kind(p), s));
+  {
+    cip_status pst = prior_pass<T>(p, a, s);
+    if (pst != CIP_OK) return pst;
+  }
   p->cur ^= 1;
   p->iteration = 0;
   p->resid_valid = false;
@@ -1002,7 +1073,7 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv,
+  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv, p->wbuf[0], p->wbuf[1], p->wcos,
                   p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
@@ -1017,10 +1088,12 @@ cip_status cip_plan_destroy(cip_plan* p) {
 cip_status cip_set_prior(cip_plan* p, cip_prior prior, double lambda, double rho, double beta, void* stream) {
   if (!p) return CIP_ERR_INVALID_ARG;
   if (prior != CIP_PRIOR_TV && prior != CIP_PRIOR_DCT8 && prior != CIP_PRIOR_L1 && prior != CIP_PRIOR_CONVDICT &&
-      prior != CIP_PRIOR_TV_ISO)
+      prior != CIP_PRIOR_TV_ISO && prior != CIP_PRIOR_WDCT)
     return fail(p, CIP_ERR_INVALID_ARG, "unknown prior");
+  if (prior == CIP_PRIOR_WDCT && !symlet_lowpass(8, p->wfilt))
+    return fail(p, CIP_ERR_CUDA, "Symmlet-8 filter construction failed");
   if (!(lambda > 0) || !(rho > 0) || !(beta > 0)) return fail(p, CIP_ERR_INVALID_ARG, "lambda, rho, beta must be > 0");
-  const int kind = prior == CIP_PRIOR_CONVDICT ? (int)CIP_PRIOR_L1 : (int)prior;
+  const int kind = tile_kind(prior);
   const int rows = p->dtype == CIP_F64 ? passA_rows<double>(p->N, kind) : passA_rows<float>(p->N, kind);
   if (p->N % rows != 0) return fail(p, CIP_ERR_UNSUPPORTED, "image size not a multiple of the row tile");
   const size_t smA = p->dtype == CIP_F64 ? passA_smem<double>(p->N, kind) : passA_smem<float>(p->N, kind);

@@ -6,7 +6,7 @@
 
 namespace cip {
 
-enum PriorKind { PRIOR_TV = 0, PRIOR_DCT8 = 1, PRIOR_L1 = 2, PRIOR_CONVDICT = 3, PRIOR_TV_ISO = 4 };
+enum PriorKind { PRIOR_TV = 0, PRIOR_DCT8 = 1, PRIOR_L1 = 2, PRIOR_CONVDICT = 3, PRIOR_TV_ISO = 4, PRIOR_WDCT = 5 };
 // the two TV priors share T = [D_h; D_v] (two components, one halo row each side)
 constexpr bool prior_is_tv(int p) { return p == PRIOR_TV || p == PRIOR_TV_ISO; }
 
@@ -157,5 +157,24 @@ template <typename T> cudaError_t launch_scale(T* a, size_t n, T f, cudaStream_t
 // conv[0] set to 1 when both relative residuals < tol (tol > 0)
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, double rho, double tol, double* out,
                                    int* conv, cudaStream_t s);
+
+// Kronecker prior T = Symmlet-8 wavelet (x) channel DCT (Section V; csrc/wavelet.cu)
+template <typename T> struct WaveFilt {
+  T h[16];  // lowpass
+  T g[16];  // highpass g_k = (-1)^k h_{15-k}
+};
+// Symmlet lowpass with p vanishing moments (2p taps) from the spectral factorisation; false if p
+// is outside [1, 8]
+bool symlet_lowpass(int p, double* h);
+// one level of the periodic DWT on the n x n coarse band of each of M planes [M][N][N]: along
+// rows (cols = false) or columns, forward or inverse; n a power of two, 32 <= n <= N
+template <typename T>
+cudaError_t launch_dwt_level(const T* in, T* out, int N, int n, int M, bool cols, bool inverse,
+                             const WaveFilt<T>& f, cudaStream_t s);
+// per pixel: channel DCT (cmat [M][M], row k = frequency), shrinkage / dual update / residual
+// partials as the other prior passes (flags PA_*), q = t - u', coefficients <- C^T q in place
+template <typename T>
+cudaError_t launch_wdct_shrink(T* coef, const T* cmat, const T* u_in, T* u_out, T* tprev, const T* t_imp,
+                               double* partials, int blocks, int N, int M, T tau, int flags, cudaStream_t s);
 
 }  // namespace cip

@@ -1,0 +1,323 @@
+// Kronecker analysis prior T = W (x) C (Section V): W the 2D periodic Symmlet-8 wavelet transform
+// of every channel (Mallat levels down to a 16 x 16 coarse band), C the orthonormal DCT-II along
+// the channels.  T is orthonormal, so the x-update is that of Eq. solx_Trans_DFT with g = 1 and the
+// t-update is the soft threshold of Eq. solt_trans on the coefficients.
+//
+// The prior pass for this T is a chain of kernels over [M][N][N] planes (x from the row spectra,
+// the wavelet levels, the per-pixel channel DCT with shrinkage and dual update, the inverse levels,
+// the row spectra of q), because the wavelet is not local to a row tile.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "kernels.h"
+
+namespace cip {
+
+// ---------------------------------------------------------------------------------------------
+// Host: the Symmlet lowpass filter from its definition (Daubechies' spectral factorisation)
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+using cd = std::complex<double>;
+
+// roots of sum_k a[k] y^k (a[deg] != 0) by the Aberth-Ehrlich simultaneous iteration
+std::vector<cd> poly_roots(const std::vector<double>& a) {
+  const int n = (int)a.size() - 1;
+  std::vector<cd> z(n);
+  if (n < 1) return z;
+  double rad = 0;  // Cauchy bound on the root moduli
+  for (int k = 0; k < n; ++k) rad = std::max(rad, std::abs(a[k] / a[n]));
+  rad = 1 + rad;
+  for (int k = 0; k < n; ++k) z[k] = std::polar(0.5 * rad, 2 * M_PI * (k + 0.25) / n);
+  for (int it = 0; it < 500; ++it) {
+    double moved = 0;
+    for (int k = 0; k < n; ++k) {
+      cd p = a[n], dp = 0;
+      for (int j = n - 1; j >= 0; --j) {
+        dp = dp * z[k] + p;
+        p = p * z[k] + a[j];
+      }
+      const cd ratio = p / dp;
+      cd s = 0;
+      for (int j = 0; j < n; ++j)
+        if (j != k) s += 1.0 / (z[k] - z[j]);
+      const cd step = ratio / (1.0 - ratio * s);
+      z[k] -= step;
+      moved = std::max(moved, std::abs(step) / std::max(1.0, std::abs(z[k])));
+    }
+    if (moved < 1e-15) break;
+  }
+  return z;
+}
+
+std::vector<cd> poly_mul_linear(const std::vector<cd>& q, cd c0, cd c1) {  // q(w) * (c0 + c1 w)
+  std::vector<cd> r(q.size() + 1, cd(0));
+  for (size_t i = 0; i < q.size(); ++i) {
+    r[i] += q[i] * c0;
+    r[i + 1] += q[i] * c1;
+  }
+  return r;
+}
+
+}  // namespace
+
+// Orthonormal lowpass of 2p taps with p vanishing moments and the most nearly linear phase:
+// |m0|^2 = cos^{2p}(w/2) P(sin^2(w/2)), P(y) = sum_{k<p} C(p-1+k, k) y^k; every root y of P gives
+// the pair z, 1/z of z^2 - 2(1 - 2y) z + 1 = 0, one of which is kept (conjugate y together); of all
+// choices the one whose factor Q(e^{iw}) = prod (1 - z e^{-iw}) has the smallest least-squares
+// deviation of its unwrapped phase from a line on [0, pi] (513 samples) is taken, and of the two
+// mirror images the one with the smaller energy centroid.  Returns false for p outside [1, 8].
+bool symlet_lowpass(int p, double* h) {
+  if (p < 1 || p > 8) return false;
+  std::vector<double> a(p);
+  double binom = 1;  // C(p-1+k, k)
+  for (int k = 0; k < p; ++k) {
+    if (k > 0) binom = binom * (p - 1 + k) / k;
+    a[k] = binom;
+  }
+  const std::vector<cd> ys = poly_roots(a);
+  std::vector<std::vector<cd>> groups;
+  std::vector<bool> used(ys.size(), false);
+  for (size_t i = 0; i < ys.size(); ++i) {
+    if (used[i]) continue;
+    used[i] = true;
+    const cd w = 1.0 - 2.0 * ys[i];
+    cd z = w + std::sqrt(w * w - 1.0);
+    if (std::abs(z) >= 1) z = 1.0 / z;
+    if (std::abs(ys[i].imag()) <= 1e-9 * std::max(1.0, std::abs(ys[i]))) {
+      groups.push_back({cd(z.real(), 0)});
+    } else {
+      size_t j = ys.size();
+      double best = 1e300;
+      for (size_t k = 0; k < ys.size(); ++k)
+        if (!used[k] && std::abs(ys[k] - std::conj(ys[i])) < best) {
+          best = std::abs(ys[k] - std::conj(ys[i]));
+          j = k;
+        }
+      if (j == ys.size()) return false;
+      used[j] = true;
+      groups.push_back({z, std::conj(z)});
+    }
+  }
+  const int L = 2 * p, K = 512;
+  double best_dev = 1e300, best_cen = 1e300;
+  std::vector<double> best_h(L);
+  for (int pick = 0; pick < (1 << groups.size()); ++pick) {
+    std::vector<cd> roots;
+    for (size_t b = 0; b < groups.size(); ++b)
+      for (const cd& z : groups[b]) roots.push_back(((pick >> b) & 1) ? 1.0 / z : z);
+    // h(w) = prod (1 - r w) (1 + w)^p in powers of w = z^-1, scaled to sum sqrt(2)
+    std::vector<cd> q{cd(1)};
+    for (const cd& r : roots) q = poly_mul_linear(q, 1.0, -r);
+    for (int k = 0; k < p; ++k) q = poly_mul_linear(q, 1.0, 1.0);
+    double sum = 0;
+    for (const cd& c : q) sum += c.real();
+    std::vector<double> hh(L);
+    for (int n = 0; n < L; ++n) hh[n] = q[n].real() * std::sqrt(2.0) / sum;
+    // unwrapped phase of Q on [0, pi] and its deviation from the least-squares line
+    std::vector<double> om(K + 1), ph(K + 1);
+    for (int k = 0; k <= K; ++k) {
+      om[k] = M_PI * k / K;
+      cd Q = 1;
+      for (const cd& r : roots) Q *= 1.0 - r * std::polar(1.0, -om[k]);
+      double v = std::arg(Q);
+      if (k > 0) {
+        while (v - ph[k - 1] > M_PI) v -= 2 * M_PI;
+        while (v - ph[k - 1] < -M_PI) v += 2 * M_PI;
+      }
+      ph[k] = v;
+    }
+    double sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (int k = 0; k <= K; ++k) {
+      sx += om[k];
+      sy += ph[k];
+      sxx += om[k] * om[k];
+      sxy += om[k] * ph[k];
+    }
+    const double n1 = K + 1, slope = (n1 * sxy - sx * sy) / (n1 * sxx - sx * sx), icpt = (sy - slope * sx) / n1;
+    double dev = 0, cen = 0;
+    for (int k = 0; k <= K; ++k) dev += (ph[k] - icpt - slope * om[k]) * (ph[k] - icpt - slope * om[k]);
+    for (int n = 0; n < L; ++n) cen += n * hh[n] * hh[n];
+    const bool tie = std::abs(dev - best_dev) <= 1e-6 * std::max(1.0, best_dev);
+    if ((!tie && dev < best_dev) || (tie && cen < best_cen)) {
+      best_dev = tie ? std::min(dev, best_dev) : dev;
+      best_cen = cen;
+      best_h = hh;
+    }
+  }
+  for (int n = 0; n < L; ++n) h[n] = best_h[n];
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device: one level of the periodic DWT along rows or columns of the n x n coarse band
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// forward: out index i < n/2 lowpass a_i = sum_k h_k in[(2i + k) mod n], i >= n/2 highpass (g)
+template <typename T, bool COLS>
+__global__ void __launch_bounds__(256) dwt_fwd_kernel(const T* __restrict__ in, T* __restrict__ out, int N, int n,
+                                                      WaveFilt<T> f) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const size_t base = (size_t)blockIdx.y * N * N;
+  const int r = idx / n, c = idx - r * n;       // output row, column inside the band
+  const int o = COLS ? r : c;                    // output index along the transformed axis
+  const bool hi = o >= n / 2;
+  const int i2 = 2 * (hi ? o - n / 2 : o);
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int j = (i2 + k) & (n - 1);
+    const T v = COLS ? in[base + (size_t)j * N + c] : in[base + (size_t)r * N + j];
+    acc = fma(hi ? f.g[k] : f.h[k], v, acc);
+  }
+  out[base + (size_t)r * N + c] = acc;
+}
+
+// inverse (transpose): x_j = sum over k = j mod 2 of h_k a_i + g_k d_i, i = ((j - k) mod n) / 2
+template <typename T, bool COLS>
+__global__ void __launch_bounds__(256) dwt_inv_kernel(const T* __restrict__ in, T* __restrict__ out, int N, int n,
+                                                      WaveFilt<T> f) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const size_t base = (size_t)blockIdx.y * N * N;
+  const int r = idx / n, c = idx - r * n;
+  const int j = COLS ? r : c;
+  const int half = n / 2;
+  T acc = T(0);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int k = (j & 1) + 2 * t;  // taps with k = j (mod 2); n >= 32 > 16 keeps j - k + n >= 0
+    const int i = ((j - k + n) & (n - 1)) >> 1;
+    const T a = COLS ? in[base + (size_t)i * N + c] : in[base + (size_t)r * N + i];
+    const T d = COLS ? in[base + (size_t)(half + i) * N + c] : in[base + (size_t)r * N + half + i];
+    acc = fma(f.h[k], a, acc);
+    acc = fma(f.g[k], d, acc);
+  }
+  out[base + (size_t)r * N + c] = acc;
+}
+
+// Per pixel over the M channels: w = C c (channel DCT), then Eq. solt_trans / Eq. subu_trans on
+// w (or t = t_imp in import mode), q = t - u', and c <- C^T q in place.  Residual partial sums
+// per block (the same five sums and order as the other prior passes) into partials[block].
+template <typename T>
+__global__ void __launch_bounds__(256) wdct_shrink_kernel(T* __restrict__ coef, const T* __restrict__ cmat,
+                                                          const T* __restrict__ u_in, T* __restrict__ u_out,
+                                                          T* __restrict__ tprev, const T* __restrict__ t_imp,
+                                                          double* __restrict__ partials, int N, int M, T tau,
+                                                          int flags) {
+  __shared__ T cs[256];
+  __shared__ double red[8][kNPart];
+  for (int i = threadIdx.x; i < M * M; i += blockDim.x) cs[i] = cmat[i];
+  __syncthreads();
+  const bool import_mode = (flags & PA_IMPORT) != 0;
+  const bool resid = (flags & PA_RESID) != 0;
+  const bool store_t = (flags & PA_STORE_T) != 0;
+  const size_t plane = (size_t)N * N;
+  T part[kNPart] = {T(0), T(0), T(0), T(0), T(0)};
+  for (size_t pix = (size_t)blockIdx.x * blockDim.x + threadIdx.x; pix < plane; pix += (size_t)gridDim.x * blockDim.x) {
+    T cin[16], q[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) cin[m] = (m < M && !import_mode) ? coef[(size_t)m * plane + pix] : T(0);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      q[k] = T(0);
+      if (k < M) {
+        T w = T(0);
+#pragma unroll
+        for (int m = 0; m < 16; ++m)
+          if (m < M) w = fma(cs[k * M + m], cin[m], w);
+        const size_t g = (size_t)k * plane + pix;
+        const T uo = u_in[g];
+        T t, un;
+        if (import_mode) {
+          t = t_imp[g];
+          un = uo;
+          w = T(0);
+        } else {
+          const T v = w + uo;
+          t = v > tau ? v - tau : (v < -tau ? v + tau : T(0));
+          un = uo + w - t;
+        }
+        u_out[g] = un;
+        if (resid) {
+          const T r = w - t;
+          part[0] = fma(r, r, part[0]);
+          part[1] = fma(w, w, part[1]);
+          part[2] = fma(t, t, part[2]);
+          part[3] = fma(un, un, part[3]);
+          const T dt = t - tprev[g];
+          part[4] = fma(dt, dt, part[4]);
+        }
+        if (store_t) tprev[g] = t;
+        q[k] = t - un;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      if (m < M) {
+        T x = T(0);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (k < M) x = fma(cs[k * M + m], q[k], x);
+        coef[(size_t)m * plane + pix] = x;
+      }
+    }
+  }
+  if (!resid) return;
+  double s[kNPart];
+#pragma unroll
+  for (int i = 0; i < kNPart; ++i) {
+    s[i] = (double)part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+  }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int i = 0; i < kNPart; ++i) red[warp][i] = s[i];
+  __syncthreads();
+  if (threadIdx.x < kNPart) {
+    double acc = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
+    partials[(size_t)blockIdx.x * kNPart + threadIdx.x] = acc;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_dwt_level(const T* in, T* out, int N, int n, int M, bool cols, bool inverse,
+                             const WaveFilt<T>& f, cudaStream_t s) {
+  if (n < 32 || n > N || (n & (n - 1))) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((n * n + 255) / 256), (unsigned)M), block(256);
+  if (!inverse) {
+    if (cols) dwt_fwd_kernel<T, true><<<grid, block, 0, s>>>(in, out, N, n, f);
+    else dwt_fwd_kernel<T, false><<<grid, block, 0, s>>>(in, out, N, n, f);
+  } else {
+    if (cols) dwt_inv_kernel<T, true><<<grid, block, 0, s>>>(in, out, N, n, f);
+    else dwt_inv_kernel<T, false><<<grid, block, 0, s>>>(in, out, N, n, f);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_wdct_shrink(T* coef, const T* cmat, const T* u_in, T* u_out, T* tprev, const T* t_imp,
+                               double* partials, int blocks, int N, int M, T tau, int flags, cudaStream_t s) {
+  if (M < 1 || M > 16 || blocks < 1) return cudaErrorInvalidValue;
+  wdct_shrink_kernel<T><<<blocks, 256, 0, s>>>(coef, cmat, u_in, u_out, tprev, t_imp, partials, N, M, tau, flags);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_dwt_level<float>(const float*, float*, int, int, int, bool, bool, const WaveFilt<float>&,
+                                             cudaStream_t);
+template cudaError_t launch_dwt_level<double>(const double*, double*, int, int, int, bool, bool,
+                                              const WaveFilt<double>&, cudaStream_t);
+template cudaError_t launch_wdct_shrink<float>(float*, const float*, const float*, float*, float*, const float*,
+                                               double*, int, int, int, float, int, cudaStream_t);
+template cudaError_t launch_wdct_shrink<double>(double*, const double*, const double*, double*, double*,
+                                                const double*, double*, int, int, int, double, int, cudaStream_t);
+
+}  // namespace cip

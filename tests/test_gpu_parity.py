@@ -93,6 +93,12 @@ STEP_CASES = [
     ("tv_iso", 64, 3, 3, "f64", 1e-2, 1.0, "gauss", (0, 1, 10, 49)),   # isotropic TV (reading R20)
     ("tv_iso", 64, 3, 3, "f32", 1e-2, 1.0, "gauss", (0, 1, 10, 49)),
     ("tv_iso", 512, 5, 5, "f32", 1e-2, 1.0, "disk", (0, 1, 10)),
+    # Kronecker Symmlet-8 (x) channel DCT (Section V, readings R24-R26)
+    ("wdct", 64, 3, 3, "f64", 1e-2, 0.5, "disk", (0, 1, 10, 40)),
+    ("wdct", 64, 3, 3, "f32", 1e-2, 0.5, "disk", (0, 1, 10, 40)),
+    ("wdct", 512, 10, 10, "f32", 1e-3, 1e-2, "disk", (0, 1, 10)),
+    ("wdct", 128, 2, 16, "f32", 1e-2, 0.5, "gauss", (0, 5)),    # 16 channels
+    ("wdct", 256, 1, 1, "f32", 1e-2, 0.5, "gauss", (0, 5)),     # one channel (C = 1)
 ]
 
 
@@ -320,3 +326,44 @@ def test_isotropic_tv_full_run(torch, dtype):
     assert rel(x, x_or) <= FINAL_TOL[dtype], rel(x, x_or)
     assert rel(x_an, x_or) > 100 * FINAL_TOL["f32"]  # the isotropic iterates really differ
     plan.close()
+
+
+@pytest.mark.parametrize("dtype,N,M,iters", [("f64", 64, 3, 50), ("f32", 128, 5, 60)])
+def test_wdct_full_run(torch, dtype, N, M, iters):
+    """Kronecker wavelet (x) DCT prior: free-running iterations from t = u = 0 against the FP64
+    oracle, final x within FINAL_TOL (1e-9 for the FP64 path: the wavelet chain rounds more often)."""
+    rng, h, y = problem(77 + N, N, M, M, "disk")
+    S = fast.analysis_setup(h, y, "wdct", 1e-2, 0.5, 1.0)
+    x_or = fast.run_analysis(S, iters)[0]
+    P = make_plan(torch, h, y, "wdct", 1e-2, 0.5, 1.0, dtype)
+    P.iterate(iters)
+    x = P.get_x().double().cpu().numpy()
+    P.close()
+    assert rel(x, x_or) <= (1e-9 if dtype == "f64" else FINAL_TOL["f32"]), rel(x, x_or)
+
+
+def test_wdct_tolerance_stop_matches_oracle(torch):
+    """The residual partial sums of the wavelet prior's shrinkage kernel: cip_iterate with tol stops
+    at the same check as the oracle (relative residuals of Eq. paramS, every 10 iterations)."""
+    rng, h, y = problem(5, 64, 3, 3, "gauss")
+    S = fast.analysis_setup(h, y, "wdct", 1e-2, 0.5, 1.0)
+    tol = 1e-3
+    t = np.zeros((3, 1, 64, 64))
+    u = np.zeros_like(t)
+    n_or = None
+    for it in range(1, 301):
+        x, t_new, u_new, w = fast.analysis_step(S, t, u)
+        if it % 10 == 0:
+            r = np.linalg.norm(w - t_new) / max(np.linalg.norm(w), np.linalg.norm(t_new))
+            s = np.linalg.norm(t_new - t) / np.linalg.norm(u_new)
+            if r < tol and s < tol:
+                n_or = it
+                break
+        t, u = t_new, u_new
+    assert n_or is not None
+    P = make_plan(torch, h, y, "wdct", 1e-2, 0.5, 1.0, "f64")
+    n = P.iterate(300, tol=tol)
+    r_rel, s_rel = P.residuals()
+    P.close()
+    assert n == n_or
+    assert r_rel < tol and s_rel < tol
