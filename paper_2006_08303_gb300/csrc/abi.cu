@@ -68,7 +68,7 @@ struct cip_plan {
   void* xcol = nullptr;                 // [H][M][CP] x-hat of the last x-update
   // Kronecker wavelet (x) DCT prior (CIP_PRIOR_WDCT): two [M][N][N] work planes, the channel DCT
   // matrix [M][M] and the Symmlet-8 lowpass
-  void* wbuf[2] = {nullptr, nullptr};
+  void* wbuf[3] = {nullptr, nullptr, nullptr};
   void* wcos = nullptr;
   double wfilt[16] = {};
   // online dictionary update (Section IV-B): sigma = 0 off.  While on, theta lives in the first L
@@ -224,9 +224,9 @@ template <typename T> cip_status alloc_state(cip_plan* p) {
     p->partials = nullptr;
   }
   if (p->prior == CIP_PRIOR_WDCT) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {  // coefficients, x / q, two lowpass bands of (N/2)^2 per channel
       free_ptr(p, p->wbuf[i]);
-      CIP_CUDA(p, dmalloc(p, &p->wbuf[i], real_elems(p, p->M) * sizeof(T)));
+      CIP_CUDA(p, dmalloc(p, &p->wbuf[i], real_elems(p, p->M) * sizeof(T) / (i == 2 ? 2 : 1)));
     }
     free_ptr(p, p->wcos);
     CIP_CUDA(p, dmalloc(p, &p->wcos, (size_t)p->M * p->M * sizeof(T)));
@@ -500,20 +500,31 @@ template <typename T> cip_status prior_pass(cip_plan* p, const PassAArgs<T>& a, 
   }
   int J = 0;
   while ((N >> (J + 1)) >= 16) ++J;  // levels down to a 16 x 16 coarse band
+  // A: coefficients (Mallat layout); B: x, later q; S0, S1: the lowpass band between levels
+  T* S[2] = {static_cast<T*>(p->wbuf[2]), static_cast<T*>(p->wbuf[2]) + real_elems(p, M) / 4};
+  const int hp = N / 2;
+  const size_t hplane = (size_t)hp * hp, plane = (size_t)N * N;
   if (!(a.flags & PA_IMPORT)) {
-    CIP_LAUNCH(p, (launch_row_c2r<T, T>(a.xh, A, N, M * N, a.tw, s)));
+    CIP_LAUNCH(p, (launch_row_c2r<T, T>(a.xh, B, N, M * N, a.tw, s)));
     for (int lev = 0; lev < J; ++lev) {
-      CIP_LAUNCH(p, launch_dwt_level<T>(A, B, N, N >> lev, M, false, false, f, s));
-      CIP_LAUNCH(p, launch_dwt_level<T>(B, A, N, N >> lev, M, true, false, f, s));
+      const T* src = lev == 0 ? B : S[(lev - 1) & 1];
+      const int sp = lev == 0 ? N : hp;
+      const size_t spl = lev == 0 ? plane : hplane;
+      const bool last = lev == J - 1;
+      CIP_LAUNCH(p, launch_dwt2_fwd<T>(src, sp, spl, A, N, last ? A : S[lev & 1], last ? N : hp,
+                                       last ? plane : hplane, N >> lev, M, f, s));
     }
   }
   CIP_LAUNCH(p, launch_wdct_shrink<T>(A, static_cast<const T*>(p->wcos), a.u_in, a.u_out, a.tprev, a.t_imp,
                                       a.partials, p->blocksA, N, M, a.tau, a.flags, s));
   for (int lev = J - 1; lev >= 0; --lev) {
-    CIP_LAUNCH(p, launch_dwt_level<T>(A, B, N, N >> lev, M, true, true, f, s));
-    CIP_LAUNCH(p, launch_dwt_level<T>(B, A, N, N >> lev, M, false, true, f, s));
+    const bool coarsest = lev == J - 1;
+    const T* ll = coarsest ? A : S[lev & 1];
+    T* dst = lev == 0 ? B : S[(lev - 1) & 1];
+    CIP_LAUNCH(p, launch_dwt2_inv<T>(ll, coarsest ? N : hp, coarsest ? plane : hplane, A, N, dst, lev == 0 ? N : hp,
+                                     lev == 0 ? plane : hplane, N >> lev, M, f, s));
   }
-  CIP_LAUNCH(p, (launch_row_r2c<T, T>(A, a.qh, N, M * N, (T)p->rho, a.tw, s)));
+  CIP_LAUNCH(p, (launch_row_r2c<T, T>(B, a.qh, N, M * N, (T)p->rho, a.tw, s)));
   return CIP_OK;
 }
 
@@ -1073,7 +1084,7 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv, p->wbuf[0], p->wbuf[1], p->wcos,
+  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv, p->wbuf[0], p->wbuf[1], p->wbuf[2], p->wcos,
                   p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)

@@ -166,11 +166,16 @@ template <typename T> struct WaveFilt {
 // Symmlet lowpass with p vanishing moments (2p taps) from the spectral factorisation; false if p
 // is outside [1, 8]
 bool symlet_lowpass(int p, double* h);
-// one level of the periodic DWT on the n x n coarse band of each of M planes [M][N][N]: along
-// rows (cols = false) or columns, forward or inverse; n a power of two, 32 <= n <= N
+// one level of the periodic 2D DWT (rows then columns) on the n x n band of each of M planes
+// (n a power of two, 32 <= n <= N).  Forward: band from `in` (pitch, plane stride) -> the three
+// detail subbands into det ([M][N][N], Mallat positions) and LL into `ll`.  Inverse: LL from `ll`
+// and the details from det -> the n x n band into `out`.
 template <typename T>
-cudaError_t launch_dwt_level(const T* in, T* out, int N, int n, int M, bool cols, bool inverse,
-                             const WaveFilt<T>& f, cudaStream_t s);
+cudaError_t launch_dwt2_fwd(const T* in, int in_pitch, size_t in_plane, T* det, int N, T* ll, int ll_pitch,
+                            size_t ll_plane, int n, int M, const WaveFilt<T>& f, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dwt2_inv(const T* ll, int ll_pitch, size_t ll_plane, const T* det, int N, T* out, int out_pitch,
+                            size_t out_plane, int n, int M, const WaveFilt<T>& f, cudaStream_t s);
 // per pixel: channel DCT (cmat [M][M], row k = frequency), shrinkage / dual update / residual
 // partials as the other prior passes (flags PA_*), q = t - u', coefficients <- C^T q in place
 template <typename T>

@@ -152,84 +152,123 @@ bool symlet_lowpass(int p, double* h) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Device: one level of the periodic DWT along rows or columns of the n x n coarse band
+// Device: one level of the periodic 2D DWT (rows then columns of the n x n band) per launch
 // ---------------------------------------------------------------------------------------------
 namespace {
 
-// forward: out index i < n/2 lowpass a_i = sum_k h_k in[(2i + k) mod n], i >= n/2 highpass (g)
-template <typename T, bool COLS>
-__global__ void __launch_bounds__(256) dwt_fwd_kernel(const T* __restrict__ in, T* __restrict__ out, int N, int n,
-                                                      WaveFilt<T> f) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * n) return;
-  const size_t base = (size_t)blockIdx.y * N * N;
-  const int r = idx / n, c = idx - r * n;       // output row, column inside the band
-  const int o = COLS ? r : c;                    // output index along the transformed axis
-  const bool hi = o >= n / 2;
-  const int i2 = 2 * (hi ? o - n / 2 : o);
-  T acc = T(0);
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int j = (i2 + k) & (n - 1);
-    const T v = COLS ? in[base + (size_t)j * N + c] : in[base + (size_t)r * N + j];
-    acc = fma(hi ? f.g[k] : f.h[k], v, acc);
+// Forward level: a CTA makes the 16 x 16 tile (i0, j0) of each of the four subbands from the
+// 46 x 46 input tile starting at (2 i0, 2 j0) (periodic in n): a_i = sum_k h_k x[(2i + k) mod n]
+// along the rows into shared memory, then the same along the columns.  The three detail subbands
+// go to det (Mallat positions of the band, pitch N, plane N^2); the LL subband to ll.
+template <typename T>
+__global__ void __launch_bounds__(256) dwt2_fwd_kernel(const T* __restrict__ in, int in_pitch, size_t in_plane,
+                                                       T* __restrict__ det, int N, T* __restrict__ ll, int ll_pitch,
+                                                       size_t ll_plane, int n, WaveFilt<T> f) {
+  __shared__ T S[46][47];
+  __shared__ T R[46][33];
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16, ch = blockIdx.z;
+  const int tid = threadIdx.x;
+  const T* src = in + (size_t)ch * in_plane;
+  for (int idx = tid; idx < 46 * 46; idx += 256) {
+    const int r = idx / 46, c = idx - r * 46;
+    S[r][c] = src[(size_t)((2 * i0 + r) & (n - 1)) * in_pitch + ((2 * j0 + c) & (n - 1))];
   }
-  out[base + (size_t)r * N + c] = acc;
+  __syncthreads();
+  for (int idx = tid; idx < 46 * 32; idx += 256) {
+    const int r = idx >> 5, o = idx & 31, oo = o & 15;
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(o < 16 ? f.h[k] : f.g[k], S[r][2 * oo + k], acc);
+    R[r][o] = acc;
+  }
+  __syncthreads();
+  const int half = n / 2;
+  for (int idx = tid; idx < 32 * 32; idx += 256) {
+    const int i = idx >> 5, o = idx & 31, ii = i & 15;
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(i < 16 ? f.h[k] : f.g[k], R[2 * ii + k][o], acc);
+    const int rb = i >> 4, cb = o >> 4, row = i0 + ii, col = j0 + (o & 15);
+    if (rb == 0 && cb == 0) ll[(size_t)ch * ll_plane + (size_t)row * ll_pitch + col] = acc;
+    else det[(size_t)ch * N * N + (size_t)(rb * half + row) * N + cb * half + col] = acc;
+  }
 }
 
-// inverse (transpose): x_j = sum over k = j mod 2 of h_k a_i + g_k d_i, i = ((j - k) mod n) / 2
-template <typename T, bool COLS>
-__global__ void __launch_bounds__(256) dwt_inv_kernel(const T* __restrict__ in, T* __restrict__ out, int N, int n,
-                                                      WaveFilt<T> f) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * n) return;
-  const size_t base = (size_t)blockIdx.y * N * N;
-  const int r = idx / n, c = idx - r * n;
-  const int j = COLS ? r : c;
-  const int half = n / 2;
-  T acc = T(0);
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const int k = (j & 1) + 2 * t;  // taps with k = j (mod 2); n >= 32 > 16 keeps j - k + n >= 0
-    const int i = ((j - k + n) & (n - 1)) >> 1;
-    const T a = COLS ? in[base + (size_t)i * N + c] : in[base + (size_t)r * N + i];
-    const T d = COLS ? in[base + (size_t)(half + i) * N + c] : in[base + (size_t)r * N + half + i];
-    acc = fma(f.h[k], a, acc);
-    acc = fma(f.g[k], d, acc);
+// Inverse level (the transpose): a CTA makes the 32 x 32 output tile (y0, x0) of the n x n band
+// from the 23 x 23 coefficient tiles of the four subbands starting at (y0/2 - 7, x0/2 - 7)
+// (periodic in n/2): x_j = sum over k = j mod 2 of h_k a_i + g_k d_i, i = (j - k)/2, first along
+// the columns, then along the rows.  LL comes from ll, the details from det (Mallat positions).
+template <typename T>
+__global__ void __launch_bounds__(256) dwt2_inv_kernel(const T* __restrict__ ll, int ll_pitch, size_t ll_plane,
+                                                       const T* __restrict__ det, int N, T* __restrict__ out,
+                                                       int out_pitch, size_t out_plane, int n, WaveFilt<T> f) {
+  __shared__ T C[4][23][24];  // subband rb * 2 + cb
+  __shared__ T V[2][32][24];  // after the column inverse: [cb][output row][coefficient column]
+  const int y0 = blockIdx.y * 32, x0 = blockIdx.x * 32, ch = blockIdx.z;
+  const int tid = threadIdx.x, half = n / 2;
+  for (int idx = tid; idx < 4 * 23 * 23; idx += 256) {
+    const int sb = idx / 529, rem = idx - sb * 529, a = rem / 23, b = rem - a * 23;
+    const int ri = (y0 / 2 - 7 + a + half) & (half - 1), ci = (x0 / 2 - 7 + b + half) & (half - 1);
+    const int rb = sb >> 1, cb = sb & 1;
+    C[sb][a][b] = sb == 0 ? ll[(size_t)ch * ll_plane + (size_t)ri * ll_pitch + ci]
+                          : det[(size_t)ch * N * N + (size_t)(rb * half + ri) * N + cb * half + ci];
   }
-  out[base + (size_t)r * N + c] = acc;
+  __syncthreads();
+  for (int idx = tid; idx < 2 * 32 * 23; idx += 256) {
+    const int cb = idx / (32 * 23), rem = idx - cb * 32 * 23, jj = rem / 23, b = rem - jj * 23;
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = (jj & 1) + 2 * t, a = (jj >> 1) - t + 7;
+      acc = fma(f.h[k], C[cb][a][b], acc);
+      acc = fma(f.g[k], C[2 + cb][a][b], acc);
+    }
+    V[cb][jj][b] = acc;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < 32 * 32; idx += 256) {
+    const int jj = idx >> 5, xx = idx & 31;
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = (xx & 1) + 2 * t, b = (xx >> 1) - t + 7;
+      acc = fma(f.h[k], V[0][jj][b], acc);
+      acc = fma(f.g[k], V[1][jj][b], acc);
+    }
+    out[(size_t)ch * out_plane + (size_t)(y0 + jj) * out_pitch + x0 + xx] = acc;
+  }
 }
 
 // Per pixel over the M channels: w = C c (channel DCT), then Eq. solt_trans / Eq. subu_trans on
 // w (or t = t_imp in import mode), q = t - u', and c <- C^T q in place.  Residual partial sums
 // per block (the same five sums and order as the other prior passes) into partials[block].
-template <typename T>
+template <typename T, int M>
 __global__ void __launch_bounds__(256) wdct_shrink_kernel(T* __restrict__ coef, const T* __restrict__ cmat,
                                                           const T* __restrict__ u_in, T* __restrict__ u_out,
                                                           T* __restrict__ tprev, const T* __restrict__ t_imp,
-                                                          double* __restrict__ partials, int N, int M, T tau,
-                                                          int flags) {
+                                                          double* __restrict__ partials, int N, T tau, int flags) {
   __shared__ T cs[256];
   __shared__ double red[8][kNPart];
   for (int i = threadIdx.x; i < M * M; i += blockDim.x) cs[i] = cmat[i];
   __syncthreads();
+  // read the matrix from shared memory at each use (volatile), so that the M^2 entries are not
+  // held in registers across the pixel loop
+  const volatile T* cv = cs;
   const bool import_mode = (flags & PA_IMPORT) != 0;
   const bool resid = (flags & PA_RESID) != 0;
   const bool store_t = (flags & PA_STORE_T) != 0;
   const size_t plane = (size_t)N * N;
   T part[kNPart] = {T(0), T(0), T(0), T(0), T(0)};
   for (size_t pix = (size_t)blockIdx.x * blockDim.x + threadIdx.x; pix < plane; pix += (size_t)gridDim.x * blockDim.x) {
-    T cin[16], q[16];
+    T cin[M], q[M];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) cin[m] = (m < M && !import_mode) ? coef[(size_t)m * plane + pix] : T(0);
+    for (int m = 0; m < M; ++m) cin[m] = import_mode ? T(0) : coef[(size_t)m * plane + pix];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      q[k] = T(0);
-      if (k < M) {
+    for (int k = 0; k < M; ++k) {
+      {
         T w = T(0);
 #pragma unroll
-        for (int m = 0; m < 16; ++m)
-          if (m < M) w = fma(cs[k * M + m], cin[m], w);
+        for (int m = 0; m < M; ++m) w = fma((T)cv[k * M + m], cin[m], w);
         const size_t g = (size_t)k * plane + pix;
         const T uo = u_in[g];
         T t, un;
@@ -257,14 +296,11 @@ __global__ void __launch_bounds__(256) wdct_shrink_kernel(T* __restrict__ coef, 
       }
     }
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      if (m < M) {
-        T x = T(0);
+    for (int m = 0; m < M; ++m) {
+      T x = T(0);
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-          if (k < M) x = fma(cs[k * M + m], q[k], x);
-        coef[(size_t)m * plane + pix] = x;
-      }
+      for (int k = 0; k < M; ++k) x = fma((T)cv[k * M + m], q[k], x);
+      coef[(size_t)m * plane + pix] = x;
     }
   }
   if (!resid) return;
@@ -289,32 +325,48 @@ __global__ void __launch_bounds__(256) wdct_shrink_kernel(T* __restrict__ coef, 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_dwt_level(const T* in, T* out, int N, int n, int M, bool cols, bool inverse,
-                             const WaveFilt<T>& f, cudaStream_t s) {
+cudaError_t launch_dwt2_fwd(const T* in, int in_pitch, size_t in_plane, T* det, int N, T* ll, int ll_pitch,
+                            size_t ll_plane, int n, int M, const WaveFilt<T>& f, cudaStream_t s) {
   if (n < 32 || n > N || (n & (n - 1))) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)((n * n + 255) / 256), (unsigned)M), block(256);
-  if (!inverse) {
-    if (cols) dwt_fwd_kernel<T, true><<<grid, block, 0, s>>>(in, out, N, n, f);
-    else dwt_fwd_kernel<T, false><<<grid, block, 0, s>>>(in, out, N, n, f);
-  } else {
-    if (cols) dwt_inv_kernel<T, true><<<grid, block, 0, s>>>(in, out, N, n, f);
-    else dwt_inv_kernel<T, false><<<grid, block, 0, s>>>(in, out, N, n, f);
-  }
+  const dim3 grid((unsigned)(n / 32), (unsigned)(n / 32), (unsigned)M);
+  dwt2_fwd_kernel<T><<<grid, 256, 0, s>>>(in, in_pitch, in_plane, det, N, ll, ll_pitch, ll_plane, n, f);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dwt2_inv(const T* ll, int ll_pitch, size_t ll_plane, const T* det, int N, T* out, int out_pitch,
+                            size_t out_plane, int n, int M, const WaveFilt<T>& f, cudaStream_t s) {
+  if (n < 32 || n > N || (n & (n - 1))) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)(n / 32), (unsigned)(n / 32), (unsigned)M);
+  dwt2_inv_kernel<T><<<grid, 256, 0, s>>>(ll, ll_pitch, ll_plane, det, N, out, out_pitch, out_plane, n, f);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_wdct_shrink(T* coef, const T* cmat, const T* u_in, T* u_out, T* tprev, const T* t_imp,
                                double* partials, int blocks, int N, int M, T tau, int flags, cudaStream_t s) {
-  if (M < 1 || M > 16 || blocks < 1) return cudaErrorInvalidValue;
-  wdct_shrink_kernel<T><<<blocks, 256, 0, s>>>(coef, cmat, u_in, u_out, tprev, t_imp, partials, N, M, tau, flags);
+  if (blocks < 1) return cudaErrorInvalidValue;
+  switch (M) {
+#define WS_CASE(m)                                                                                              \
+  case m:                                                                                                      \
+    wdct_shrink_kernel<T, m><<<blocks, 256, 0, s>>>(coef, cmat, u_in, u_out, tprev, t_imp, partials, N, tau, flags); \
+    break;
+    WS_CASE(1) WS_CASE(2) WS_CASE(3) WS_CASE(4) WS_CASE(5) WS_CASE(6) WS_CASE(7) WS_CASE(8)
+    WS_CASE(9) WS_CASE(10) WS_CASE(11) WS_CASE(12) WS_CASE(13) WS_CASE(14) WS_CASE(15) WS_CASE(16)
+#undef WS_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-template cudaError_t launch_dwt_level<float>(const float*, float*, int, int, int, bool, bool, const WaveFilt<float>&,
-                                             cudaStream_t);
-template cudaError_t launch_dwt_level<double>(const double*, double*, int, int, int, bool, bool,
-                                              const WaveFilt<double>&, cudaStream_t);
+template cudaError_t launch_dwt2_fwd<float>(const float*, int, size_t, float*, int, float*, int, size_t, int, int,
+                                            const WaveFilt<float>&, cudaStream_t);
+template cudaError_t launch_dwt2_fwd<double>(const double*, int, size_t, double*, int, double*, int, size_t, int, int,
+                                             const WaveFilt<double>&, cudaStream_t);
+template cudaError_t launch_dwt2_inv<float>(const float*, int, size_t, const float*, int, float*, int, size_t, int,
+                                            int, const WaveFilt<float>&, cudaStream_t);
+template cudaError_t launch_dwt2_inv<double>(const double*, int, size_t, const double*, int, double*, int, size_t,
+                                             int, int, const WaveFilt<double>&, cudaStream_t);
 template cudaError_t launch_wdct_shrink<float>(float*, const float*, const float*, float*, float*, const float*,
                                                double*, int, int, int, float, int, cudaStream_t);
 template cudaError_t launch_wdct_shrink<double>(double*, const double*, const double*, double*, double*,
