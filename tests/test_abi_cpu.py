@@ -37,6 +37,8 @@ def test_invalid_sizes_rejected_before_device_use(L):
     assert L.cip_plan_create(None, 64, 3, 3, 0, ctypes.byref(opt)) == 1
     assert L.cip_plan_create(ctypes.byref(h), 64, 3, 3, 7, ctypes.byref(opt)) == 1   # bad dtype
     assert L.cip_set_code_gradient_weight(None, 0.01) == 1                            # null plan
+    assert L.cip_set_dictionary_learning(None, 1.0, None) == 1                         # null plan
+    assert L.cip_get_dictionary(None, None, None) == 1
 
 
 def test_plan_bytes_accounts_for_factor_and_state(L):
