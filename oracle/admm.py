@@ -613,6 +613,106 @@ def convdict_step(C: ConvDictSetup, z: np.ndarray, t: np.ndarray, u: np.ndarray)
     return x, z_new, t_new, u_new
 
 
+# ---------------------------------------------------------------------------
+# 3D convolutional dictionary (Section IV-B, the 3D case of Alg. 2; readings R27-R28): L filters
+# d_l of Q x P x P taps (channel, row, column), one 3D code map z_l of S x N x N per filter,
+# x_s = sum_l (d_l (*)_3 z_l)_s with circular convolution along all three axes
+# ---------------------------------------------------------------------------
+def dft1_matrix(S: int, sign: int = -1) -> np.ndarray:
+    """S-point DFT matrix, entries exp(sign 2 pi i ((j k) mod S) / S)."""
+    j = np.arange(S)
+    return np.exp(sign * 2j * math.pi * ((j[:, None] * j[None, :]) % S) / S)
+
+
+def dft3(v: np.ndarray) -> np.ndarray:
+    """Unnormalised 3D DFT over the last three axes [..., S, N, N]: the 2D DFT of every slice,
+    then the 1D DFT along the channel axis (F_3D = F_1D (x) F_2D)."""
+    V = dft2(v)
+    return np.einsum("ks,...sab->...kab", dft1_matrix(v.shape[-3]), V)
+
+
+def idft3(V: np.ndarray) -> np.ndarray:
+    S = V.shape[-3]
+    W = np.einsum("sk,...kab->...sab", dft1_matrix(S, +1), V) / S
+    return idft2(W)
+
+
+def embed_filters3d(d: np.ndarray, N: int, S: int) -> np.ndarray:
+    """Q x P x P filters (centre (Q//2, P//2, P//2)) placed on the S x N x N torus with the centre
+    at (0, 0, 0) (reading R27)."""
+    L, Q, P, _ = d.shape
+    out = np.zeros((L, S, N, N))
+    for l in range(L):
+        for q in range(Q):
+            for i in range(P):
+                for j in range(P):
+                    out[l, (q - Q // 2) % S, (i - P // 2) % N, (j - P // 2) % N] += d[l, q, i, j]
+    return out
+
+
+@dataclass
+class ConvDict3DSetup:
+    N: int
+    M: int          # image channels S
+    L: int
+    lam: float
+    rho: float
+    beta: float
+    Pinv: np.ndarray    # [N, N, M, M] (I + beta Lambda^H Lambda)^{-1}
+    bhat: np.ndarray    # [M, N, N]
+    theta3: np.ndarray  # [L, M, N, N] 3D DFT of the embedded filters (kappa, w1, w2)
+
+
+def convdict3d_setup(h: np.ndarray, y: np.ndarray, d3: np.ndarray, lam: float, rho: float,
+                     beta: float) -> ConvDict3DSetup:
+    """Alg. 2 setup for 3D filters: the x-update factor is the 2D one (t = 1, Eq. solx_synt_DFT);
+    Theta_l is the 3D DFT of the embedded filter."""
+    K, M, N, _ = h.shape
+    if d3.shape[1] > M:
+        raise ValueError("filter depth Q must not exceed the channel count")
+    Lam = psf_spectra(h)
+    Pinv = np.linalg.inv(form_psi(Lam, np.ones((N, N)), 1.0, beta))
+    theta3 = dft3(embed_filters3d(d3, N, M))
+    return ConvDict3DSetup(N, M, d3.shape[0], lam, rho, beta, Pinv, rhs_bhat(Lam, y, beta), theta3)
+
+
+def convdict3d_step(C: ConvDict3DSetup, z: np.ndarray, t: np.ndarray, u: np.ndarray):
+    """One iteration of Alg. 2 with 3D filters, z, t, u [L, S, N, N]:
+    x: the last term of Eq. solx_synt_DFT is F~ D~ z = (F_1D^H (x) I) sum_l Theta_l F_3D z_l, i.e.
+       the 3D spectra multiplied and summed over l, then a 1D inverse DFT along the channel axis;
+    z: the normal equation Eq. solz, (rho I + D~^H D~) z = D~^H x + rho (t - u), is diagonal plus
+       rank one in every 3D bin (Sherman-Morrison, Eq. solz_DFT_SM with reading R10), with
+       D~^H x <-> conj(Theta_l) F_3D x;
+    t, u: Eqs. softADMM and subu_dic."""
+    S = C.M
+    Zh = dft3(z)                                                    # [L, S(kappa), N, N]
+    q = np.einsum("lkab,lkab->kab", C.theta3, Zh)                   # F_3D of D~ z
+    p = np.einsum("sk,kab->sab", dft1_matrix(S, +1), q) / S         # 2D spectra of (D~ z)_s
+    xhat = apply_per_bin(C.Pinv, C.bhat + p)
+    x = idft2(xhat).real
+    X3 = np.einsum("ks,sab->kab", dft1_matrix(S), xhat)             # F_3D x
+    c = C.theta3.conj() * X3[None] + C.rho * dft3(t - u)
+    v = np.empty_like(c)
+    for k in range(S):
+        for a in range(C.N):
+            for b in range(C.N):
+                v[:, k, a, b] = sherman_morrison(C.theta3[:, k, a, b], c[:, k, a, b], C.rho)
+    z_new = idft3(v).real
+    t_new = soft(z_new + u, C.lam / C.rho)
+    u_new = u + z_new - t_new
+    return x, z_new, t_new, u_new
+
+
+def run_convdict3d(C: ConvDict3DSetup, iters: int):
+    z = np.zeros((C.L, C.M, C.N, C.N))
+    t = np.zeros_like(z)
+    u = np.zeros_like(z)
+    x = None
+    for _ in range(iters):
+        x, z, t, u = convdict3d_step(C, z, t, u)
+    return x, z, t, u
+
+
 def run_convdict(C: ConvDictSetup, iters: int, keep_history: bool = False):
     """Alg. 2 from z^0 = t^0 = u^0 = 0 (reading R5)."""
     z = np.zeros((C.L, C.M, C.N, C.N))

@@ -243,6 +243,58 @@ def run_convdict_learn(h, y, d0, lam, rho, beta, sigma: float, iters: int):
     return x, z, t, u, ref.crop_filters(g, P)
 
 
+@dataclass
+class FastConvDict3D:
+    N: int
+    M: int
+    L: int
+    lam: float
+    rho: float
+    beta: float
+    Pinv: np.ndarray    # [N, H, M, M]
+    bhat: np.ndarray    # [N, H, M]
+    theta3: np.ndarray  # [L, S(kappa), N, H]
+
+
+def convdict3d_setup(h, y, d3, lam, rho, beta) -> FastConvDict3D:
+    """Same setup as oracle.admm.convdict3d_setup on the half spectrum (3D DFT = rfft2 of every
+    slice, then the full FFT along the channel axis)."""
+    K, M, N, _ = h.shape
+    Lam = np.moveaxis(rfft2(h), (0, 1), (2, 3))
+    Pinv = np.linalg.inv(np.eye(M) + beta * np.einsum("abki,abkj->abij", Lam.conj(), Lam))
+    Y = np.moveaxis(rfft2(y), 0, 2)
+    bhat = beta * np.einsum("abkm,abk->abm", Lam.conj(), Y)
+    theta3 = sfft.fft(rfft2(ref.embed_filters3d(d3, N, M)), axis=1)
+    return FastConvDict3D(N, M, d3.shape[0], lam, rho, beta, Pinv, bhat, theta3)
+
+
+def convdict3d_step(C: FastConvDict3D, z, t, u):
+    """Same steps as oracle.admm.convdict3d_step, z/t/u [L, S, N, N]."""
+    Zh = sfft.fft(rfft2(z), axis=1)                              # [L, S, N, H]
+    q = np.einsum("lkab,lkab->kab", C.theta3, Zh)
+    p = np.moveaxis(sfft.ifft(q, axis=0), 0, 2)                   # [N, H, S]
+    X = np.matmul(C.Pinv, (C.bhat + p)[..., None])[..., 0]       # [N, H, S]
+    x = irfft2(np.moveaxis(X, 2, 0), C.N)
+    X3 = sfft.fft(np.moveaxis(X, 2, 0), axis=0)                  # [S, N, H]
+    c = C.theta3.conj() * X3[None] + C.rho * sfft.fft(rfft2(t - u), axis=1)
+    dot = np.sum(C.theta3 * c, axis=0, keepdims=True)
+    nrm = np.sum(np.abs(C.theta3) ** 2, axis=0, keepdims=True)
+    v = (c - C.theta3.conj() * dot / (C.rho + nrm)) / C.rho
+    z_new = irfft2(sfft.ifft(v, axis=1), C.N)
+    t_new = ref.soft(z_new + u, C.lam / C.rho)
+    return x, z_new, t_new, u + z_new - t_new
+
+
+def run_convdict3d(C: FastConvDict3D, iters: int):
+    z = np.zeros((C.L, C.M, C.N, C.N))
+    t = np.zeros_like(z)
+    u = np.zeros_like(z)
+    x = None
+    for _ in range(iters):
+        x, z, t, u = convdict3d_step(C, z, t, u)
+    return x, z, t, u
+
+
 def run_convdict(C: FastConvDict, iters: int):
     z = np.zeros((C.L, C.M, C.N, C.N))
     t = np.zeros_like(z)

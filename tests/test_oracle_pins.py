@@ -673,3 +673,79 @@ def test_fast_wdct_matches_naive():
     xn = admm.run_analysis(S, 6)[0]
     xf = fast.run_analysis(F, 6)[0]
     assert rel(xf, xn) < 1e-11
+
+
+# ----------------------------------------------------------------- 3D convolutional dictionary
+def test_dft3_matches_library():
+    v = RNG.standard_normal((2, 3, 6, 6))
+    assert np.allclose(admm.dft3(v), np.fft.fftn(v, axes=(-3, -2, -1)), atol=1e-12)
+    assert np.allclose(admm.idft3(admm.dft3(v)).real, v, atol=1e-12)
+
+
+def conv3_brute(z, d3e):
+    """Circular 3D convolution by its definition: out[s,i,j] = sum d[q,a,b] z[s-q, i-a, j-b]."""
+    S, N, _ = z.shape
+    out = np.zeros_like(z)
+    for q in range(S):
+        for a in range(N):
+            for b in range(N):
+                if d3e[q, a, b] != 0.0:
+                    out += d3e[q, a, b] * np.roll(np.roll(np.roll(z, q, axis=0), a, axis=1), b, axis=2)
+    return out
+
+
+@pytest.fixture(scope="module")
+def cd3():
+    rng = np.random.default_rng(8)
+    N, K, S, L, Q, P = 6, 2, 3, 2, 3, 3
+    d3 = rng.standard_normal((L, Q, P, P))
+    h = random_psfs(rng, K, S, N)
+    y = rng.standard_normal((K, N, N))
+    C = admm.convdict3d_setup(h, y, d3, 0.1, 0.9, 1.7)
+    z, t, u = (rng.standard_normal((L, S, N, N)) for _ in range(3))
+    return dict(N=N, S=S, L=L, d3=d3, h=h, y=y, C=C, z=z, t=t, u=u)
+
+
+def test_convdict3d_x_and_z_update_dense(cd3):
+    """The 3D case of Section IV-B solved densely with the explicit circular 3D convolution
+    operator: x = argmin beta/2||y - Hx||^2 + 1/2||D~z - x||^2 and the normal equation Eq. solz
+    for z match the oracle's per-bin (1D inverse DFT along the channels, Sherman-Morrison) forms."""
+    N, S, L, d3, h, y, C = (cd3[k] for k in ("N", "S", "L", "d3", "h", "y", "C"))
+    z, t, u = cd3["z"], cd3["t"], cd3["u"]
+    de = admm.embed_filters3d(d3, N, S)
+    Dop = lambda zz: sum(conv3_brute(zz[l], de[l]) for l in range(L))
+    H = dense_operator(lambda v: admm.forward_H(v, h), (S, N, N))
+    D = dense_operator(Dop, (L, S, N, N))
+    A = np.concatenate([math.sqrt(C.beta) * H, np.eye(S * N * N)])
+    b = np.concatenate([math.sqrt(C.beta) * y.ravel(), Dop(z).ravel()])
+    x_ls = np.linalg.lstsq(A, b, rcond=None)[0].reshape(S, N, N)
+    A2 = np.concatenate([D, math.sqrt(C.rho) * np.eye(L * S * N * N)])
+    b2 = np.concatenate([x_ls.ravel(), math.sqrt(C.rho) * (t - u).ravel()])
+    z_ls = np.linalg.lstsq(A2, b2, rcond=None)[0].reshape(L, S, N, N)
+    x, z_new, t_new, u_new = admm.convdict3d_step(C, z, t, u)
+    assert rel(x, x_ls) < 1e-10
+    assert rel(z_new, z_ls) < 1e-9
+    assert np.allclose(u_new, u + z_new - t_new, atol=0)
+
+
+def test_convdict3d_with_one_channel_tap_is_the_2d_dictionary(cd8):
+    """Q = 1: a 3D filter with a single channel tap convolves every channel with the same 2D
+    filter, so Alg. 2 with 3D codes equals Alg. 2 with per-channel 2D codes."""
+    C2 = cd8["C"]
+    d = cd8["d"]
+    C3 = admm.convdict3d_setup(cd8["h"], cd8["y"], d[:, None], C2.lam, C2.rho, C2.beta)
+    z, t, u = cd8["z"], cd8["t"], cd8["u"]
+    for a, b in zip(admm.convdict3d_step(C3, z, t, u), admm.convdict_step(C2, z, t, u)):
+        assert rel(a, b) < 1e-11
+
+
+def test_fast_convdict3d_matches_naive(cd3):
+    C = cd3["C"]
+    F = fast.convdict3d_setup(cd3["h"], cd3["y"], cd3["d3"], C.lam, C.rho, C.beta)
+    z = np.zeros((cd3["L"], cd3["S"], cd3["N"], cd3["N"]))
+    t, u = np.zeros_like(z), np.zeros_like(z)
+    zn, tn, un = z, t, u
+    for _ in range(4):
+        xf, z, t, u = fast.convdict3d_step(F, z, t, u)
+        xn, zn, tn, un = admm.convdict3d_step(C, zn, tn, un)
+    assert rel(xf, xn) < 1e-11 and rel(z, zn) < 1e-11
