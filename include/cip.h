@@ -96,6 +96,12 @@ const char* cip_version(void);
 const char* cip_status_string(cip_status s);
 const char* cip_last_error(const cip_plan* plan); /* plan may be NULL: last error of plan creation */
 
+/* The wavelet lowpass filter of CIP_PRIOR_WDCT for p vanishing moments (Section V names p = 8,
+ * "Symmlet-8"): writes the 2p taps h[0..2p) of the orthonormal filter from Daubechies' spectral
+ * factorisation with the least-asymmetric root choice (the highpass is g_k = (-1)^k h_{2p-1-k}).
+ * Host computation only (no device use).  CIP_ERR_INVALID_ARG for a null h or p outside [1, 8]. */
+cip_status cip_wavelet_lowpass(int p, double* h);
+
 /* Create a plan for N x N images, K measurements, M channels (1 <= K, M <= 16;
  * N a power of two in [64, 2048]).  Allocates all device buffers on the
  * current device.  opt may be NULL. */

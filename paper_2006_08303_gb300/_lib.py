@@ -49,6 +49,7 @@ SIGNATURES = {
     "cip_server_destroy": (c_int, [c_void_p]),
     "cip_version": (c_char_p, []),
     "cip_status_string": (c_char_p, [c_int]),
+    "cip_wavelet_lowpass": (c_int, [c_int, P_double]),
     "cip_last_error": (c_char_p, [c_void_p]),
     "cip_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, ctypes.POINTER(cip_options)]),
     "cip_plan_destroy": (c_int, [c_void_p]),

@@ -68,6 +68,15 @@ def version() -> str:
     return _lib.load().cip_version().decode()
 
 
+def wavelet_lowpass(p: int = 8) -> np.ndarray:
+    """Lowpass taps of the wavelet prior's filter with p vanishing moments (cip_wavelet_lowpass)."""
+    h = (ctypes.c_double * (2 * p))()
+    st = _lib.load().cip_wavelet_lowpass(p, h)
+    if st != 0:
+        raise CipError(st, "cip_wavelet_lowpass: p must be in [1, 8]")
+    return np.array(h[:], dtype=np.float64)
+
+
 def plan_bytes(N: int, K: int, M: int, dtype: str = "f32", prior: str = "tv") -> int:
     return int(_lib.load().cip_plan_bytes(N, K, M, DTYPES[dtype], PRIORS[prior]))
 

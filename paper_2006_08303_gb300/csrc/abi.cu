@@ -951,6 +951,11 @@ extern "C" {
 
 const char* cip_version(void) { return "cip 0.1 (sm_103a)"; }
 
+cip_status cip_wavelet_lowpass(int p, double* h) {
+  if (!h || p < 1 || p > 8) return CIP_ERR_INVALID_ARG;
+  return symlet_lowpass(p, h) ? CIP_OK : CIP_ERR_INVALID_ARG;
+}
+
 const char* cip_status_string(cip_status s) {
   switch (s) {
     case CIP_OK: return "ok";

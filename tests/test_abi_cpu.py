@@ -2,6 +2,8 @@
 declares; argument checks that need no GPU.  CPU only (no compute call)."""
 import ctypes
 
+import numpy as np
+
 import pytest
 
 from paper_2006_08303_gb300 import _lib, build
@@ -50,3 +52,17 @@ def test_plan_bytes_accounts_for_factor_and_state(L):
     assert 3 * factor + lam64 < b < 1.5 * (3 * factor + lam64)
     assert L.cip_plan_bytes(100, 1, 1, 0, 0) == 0
     assert L.cip_plan_bytes(512, 10, 10, 1, 1) > b
+
+
+def test_wavelet_filter_of_the_library_matches_the_oracle(L):
+    """Host logic of the wavelet prior: the library builds its Symmlet filter itself (Aberth root
+    finding and its own phase-linearity selection); it must agree with the oracle's independent
+    construction (numpy roots, reading R24) for every supported number of vanishing moments."""
+    from oracle import admm
+    for p in range(1, 9):
+        h = (ctypes.c_double * (2 * p))()
+        assert L.cip_wavelet_lowpass(p, h) == 0
+        assert np.abs(np.array(h[:]) - admm.symlet_lowpass(p)).max() < 1e-12, p
+    h = (ctypes.c_double * 2)()
+    assert L.cip_wavelet_lowpass(0, h) == 1 and L.cip_wavelet_lowpass(9, h) == 1
+    assert L.cip_wavelet_lowpass(8, None) == 1
