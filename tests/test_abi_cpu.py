@@ -1,9 +1,9 @@
 """The C-ABI library builds, loads and exports every symbol include/cip.h
-declares; argument checks that need no GPU.  CPU only (no compute call)."""
+declares; argument checks and host-side logic that need no GPU.  CPU only (no device
+compute call)."""
 import ctypes
 
 import numpy as np
-
 import pytest
 
 from paper_2006_08303_gb300 import _lib, build
