@@ -985,6 +985,7 @@ size_t cip_plan_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior) {
   b += (size_t)K * M * N * P * 16;            // FP64 PSF spectra
   b += (size_t)kTwN * (16 + 2 * e) + N * 8;   // tables
   b += (size_t)(N / 2) * M * kNPart * 8 + 4096;
+  if (prior == CIP_PRIOR_WDCT) b += 5 * M * real / 2 + (size_t)M * M * e;  // wavelet work planes, DCT matrix
   return b;
 }
 

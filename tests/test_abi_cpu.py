@@ -52,6 +52,9 @@ def test_plan_bytes_accounts_for_factor_and_state(L):
     assert 3 * factor + lam64 < b < 1.5 * (3 * factor + lam64)
     assert L.cip_plan_bytes(100, 1, 1, 0, 0) == 0
     assert L.cip_plan_bytes(512, 10, 10, 1, 1) > b
+    # the wavelet prior adds its work planes: x / q and the coefficients (N^2 each) and two
+    # lowpass bands of (N/2)^2 per channel, plus the M x M channel DCT
+    assert L.cip_plan_bytes(512, 10, 10, 0, 5) - b == 10 * 512 * 512 * 4 * 5 // 2 + 100 * 4
 
 
 def test_wavelet_filter_of_the_library_matches_the_oracle(L):
