@@ -770,11 +770,16 @@ def dict_update(x: np.ndarray, z: np.ndarray, g: np.ndarray, e: np.ndarray, sigm
 
 
 def run_convdict_learn(h: np.ndarray, y: np.ndarray, d0: np.ndarray, lam: float, rho: float, beta: float,
-                       sigma: float, iters: int):
+                       sigma: float, iters: int, check_every: int = 0, tau: float = 2.0, mu: float = 10.0):
     """Alg. 2 with the online dictionary update after every iteration (reading R21): the x-, z-,
     t- and u-updates use the current filters g, then one filter-ADMM step updates (d, g, e) from
-    the new x and z.  From z = t = u = 0, g = the given unit-norm filters, e = 0.  Returns
-    (x, z, t, u, filters [L, P, P])."""
+    the new x and z.  From z = t = u = 0, g = the given unit-norm filters, e = 0.
+
+    check_every > 0 adapts sigma like rho (Section V applies the Eq. paramS rule to sigma too,
+    reading R29): after every check_every-th iteration, with r = ||d - g|| and
+    s = sigma ||g - g_prev||, sigma' = adapt_rho(sigma, r, s, tau, mu), and on a change the scaled
+    dual is rescaled, e <- e sigma / sigma', so that the multiplier sigma e is kept.
+    Returns (x, z, t, u, filters [L, P, P]), plus the sigma after each iteration when adapting."""
     P = d0.shape[-1]
     C = convdict_setup(h, y, d0, lam, rho, beta)
     g = embed_filters(d0, C.N)
@@ -783,11 +788,23 @@ def run_convdict_learn(h: np.ndarray, y: np.ndarray, d0: np.ndarray, lam: float,
     t = np.zeros_like(z)
     u = np.zeros_like(z)
     x = None
-    for _ in range(iters):
+    sigmas = []
+    for it in range(iters):
         C.theta = dft2(g)
         x, z, t_new, u = convdict_step(C, z, t, u)
         t = t_new
-        _, g, e = dict_update(x, z, g, e, sigma, P)
+        g_prev = g
+        d, g, e = dict_update(x, z, g, e, sigma, P)
+        if check_every > 0 and (it + 1) % check_every == 0:
+            r = float(np.linalg.norm(d - g))
+            s_ = sigma * float(np.linalg.norm(g - g_prev))
+            sigma_new = adapt_rho(sigma, r, s_, tau, mu)
+            if sigma_new != sigma:
+                e = e * (sigma / sigma_new)
+                sigma = sigma_new
+        sigmas.append(sigma)
+    if check_every > 0:
+        return x, z, t, u, crop_filters(g, P), sigmas
     return x, z, t, u, crop_filters(g, P)
 
 

@@ -225,8 +225,10 @@ def dict_update(x, z, g, e, sigma: float, P: int):
     return d, g_new, e + d - g_new
 
 
-def run_convdict_learn(h, y, d0, lam, rho, beta, sigma: float, iters: int):
-    """Same schedule as oracle.admm.run_convdict_learn.  Returns (x, z, t, u, filters [L, P, P])."""
+def run_convdict_learn(h, y, d0, lam, rho, beta, sigma: float, iters: int, check_every: int = 0,
+                       tau: float = 2.0, mu: float = 10.0):
+    """Same schedule as oracle.admm.run_convdict_learn (with the same optional adaptation of sigma).
+    Returns (x, z, t, u, filters [L, P, P]) plus the sigmas when adapting."""
     P = d0.shape[-1]
     C = convdict_setup(h, y, d0, lam, rho, beta)
     N = C.N
@@ -236,10 +238,22 @@ def run_convdict_learn(h, y, d0, lam, rho, beta, sigma: float, iters: int):
     t = np.zeros_like(z)
     u = np.zeros_like(z)
     x = None
-    for _ in range(iters):
+    sigmas = []
+    for it in range(iters):
         C.theta = np.moveaxis(rfft2(g), 0, 2)
         x, z, t, u = convdict_step(C, z, t, u)
-        _, g, e = dict_update(x, z, g, e, sigma, P)
+        g_prev = g
+        d, g, e = dict_update(x, z, g, e, sigma, P)
+        if check_every > 0 and (it + 1) % check_every == 0:
+            r = float(np.linalg.norm(d - g))
+            s_ = sigma * float(np.linalg.norm(g - g_prev))
+            sigma_new = ref.adapt_rho(sigma, r, s_, tau, mu)
+            if sigma_new != sigma:
+                e = e * (sigma / sigma_new)
+                sigma = sigma_new
+        sigmas.append(sigma)
+    if check_every > 0:
+        return x, z, t, u, ref.crop_filters(g, P), sigmas
     return x, z, t, u, ref.crop_filters(g, P)
 
 

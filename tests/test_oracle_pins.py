@@ -749,3 +749,48 @@ def test_fast_convdict3d_matches_naive(cd3):
         xf, z, t, u = fast.convdict3d_step(F, z, t, u)
         xn, zn, tn, un = admm.convdict3d_step(C, zn, tn, un)
     assert rel(xf, xn) < 1e-11 and rel(z, zn) < 1e-11
+
+
+# ----------------------------------------------------------------- adaptive sigma (filter ADMM)
+def test_sigma_adaptation_never_triggered_is_the_fixed_run(cd8):
+    C = cd8["C"]
+    args = (cd8["h"], cd8["y"], cd8["d"], C.lam, C.rho, C.beta, 2.0, 6)
+    fixed = admm.run_convdict_learn(*args)
+    adapt = admm.run_convdict_learn(*args, check_every=2, tau=2.0, mu=1e30)
+    assert all(s == 2.0 for s in adapt[5])
+    for a, b in zip(fixed, adapt[:5]):
+        assert np.array_equal(a, b)
+
+
+def test_sigma_adaptation_keeps_the_unscaled_multiplier(cd8):
+    """Reading R29: at a change of sigma the multiplier sigma e is kept.  An independent loop in
+    unscaled form (multiplier m; the filter step fed e = m / sigma, then m = sigma e') under the
+    same sigma schedule gives the oracle's iterates."""
+    C0 = cd8["C"]
+    h, y, d = cd8["h"], cd8["y"], cd8["d"]
+    iters, ce = 8, 2
+    x_a, z_a, t_a, u_a, f_a, sig = admm.run_convdict_learn(h, y, d, C0.lam, C0.rho, C0.beta, 2.0, iters,
+                                                           check_every=ce, tau=2.0, mu=1.01)
+    assert len(set(sig)) > 1  # the schedule really changes sigma
+    P = d.shape[-1]
+    C = admm.convdict_setup(h, y, d, C0.lam, C0.rho, C0.beta)
+    g = admm.embed_filters(d, C.N)
+    m = np.zeros_like(g)
+    z = np.zeros((C.L, C.M, C.N, C.N)); t = np.zeros_like(z); u = np.zeros_like(z)
+    sigma = 2.0
+    for it in range(iters):
+        C.theta = admm.dft2(g)
+        x, z, t, u = admm.convdict_step(C, z, t, u)
+        _, g, e_new = admm.dict_update(x, z, g, m / sigma, sigma, P)
+        m = sigma * e_new
+        sigma = sig[it]       # the schedule; m is left as it is
+    assert rel(admm.crop_filters(g, P), f_a) < 1e-12 and rel(x, x_a) < 1e-12
+
+
+def test_fast_sigma_adaptation_matches_naive(cd8):
+    C = cd8["C"]
+    args = (cd8["h"], cd8["y"], cd8["d"], C.lam, C.rho, C.beta, 2.0, 6)
+    n = admm.run_convdict_learn(*args, check_every=2, tau=2.0, mu=1.01)
+    f = fast.run_convdict_learn(*args, check_every=2, tau=2.0, mu=1.01)
+    assert n[5] == f[5]
+    assert rel(f[4], n[4]) < 1e-10 and rel(f[0], n[0]) < 1e-10
