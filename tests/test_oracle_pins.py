@@ -794,3 +794,19 @@ def test_fast_sigma_adaptation_matches_naive(cd8):
     f = fast.run_convdict_learn(*args, check_every=2, tau=2.0, mu=1.01)
     assert n[5] == f[5]
     assert rel(f[4], n[4]) < 1e-10 and rel(f[0], n[0]) < 1e-10
+
+
+def test_convdict_x_update_minimises_the_synthesis_objective(cd8):
+    """Reading R9: the x-update of Alg. 2 (Eq. solx_synt_DFT, t = 1) is the minimiser over x of
+    beta/2 ||y - Hx||^2 + 1/2 ||D~z - x||^2 (+ lam ||z||_1, constant in x): perturbations of x
+    raise the objective, by the quadratic amount the Hessian beta H^T H + I predicts."""
+    C = cd8["C"]
+    z, t, u = cd8["z"], cd8["t"], cd8["u"]
+    x, _, _, _ = admm.convdict_step(C, z, t, u)
+    f = lambda xx: admm.convdict_objective(xx, z, cd8["d"], cd8["h"], cd8["y"], C.lam, C.beta)
+    f0 = f(x)
+    rng = np.random.default_rng(21)
+    for _ in range(5):
+        dx = 1e-2 * rng.standard_normal(x.shape)
+        quad = 0.5 * C.beta * float(np.sum(admm.forward_H(dx, cd8["h"]) ** 2)) + 0.5 * float(np.sum(dx * dx))
+        assert abs(f(x + dx) - f0 - quad) < 1e-9 * max(1.0, abs(f0))
