@@ -810,3 +810,54 @@ def test_convdict_x_update_minimises_the_synthesis_objective(cd8):
         dx = 1e-2 * rng.standard_normal(x.shape)
         quad = 0.5 * C.beta * float(np.sum(admm.forward_H(dx, cd8["h"]) ** 2)) + 0.5 * float(np.sum(dx * dx))
         assert abs(f(x + dx) - f0 - quad) < 1e-9 * max(1.0, abs(f0))
+
+
+def test_filter_admm_reaches_a_kkt_point_and_the_printed_dual_sign_diverges():
+    """Reading R22.  For fixed x and codes z, repeating the filter step with e <- e + d - g reaches
+    a fixed point that satisfies the optimality conditions of Eq. Constrained2: d = g, g on the
+    P x P support with unit norm, and the multiplier sigma e equal to Z^H (x - Z g) (the d-step's
+    normal equation at d = g), the same multiplier for two values of sigma.  With the sign as
+    printed (e <- e + g - d) the same iteration diverges."""
+    rng = np.random.default_rng(2)
+    N, L, S, P = 16, 3, 2, 5
+    z = rng.standard_normal((L, S, N, N)) * (rng.random((L, S, N, N)) < 0.1)
+    x = rng.standard_normal((S, N, N))
+    g0 = admm.project_filters(rng.standard_normal((L, N, N)), P)
+    mult = []
+    for sigma in (100.0, 1000.0):
+        g, e = g0.copy(), np.zeros_like(g0)
+        for _ in range(2000):
+            d, g, e = fast.dict_update(x, z, g, e, sigma, P)
+        assert rel(d, g) < 1e-10
+        assert np.allclose(np.sqrt(np.sum(admm.crop_filters(g, P) ** 2, axis=(1, 2))), 1.0)
+        mask = admm.embed_filters(np.ones((1, P, P)), N)[0] != 0
+        assert np.all(g[:, ~mask] == 0)
+        r = x - np.stack([sum(admm.circconv2(z[l, s], g[l]) for l in range(L)) for s in range(S)])
+        zh_r = np.stack([sum(admm.circcorr2(r[s], z[l, s]) for s in range(S)) for l in range(L)])
+        assert rel(sigma * e, zh_r) < 1e-8
+        mult.append(sigma * e)
+    assert rel(mult[0], mult[1]) < 1e-8
+    g, e = g0.copy(), np.zeros_like(g0)
+    for _ in range(300):
+        d, g_new, _ = fast.dict_update(x, z, g, e, 100.0, P)
+        e = e + g_new - d
+        g = g_new
+    assert np.linalg.norm(e) > 1e6 * np.linalg.norm(mult[0]) / 100.0
+
+
+def test_convdict3d_x_update_is_stationary(cd3):
+    """3D case of the x-update: beta/2 ||y - Hx||^2 + 1/2 ||D~z - x||^2 with D~ the circular 3D
+    convolution is minimised (first-order term zero, quadratic term as the Hessian predicts)."""
+    C, N, S, L = cd3["C"], cd3["N"], cd3["S"], cd3["L"]
+    z = cd3["z"]
+    x, _, _, _ = admm.convdict3d_step(C, z, cd3["t"], cd3["u"])
+    de = admm.embed_filters3d(cd3["d3"], N, S)
+    Dz = sum(conv3_brute(z[l], de[l]) for l in range(L))
+    f = lambda xx: 0.5 * C.beta * float(np.sum((cd3["y"] - admm.forward_H(xx, cd3["h"])) ** 2)) + \
+        0.5 * float(np.sum((Dz - xx) ** 2))
+    f0 = f(x)
+    rng = np.random.default_rng(4)
+    for _ in range(4):
+        dx = 1e-2 * rng.standard_normal(x.shape)
+        quad = 0.5 * C.beta * float(np.sum(admm.forward_H(dx, cd3["h"]) ** 2)) + 0.5 * float(np.sum(dx * dx))
+        assert abs(f(x + dx) - f0 - quad) < 1e-9 * max(1.0, abs(f0))
