@@ -32,10 +32,29 @@ sys.path.insert(0, ROOT)
 N, M, K, ITERS = 512, 10, 10, 200
 WORKLOAD = f"spectral_dct_{N}x{N}x{M} (K={K}, 8x8 DCT l1, lambda=1e-3, rho=1e-2, beta=1, {ITERS} iterations)"
 METRIC = "ADMM voxel-iter/s"
-# DRAM bytes (read + write) per launch of each pass on this workload, from one ncu capture of the
-# current kernels (profiles/passes_spectral_dct_512x512x10.md; the column pass is the sum of its
-# three split kernels).  Set an entry to None when its kernels change until they are re-captured.
-TRAFFIC_BYTES = {"column_pass": 102_307_000, "prior_pass": 21_200_000}
+# DRAM bytes (read + write) per launch of each pass on this workload, from one ncu capture, with
+# the hash of the kernel sources the capture was taken from (kernel_sources_hash()).  The figure
+# is reported only while the sources still hash to that value; any change to a kernel makes it
+# null until the kernels are captured again.
+TRAFFIC_CAPTURE = {"sources": None, "bytes": {}}
+KERNEL_SOURCES = ("colpass.cu", "passA.cu", "fft.cuh", "common.cuh", "kernels.h")
+
+
+def kernel_sources_hash() -> str:
+    """sha256 (16 hex digits) over the CUDA sources of the two passes of an iteration."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2006_08303_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str):
+    """ncu DRAM bytes per launch of `kernel`, or None when the capture predates the sources."""
+    if TRAFFIC_CAPTURE["sources"] != kernel_sources_hash():
+        return None
+    return TRAFFIC_CAPTURE["bytes"].get(kernel)
 
 
 def peaks():
@@ -162,29 +181,55 @@ def replica_throughput(local_ms: float, units_per_rank: float, dist=None, device
 
 
 def run_reference(args, rank, world):
+    """The oracle arm: the fast FP64 oracle on this host's cores, on the headline instance.  Its
+    setup runs once, untimed; each timed step is `--ref-iters` ADMM iterations of the instance,
+    so `steps` and `ms_per_step` are exactly what was timed and `value` is the iteration rate."""
+    from oracle import fast
     from paper_2006_08303_gb300 import inputs
     if rank != 0:
         return
     prob = inputs.spectral_dct()
-    vals = []
-    for _ in range(args.warmup):
-        cpu_oracle_sample(prob, 2)
     t0 = time.perf_counter()
+    S = fast.analysis_setup(prob.h, prob.y, prob.prior, prob.lam, prob.rho, prob.beta)
+    setup_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        fast.run_analysis(S, 1)
+    times = []
+    t_all = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_oracle_sample(prob, args.ref_iters))
-    wall = time.perf_counter() - t0
-    v = statistics.median([x["value"] for x in vals])
-    cb = dict(vals[0])
-    cb["value"] = v
+        t1 = time.perf_counter()
+        fast.run_analysis(S, args.ref_iters)
+        times.append(time.perf_counter() - t1)
+    wall = time.perf_counter() - t_all
+    ms = 1e3 * sum(times) / len(times)
+    v = prob.voxels * args.ref_iters / (ms / 1e3)
+    cb = {"value": v, "unit": "voxel-iter/s", "cores": os.cpu_count(), "cpu_model": _cpu_model(),
+          "kind": "oracle",
+          "sample": f"fast FP64 oracle (scipy.fft, {fast.WORKERS} workers): {args.ref_iters} iterations of the "
+                    f"{prob.N}x{prob.N}x{prob.M} instance per step (setup once, untimed: {setup_s:.2f} s)"}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "voxel-iter/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * prob.voxels * prob.iters / v, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N, "M": M, "K": K, "iters": ITERS},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "M": M, "K": K, "iters": ITERS,
+                       "step": f"{args.ref_iters} ADMM iterations (setup excluded)"},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
+
+
+def oracle_final_error(prob, x_gpu: np.ndarray):
+    """Relative L2 error of the reconstruction after prob.iters iterations against the fast FP64
+    oracle run in full on this host (the accuracy half of the metric)."""
+    from oracle import fast
+    t0 = time.perf_counter()
+    S = fast.analysis_setup(prob.h, prob.y, prob.prior, prob.lam, prob.rho, prob.beta)
+    x_or = fast.run_analysis(S, prob.iters)[0]
+    dt = time.perf_counter() - t0
+    err = float(np.linalg.norm(x_gpu.astype(np.float64) - x_or) / np.linalg.norm(x_or))
+    return {"rel_err_final": err, "tolerance": 1e-4, "within_tolerance": err <= 1e-4,
+            "oracle": f"fast FP64 oracle, {prob.iters} iterations of the same instance on {os.cpu_count()} "
+                      f"host cores ({dt:.0f} s)"}
 
 
 # ---------------------------------------------------------------------------
@@ -566,6 +611,42 @@ def run_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def above_l2(torch, api, inputs, peak, iters=50):
+    """The same spectral DCT model at 1024 x 1024 x 10: its per-iteration bytes (526 MB) are four
+    times the 129 MB L2, so the passes stream from HBM.  Iterations only (setup excluded), timed
+    with CUDA events on the launching stream after three warm-up iterations, then once more with
+    per-kernel events for the roofline of each pass."""
+    pr = inputs.spectral_dct(N=1024, M=10, iters=iters)
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+    P = api.Plan(pr.N, pr.K, pr.M, "f32")
+    P.set_prior(pr.prior, pr.lam, pr.rho, pr.beta)
+    P.set_psfs(f(pr.h))
+    P.set_measurements(f(pr.y))
+    P.iterate(3)
+    P.reset_state()
+    t = _ev_time(torch, lambda: P.iterate(iters))
+    P.set_timing(True)
+    P.iterate(iters)
+    kt = P.get_timing()
+    cfg = P.config()
+    P.close()
+    ab = algorithmic_bytes(pr.N, pr.M, pr.prior)
+    avg = {"column_pass": kt["column_pass_ms"] / max(kt["column_pass_n"], 1),
+           "prior_pass": kt["prior_pass_ms"] / max(kt["prior_pass_n"], 1)}
+    roof = {}
+    for k in ("column_pass", "prior_pass"):
+        a = ab[k] / (avg[k] / 1e3) / 1e9
+        roof[k] = {"bound": "hbm", "achieved": round(a, 1), "peak": peak, "unit": "GB/s", "frac": round(a / peak, 4),
+                   "avg_launch_us": round(avg[k] * 1e3, 2), "algorithmic_bytes": ab[k]}
+    per_iter = ab["column_pass"] + ab["prior_pass"]
+    return {"workload": f"spectral_dct_{pr.N}x{pr.N}x{pr.M} (same generators and parameters, {iters} iterations)",
+            "iterations_only": {"value": pr.voxels * iters / t, "unit": "voxel-iter/s", "ms": 1e3 * t},
+            "iteration_roofline": {"achieved": round(per_iter * iters / t / 1e9, 1), "peak": peak, "unit": "GB/s",
+                                   "frac": round(per_iter * iters / t / 1e9 / peak, 4),
+                                   "algorithmic_bytes_per_iteration": per_iter},
+            "roofline": roof, "launch": cfg}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -574,6 +655,8 @@ def main():
     ap.add_argument("--impl", default="cip", choices=["cip", "reference"])
     ap.add_argument("--ref-iters", type=int, default=10, help="iterations per oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the full FP64-oracle run behind rel_err_final")
+    ap.add_argument("--no-above-l2", action="store_true", help="skip the 1024 x 1024 x 10 sub-measurement")
     ap.add_argument("--workload", default="spectral_dct",
                     choices=["spectral_dct", "convdict", "dictlearn", "batch", "serve", "precision", "single",
                              "adaptive"])
@@ -706,7 +789,8 @@ def main():
     peak = pk["hbm_gbs"] if pk else 6800.0
     achieved = byts / (avg / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": TRAFFIC_BYTES.get(dom), "kernel": dom,
+            "frac": round(achieved / peak, 4), "traffic": measured_traffic(dom), "kernel": dom,
+            "kernel_sources": kernel_sources_hash(),
             "peak_source": "measured" if pk else "fallback",
             "avg_launch_us": {"column_pass": round(avgB * 1e3, 2), "prior_pass": round(avgA * 1e3, 2)},
             "algorithmic_bytes": ab,
@@ -727,8 +811,14 @@ def main():
                                 "note": "iterations phase alone (setup excluded), from the per-kernel timing pass"},
             "gpu_launches": int(launches) * args.steps,
             "clocks": clk}
+    if rank == 0 and not args.no_above_l2:
+        line["above_l2"] = above_l2(torch, api, inputs, peak)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(prob, args.ref_iters)
+    if rank == 0 and not args.no_accuracy:
+        acc = oracle_final_error(prob, x_dev.double().cpu().numpy())
+        line["rel_err_final"] = acc["rel_err_final"]
+        line["accuracy"] = acc
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -75,12 +75,15 @@ typedef enum cip_prior {
 } cip_prior;
 
 typedef struct cip_options {
-  int col_tile;     /* columns per CTA of the column pass (1, 2 or 4); 0 = automatic */
+  int col_tile;     /* accepted for compatibility (0, 1, 2 or 4); the fused column pass works on one
+                       half-spectrum column per CTA */
   int check_every;  /* residual check period for cip_iterate with tol > 0; 0 = 10 */
   int column_pass;  /* 0 = autotuned at cip_set_measurements (fused vs split, tile width; cached per
                        N, M, dtype for the process, and in the file named by the environment variable
                        CIP_TUNE_CACHE when set, one "N M dtype mode cc" line per decision, read on
-                       first use), 1 = fused cluster kernel, 2 = split (column FFT / solve / FFT) */
+                       first use), 1 = fused kernel (one CTA per half-spectrum column, factor
+                       streamed by TMA bulk copies; CIP_ERR_UNSUPPORTED where its tile does not fit
+                       in shared memory), 2 = split (column FFT / solve / FFT) */
   int precision;    /* CIP_F32 plans: 0 = mixed (factor and data term Psi^{-1} beta Lambda^H F y formed
                        in double-float, about 44 bits, rounded once; the default), 1 = plain FP32
                        method (factor formed and
@@ -145,6 +148,20 @@ cip_status cip_set_measurements(cip_plan* plan, const void* y, void* stream);
  * (Eq. softADMM) and u += z - t (Eq. subu_dic), from z = t = u = 0.  The ADMM variables
  * t, u and the coefficient maps z have shape [M][L][N][N] (channel-major). */
 cip_status cip_set_dictionary(cip_plan* plan, const void* filters, int L, int P, void* stream);
+
+/* Convolutional dictionary with 3D filters (Section IV-B, 3D case): filters d[L][Q][P][P] (plan
+ * dtype, centre at (Q/2, P/2, P/2), 1 <= L <= 32, 1 <= Q <= M), embedded on the M x N x N torus
+ * with the centre at (0,0,0) -- the convolution is circular along the channels too -- and one
+ * code map of M x N x N per filter, so t, u and z keep the [M][L][N][N] shape of the 2D
+ * dictionary.  Theta_l(kappa, w) is the 3D DFT of filter l (FP64-formed, rounded once); the
+ * x-update keeps the 2D factor (I + beta Lambda^H Lambda)^{-1} with its last term
+ * (F_1D^H (x) I) sum_l Theta_l F_3D z_l (Eq. solx_synt_DFT), and the z-update solves
+ * Eq. solz_DFT_SM by Sherman-Morrison in every 3D bin (kappa, w), with M-point DFTs along the
+ * channels around it.  Call after cip_set_prior(CIP_PRIOR_CONVDICT, ...) and before
+ * cip_set_psfs.  Q = 1 is the 2D dictionary.  CIP_ERR_UNSUPPORTED with the code gradient
+ * penalty or the online dictionary update on (both 2D only), or when M * L is too large for the
+ * per-bin tile. */
+cip_status cip_set_dictionary_3d(cip_plan* plan, const void* filters, int L, int Q, int P, void* stream);
 
 /* Gradient (Tikhonov) penalty on the codes of a CIP_PRIOR_CONVDICT plan (Section III-B,
  * "Convolutional Dictionary with Tikhonov Regularization", Eq. DL_PriorHP_conv in 2D):
@@ -243,6 +260,15 @@ cip_status cip_set_timing(cip_plan* plan, int on);
 cip_status cip_get_timing(cip_plan* plan, double* prior_pass_ms, int* prior_pass_n, double* column_pass_ms,
                           int* column_pass_n);
 
+/* Test-only fault switch for the bounded device waits (no counterpart in the paper).
+ * kind 1: the prior pass of CIP_PRIOR_DCT8 / CIP_PRIOR_L1 plans (at sizes whose u rows it stages
+ * in shared memory by a bulk copy) arms its copy barrier for two arrivals, gives one and issues no
+ * copy, then waits at most 64 polls: the wait gives up with nothing in flight, the kernel reads u
+ * from global memory instead (the iterate is unchanged) and flags the plan, so that
+ * cip_get_residuals (and the residual checks of cip_iterate) return CIP_ERR_TIMEOUT until the
+ * next state reset.  kind 0: off (the default).  CIP_ERR_INVALID_ARG for other kinds. */
+cip_status cip_set_test_fault(cip_plan* plan, int kind);
+
 /* Number of CUDA kernels this plan has launched since creation. */
 cip_status cip_get_launches(cip_plan* plan, unsigned long long* launches);
 
@@ -318,8 +344,11 @@ cip_status cip_server_destroy(cip_server* srv);
  * aliasing the inputs), and stores the relative residuals
  * {r/max(||Tx||,||t||), s/||rho u_out||}, r = ||Tx - t||,
  * s = rho ||t - t_prev||, into resid_out[2] (host or device pointer; a host
- * pointer makes the call synchronise the stream).  Same results as the prior
- * pass inside cip_iterate.
+ * pointer makes the call synchronise the stream, so while `stream` is being
+ * captured resid_out must be device memory: CIP_ERR_INVALID_ARG otherwise).
+ * Same results as the prior pass inside cip_iterate.  Each launch's own status
+ * is checked; an error the caller left pending is neither reported as this
+ * call's nor cleared.
  *
  * No cudaMalloc, cudaFree or other allocating call is made.  Its scratch
  * (per-block partial sums) is a fixed static device array of 1.25 MiB that

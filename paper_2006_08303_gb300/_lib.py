@@ -68,6 +68,7 @@ SIGNATURES = {
     "cip_state_export": (c_int, [c_void_p, c_void_p, c_void_p]),
     "cip_state_restore": (c_int, [c_void_p, c_void_p, c_void_p]),
     "cip_set_timing": (c_int, [c_void_p, c_int]),
+    "cip_set_test_fault": (c_int, [c_void_p, c_int]),
     "cip_get_timing": (c_int, [c_void_p, P_double, P_int, P_double, P_int]),
     "cip_get_config": (c_int, [c_void_p, P_int, P_int, P_int, P_int, P_int]),
     "cip_get_launches": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -76,6 +77,7 @@ SIGNATURES = {
     "cip_batch_last_error": (c_char_p, [c_void_p]),
     "cip_batch_destroy": (c_int, [c_void_p]),
     "cip_set_dictionary": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "cip_set_dictionary_3d": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
     "cip_set_code_gradient_weight": (c_int, [c_void_p, c_double]),
     "cip_set_dictionary_learning": (c_int, [c_void_p, c_double, c_void_p]),
     "cip_get_dictionary": (c_int, [c_void_p, c_void_p, c_void_p]),

@@ -124,6 +124,16 @@ class Plan:
         self.L = L
         self.filter_size = P
 
+    def set_dictionary_3d(self, filters, stream=None):
+        """3D filters [L][Q][P][P] of the convolutional dictionary (Section IV-B, 3D case;
+        cip_set_dictionary_3d), after set_prior('convdict', ...)."""
+        L, Q, P = int(filters.shape[0]), int(filters.shape[1]), int(filters.shape[-1])
+        p, keep = _ptr_and_check(filters, self.dtype, (L, Q, P, P))
+        self._check(self._L.cip_set_dictionary_3d(self._h, ctypes.c_void_p(p), L, Q, P, _stream_ptr(stream)))
+        self.L = L
+        self.filter_size = P
+        self.filter_depth = Q
+
     def set_rho_adaptation(self, tau: float = 2.0, mu: float = 10.0):
         """Adaptive penalty of Eq. paramS at the residual checks (tau = 0: off); call before
         set_measurements."""
@@ -262,6 +272,11 @@ class Plan:
 
     def set_timing(self, on: bool):
         self._check(self._L.cip_set_timing(self._h, 1 if on else 0))
+
+    def set_test_fault(self, kind: int):
+        """Test-only fault switch (cip_set_test_fault): 1 = the prior pass's staged-copy wait can
+        never complete and gives up after a few polls; 0 = off."""
+        self._check(self._L.cip_set_test_fault(self._h, int(kind)))
 
     def get_timing(self):
         a, b = ctypes.c_double(), ctypes.c_double()

@@ -21,13 +21,13 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = [
     ("abi.cu", [], "abi.o"),
     ("passA.cu", [], "passA.o"),
-    ("passB.cu", ["-DPASSB_T=float"], "passB_f32.o"),
-    ("passB.cu", ["-DPASSB_T=double"], "passB_f64.o"),
+    ("colpass.cu", [], "colpass.o"),
     ("fft_kernels.cu", [], "fft_kernels.o"),
     ("factor.cu", [], "factor.o"),
     ("noalloc.cu", [], "noalloc.o"),
     ("colsplit.cu", [], "colsplit.o"),
     ("convdict.cu", [], "convdict.o"),
+    ("convdict3d.cu", [], "convdict3d.o"),
     ("wavelet.cu", [], "wavelet.o"),
     ("serve.cu", [], "serve.o"),
 ]

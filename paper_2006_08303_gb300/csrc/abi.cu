@@ -59,9 +59,12 @@ struct cip_plan {
   int cur = 0;  // index of the u buffer holding the current u
   size_t esz = 4;
   int rowsA = 8, cc = 1, blocksA = 0, blocksB = 0;
-  int colmode = 1;  // column pass: 1 fused cluster kernel, 2 split (FFT / solve / FFT)
-  // convolutional dictionary (prior CIP_PRIOR_CONVDICT): L filters of P x P
-  int L = 0, Pf = 0;
+  int colmode = 1;  // column pass: 1 fused kernel, 2 split (FFT / solve / FFT)
+  int test_fault = 0;  // test-only fault switch (cip_set_test_fault)
+  // convolutional dictionary (prior CIP_PRIOR_CONVDICT): L filters of P x P, or of Q x P x P
+  // (3D dictionary, Q >= 1; Q = 0 for the 2D dictionary)
+  int L = 0, Pf = 0, Q = 0;
+  void* w3 = nullptr;                   // 3D dictionary: exp(-2 pi i j / M), j < M, FP64 (setup)
   void* theta = nullptr;                // [H][L][CP] DFT of the embedded filters
   void* pbuf[2] = {nullptr, nullptr};   // [H][M][CP] p = sum_l theta_l v_l (ping-pong)
   int pcur = 0;
@@ -202,8 +205,8 @@ template <typename T> cip_status alloc_state(cip_plan* p) {
     // row spectra of v and of rho (t - u) over the coefficient maps, the column buffer and p, x
     free_ptr(p, p->xh);
     free_ptr(p, p->qh);
-    CIP_CUDA(p, dmalloc(p, &p->xh, half_elems(p, S) * sizeof(C)));
-    CIP_CUDA(p, dmalloc(p, &p->qh, half_elems(p, S) * sizeof(C)));
+    CIP_CUDA(p, dmalloc(p, &p->xh, col_elems(p, S) * sizeof(C)));
+    CIP_CUDA(p, dmalloc(p, &p->qh, col_elems(p, S) * sizeof(C)));
     free_ptr(p, p->colbuf);
     CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, S) * sizeof(C)));
     for (int i = 0; i < 2; ++i) {
@@ -249,8 +252,8 @@ template <typename T> cip_status reset_state(cip_plan* p, cudaStream_t s) {
   using C = typename CT<T>::type;
   const size_t nc = ncomp_of(p->prior);
   const int S = smaps(p);
-  CIP_CUDA(p, cudaMemsetAsync(p->xh, 0, half_elems(p, S) * sizeof(C), s));
-  CIP_CUDA(p, cudaMemsetAsync(p->qh, 0, half_elems(p, S) * sizeof(C), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->xh, 0, col_elems(p, S) * sizeof(C), s));
+  CIP_CUDA(p, cudaMemsetAsync(p->qh, 0, col_elems(p, S) * sizeof(C), s));
   CIP_CUDA(p, cudaMemsetAsync(p->conv, 0, 2 * sizeof(int), s));
   CIP_CUDA(p, cudaMemsetAsync(p->u[0], 0, real_elems(p, S) * nc * sizeof(T), s));
   CIP_CUDA(p, cudaMemsetAsync(p->u[1], 0, real_elems(p, S) * nc * sizeof(T), s));
@@ -317,7 +320,16 @@ template <typename T> cip_status form_factor(cip_plan* p, cudaStream_t s) {
 
 // theta as the column solve reads it: the learnt spectra while the dictionary update is on
 const void* theta_of(const cip_plan* p) { return p->dl_sigma > 0 ? p->dl_spec : p->theta; }
-int theta_planes(const cip_plan* p) { return p->dl_sigma > 0 ? 2 * p->L : p->L; }
+int theta_planes(const cip_plan* p) { return p->Q > 0 ? p->M * p->L : (p->dl_sigma > 0 ? 2 * p->L : p->L); }
+
+// exp(-2 pi i j / M), j < M, with the angle reduced through (j mod M) exactly
+void channel_twiddles(int M, double* re, double* im) {
+  for (int j = 0; j < M; ++j) {
+    const double a = 2.0 * M_PI * (double)j / (double)M;
+    re[j] = std::cos(a);
+    im[j] = -std::sin(a);
+  }
+}
 
 // buffers of the dictionary update for the plan's current L (allocated once per L)
 cip_status alloc_dict(cip_plan* p) {
@@ -348,20 +360,39 @@ template <typename T> cip_status do_set_dictionary(cip_plan* p, const void* d, c
   using C = typename CT<T>::type;
   cip_status st = alloc_state<T>(p);
   if (st != CIP_OK) return st;
+  const int Qd = p->Q > 0 ? p->Q : 1;
   Staging sg;
   const void* dd = nullptr;
-  st = stage_in(p, d, (size_t)p->L * p->Pf * p->Pf * sizeof(T), s, sg, &dd);
+  st = stage_in(p, d, (size_t)p->L * Qd * p->Pf * p->Pf * sizeof(T), s, sg, &dd);
   if (st != CIP_OK) return st;
   double* emb = nullptr;
   using R = typename SetupReal<T>::type;
   SetupC<T>* th64 = nullptr;
-  CIP_CUDA(p, cudaMallocAsync((void**)&emb, real_elems(p, p->L) * sizeof(double), s));
-  CIP_CUDA(p, cudaMallocAsync((void**)&th64, half_elems(p, p->L) * sizeof(SetupC<T>), s));
-  cudaError_t e = cudaMemsetAsync(emb, 0, real_elems(p, p->L) * sizeof(double), s);
-  if (e == cudaSuccess) e = launch_embed_filters<T>(static_cast<const T*>(dd), emb, p->L, p->Pf, p->N, s);
-  if (e == cudaSuccess) e = launch_row_r2c<R, double>(emb, th64, p->N, p->L * p->N, R(1.0f), setup_buf<T>(p->tw64), s);
-  if (e == cudaSuccess) e = launch_col_c2c<R>(th64, p->N, p->L, -1, setup_buf<T>(p->tw64), s);
-  if (e == cudaSuccess) e = launch_theta_store<T>(th64, static_cast<C*>(p->theta), p->L, p->N, s);
+  // 2D: one N x N plane per filter; 3D: M planes per filter (the filter on the M x N x N torus)
+  const int planes = p->Q > 0 ? p->L * p->M : p->L;
+  if (p->Q > 0) {
+    free_ptr(p, p->theta);
+    CIP_CUDA(p, dmalloc(p, &p->theta, col_elems(p, planes) * sizeof(C)));
+    if (!p->w3) CIP_CUDA(p, dmalloc(p, &p->w3, 16 * sizeof(double2)));
+    double re[16], im[16];
+    channel_twiddles(p->M, re, im);
+    double2 w[16];
+    for (int j = 0; j < p->M; ++j) w[j] = make_double2(re[j], im[j]);
+    CIP_CUDA(p, cudaMemcpyAsync(p->w3, w, p->M * sizeof(double2), cudaMemcpyHostToDevice, s));
+    CIP_CUDA(p, cudaStreamSynchronize(s));  // w lives on this stack frame
+  }
+  CIP_CUDA(p, cudaMallocAsync((void**)&emb, real_elems(p, planes) * sizeof(double), s));
+  CIP_CUDA(p, cudaMallocAsync((void**)&th64, half_elems(p, planes) * sizeof(SetupC<T>), s));
+  cudaError_t e = cudaMemsetAsync(emb, 0, real_elems(p, planes) * sizeof(double), s);
+  if (e == cudaSuccess)
+    e = p->Q > 0 ? launch_embed_filters3d<T>(static_cast<const T*>(dd), emb, p->L, p->Q, p->Pf, p->M, p->N, s)
+                 : launch_embed_filters<T>(static_cast<const T*>(dd), emb, p->L, p->Pf, p->N, s);
+  if (e == cudaSuccess) e = launch_row_r2c<R, double>(emb, th64, p->N, planes * p->N, R(1.0f), setup_buf<T>(p->tw64), s);
+  if (e == cudaSuccess) e = launch_col_c2c<R>(th64, p->N, planes, -1, setup_buf<T>(p->tw64), s);
+  if (e == cudaSuccess)
+    e = p->Q > 0 ? launch_theta3_store<T>(th64, static_cast<C*>(p->theta), static_cast<const double2*>(p->w3), p->L,
+                                          p->M, p->N, s)
+                 : launch_theta_store<T>(th64, static_cast<C*>(p->theta), p->L, p->N, s);
   if (e == cudaSuccess) p->launches += 4;
   cudaFreeAsync(emb, s);
   cudaFreeAsync(th64, s);
@@ -475,11 +506,38 @@ template <typename T> PassAArgs<T> passA_args(cip_plan* p, int flags) {
   // the dictionary's column solve works on spectra scaled by 1/N^2 (see convdict.cu)
   a.qscale = is_cd(p) ? (T)(0.5 * p->rho / ((double)p->N * p->N)) : (T)(0.5 * p->rho);
   a.flags = flags;
+  a.test_fault = p->test_fault;
   fill_dct<T>(a.dct);
   return a;
 }
 
 template <typename T> PassBArgs<T> passB_args(cip_plan* p);
+
+// Row transforms between the column-layout row spectra and real rows ([maps][N][N]), run by the
+// prior-pass kernel without a prior: x = row IDFT of `spec` into `rows` (read-back, wavelet
+// chain), or spec = row DFT of scale * rows.
+template <typename T> cudaError_t rows_from_spec(cip_plan* p, const void* spec, int maps, void* rows, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  PassAArgs<T> a{};
+  a.xh = static_cast<const C*>(spec);
+  a.u_out = static_cast<T*>(rows);
+  a.err = p->conv + 1;
+  a.tw = static_cast<const C*>(p->tw);
+  a.M = maps;
+  return launch_passA<T>(a, p->N, ROWS_OUT, s);
+}
+template <typename T>
+cudaError_t spec_from_rows(cip_plan* p, const void* rows, int maps, double scale, void* spec, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  PassAArgs<T> a{};
+  a.qh = static_cast<C*>(spec);
+  a.u_in = static_cast<const T*>(rows);
+  a.err = p->conv + 1;
+  a.tw = static_cast<const C*>(p->tw);
+  a.M = maps;
+  a.qscale = (T)(0.5 * scale);  // the 1/2 of the pair extraction
+  return launch_passA<T>(a, p->N, ROWS_IN, s);
+}
 
 // The prior pass: one fused kernel per row tile for TV, DCT and l1; for the wavelet (x) DCT prior
 // (not local to a row tile) the chain x = row IDFT, J wavelet levels, channel DCT + shrinkage +
@@ -505,7 +563,7 @@ template <typename T> cip_status prior_pass(cip_plan* p, const PassAArgs<T>& a, 
   const int hp = N / 2;
   const size_t hplane = (size_t)hp * hp, plane = (size_t)N * N;
   if (!(a.flags & PA_IMPORT)) {
-    CIP_LAUNCH(p, (launch_row_c2r<T, T>(a.xh, B, N, M * N, a.tw, s)));
+    CIP_LAUNCH(p, rows_from_spec<T>(p, a.xh, M, B, s));
     for (int lev = 0; lev < J; ++lev) {
       const T* src = lev == 0 ? B : S[(lev - 1) & 1];
       const int sp = lev == 0 ? N : hp;
@@ -524,8 +582,30 @@ template <typename T> cip_status prior_pass(cip_plan* p, const PassAArgs<T>& a, 
     CIP_LAUNCH(p, launch_dwt2_inv<T>(ll, coarsest ? N : hp, coarsest ? plane : hplane, A, N, dst, lev == 0 ? N : hp,
                                      lev == 0 ? plane : hplane, N >> lev, M, f, s));
   }
-  CIP_LAUNCH(p, (launch_row_r2c<T, T>(B, a.qh, N, M * N, (T)p->rho, a.tw, s)));
+  CIP_LAUNCH(p, spec_from_rows<T>(p, B, M, p->rho, a.qh, s));
   return CIP_OK;
+}
+
+// arguments of the 3D dictionary's per-bin solve
+template <typename T> CD3Args<T> cd3_args(cip_plan* p) {
+  using C = typename CT<T>::type;
+  CD3Args<T> a;
+  a.colbuf = static_cast<C*>(p->colbuf);
+  a.theta = static_cast<const C*>(p->theta);
+  a.p_in = static_cast<const C*>(p->pbuf[p->pcur]);
+  a.p_out = static_cast<C*>(p->pbuf[p->pcur ^ 1]);
+  a.xb = static_cast<const C*>(p->bhat);
+  a.pinv = static_cast<const C*>(p->pinv);
+  a.xcol = static_cast<C*>(p->xcol);
+  a.N = p->N;
+  a.M = p->M;
+  a.L = p->L;
+  a.rho = (T)p->rho;
+  a.n2 = (T)((double)p->N * p->N);
+  double re[16], im[16];
+  channel_twiddles(p->M, re, im);
+  for (int j = 0; j < 16; ++j) a.w[j] = j < p->M ? mk<C>(re[j], im[j]) : mk<C>(0.0, 0.0);
+  return a;
 }
 
 // the column pass in the plan's chosen form
@@ -535,8 +615,16 @@ template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mo
     // dictionary: column DFT of rho (t - u) over the L*M coefficient maps, the per-(bin, channel)
     // x- and z-update, inverse column DFT of v
     const int S = smaps(p);
-    CIP_LAUNCH(p, launch_colfft_fwd<T>(static_cast<const C*>(p->qh), static_cast<C*>(p->colbuf),
-                                       static_cast<const C*>(p->tw), p->N, S, s));
+    CIP_LAUNCH(p, launch_cols_fft<T>(static_cast<const C*>(p->qh), static_cast<C*>(p->colbuf),
+                                     static_cast<const C*>(p->tw), p->N, S, -1, s));
+    if (p->Q > 0) {
+      CD3Args<T> a = cd3_args<T>(p);
+      CIP_LAUNCH(p, launch_cd3_solve<T>(a, s));
+      CIP_LAUNCH(p, launch_cols_fft<T>(static_cast<const C*>(p->colbuf), static_cast<C*>(p->xh),
+                                       static_cast<const C*>(p->tw), p->N, S, +1, s));
+      p->pcur ^= 1;
+      return CIP_OK;
+    }
     CDArgs<T> a;
     a.colbuf = static_cast<C*>(p->colbuf);
     a.theta = static_cast<const C*>(theta_of(p));
@@ -554,8 +642,8 @@ template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mo
     a.mu = (T)p->mu;
     a.n2 = (T)((double)p->N * p->N);
     CIP_LAUNCH(p, launch_cd_solve<T>(a, s));
-    CIP_LAUNCH(p, launch_colfft_inv<T>(static_cast<const C*>(p->colbuf), static_cast<C*>(p->xh),
-                                       static_cast<const C*>(p->tw), p->N, S, s));
+    CIP_LAUNCH(p, launch_cols_fft<T>(static_cast<const C*>(p->colbuf), static_cast<C*>(p->xh),
+                                     static_cast<const C*>(p->tw), p->N, S, +1, s));
     p->pcur ^= 1;
     return CIP_OK;
   }
@@ -566,7 +654,8 @@ template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mo
     CIP_CUDA(p, launch_passB_split<T>(b, static_cast<C*>(p->colbuf), p->N, s, &n));
     p->launches += n;
   } else {
-    CIP_LAUNCH(p, launch_passB<T>(b, p->N, cc, s));
+    (void)cc;
+    CIP_LAUNCH(p, launch_colpass_fused<T>(b, smaps(p), p->conv + 1, s));
   }
   return CIP_OK;
 }
@@ -610,22 +699,21 @@ template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
     if (it != g_tune.end()) {
       p->colmode = it->second.first;
       if (p->colmode == 1) p->cc = it->second.second;
-      p->blocksB = p->M * ((p->N / 2 + 1 + p->cc - 1) / p->cc);
+      p->blocksB = p->colmode == 1 ? p->N / 2 + 1 : p->M * (p->N / 2 + 1);
       // a cached choice of the split form still needs this plan's own column buffer
       if (p->colmode == 2 && !p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
       return CIP_OK;
     }
   }
   if (!p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
-  std::vector<std::pair<int, int>> cands = {{1, 1}, {1, 2}, {1, 4}, {2, 0}};
+  std::vector<std::pair<int, int>> cands = {{2, 0}};
+  if (colpass_fused_fits<T>(p->N, p->M)) cands.insert(cands.begin(), {1, 1});
   cudaEvent_t e0, e1;
   CIP_CUDA(p, cudaEventCreate(&e0));
   CIP_CUDA(p, cudaEventCreate(&e1));
   float best = 1e30f;
   std::pair<int, int> pick = {p->colmode, p->cc};
   for (auto& c : cands) {
-    if (c.first == 1 && passB_smem<T>(p->N, p->M, c.second) > 200 * 1024) continue;
-    if (c.first == 1 && p->N * c.second / (sizeof(T) == 4 ? 8 : 16) > 1024) continue;
     cip_status st = CIP_OK;
     for (int w = 0; w < 2 && st == CIP_OK; ++w) st = column_pass<T>(p, s, c.first, c.second);
     if (st != CIP_OK) return st;
@@ -645,7 +733,7 @@ template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
   cudaEventDestroy(e1);
   p->colmode = pick.first;
   if (pick.first == 1) p->cc = pick.second;
-  p->blocksB = p->M * ((p->N / 2 + 1 + p->cc - 1) / p->cc);
+  p->blocksB = p->colmode == 1 ? p->N / 2 + 1 : p->M * (p->N / 2 + 1);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = {p->colmode, p->cc};
   tune_cache_store(key, g_tune[key]);
@@ -660,6 +748,7 @@ template <typename T> PassBArgs<T> passB_args(cip_plan* p) {
   b.pinv = static_cast<const C*>(p->pinv);
   b.bhat = static_cast<const C*>(p->bhat);
   b.tw = static_cast<const C*>(p->tw);
+  b.N = p->N;
   b.M = p->M;
   b.plain = p->opt.precision == 1 ? 1 : 0;
   return b;
@@ -847,20 +936,17 @@ template <typename T> cip_status enqueue_iteration(cip_plan* p, cudaStream_t s, 
   return CIP_OK;
 }
 
-// inverse row DFT of `maps` row-domain half spectra into a caller array (host or device)
+// inverse row DFT of `maps` column-layout row spectra into a caller array (host or device)
 template <typename T>
 cip_status rows_out(cip_plan* p, const void* rows, int maps, void* out, cudaStream_t s) {
-  using C = typename CT<T>::type;
   const size_t bytes = real_elems(p, maps) * sizeof(T);
   if (is_device_ptr(out)) {
-    CIP_LAUNCH(p, (launch_row_c2r<T, T>(static_cast<const C*>(rows), static_cast<T*>(out), p->N, maps * p->N,
-                                        static_cast<const C*>(p->tw), s)));
+    CIP_LAUNCH(p, rows_from_spec<T>(p, rows, maps, out, s));
     return CIP_OK;
   }
   void* tmp = nullptr;
   CIP_CUDA(p, cudaMallocAsync(&tmp, bytes, s));
-  cudaError_t e = launch_row_c2r<T, T>(static_cast<const C*>(rows), static_cast<T*>(tmp), p->N, maps * p->N,
-                                       static_cast<const C*>(p->tw), s);
+  cudaError_t e = rows_from_spec<T>(p, rows, maps, tmp, s);
   if (e == cudaSuccess) p->launches++;
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(tmp, s);
@@ -872,11 +958,11 @@ cip_status rows_out(cip_plan* p, const void* rows, int maps, void* out, cudaStre
 template <typename T> cip_status get_x_impl(cip_plan* p, void* x, cudaStream_t s) {
   using C = typename CT<T>::type;
   if (!is_cd(p)) return rows_out<T>(p, p->xh, p->M, x, s);
-  // dictionary: x-hat is kept column-contiguous; inverse column DFT to row spectra first
+  // dictionary: x-hat is kept per bin; inverse column DFT to row spectra first
   void* rows = nullptr;
-  CIP_CUDA(p, cudaMallocAsync(&rows, half_elems(p, p->M) * sizeof(C), s));
-  cudaError_t e = launch_colfft_inv<T>(static_cast<const C*>(p->xcol), static_cast<C*>(rows),
-                                       static_cast<const C*>(p->tw), p->N, p->M, s);
+  CIP_CUDA(p, cudaMallocAsync(&rows, col_elems(p, p->M) * sizeof(C), s));
+  cudaError_t e = launch_cols_fft<T>(static_cast<const C*>(p->xcol), static_cast<C*>(rows),
+                                     static_cast<const C*>(p->tw), p->N, p->M, +1, s);
   if (e != cudaSuccess) {
     cudaFreeAsync(rows, s);
     CIP_CUDA(p, e);
@@ -896,10 +982,15 @@ template <typename T> cip_status import_z(cip_plan* p, const void* z, cudaStream
   cip_status r = stage_in(p, z, real_elems(p, S) * sizeof(T), s, sz, &dz);
   if (r != CIP_OK) return r;
   // row DFT into xh (overwritten by the next column pass), column DFT into colbuf
-  CIP_LAUNCH(p, (launch_row_r2c<T, T>(static_cast<const T*>(dz), static_cast<C*>(p->xh), p->N, S * p->N, (T)1,
-                                      static_cast<const C*>(p->tw), s)));
-  CIP_LAUNCH(p, launch_colfft_fwd<T>(static_cast<const C*>(p->xh), static_cast<C*>(p->colbuf),
-                                     static_cast<const C*>(p->tw), p->N, S, s));
+  CIP_LAUNCH(p, spec_from_rows<T>(p, dz, S, 1.0, p->xh, s));
+  CIP_LAUNCH(p, launch_cols_fft<T>(static_cast<const C*>(p->xh), static_cast<C*>(p->colbuf),
+                                   static_cast<const C*>(p->tw), p->N, S, -1, s));
+  if (p->Q > 0) {
+    CD3Args<T> a = cd3_args<T>(p);
+    CIP_LAUNCH(p, launch_p3_from_z<T>(static_cast<const C*>(p->colbuf), static_cast<const C*>(p->theta),
+                                      static_cast<C*>(p->pbuf[p->pcur]), a, 0.0, s));
+    return CIP_OK;
+  }
   CIP_LAUNCH(p, launch_p_from_z<T>(static_cast<const C*>(p->colbuf), static_cast<const C*>(theta_of(p)),
                                    static_cast<C*>(p->pbuf[p->pcur]), p->N, p->M, p->L, s, 0.0, theta_planes(p)));
   return CIP_OK;
@@ -977,8 +1068,10 @@ size_t cip_plan_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior) {
   const size_t e = dtype == CIP_F64 ? 8 : 4;
   const size_t P = (size_t)half_pitch(N), half = (size_t)N * P * 2 * e, real = (size_t)N * N * e;
   const size_t nc = prior_is_tv(prior) ? 2 : 1;
+  const size_t colc = (size_t)(N / 2 + 1) * col_pitch(N) * 2 * e;  // one map in the column layout
   size_t b = 0;
-  b += 3 * M * half;                          // xh, qh, bhat
+  b += 3 * M * colc;                          // xh, qh, bhat
+  b += M * colc;                              // split column buffer (autotuner)
   b += (size_t)M * (M + 1) / 2 * half;        // pinv
   b += (size_t)M * (M + 1) / 2 * N * P * 16;  // FP64 copy of pinv (data term at set_measurements)
   b += 3 * nc * M * real;                     // u[2], tprev
@@ -1010,27 +1103,24 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
   p->esz = dtype == CIP_F64 ? 8 : 4;
   if (opt) p->opt = *opt;
   const size_t ce = 2 * p->esz;  // complex element size
-  int cc = p->opt.col_tile;
-  if (cc == 0) cc = dtype == CIP_F64 ? passB_cols<double>(N, M) : passB_cols<float>(N, M);
-  if (cc != 1 && cc != 2 && cc != 4) {
+  const int cc = p->opt.col_tile;
+  if (cc != 0 && cc != 1 && cc != 2 && cc != 4) {
     delete p;
     return fail(nullptr, CIP_ERR_INVALID_ARG, "col_tile must be 0, 1, 2 or 4");
   }
-  p->cc = cc;
-  const size_t smB = dtype == CIP_F64 ? passB_smem<double>(N, M, cc) : passB_smem<float>(N, M, cc);
-  int dev = 0, smem_optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem_optin > 0 && smB > (size_t)smem_optin) {
+  p->cc = cc == 0 ? 1 : cc;
+  const bool fused_ok = dtype == CIP_F64 ? colpass_fused_fits<double>(N, M) : colpass_fused_fits<float>(N, M);
+  if (p->opt.column_pass == 1 && !fused_ok) {
     delete p;
-    return fail(nullptr, CIP_ERR_UNSUPPORTED, "column tile does not fit in shared memory for this N, M and dtype");
+    return fail(nullptr, CIP_ERR_UNSUPPORTED, "the fused column pass does not fit in shared memory for this N, M and dtype");
   }
-  p->blocksB = (N / 2 + 1 + cc - 1) / cc;
+  p->blocksB = N / 2 + 1;
   if (p->opt.precision != 0 && (p->opt.precision != 1 || dtype != CIP_F32)) {
     delete p;
     return fail(nullptr, CIP_ERR_INVALID_ARG, "precision must be 0, or 1 (plain FP32) for CIP_F32 plans");
   }
-  p->colmode = p->opt.column_pass == 2 ? 2 : 1;
+  p->colmode = (p->opt.column_pass == 2 || !fused_ok) ? 2 : 1;
+  if (p->colmode == 2) p->blocksB = M * (N / 2 + 1);
   if (p->opt.column_pass < 0 || p->opt.column_pass > 2) {
     delete p;
     return fail(nullptr, CIP_ERR_INVALID_ARG, "column_pass must be 0, 1 or 2");
@@ -1043,8 +1133,8 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
       return fail(nullptr, CIP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e_)); \
     }                                                                                           \
   } while (0)
-  ALLOC(p->xh, half_elems(p, M) * ce);
-  ALLOC(p->qh, half_elems(p, M) * ce);
+  ALLOC(p->xh, col_elems(p, M) * ce);
+  ALLOC(p->qh, col_elems(p, M) * ce);
   ALLOC(p->bhat, col_elems(p, M) * ce);
   ALLOC(p->tw, (size_t)kTwN * ce);
   ALLOC(p->tw64, (size_t)kTwN * 16);  // complex double-float (complex64 plans) or complex128
@@ -1090,7 +1180,7 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv, p->wbuf[0], p->wbuf[1], p->wbuf[2], p->wcos,
+  void* bufs[] = {p->w3, p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv, p->wbuf[0], p->wbuf[1], p->wbuf[2], p->wcos,
                   p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
@@ -1183,8 +1273,29 @@ cip_status cip_get_u(cip_plan* p, void* u, void* stream) {
   return copy_out(p, u, p->u[p->cur], real_elems(p, smaps(p)) * ncomp_of(p->prior) * p->esz, p->ast);
 }
 
+cip_status cip_set_dictionary_3d(cip_plan* p, const void* filters, int L, int Q, int P, void* stream) {
+  if (!p || !filters) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "cip_set_prior(CIP_PRIOR_CONVDICT) must precede cip_set_dictionary_3d");
+  if (p->opt.precision != 0) return fail(p, CIP_ERR_UNSUPPORTED, "the plain FP32 method covers analysis priors only");
+  if (L < 1 || L > 32) return fail(p, CIP_ERR_UNSUPPORTED, "L must be in [1, 32]");
+  if (Q < 1 || Q > p->M) return fail(p, CIP_ERR_INVALID_ARG, "filter depth must be in [1, M]");
+  if (P < 1 || P > p->N) return fail(p, CIP_ERR_INVALID_ARG, "filter size must be in [1, N]");
+  if (p->dl_sigma > 0) return fail(p, CIP_ERR_UNSUPPORTED, "the online dictionary update covers 2D filters only");
+  if (p->mu > 0) return fail(p, CIP_ERR_UNSUPPORTED, "the code gradient penalty covers 2D filters only");
+  const bool fits = p->dtype == CIP_F32 ? cd3_fits<float>(p->M, L) : cd3_fits<double>(p->M, L);
+  if (!fits) return fail(p, CIP_ERR_UNSUPPORTED, "M * L too large for the 3D dictionary's per-bin tile");
+  p->L = L;
+  p->Pf = P;
+  p->Q = Q;
+  p->have_y = false;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->ast = s;
+  return DISPATCH_T(p, do_set_dictionary<float>(p, filters, s), do_set_dictionary<double>(p, filters, s));
+}
+
 cip_status cip_set_dictionary(cip_plan* p, const void* filters, int L, int P, void* stream) {
   if (!p || !filters) return fail(p, CIP_ERR_INVALID_ARG, "null argument");
+  p->Q = 0;
   if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "cip_set_prior(CIP_PRIOR_CONVDICT) must precede cip_set_dictionary");
   if (p->opt.precision != 0) return fail(p, CIP_ERR_UNSUPPORTED, "the plain FP32 method covers analysis priors only");
   if (L < 1 || L > 32) return fail(p, CIP_ERR_UNSUPPORTED, "L must be in [1, 32]");
@@ -1201,6 +1312,7 @@ cip_status cip_set_code_gradient_weight(cip_plan* p, double mu) {
   if (!p) return CIP_ERR_INVALID_ARG;
   if (!is_cd(p)) return fail(p, CIP_ERR_STATE, "the gradient penalty applies to CIP_PRIOR_CONVDICT plans only");
   if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(p, CIP_ERR_INVALID_ARG, "mu must be finite and >= 0");
+  if (mu > 0 && p->Q > 0) return fail(p, CIP_ERR_UNSUPPORTED, "the code gradient penalty covers 2D filters only");
   p->mu = mu;
   return CIP_OK;
 }
@@ -1212,6 +1324,7 @@ cip_status cip_set_dictionary_learning(cip_plan* p, double sigma, void* stream) 
     return fail(p, CIP_ERR_STATE, "dictionary learning needs a CIP_PRIOR_CONVDICT plan after cip_set_dictionary");
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(p, CIP_ERR_INVALID_ARG, "sigma must be finite and >= 0");
   if (sigma > 0 && p->M > 8) return fail(p, CIP_ERR_UNSUPPORTED, "dictionary learning supports M <= 8 channels");
+  if (sigma > 0 && p->Q > 0) return fail(p, CIP_ERR_UNSUPPORTED, "the online dictionary update covers 2D filters only");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   p->ast = s;
   const size_t ce = 2 * p->esz;
@@ -1330,7 +1443,7 @@ cip_status cip_state_import(cip_plan* p, const void* t, const void* u, void* str
 // device buffers that make up the ADMM state, in checkpoint order
 static std::vector<std::pair<void*, size_t>> state_segments(cip_plan* p) {
   const int S = smaps(p);
-  const size_t hb = half_elems(p, S) * 2 * p->esz;
+  const size_t hb = col_elems(p, S) * 2 * p->esz;
   const size_t ub = real_elems(p, S) * ncomp_of(p->prior) * p->esz;
   std::vector<std::pair<void*, size_t>> seg = {{p->xh, hb}, {p->qh, hb}, {p->u[p->cur], ub}, {p->tprev, ub}};
   if (is_cd(p)) {
@@ -1433,6 +1546,13 @@ cip_status cip_get_timing(cip_plan* p, double* a_ms, int* a_n, double* b_ms, int
   if (b_ms) *b_ms = tb;
   if (b_n) *b_n = p->nB;
   p->nA = p->nB = 0;
+  return CIP_OK;
+}
+
+cip_status cip_set_test_fault(cip_plan* p, int kind) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  if (kind != 0 && kind != 1) return fail(p, CIP_ERR_INVALID_ARG, "test fault kind must be 0 or 1");
+  p->test_fault = kind;
   return CIP_OK;
 }
 
@@ -1685,7 +1805,7 @@ size_t plan_resident_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior
   const size_t H = N / 2 + 1, P = half_pitch(N), CP = col_pitch(N);
   const size_t nc = prior_is_tv(prior) ? 2 : 1;
   const size_t npk = (size_t)M * (M + 1) / 2;
-  size_t b = 2 * (size_t)M * N * P * c;       // xh, qh
+  size_t b = 2 * (size_t)M * H * CP * c;      // xh, qh (column layout)
   b += (size_t)M * H * CP * c;                // data term
   b += npk * H * CP * c;                      // factor
   b += (size_t)M * H * CP * c;                // column buffer of the split form

@@ -1,10 +1,12 @@
 // Split form of the column pass (the x-update of Eq. solx_Trans_DFT, three
-// kernels instead of one): a forward column DFT that writes the spectra
-// column-contiguous ([k2][m][k1]), an element-wise per-frequency solve
-// X = xb + Psi^{-1}/N^2 Q over that layout, and an inverse column DFT back to
-// row-domain half spectra.  It moves 16 more bytes per voxel than the fused
-// cluster kernel but every launch is fully parallel and every access is
-// coalesced; the plan's autotuner chooses between the two per shape.
+// kernels instead of one): a forward column DFT of q-hat into the column
+// buffer, an element-wise per-frequency solve X = xb + Psi^{-1}/N^2 Q over
+// that layout, and an inverse column DFT into x-hat.  It moves 16 more bytes
+// per voxel than the fused kernel (colpass.cu) but needs no shared-memory tile
+// of all channels; the plan's autotuner chooses between the two per shape.
+//
+// The row-layout column DFTs here (rows [maps][N][P] <-> columns [H][maps][CP])
+// serve the online dictionary update, whose filter spectra keep that layout.
 #include "fft.cuh"
 #include "kernels.h"
 
@@ -232,11 +234,12 @@ cudaError_t solve_m(typename CT<T>::type* colbuf, const typename CT<T>::type* pi
 template <typename T>
 cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colbuf, int N, cudaStream_t s,
                                int* launches) {
-  cudaError_t e = colfft_n<T, -1>(a.qh, colbuf, a.tw, N, a.M, s);
+  // q-hat and x-hat use the column layout already: the column DFTs need no transposition
+  cudaError_t e = launch_cols_fft<T>(a.qh, colbuf, a.tw, N, a.M, -1, s);
   if (e != cudaSuccess) return e;
   e = solve_m<T>(colbuf, a.pinv, a.bhat, N, a.M, a.plain, s);
   if (e != cudaSuccess) return e;
-  e = colfft_n<T, +1>(colbuf, a.xh, a.tw, N, a.M, s);
+  e = launch_cols_fft<T>(colbuf, a.xh, a.tw, N, a.M, +1, s);
   if (launches) *launches += 3;
   return e;
 }

@@ -103,6 +103,10 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned coun
 __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
+// plain arrival (no transactions): a consumer releasing a buffer
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 // contiguous global -> shared copy by the TMA unit; both addresses 16-byte aligned, bytes a
 // multiple of 16; completion is counted on `bar`
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
@@ -120,15 +124,33 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// Bounded wait for phase `parity` of `bar`: gives up after a fixed number of
-// polls (each poll itself suspends for a short, hardware-chosen time), records
-// the failure in *err and returns false, so that a lost copy ends the kernel
-// with an error status instead of a hung GPU.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, int* err) {
-  for (int i = 0; i < (1 << 22); ++i)
+// Bounded wait for phase `parity` of `bar`: gives up after one second of the
+// GPU's global timer (or 2^22 polls, whichever comes first), records the
+// failure in *err and returns false, so that a lost copy ends the kernel with an
+// error status instead of a hung GPU.  A legitimate wait lasts microseconds.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, int* err,
+                                                  int max_polls = 1 << 22) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < max_polls; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63 && global_ns() - t0 > 1000000000ull) break;
+  }
   if (err) atomicExch(err, 1);
   return false;
+}
+
+// The same wait by every lane of a converged warp (each lane's own successful wait orders its
+// later reads after the asynchronous writes), with one decision for the whole warp: it goes on
+// only if every lane saw the phase complete.
+__device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, unsigned parity, int* err) {
+  const bool mine = mbar_wait_bounded(bar, parity, err);
+  return __all_sync(0xffffffffu, mine) != 0;
 }
 
 // Kernel attributes (shared-memory size, carveout, cluster size) are per function and per
@@ -181,6 +203,21 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   }
   cfg.attrs = attr;
   cfg.numAttrs = n;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// Plain launch through cudaLaunchKernelEx: the returned status is this launch's own, so a caller
+// neither mistakes an earlier pending error for it nor has to clear that error to see it.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_plain(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 

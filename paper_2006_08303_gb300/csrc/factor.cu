@@ -427,8 +427,7 @@ template cudaError_t launch_scale<double>(double*, size_t, double, cudaStream_t)
 
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, double rho, double tol, double* out, int* conv,
                                    cudaStream_t s) {
-  reduce_kernel<<<1, 256, 0, s>>>(partials, nblocks, rho, tol, out, conv);
-  return cudaGetLastError();
+  return launch_plain(reduce_kernel, dim3(1), dim3(256), 0, s, partials, nblocks, rho, tol, out, conv);
 }
 
 template cudaError_t launch_factor<float>(const cdf*, const double*, int, int, int, int, double, double, float2*,

@@ -200,6 +200,99 @@ __device__ __forceinline__ void fft_team(C* buf, int tid, const C* __restrict__ 
   if constexpr (REM == 2) stockham_stage<C, LOGN, NF, E, SIGN, 4, (1 << (3 * S8))>(buf, f, tt, tw, ts, active);
 }
 
+// ---- stages with separate input and output accessors ------------------------
+// The same radix-R Stockham stage as stockham_stage, for one FFT per team of
+// TT = N/E threads, but the stage reads its inputs through `in(i0, off)` and
+// writes its outputs through `out(i0, off, v)` (element i0 + off, where off is
+// a compile-time multiple of N/R or of LS).  A first stage can then read data
+// exactly as a bulk copy left it (unpadded, or straight from global memory) and
+// a last stage can write its natural-order results straight to global memory;
+// stages in between address the padded layout spad().  `mid()` runs between
+// the reads and the writes (a team barrier when in and out alias).
+//   reads:  x[t + r N/R]                                 (i0 = t, off = r N/R)
+//   writes: y[(t/LS) LS R + (t mod LS) + r LS]           (i0 = base, off = r LS)
+// For every stage of a radix-8 (+ one radix-2/4) decomposition of N >= 64,
+// (i0 mod 16) + (off mod 16) < 16, so spad(i0 + off) = spad(i0) + off + off/16.
+template <typename C, int LOGN, int E, int SIGN, int R, int LS, class In, class Mid, class Out>
+__device__ __forceinline__ void fft_stage_io(int tt, const C* __restrict__ tw, In&& in, Mid&& mid, Out&& out) {
+  constexpr int N = 1 << LOGN;
+  constexpr int B = E / R;
+  constexpr int TT = N / E;
+  static_assert(E % R == 0, "E must be a multiple of the radix");
+  constexpr bool HOIST = LS > 1 && B <= 2;  // twiddles ahead of the barrier when registers allow
+  C a[E];
+  C w[HOIST ? B * (R - 1) : 1];
+  if constexpr (HOIST) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = (tt + TT * b) & (LS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = ldg_tw(&tw[r * j * (kTwN / (LS * R))]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int t = tt + TT * b;
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[b * R + r] = in(t, r * (N / R));
+  }
+  mid();
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int t = tt + TT * b;
+    const int j = t & (LS - 1);
+    if constexpr (LS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C wr = HOIST ? w[b * (R - 1) + r - 1] : ldg_tw(&tw[r * j * (kTwN / (LS * R))]);
+        if (SIGN > 0) wr.y = -wr.y;
+        a[b * R + r] = cmul(a[b * R + r], wr);
+      }
+    }
+    dft_r<R, SIGN>(&a[b * R]);
+    const int base = (t / LS) * LS * R + j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out(base, r * LS, a[b * R + r]);
+  }
+}
+
+// Whole FFT of length 2^LOGN by one team: the first stage reads through `in0`,
+// the last writes through `outL`, stages in between use the padded buffer
+// `buf` (spad layout, at least spad(N) elements).  `sync()` is the team
+// barrier.  When in0 reads `buf` itself (unpadded), the first stage's reads
+// complete before any write; when outL writes to `buf`, the last stage's
+// writes follow a barrier after its reads.  outL_alias says whether outL
+// writes memory that the last stage reads (then a barrier separates them).
+template <typename C, int LOGN, int E, int SIGN, bool OUTL_ALIAS, class In0, class OutL, class Sync>
+__device__ __forceinline__ void fft_team_io(C* buf, int tt, const C* __restrict__ tw, const Sync& sync, In0&& in0,
+                                            OutL&& outL) {
+  constexpr int S8 = LOGN / 3;
+  constexpr int REM = LOGN % 3;
+  constexpr int NST = S8 + (REM ? 1 : 0);
+  static_assert(NST >= 2, "at least two stages");
+  auto pin = [&](int i0, int off) { return buf[spad(i0) + off + (off >> 4)]; };
+  auto pout = [&](int i0, int off, C v) { buf[spad(i0) + off + (off >> 4)] = v; };
+  auto bar = [&]() { sync(); };
+  auto none = [&]() {};
+  // stage 0 (LS = 1, radix 8): in0 -> padded
+  fft_stage_io<C, LOGN, E, SIGN, 8, 1>(tt, tw, in0, bar, pout);
+  sync();
+  // middle radix-8 stages
+  if constexpr (NST >= 3) {
+    fft_stage_io<C, LOGN, E, SIGN, 8, 8>(tt, tw, pin, bar, pout);
+    sync();
+  }
+  if constexpr (NST >= 4) {
+    fft_stage_io<C, LOGN, E, SIGN, 8, 64>(tt, tw, pin, bar, pout);
+    sync();
+  }
+  // last stage: radix 8 at LS = 8^(S8-1) when REM == 0, else radix 2/4 at LS = 8^S8
+  constexpr int RL = REM == 0 ? 8 : (REM == 1 ? 2 : 4);
+  constexpr int LSL = REM == 0 ? (1 << (3 * (S8 - 1))) : (1 << (3 * S8));
+  if constexpr (OUTL_ALIAS) fft_stage_io<C, LOGN, E, SIGN, RL, LSL>(tt, tw, pin, bar, outL);
+  else fft_stage_io<C, LOGN, E, SIGN, RL, LSL>(tt, tw, pin, none, outL);
+}
+
 // ---- two real rows through one complex FFT ---------------------------------
 // Inverse: from the half spectra Xa[k], Xb[k] (k = 0..N/2) of two real rows,
 // build Z[k] = Xa[k] + i Xb[k] over the full length using Hermitian symmetry;

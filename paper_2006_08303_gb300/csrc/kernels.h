@@ -7,6 +7,9 @@
 namespace cip {
 
 enum PriorKind { PRIOR_TV = 0, PRIOR_DCT8 = 1, PRIOR_L1 = 2, PRIOR_CONVDICT = 3, PRIOR_TV_ISO = 4, PRIOR_WDCT = 5 };
+// row transforms of the prior-pass kernel without a prior: x rows out of the column-layout
+// spectra (ROWS_OUT: read-back, wavelet chain), or q-hat from real rows (ROWS_IN)
+enum RowKind { ROWS_OUT = 100, ROWS_IN = 101 };
 // the two TV priors share T = [D_h; D_v] (two components, one halo row each side)
 constexpr bool prior_is_tv(int p) { return p == PRIOR_TV || p == PRIOR_TV_ISO; }
 
@@ -20,10 +23,14 @@ inline int prior_ncomp(int prior) { return prior_is_tv(prior) ? 2 : 1; }
 //   x = row-IDFT(xh)  ->  w = T x  ->  t = soft(w + u, tau)  ->  u' = u + w - t
 //   -> q = qscale * T^T (t - u')  ->  qh = row-DFT(q) (half spectrum, pair-extracted)
 // In IMPORT mode x is not used: t comes from t_imp and u' = u_in.
+// The row spectra xh and qh use the column layout [N/2+1][maps][col_pitch(N)]: for each
+// half-spectrum column k2 the N row values of every map are contiguous.
+// ROWS_OUT: x = row-IDFT(xh) is written to u_out ([maps][N][N]) and nothing else happens.
+// ROWS_IN: qh = row-DFT(2 qscale u_in) from real rows u_in ([maps][N][N]).
 template <typename T> struct PassAArgs {
   using C = typename CT<T>::type;
-  const C* xh;      // [M][N][P]
-  C* qh;            // [M][N][P]
+  const C* xh;      // [N/2+1][M][CP] (column layout)
+  C* qh;            // [N/2+1][M][CP] (column layout)
   const T* u_in;    // [M][ncomp][N][N]
   T* u_out;         // [M][ncomp][N][N]
   T* tprev;         // [M][ncomp][N][N] (STORE_T writes t, RESID reads t_prev)
@@ -35,6 +42,8 @@ template <typename T> struct PassAArgs {
   T tau;            // lambda / rho
   T qscale;         // rho / 2 (the 1/2 of the pair extraction is folded here)
   int flags;
+  int test_fault;   // 1: the staged u copy is replaced by a barrier that never completes (test of
+                    // the bounded wait: no copy is issued, the wait gives up after 64 polls)
   T dct[64];        // orthonormal DCT-II, dct[k*8+n]
 };
 
@@ -42,11 +51,12 @@ template <typename T> struct PassAArgs {
 // term precomputed:  Q = col-DFT(qh);  X(w) = xb(w) + Pinv(w) Q(w);  xh = col-IDFT(X)
 template <typename T> struct PassBArgs {
   using C = typename CT<T>::type;
-  const C* qh;      // [M][N][P]
-  C* xh;            // [M][N][P]
+  const C* qh;      // [N/2+1][M][CP] (column layout)
+  C* xh;            // [N/2+1][M][CP] (column layout)
   const C* pinv;    // [N/2+1][M(M+1)/2][N] packed upper triangle per bin, scaled by 1/N^2
   const C* bhat;    // [N/2+1][M][N]: xb = Psi^{-1} beta Lambda^H F y / N^2 (FP64-formed)
   const C* tw;
+  int N;
   int M;
   int plain;        // 1: plain FP32 method, bhat holds b = beta Lambda^H F y and X = Pinv (b + Q)
 };
@@ -76,6 +86,32 @@ template <typename T> struct CDArgs {
   T n2;            // N^2
 };
 template <typename T> cudaError_t launch_cd_solve(const CDArgs<T>& a, cudaStream_t s);
+
+// 3D dictionary (Section IV-B, 3D case; csrc/convdict3d.cu): the same column layout for the
+// channel-domain spectra; theta holds Theta_l(kappa, w) at plane kappa*L + l of [H][M*L][CP].
+template <typename T> struct CD3Args {
+  using C = typename CT<T>::type;
+  C* colbuf;       // [H][M*L]: in G = col-DFT of rho (t - u) / N^2, out V (channel-major, m*L + l)
+  const C* theta;  // [H][M*L]: 3D DFT of the embedded filters, plane kappa*L + l
+  const C* p_in;   // [H][M]
+  C* p_out;        // [H][M]
+  const C* xb;     // [H][M]
+  const C* pinv;   // [H][M(M+1)/2]
+  C* xcol;         // [H][M]
+  int N, M, L;
+  T rho, n2;
+  C w[16];         // exp(-2 pi i j / M), j < M
+};
+template <typename T> cudaError_t launch_cd3_solve(const CD3Args<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_p3_from_z(const typename CT<T>::type* zcol, const typename CT<T>::type* th3,
+                             typename CT<T>::type* p, const CD3Args<T>& a, double scale, cudaStream_t s);
+template <typename Tin>
+cudaError_t launch_embed_filters3d(const Tin* d, double* out, int L, int Q, int P, int M, int N, cudaStream_t s);
+template <typename T>
+cudaError_t launch_theta3_store(const SetupC<T>* th64, typename CT<T>::type* th, const double2* w, int L, int M, int N,
+                                cudaStream_t s);
+template <typename T> bool cd3_fits(int M, int L);
 template <typename T>
 cudaError_t launch_p_from_z(const typename CT<T>::type* zcol, const typename CT<T>::type* th,
                             typename CT<T>::type* p, int N, int M, int L, cudaStream_t s,
@@ -105,10 +141,19 @@ template <typename T> int passA_rows(int N, int prior);
 template <typename T> size_t passA_smem(int N, int prior);
 template <typename T> cudaError_t launch_passA(const PassAArgs<T>& a, int N, int prior, cudaStream_t s);
 
-template <typename T> int passB_cols(int N, int M);
-template <typename T> size_t passB_smem(int N, int M, int cc);
-template <typename T> cudaError_t launch_passB(const PassBArgs<T>& a, int N, int cc, cudaStream_t s);
-// split form: column FFT to [N/2+1][M][N] in colbuf, per-bin solve in place, inverse column FFT
+// Fused column pass (csrc/colpass.cu): one CTA per half-spectrum column, factor and data term
+// streamed through a ring of TMA bulk copies.  fits: the tile and at least two ring stages fit in
+// shared memory.  `err` is set when a bounded wait gives up.
+template <typename T> bool colpass_fused_fits(int N, int M);
+template <typename T> size_t colpass_fused_smem(int N, int M);
+template <typename T> cudaError_t launch_colpass_fused(const PassBArgs<T>& b, int S, int* err, cudaStream_t s);
+// column DFTs of every (k2, map) column of the column layout, src -> dst (may alias);
+// sign < 0 forward, > 0 inverse (unnormalised)
+template <typename T>
+cudaError_t launch_cols_fft(const typename CT<T>::type* src, typename CT<T>::type* dst,
+                            const typename CT<T>::type* tw, int N, int maps, int sign, cudaStream_t s);
+// split form: column FFT of qh into colbuf (same layout), per-bin solve in place, inverse column FFT
+// into xh
 template <typename T>
 cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colbuf, int N, cudaStream_t s,
                                int* launches);

@@ -165,7 +165,18 @@ cip_status run(int prior, int N, int M, double lambda, double rho, const void* x
   cip_status st = scratch_ptr(&scratch);
   if (st != CIP_OK) return st;
   const T tau = (T)(lambda / rho);
+  // Under stream capture only device memory can receive the residuals: a copy to pageable host
+  // memory and the stream synchronisation it needs would invalidate the caller's capture.
+  cudaPointerAttributes at;
+  const bool dev_out = cudaPointerGetAttributes(&at, resid_out) == cudaSuccess &&
+                       (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return CIP_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone && !dev_out) return CIP_ERR_INVALID_ARG;
+  // every launch below reports its own status (no cudaGetLastError: an error the caller left
+  // pending is neither taken for this call's nor cleared)
   int nblk = 0;
+  cudaError_t e = cudaSuccess;
   if (prior == PRIOR_DCT8) {
     const size_t nb8 = (size_t)M * (N / 8) * (N / 8);
     nblk = (int)((nb8 + kThreads - 1) / kThreads);
@@ -175,25 +186,21 @@ cip_status run(int prior, int N, int M, double lambda, double rho, const void* x
         const double a = k == 0 ? sqrt(1.0 / 8.0) : sqrt(2.0 / 8.0);
         d.dct[k * 8 + n] = (T)(a * cos(M_PI * (2 * n + 1) * k / 16.0));
       }
-    shrink_dual_dct<T><<<nblk, kThreads, 0, s>>>((const T*)x, (const T*)u_in, (const T*)t_prev, (T*)u_out,
-                                                 (T*)t_out, N, M, tau, d, scratch);
+    e = launch_plain(shrink_dual_dct<T>, dim3(nblk), dim3(kThreads), 0, s, (const T*)x, (const T*)u_in,
+                     (const T*)t_prev, (T*)u_out, (T*)t_out, N, M, tau, d, scratch);
   } else {
     const size_t total = (size_t)M * N * N;
     nblk = (int)((total + kPixPerBlock - 1) / kPixPerBlock);
     if (prior == PRIOR_TV)
-      shrink_dual_px<T, PRIOR_TV><<<nblk, kThreads, 0, s>>>((const T*)x, (const T*)u_in, (const T*)t_prev,
-                                                            (T*)u_out, (T*)t_out, N, M, tau, scratch);
+      e = launch_plain(shrink_dual_px<T, PRIOR_TV>, dim3(nblk), dim3(kThreads), 0, s, (const T*)x, (const T*)u_in,
+                       (const T*)t_prev, (T*)u_out, (T*)t_out, N, M, tau, scratch);
     else
-      shrink_dual_px<T, PRIOR_L1><<<nblk, kThreads, 0, s>>>((const T*)x, (const T*)u_in, (const T*)t_prev,
-                                                            (T*)u_out, (T*)t_out, N, M, tau, scratch);
+      e = launch_plain(shrink_dual_px<T, PRIOR_L1>, dim3(nblk), dim3(kThreads), 0, s, (const T*)x, (const T*)u_in,
+                       (const T*)t_prev, (T*)u_out, (T*)t_out, N, M, tau, scratch);
   }
-  if (cudaGetLastError() != cudaSuccess) return CIP_ERR_CUDA;
+  if (e != cudaSuccess) return CIP_ERR_CUDA;
   double* result = scratch + (size_t)kScratchBlocks * kNPart;
   if (launch_reduce_partials(scratch, nblk, rho, 0.0, result, nullptr, s) != cudaSuccess) return CIP_ERR_CUDA;
-  cudaPointerAttributes at;
-  const bool dev_out = cudaPointerGetAttributes(&at, resid_out) == cudaSuccess &&
-                       (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
-  cudaGetLastError();
   if (cudaMemcpyAsync(resid_out, result + kNPart, 2 * sizeof(double),
                       dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return CIP_ERR_CUDA;

@@ -62,12 +62,17 @@ template <typename T> constexpr int elems_a(int N, int prior) {
   return (sizeof(T) == 4 && N <= 1024) ? ((N == 512 && !prior_is_tv(prior)) ? 16 : 8) : 16;
 }
 
+// Pitch of the row-pair FFT buffers (complex elements): the padded FFT layout plus 4 slots from
+// N = 256 on, so that the 4 or 5 buffers a warp writes at once (pair p, consecutive columns k,
+// when the column-layout spectra are gathered or scattered) start in different bank groups.
+constexpr int zs_of(int N) { return spad(N) + (N >= 256 ? 4 : 0); }
+
 // rows per tile
 template <typename T> constexpr int rows_for(int N, int prior) {
   if (!prior_is_tv(prior)) return 8;
   using C = typename CT<T>::type;
   for (int R = 8; R >= 2; R /= 2) {
-    size_t zs = (size_t)spad(N);
+    size_t zs = (size_t)zs_of(N);
     size_t sm = (size_t)((R + 2) / 2) * zs * sizeof(C) + (size_t)(2 * R + 1) * N * sizeof(T);
     if (sm <= 200 * 1024) return R;
   }
@@ -79,13 +84,14 @@ template <typename T> constexpr int rows_for(int N, int prior) {
 // column pass), when the staging area keeps the CTA within ~100 KB
 template <typename T> constexpr bool u_staged(int N, int prior, int R) {
   using C = typename CT<T>::type;
-  return !prior_is_tv(prior) && (size_t)(R / 2) * spad(N) * sizeof(C) + (size_t)R * N * sizeof(T) <= 100 * 1024;
+  return !prior_is_tv(prior) && prior < ROWS_OUT &&
+         (size_t)(R / 2) * zs_of(N) * sizeof(C) + (size_t)R * N * sizeof(T) <= 100 * 1024;
 }
 
 template <typename T> constexpr size_t smem_for(int N, int prior, int R) {
   using C = typename CT<T>::type;
   const int halo = prior_is_tv(prior) ? 1 : 0;
-  size_t sm = (size_t)((R + 2 * halo) / 2) * spad(N) * sizeof(C);
+  size_t sm = (size_t)((R + 2 * halo) / 2) * zs_of(N) * sizeof(C);
   if (prior_is_tv(prior)) sm += (size_t)(2 * R + 1) * N * sizeof(T);
   if (u_staged<T>(N, prior, R)) sm += (size_t)R * N * sizeof(T);
   return sm;
@@ -203,12 +209,12 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   using C = typename CT<T>::type;
   constexpr int N = 1 << LOGN;
   constexpr int H = N / 2 + 1;
-  constexpr int P = half_pitch(N);
   constexpr int HALO = prior_is_tv(PRIOR) ? 1 : 0;
   constexpr int ROWS = R + 2 * HALO;
   constexpr int NPIN = ROWS / 2;
   constexpr int NPOUT = R / 2;
-  constexpr int ZS = spad(N);
+  constexpr int ZS = zs_of(N);
+  constexpr int CP = col_pitch(N);
   constexpr int E = elems_a<T>(N, PRIOR);
   constexpr int TEAM = N / E;
   constexpr int NCOMP = prior_is_tv(PRIOR) ? 2 : 1;
@@ -217,6 +223,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   T* ah = reinterpret_cast<T*>(zb + NPIN * ZS);  // TV only: [R][N], a_h at tile rows 1..R
   T* av = ah + R * N;                             // TV only: [R+1][N], a_v at tile rows 0..R
   constexpr bool USTAGE = u_staged<T>(N, PRIOR, R);
+  static_assert(!USTAGE || (NPIN * ZS * sizeof(C)) % 16 == 0, "the TMA destination must be 16-byte aligned");
   T* us = reinterpret_cast<T*>(zb + NPIN * ZS);   // DCT / l1 with USTAGE: [R][N] rows r0.. of u_in
   __shared__ unsigned long long ubar;
 
@@ -224,17 +231,21 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   const int nth = blockDim.x;
   const int m = blockIdx.y;
   const int r0 = blockIdx.x * R;
-  const bool import_mode = (a.flags & PA_IMPORT) != 0;
+  constexpr bool ROWXF = PRIOR >= ROWS_OUT;  // row transform only (read-back, wavelet chain)
+  const bool import_mode = PRIOR == ROWS_IN || (a.flags & PA_IMPORT) != 0;
   const bool resid = (a.flags & PA_RESID) != 0;
   const bool store_t = (a.flags & PA_STORE_T) != 0;
   const T tau = a.tau;
   const size_t plane = (size_t)N * N;
-  const T* u_in = a.u_in + (size_t)m * NCOMP * plane;
-  T* u_out = a.u_out + (size_t)m * NCOMP * plane;
+  const T* u_in = a.u_in ? a.u_in + (size_t)m * NCOMP * plane : nullptr;
+  T* u_out = a.u_out ? a.u_out + (size_t)m * NCOMP * plane : nullptr;
   T* tprev = a.tprev ? a.tprev + (size_t)m * NCOMP * plane : nullptr;
   const T* timp = a.t_imp ? a.t_imp + (size_t)m * NCOMP * plane : nullptr;
   const T* tprev_rd = resid ? tprev : nullptr;
   T part[kNPart] = {T(0), T(0), T(0), T(0), T(0)};
+  // false when this thread's bounded wait for the staged u rows gave up: it then reads u from
+  // global memory (the same values), never the shared-memory rows the copy may not have written
+  bool u_ok = true;
 
   auto grow = [&](int j) { return (r0 - HALO + j) & (N - 1); };
 
@@ -243,14 +254,21 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
     // multiple of 8 and N >= 64), fetched by the TMA unit while the previous kernel drains
     if (tid == 0) {
       constexpr unsigned bytes = (unsigned)(R * N * sizeof(T));
-      mbar_init(&ubar, 1);
-      mbar_arrive_expect_tx(&ubar, bytes);
-      bulk_copy_g2s(us, u_in + (size_t)r0 * N, bytes, &ubar);
+      if (a.test_fault == 1) {
+        // test of the bounded wait: two arrivals expected, one given, no copy issued, so the
+        // phase never completes and nothing is in flight when the wait gives up
+        mbar_init(&ubar, 2);
+        mbar_arrive(&ubar);
+      } else {
+        mbar_init(&ubar, 1);
+        mbar_arrive_expect_tx(&ubar, bytes);
+        bulk_copy_g2s(us, u_in + (size_t)r0 * N, bytes, &ubar);
+      }
     }
     __syncthreads();  // the barrier is initialised before anyone waits on it
   }
   // L2 prefetch of the u rows (and t_prev rows) read after the inverse FFT
-  if (tid < 2 * NCOMP && !(USTAGE && (tid & 1) == 0)) {
+  if (!ROWXF && tid < 2 * NCOMP && !(USTAGE && (tid & 1) == 0)) {
     const T* src = (tid & 1) ? tprev_rd : u_in;
     if (src) {
       const size_t comp = (size_t)(tid >> 1) * plane;
@@ -262,25 +280,25 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   grid_dep_wait();  // x (and u, t) of the previous kernels are complete from here on
   grid_dep_launch();
   if (!import_mode) {
-    // 1. load row half-spectra (two rows per complex FFT) and invert the row DFT
-    const C* xh = a.xh + (size_t)m * N * P;
-    if constexpr (sizeof(C) == 8) {
-      // complex64: bins k, k+1 per 16-byte load (P even; k = N/2 + 1 lies inside the pitch, unused)
-      constexpr int HP = N / 4 + 1;
-      for (int idx = tid; idx < NPIN * HP; idx += nth) {
-        const int p = idx / HP, k = 2 * (idx - p * HP);
-        const float4 va = *reinterpret_cast<const float4*>(xh + (size_t)grow(2 * p) * P + k);
-        const float4 vb = *reinterpret_cast<const float4*>(xh + (size_t)grow(2 * p + 1) * P + k);
-        pair_spectrum_put(zb + p * ZS, N, k, mk<C>(va.x, va.y), mk<C>(vb.x, vb.y));
-        if (k + 1 < H) pair_spectrum_put(zb + p * ZS, N, k + 1, mk<C>(va.z, va.w), mk<C>(vb.z, vb.w));
+    // 1. gather the row half-spectra of the tile (two rows per complex FFT) from the column
+    //    layout and invert the row DFT; thread = (pair p, column k) with p fastest, so that a warp
+    //    reads the contiguous row segments of a few columns
+    const C* xh = a.xh + (size_t)m * CP;
+    const size_t kstride = (size_t)a.M * CP;
+    for (int idx = tid; idx < NPIN * H; idx += nth) {
+      const int p = idx % NPIN, k = idx / NPIN;
+      const C* col = xh + (size_t)k * kstride;
+      C xa, xb;
+      if constexpr (sizeof(C) == 8 && !HALO) {
+        // rows r0 + 2p, r0 + 2p + 1: adjacent, 16-byte aligned (r0 even, CP even)
+        const float4 v = *reinterpret_cast<const float4*>(col + r0 + 2 * p);
+        xa = mk<C>(v.x, v.y);
+        xb = mk<C>(v.z, v.w);
+      } else {
+        xa = col[grow(2 * p)];
+        xb = col[grow(2 * p + 1)];
       }
-    } else {
-      for (int idx = tid; idx < NPIN * H; idx += nth) {
-        const int p = idx / H, k = idx - p * H;
-        const C xa = xh[(size_t)grow(2 * p) * P + k];
-        const C xb = xh[(size_t)grow(2 * p + 1) * P + k];
-        pair_spectrum_put(zb + p * ZS, N, k, xa, xb);
-      }
+      pair_spectrum_put(zb + p * ZS, N, k, xa, xb);
     }
     __syncthreads();
     {
@@ -290,6 +308,16 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
         fft_team<C, LOGN, 1, E, +1>(zb + (team < NPIN ? team : 0) * ZS, tid % TEAM, a.tw, ts, team < NPIN);
     }
     __syncthreads();
+  }
+  if constexpr (PRIOR == ROWS_OUT) {
+    // x rows r0 .. r0 + R - 1 of map m into u_out ([maps][N][N])
+    for (int idx = tid; idx < NPIN * N; idx += nth) {
+      const int p = idx / N, n = idx - p * N;
+      const C z = zb[p * ZS + spad(n)];
+      u_out[(size_t)(r0 + 2 * p) * N + n] = z.x;
+      u_out[(size_t)(r0 + 2 * p + 1) * N + n] = z.y;
+    }
+    return;
   }
 
   // 2. analysis operator, shrinkage, dual update; 3. q = qscale T^T (t - u')
@@ -377,7 +405,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
       }
       __syncthreads();
     }
-    if constexpr (USTAGE) mbar_wait_bounded(&ubar, 0, a.err);
+    if constexpr (USTAGE) u_ok = mbar_wait_bounded(&ubar, 0, a.err, a.test_fault ? 64 : (1 << 22));
     // column DCT -> coefficients w; shrink; dual; inverse column DCT of (t - u')
     for (int idx = tid; idx < (R / 8) * N; idx += nth) {
       const int br = idx / N, c = idx - br * N;
@@ -394,7 +422,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const size_t g = (size_t)(r0 + br * 8 + k) * N + c;
-        const T uo = USTAGE ? us[(br * 8 + k) * N + c] : u_in[g];
+        const T uo = (USTAGE && u_ok) ? us[(br * 8 + k) * N + c] : u_in[g];
         T t, un;
         if (import_mode) {
           t = timp[g];
@@ -422,8 +450,15 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
 #pragma unroll
       for (int n = 0; n < 8; ++n) zb[p * ZS + spad(c0 + n)] = mk<C>(o[n].x * a.qscale, o[n].y * a.qscale);
     }
+  } else if constexpr (PRIOR == ROWS_IN) {
+    // q rows from real rows: zb = qscale (u_in[r0 + 2p], u_in[r0 + 2p + 1])
+    for (int idx = tid; idx < NPOUT * N; idx += nth) {
+      const int p = idx / N, n = idx - p * N;
+      zb[p * ZS + spad(n)] = mk<C>(u_in[(size_t)(r0 + 2 * p) * N + n] * a.qscale,
+                                   u_in[(size_t)(r0 + 2 * p + 1) * N + n] * a.qscale);
+    }
   } else {  // PRIOR_L1: T = I
-    if constexpr (USTAGE) mbar_wait_bounded(&ubar, 0, a.err);
+    if constexpr (USTAGE) u_ok = mbar_wait_bounded(&ubar, 0, a.err, a.test_fault ? 64 : (1 << 22));
     for (int idx = tid; idx < NPOUT * N; idx += nth) {
       const int p = idx / N, c = idx - p * N;
       const C z = zb[p * ZS + spad(c)];
@@ -432,7 +467,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const size_t g = (size_t)(r0 + 2 * p + s) * N + c;
-        const T uo = USTAGE ? us[(2 * p + s) * N + c] : u_in[g];
+        const T uo = (USTAGE && u_ok) ? us[(2 * p + s) * N + c] : u_in[g];
         T t, un;
         if (import_mode) {
           t = timp[g];
@@ -458,34 +493,27 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
       fft_team<C, LOGN, 1, E, -1>(zb + (team < NPOUT ? team : 0) * ZS, tid % TEAM, a.tw, ts, team < NPOUT);
   }
   __syncthreads();
-  C* qh = a.qh + (size_t)m * N * P;
-  if constexpr (sizeof(C) == 8) {
-    constexpr int HP = N / 4 + 1;
-    for (int idx = tid; idx < NPOUT * HP; idx += nth) {
-      const int p = idx / HP, k = 2 * (idx - p * HP);
-      C qa0, qb0, qa1, qb1;
-      pair_spectrum_get(zb + p * ZS, N, k, qa0, qb0);
-      C* ra = qh + (size_t)(r0 + 2 * p) * P + k;
-      C* rb = qh + (size_t)(r0 + 2 * p + 1) * P + k;
-      if (k + 1 < H) {
-        pair_spectrum_get(zb + p * ZS, N, k + 1, qa1, qb1);
-        *reinterpret_cast<float4*>(ra) = make_float4(qa0.x, qa0.y, qa1.x, qa1.y);
-        *reinterpret_cast<float4*>(rb) = make_float4(qb0.x, qb0.y, qb1.x, qb1.y);
-      } else {
-        *ra = qa0;
-        *rb = qb0;
-      }
-    }
-  } else {
-    for (int idx = tid; idx < NPOUT * H; idx += nth) {
-      const int p = idx / H, k = idx - p * H;
-      C qa, qb;
-      pair_spectrum_get(zb + p * ZS, N, k, qa, qb);
-      qh[(size_t)(r0 + 2 * p) * P + k] = qa;
-      qh[(size_t)(r0 + 2 * p + 1) * P + k] = qb;
+  // 5. scatter the row half-spectra of q into the column layout: rows r0 + 2p, r0 + 2p + 1 of
+  //    column k are adjacent (one 16-byte store for complex64)
+  C* qh = a.qh + (size_t)m * CP;
+  const size_t qstride = (size_t)a.M * CP;
+  for (int idx = tid; idx < NPOUT * H; idx += nth) {
+    const int p = idx % NPOUT, k = idx / NPOUT;
+    C qa, qb;
+    pair_spectrum_get(zb + p * ZS, N, k, qa, qb);
+    C* col = qh + (size_t)k * qstride + r0 + 2 * p;
+    if constexpr (sizeof(C) == 8) {
+      *reinterpret_cast<float4*>(col) = make_float4(qa.x, qa.y, qb.x, qb.y);
+    } else {
+      col[0] = qa;
+      col[1] = qb;
     }
   }
   if (resid) block_reduce_store<T>(part, a.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kNPart);
+  if constexpr (USTAGE) {
+    // a copy that was only late must not write this CTA's shared memory after the CTA ends
+    if (tid == 0 && !u_ok && a.test_fault == 0) mbar_wait_bounded(&ubar, 0, a.err);
+  }
 }
 
 template <typename T, int LOGN, int PRIOR>
@@ -533,6 +561,8 @@ template <typename T> cudaError_t launch_passA(const PassAArgs<T>& a, int N, int
     case PRIOR_TV_ISO: return dispatchA<T, PRIOR_TV_ISO>(a, N, s);
     case PRIOR_DCT8: return dispatchA<T, PRIOR_DCT8>(a, N, s);
     case PRIOR_L1: return dispatchA<T, PRIOR_L1>(a, N, s);
+    case ROWS_OUT: return dispatchA<T, ROWS_OUT>(a, N, s);
+    case ROWS_IN: return dispatchA<T, ROWS_IN>(a, N, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -265,6 +265,48 @@ def convdict_problem(seed: int = BASE_SEED + 2, N: int = 256, M: int = 5, L: int
                    filters=d, dtype=dtype)
 
 
+def channel_profile_filters(rng: np.random.Generator, d2: np.ndarray, Q: int) -> np.ndarray:
+    """3D filters [L][Q][P][P]: each 2D filter times a Gaussian profile along the channels (centre
+    Q//2, width U[0.7, 2] channels), scaled to unit L2 (data synthesis for the 3D dictionary)."""
+    L = d2.shape[0]
+    q = np.arange(Q) - Q // 2
+    out = np.empty((L,) + (Q,) + d2.shape[1:], dtype=np.float64)
+    for l in range(L):
+        w = np.exp(-(q * q) / (2.0 * rng.uniform(0.7, 2.0) ** 2))
+        out[l] = w[:, None, None] * d2[l][None]
+        out[l] /= np.linalg.norm(out[l])
+    return out
+
+
+def convdict3d_image(d3: np.ndarray, z: np.ndarray) -> np.ndarray:
+    """x = sum_l d3_l (*) z_l with circular 3D convolution over (channel, row, column), filters
+    [L][Q][P][P] centred at (Q//2, P//2, P//2), codes [L][M][N][N] (data synthesis)."""
+    L, Q, P, _ = d3.shape
+    M, N = z.shape[1], z.shape[-1]
+    emb = np.zeros((L, M, N, N))
+    iq, ip = (np.arange(Q) - Q // 2) % M, (np.arange(P) - P // 2) % N
+    for l in range(L):
+        emb[l][np.ix_(iq, ip, ip)] = d3[l]
+    Xh = np.einsum("lkab,lkab->kab", np.fft.fftn(emb, axes=(1, 2, 3)), np.fft.fftn(z, axes=(1, 2, 3)))
+    return np.fft.ifftn(Xh, axes=(0, 1, 2)).real
+
+
+def convdict3d_problem(seed: int = BASE_SEED + 5, N: int = 256, M: int = 16, L: int = 6, Q: int = 5, P: int = 11,
+                       iters: int = 30, dtype: str = "f32") -> Problem:
+    """3D convolutional dictionary (Section V's spectral experiment in shape: filters of Q taps
+    along the channels): Gabor P x P filters times a Gaussian channel profile, 1%
+    Bernoulli-Gaussian 3D codes, Gaussian defocus PSFs as in the tiny instance, 25 dB,
+    lambda=0.15, beta=4, rho=8."""
+    rng = np.random.default_rng(seed)
+    d3 = channel_profile_filters(rng, gabor_filters(rng, L, P), Q)
+    z = bernoulli_gaussian_codes(rng, L, M, N, 0.01)
+    x = convdict3d_image(d3, z)
+    h = gaussian_psf_bank(N, M, M)
+    y, _ = measure(rng, x, h, 25.0)
+    return Problem(f"convdict3d_{N}x{N}x{M}_L{L}_Q{Q}", N, M, M, "convdict", 0.15, 8.0, 4.0, iters, h, y, x,
+                   filters=d3, dtype=dtype)
+
+
 def mixed_batch(seed: int = BASE_SEED + 3, n_inst: int = 64, sizes: Sequence[int] = (128, 256, 512, 1024),
                 Ms: Sequence[int] = (3, 5, 10), iters: int = 100) -> List[Problem]:
     """Uneven batch: N uniform over ``sizes``, M=K uniform over ``Ms``; M=3
