@@ -10,10 +10,11 @@
 // R-row segments.
 //
 // Fused form (colpass_fused_kernel): one CTA per column k2.
-//   * a producer warp streams the factor and data-term planes of the column
-//     through a ring of shared-memory stages (32 bins x (npk + M) planes per
-//     stage, one TMA bulk copy per plane segment, completed on an mbarrier);
-//     the first stages are requested before the grid dependency, since they do
+//   * a producer warp streams the factor and data term of the column through a
+//     ring of shared-memory stages (32 bins x (npk + M) planes per stage: two
+//     bulk copies, since both are stored blocked by 32 bins of a column, see
+//     binp), completed on mbarriers; the first stages, and the rest of the
+//     column into L2, are requested before the grid dependency, since they do
 //     not depend on the preceding prior pass;
 //   * after the dependency it fetches q-hat of the M channels (one bulk copy
 //     per channel) into the channel slots of the tile;
@@ -166,8 +167,8 @@ template <typename T> struct FusedArgs {
   using C = typename CT<T>::type;
   const C* qh;    // [H][S][CP] q-hat row spectra (column layout)
   C* xh;          // [H][S][CP] x-hat row spectra (column layout)
-  const C* pinv;  // [H][npk][CP] packed Psi^{-1} / N^2
-  const C* xb;    // [H][M][CP] data term / N^2 (or b for the plain FP32 method)
+  const C* pinv;  // packed Psi^{-1} / N^2, blocked by 32 bins (binp, npk planes)
+  const C* xb;    // data term / N^2 (or b for the plain FP32 method), blocked by 32 bins (M planes)
   const C* tw;
   int* err;       // set to 1 when a bounded wait gives up
   int M, S, npk, nstage, plain;
@@ -217,20 +218,30 @@ __global__ void __launch_bounds__(fused_threads<T, LOGN, MMAX>(), fused_minblock
 
   if (warp == cons_warps) {
     // ---------------- producer warp ----------------
-    const unsigned seg = kStageBins * sizeof(C);
+    // stage s = bin block s of the column: its npk factor planes and M data-term planes are two
+    // contiguous runs of the blocked layouts, fetched by two bulk copies
+    const unsigned fbytes = (unsigned)(npk * kStageBins * sizeof(C)), xbytes = (unsigned)(M * kStageBins * sizeof(C));
     auto issue_stage = [&](int s) {
       const int slot = s % NS;
       C* dstg = ring + (size_t)slot * planes * kStageBins;
-      if (lane == 0) mbar_arrive_expect_tx(&full[slot], seg * planes);
-      __syncwarp();
-      for (int p = lane; p < planes; p += 32) {
-        const C* src = p < npk ? a.pinv + ((size_t)k2 * npk + p) * CP + s * kStageBins
-                               : a.xb + ((size_t)k2 * M + (p - npk)) * CP + s * kStageBins;
-        bulk_copy_g2s(dstg + (size_t)p * kStageBins, src, seg, &full[slot]);
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&full[slot], fbytes + xbytes);
+        bulk_copy_g2s(dstg, a.pinv + binp(k2, 0, s * kStageBins, npk, N), fbytes, &full[slot]);
+        bulk_copy_g2s(dstg + (size_t)npk * kStageBins, a.xb + binp(k2, 0, s * kStageBins, M, N), xbytes, &full[slot]);
       }
+      __syncwarp();
     };
     int s = 0;
     for (; s < NS && s < NSC; ++s) issue_stage(s);  // independent of the preceding kernel
+    // The rest of the column's factor and data term into L2 as well: the preceding prior pass is
+    // compute-bound and leaves HBM bandwidth unused while this CTA waits for it (one contiguous
+    // run each in the blocked layout; requests of at most 64 KB)
+    if (lane == 0 && NSC > NS) {
+      const size_t f0 = binp(k2, 0, NS * kStageBins, npk, N), f1 = binp(k2, 0, 0, npk, N) + (size_t)N * npk;
+      const size_t x0 = binp(k2, 0, NS * kStageBins, M, N), x1 = binp(k2, 0, 0, M, N) + (size_t)N * M;
+      for (size_t o = f0; o < f1; o += 8192) prefetch_l2(a.pinv + o, (f1 - o < 8192 ? f1 - o : 8192) * sizeof(C));
+      for (size_t o = x0; o < x1; o += 8192) prefetch_l2(a.xb + o, (x1 - o < 8192 ? x1 - o : 8192) * sizeof(C));
+    }
     grid_dep_wait();
     grid_dep_launch();
     if (lane == 0) mbar_arrive_expect_tx(tfull, (unsigned)(M * N * sizeof(C)));

@@ -137,16 +137,13 @@ __global__ void __launch_bounds__(kSolveThreads, solve_minblocks<T, MMAX>())
   const int k1 = blockIdx.x * kSolveThreads + threadIdx.x;
   const int k2 = blockIdx.y;
   {
+    // the CTA's bins [k1lo, k1lo + 128) are whole 32-bin blocks: one contiguous run of the
+    // blocked factor and one of the data term
     const int npk = M * (M + 1) / 2;
-    const int CP = col_pitch(N);
     const int k1lo = blockIdx.x * kSolveThreads;
     const int cnt = min(kSolveThreads, N - k1lo);
-    const int j = threadIdx.x;
-    if (j < npk + M) {
-      const C* base = (j < npk) ? pinv + ((size_t)k2 * npk + j) * CP + k1lo
-                                : xb + ((size_t)k2 * M + (j - npk)) * CP + k1lo;
-      prefetch_l2(base, (size_t)cnt * sizeof(C));
-    }
+    if (threadIdx.x == 0) prefetch_l2(pinv + binp(k2, 0, k1lo, npk, N), (size_t)cnt * npk * sizeof(C));
+    if (threadIdx.x == 1) prefetch_l2(xb + binp(k2, 0, k1lo, M, N), (size_t)cnt * M * sizeof(C));
   }
   grid_dep_wait();  // the forward column DFTs are complete from here on
   grid_dep_launch();
@@ -154,14 +151,14 @@ __global__ void __launch_bounds__(kSolveThreads, solve_minblocks<T, MMAX>())
   const int npk = M * (M + 1) / 2;
   const int CP = col_pitch(N);
   C* col = colbuf + (size_t)k2 * M * CP + k1;
-  const C* xcol = xb + (size_t)k2 * M * CP + k1;
-  const C* pcol = pinv + (size_t)k2 * npk * CP + k1;
+  const C* xcol = xb + binp(k2, 0, k1, M, N);      // plane stride kBinBlock
+  const C* pcol = pinv + binp(k2, 0, k1, npk, N);  // plane stride kBinBlock
   C r[MMAX], x[MMAX];
 #pragma unroll
   for (int i = 0; i < MMAX; ++i) {
     if (i < M) {
       r[i] = col[(size_t)i * CP];
-      x[i] = xcol[(size_t)i * CP];
+      x[i] = xcol[(size_t)i * kBinBlock];
       if (plain) {  // plain FP32 method: X = Pinv (b + Q)
         r[i] = cadd(r[i], x[i]);
         x[i] = mk<C>(0.0, 0.0);
@@ -175,7 +172,7 @@ __global__ void __launch_bounds__(kSolveThreads, solve_minblocks<T, MMAX>())
 #pragma unroll
       for (int j = i; j < MMAX; ++j) {
         if (j < M) {
-          const C pij = pcol[(size_t)pk * CP];
+          const C pij = pcol[(size_t)pk * kBinBlock];
           ++pk;
           cfma(x[i], pij, r[j]);
           if (j != i) cfmac(x[j], pij, r[i]);

@@ -79,6 +79,15 @@ __host__ __device__ __forceinline__ constexpr int half_pitch(int N) { return N /
 // so that consecutive planes are not a power-of-two stride apart.
 __host__ __device__ __forceinline__ constexpr int col_pitch(int N) { return N + 32; }
 
+// Per-bin planes of the factor Psi^{-1} and of the data term, blocked by 32 bins of a column:
+// [k2][k1 / 32][plane][32].  The planes of 32 consecutive bins of one column form one
+// contiguous run, which the fused column pass fetches with a single bulk copy per ring stage,
+// and a warp reading one plane of 32 consecutive bins reads one contiguous segment.
+constexpr int kBinBlock = 32;
+__host__ __device__ __forceinline__ size_t binp(int k2, int plane, int k1, int nplanes, int N) {
+  return (((size_t)k2 * (N / kBinBlock) + (k1 >> 5)) * nplanes + plane) * kBinBlock + (k1 & (kBinBlock - 1));
+}
+
 // Bulk prefetch of [p, p + bytes) into L2 (TMA unit, no shared memory, no
 // completion to wait for).  The range is widened to 16-byte boundaries; the
 // caller guarantees that the widened range lies inside one allocation.

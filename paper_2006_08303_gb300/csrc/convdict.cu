@@ -35,20 +35,20 @@ __global__ void __launch_bounds__(128) cd_solve_kernel(CDArgs<T> a) {
   // stored factor is Psi^{-1}/N^2, so x = xb + N^2 (Psi^{-1}/N^2) p.
   // x_m = xb_m + sum_j P(m, j) p_j  (P Hermitian, packed upper triangle per bin)
   const C* pin = a.p_in + (size_t)k2 * M * CP + k1;
-  const C* pcol = a.pinv + (size_t)k2 * npk * CP + k1;
+  const C* pcol = a.pinv + binp(k2, 0, k1, npk, N);  // plane stride kBinBlock
   C acc = mk<C>(0.0, 0.0);
 #pragma unroll
   for (int j = 0; j < MMAX; ++j) {
     if (j < M) {
       const int i0 = min(m, j), j0 = max(m, j);
       const int pk = i0 * M - (i0 * (i0 - 1)) / 2 + (j0 - i0);
-      const C pij = pcol[(size_t)pk * CP];
+      const C pij = pcol[(size_t)pk * kBinBlock];
       const C pj = pin[(size_t)j * CP];
       if (m <= j) cfma(acc, pij, pj);
       else cfmac(acc, pij, pj);
     }
   }
-  C x = a.xb[((size_t)k2 * M + m) * CP + k1];
+  C x = a.xb[binp(k2, m, k1, M, N)];
   x.x += a.n2 * acc.x;
   x.y += a.n2 * acc.y;
   a.xcol[((size_t)k2 * M + m) * CP + k1] = x;

@@ -159,10 +159,10 @@ __global__ void __launch_bounds__(kFacThreads) factor_kernel(const SetupC<Tout>*
     }
   }
   // Psi^{-1} = W^H W, packed upper, scaled by 1/N^2 (exact: N is a power of two); the
-  // plan-precision copy is stored [k2][pk][k1] (contiguous bins along a column), the
-  // setup-precision copy [pk][k1][P]
+  // plan-precision copy is stored blocked by 32 bins of a column (binp), the setup-precision
+  // copy [pk][k1][P]
   const float sc = 1.0f / ((float)N * (float)N);
-  const size_t colbase = (size_t)k2 * (M * (M + 1) / 2) * col_pitch(N) + k1;
+  const int npk = M * (M + 1) / 2;
   int pk = 0;
   for (int i = 0; i < M; ++i) {
     for (int j = i; j < M; ++j) {
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kFacThreads) factor_kernel(const SetupC<Tout>*
       for (int k = j; k < M; ++k) cfmac(t, A(tri(k, i)), A(tri(k, j)));
       if (i == j) t.y = R(0.0f);
       t = cscale_pow2(t, sc);
-      pinv[colbase + (size_t)pk * col_pitch(N)] = cconv<C>(t);
+      pinv[binp(k2, pk, k1, npk, N)] = cconv<C>(t);
       if (pinv64) pinv64[(size_t)pk * mplane + off] = t;
       ++pk;
     }
@@ -253,7 +253,7 @@ __global__ void factor_pinv_kernel(const SetupC<Tout>* __restrict__ lam, const d
         }
       }
       if (i == j) im = 0.0;
-      pinv[((size_t)k2 * (M * (M + 1) / 2) + pk) * col_pitch(N) + k1] = mk<C>(re * sc, im * sc);
+      pinv[binp(k2, pk, k1, M * (M + 1) / 2, N)] = mk<C>(re * sc, im * sc);
       if (pinv64) pinv64[(size_t)pk * mplane + off] = cconv<SetupC<Tout>>(make_double2(re * sc, im * sc));
       ++pk;
     }
@@ -312,10 +312,10 @@ __global__ void __launch_bounds__(128) rhs_kernel(const SetupC<Tout>* __restrict
       }
     }
   }
-  // stored [k2][m][k1]: the bins of one column are contiguous for the column pass
+  // stored blocked by 32 bins of a column (binp), as the factor
 #pragma unroll
   for (int m = 0; m < MMAX; ++m)
-    if (m < M) xb[((size_t)k2 * M + m) * col_pitch(N) + k1] = cconv<C>(x[m]);
+    if (m < M) xb[binp(k2, m, k1, M, N)] = cconv<C>(x[m]);
 }
 
 template <typename Tout>
@@ -515,14 +515,14 @@ __global__ void __launch_bounds__(128) factor_fp32_kernel(const cdf* __restrict_
     }
   }
   const float sc = 1.0f / ((float)N * (float)N);
-  const size_t colbase = (size_t)k2 * (M * (M + 1) / 2) * col_pitch(N) + k1;
+  const int npk = M * (M + 1) / 2;
   int pk = 0;
   for (int i = 0; i < M; ++i)
     for (int j = i; j < M; ++j) {
       float2 s = make_float2(0.f, 0.f);
       for (int k = j; k < M; ++k) cfmac(s, W[k][i], W[k][j]);
       if (i == j) s.y = 0.f;
-      pinv[colbase + (size_t)pk * col_pitch(N)] = make_float2(s.x * sc, s.y * sc);
+      pinv[binp(k2, pk, k1, npk, N)] = make_float2(s.x * sc, s.y * sc);
       ++pk;
     }
 }
@@ -539,7 +539,7 @@ __global__ void rhs_fp32_kernel(const cdf* __restrict__ lam, const cdf* __restri
     for (int k = 0; k < K; ++k) {
       cfmac(acc, cconv<float2>(lam[(size_t)(k * M + m) * mplane + off]), cconv<float2>(yhat[(size_t)k * mplane + off]));
     }
-    b[((size_t)k2 * M + m) * col_pitch(N) + k1] = make_float2(beta * acc.x, beta * acc.y);
+    b[binp(k2, m, k1, M, N)] = make_float2(beta * acc.x, beta * acc.y);
   }
 }
 

@@ -10,7 +10,9 @@
 // twiddles w_{Ls R}^{r (t mod Ls)}, does a radix-R DFT in registers and
 // writes y[(t/Ls) Ls R + t mod Ls + r Ls] (autosorting Stockham, natural
 // order in and out).  Twiddles come from a table of exp(-2 pi i k / 2048)
-// computed on the host in FP64 and rounded once.
+// computed on the host in FP64 and rounded once; a radix-8 butterfly loads
+// only w^j and w^4j and forms w^2j, w^3j, w^5j, w^6j, w^7j by at most two
+// complex products (a few ulp), since table loads stalled the stages.
 #pragma once
 #include "common.cuh"
 
@@ -139,7 +141,14 @@ __device__ __forceinline__ void stockham_stage(C* buf, int f, int tt, const C* _
     for (int b = 0; b < B; ++b) {
       const int j = (tt + TT * b) & (LS - 1);
 #pragma unroll
-      for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = ldg_tw(&tw[r * j * (kTwN / (LS * R))]);
+      if constexpr (R == 8) {
+        const C w1 = ldg_tw(&tw[j * (kTwN / (LS * R))]), w4 = ldg_tw(&tw[4 * j * (kTwN / (LS * R))]);
+        const C w2 = cmul(w1, w1), w3 = cmul(w1, w2);
+        C* ww = &w[b * (R - 1)];
+        ww[0] = w1; ww[1] = w2; ww[2] = w3; ww[3] = w4; ww[4] = cmul(w4, w1); ww[5] = cmul(w4, w2); ww[6] = cmul(w4, w3);
+      } else {
+        for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = ldg_tw(&tw[r * j * (kTwN / (LS * R))]);
+      }
     }
   }
   // Padded addresses as base + constant: with q = (N/R)*NF, the unpadded
@@ -227,7 +236,14 @@ __device__ __forceinline__ void fft_stage_io(int tt, const C* __restrict__ tw, I
     for (int b = 0; b < B; ++b) {
       const int j = (tt + TT * b) & (LS - 1);
 #pragma unroll
-      for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = ldg_tw(&tw[r * j * (kTwN / (LS * R))]);
+      if constexpr (R == 8) {
+        const C w1 = ldg_tw(&tw[j * (kTwN / (LS * R))]), w4 = ldg_tw(&tw[4 * j * (kTwN / (LS * R))]);
+        const C w2 = cmul(w1, w1), w3 = cmul(w1, w2);
+        C* ww = &w[b * (R - 1)];
+        ww[0] = w1; ww[1] = w2; ww[2] = w3; ww[3] = w4; ww[4] = cmul(w4, w1); ww[5] = cmul(w4, w2); ww[6] = cmul(w4, w3);
+      } else {
+        for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = ldg_tw(&tw[r * j * (kTwN / (LS * R))]);
+      }
     }
   }
 #pragma unroll

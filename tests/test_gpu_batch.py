@@ -78,6 +78,46 @@ def test_batch_matches_oracle(torch):
     Q.close()
 
 
+def test_batch_classes_match_oracle_after_100_iterations(torch):
+    """One instance per (N, M) class of the 64-instance mixed batch -- N in {128, 256, 512, 1024},
+    M = K in {3, 5, 10}, rectangles + Gaussian PSFs for M = 3, spectral images + disk-plus-Gaussian
+    PSFs otherwise, TV, lambda = 1e-2, rho = 1 -- iterated together in one batch for 100 iterations;
+    every instance's x against the FP64 oracle at <= 1e-4."""
+    from paper_2006_08303_gb300 import api
+    classes = [(128, 3), (128, 10), (256, 5), (512, 3), (512, 10), (1024, 10)]
+    probs = []
+    for i, (N, M) in enumerate(classes):
+        rng = np.random.default_rng(1000 + i)
+        if M == 3:
+            x = inputs.rectangles_image(rng, N, M)
+            h = inputs.gaussian_psf_bank(N, M, M)
+        else:
+            x = inputs.spectral_image(rng, N, M)
+            h = inputs.disk_gaussian_psf_bank(N, M, M)
+        y, _ = inputs.measure(rng, x, h, 30.0)
+        probs.append((N, M, h, y))
+    plans = []
+    for N, M, h, y in probs:
+        P = api.Plan(N, M, M, "f32")
+        P.set_prior("tv", 1e-2, 1.0, 1.0)
+        P.set_psfs(torch.as_tensor(h, dtype=torch.float32).cuda())
+        P.set_measurements(torch.as_tensor(y, dtype=torch.float32).cuda())
+        plans.append(P)
+    B = api.Batch(plans)
+    B.iterate(100)
+    torch.cuda.synchronize()
+    errs = {}
+    for (N, M, h, y), P in zip(probs, plans):
+        S = fast.analysis_setup(h, y, "tv", 1e-2, 1.0, 1.0)
+        x_or, _, _, _, _ = fast.run_analysis(S, 100)
+        errs[(N, M)] = rel(P.get_x().double().cpu().numpy(), x_or)
+    B.close()
+    for P in plans:
+        P.close()
+    print("batch classes, rel err after 100 iterations:", {f"{k[0]}x{k[1]}": f"{v:.2e}" for k, v in errs.items()})
+    assert max(errs.values()) <= 1e-4, errs
+
+
 def test_plain_fp32_method_is_less_accurate_on_ill_conditioned_bins(torch):
     """The plain FP32 method (factor formed and applied in FP32) versus the mixed path on the
     spectral DCT instance (rho = 1e-2, kappa(Psi) ~ 1e4): both run, the mixed path stays within the

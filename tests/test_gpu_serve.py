@@ -57,6 +57,11 @@ def test_served_results_equal_alone(torch):
             time.sleep(0.05)  # later requests arrive while the first ones run
     results = [S.wait(rid) for rid, _ in ids]
     S.close()
+    # continuous batching: requests were in flight on the device at the same time (one admitted
+    # while another was still running), not served one after another
+    overlaps = sum(1 for a in results for b in results
+                   if a is not b and a["t_admit"] < b["t_done"] and b["t_admit"] < a["t_done"])
+    assert overlaps > 0, [(r["t_admit"], r["t_done"]) for r in results]
     for (rid, x_out), res, (h, y, prior, lam, rho) in zip(ids, results, reqs):
         assert res["state"] == "done", res
         assert res["t_submit"] <= res["t_admit"] <= res["t_done"]
@@ -140,6 +145,11 @@ def test_served_k_differs_from_m(torch):
     ids = [S.submit(h, y, prior, lam, rho, tol=1e-3, max_iter=150) for (h, y, prior, lam, rho) in reqs]
     results = [S.wait(rid) for rid, _ in ids]
     S.close()
+    # continuous batching: requests were in flight on the device at the same time (one admitted
+    # while another was still running), not served one after another
+    overlaps = sum(1 for a in results for b in results
+                   if a is not b and a["t_admit"] < b["t_done"] and b["t_admit"] < a["t_done"])
+    assert overlaps > 0, [(r["t_admit"], r["t_done"]) for r in results]
     for (rid, x_out), res, (h, y, prior, lam, rho) in zip(ids, results, reqs):
         assert res["state"] == "done", res
         x_alone, n_alone = alone(torch, h, y, prior, lam, rho, 1e-3, 150)

@@ -120,7 +120,6 @@ def test_noalloc_under_stream_capture_allocates_nothing(prior):
     # first call on this device outside any capture (it looks up the scratch array's address)
     api.shrink_dual_noalloc(prior, Pr.lam, Pr.rho, x, u_in, t_prev, u_a, r_a, t_out=t_a)
     torch.cuda.synchronize()
-    alloc0 = torch.cuda.memory_allocated()
 
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
@@ -133,21 +132,27 @@ def test_noalloc_under_stream_capture_allocates_nothing(prior):
                 api.shrink_dual_noalloc(prior, Pr.lam, Pr.rho, x, u_in, t_prev, u_b, host, t_out=t_b, stream=side)
             assert ei.value.status == 1
     torch.cuda.current_stream().wait_stream(side)
-    torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()  # after the graph's own instantiation
     for _ in range(2):  # two replays in a row
         u_b.zero_()
         r_b.zero_()
+        torch.cuda.synchronize()
+        free_r0, _ = torch.cuda.mem_get_info()
         g.replay()
         torch.cuda.synchronize()
+        free_r1, _ = torch.cuda.mem_get_info()
+        assert free_r1 == free_r0, (free_r0, free_r1)
         assert torch.equal(u_b, u_a) and torch.equal(t_b, t_a)
         assert torch.equal(r_b, r_a)
-    # and two more plain calls: nothing allocated by the library at any point
+    # and two more plain calls: nothing allocated by the library at any point (measured around the
+    # library calls alone, with no torch operation in between)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
     for _ in range(2):
         api.shrink_dual_noalloc(prior, Pr.lam, Pr.rho, x, u_in, t_prev, u_b, r_b, t_out=t_b)
     torch.cuda.synchronize()
-    assert torch.equal(u_b, u_a) and torch.equal(r_b, r_a)
     free1, _ = torch.cuda.mem_get_info()
     assert torch.cuda.memory_allocated() == alloc0
     assert free1 == free0, (free0, free1)
+    assert torch.equal(u_b, u_a) and torch.equal(r_b, r_a)
     del g
