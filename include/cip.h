@@ -83,7 +83,10 @@ typedef struct cip_options {
                        CIP_TUNE_CACHE when set, one "N M dtype mode cc" line per decision, read on
                        first use), 1 = fused kernel (one CTA per half-spectrum column, factor
                        streamed by TMA bulk copies; CIP_ERR_UNSUPPORTED where its tile does not fit
-                       in shared memory), 2 = split (column FFT / solve / FFT) */
+                       in shared memory), 2 = split (column FFT / solve / FFT).  TV plans with
+                       N >= 2048 always use the split form: it carries their low-column correction
+                       (near DC the x-update takes Q from the transforms of the two components of
+                       t - u, not of T^H (t - u), whose FP32 rounding Psi^{-1} amplifies) */
   int precision;    /* CIP_F32 plans: 0 = mixed (factor and data term Psi^{-1} beta Lambda^H F y formed
                        in double-float, about 44 bits, rounded once; the default), 1 = plain FP32
                        method (factor formed and

@@ -61,6 +61,9 @@ struct cip_plan {
   int rowsA = 8, cc = 1, blocksA = 0, blocksB = 0;
   int colmode = 1;  // column pass: 1 fused kernel, 2 split (FFT / solve / FFT)
   int test_fault = 0;  // test-only fault switch (cip_set_test_fault)
+  // TV at N >= kLowFixMinN: low-column correction of the x-update (launch_passB_split)
+  void* lowbuf = nullptr;  // [2][kLowK][M][CP] low-frequency row DFTs of the components of t - u
+  void* lowq = nullptr;    // [2][kLowK][M][CP] their column DFTs
   // convolutional dictionary (prior CIP_PRIOR_CONVDICT): L filters of P x P, or of Q x P x P
   // (3D dictionary, Q >= 1; Q = 0 for the 2D dictionary)
   int L = 0, Pf = 0, Q = 0;
@@ -150,6 +153,13 @@ int smaps(const cip_plan* p) { return is_cd(p) ? p->M * p->L : p->M; }
 
 bool valid_n(int N) { return N >= 64 && N <= 2048 && (N & (N - 1)) == 0; }
 
+// TV plans from this size on take Q of the columns k2 < kLowK from the transforms of the
+// components of t - u (launch_passB_split): below it the FP32 rounding that Psi^{-1} amplifies
+// near DC stays within the per-step tolerance
+constexpr int kLowFixMinN = 2048;
+bool low_fix(const cip_plan* p) { return !is_cd(p) && prior_is_tv(p->prior) && p->N >= kLowFixMinN; }
+size_t low_elems(const cip_plan* p) { return (size_t)kLowK * p->M * col_pitch(p->N); }
+
 // sizes in elements
 size_t half_elems(const cip_plan* p, int maps) { return (size_t)maps * p->N * p->P; }
 // column-contiguous per-bin planes [N/2+1][planes][col_pitch(N)] (+ slack for 16-byte prefetch widening)
@@ -201,6 +211,14 @@ template <typename T> cip_status alloc_state(cip_plan* p) {
   }
   free_ptr(p, p->tprev);
   CIP_CUDA(p, dmalloc(p, &p->tprev, real_elems(p, S) * nc * sizeof(T)));
+  free_ptr(p, p->lowbuf);
+  free_ptr(p, p->lowq);
+  if (low_fix(p)) {
+    CIP_CUDA(p, dmalloc(p, &p->lowbuf, 2 * low_elems(p) * sizeof(C)));
+    CIP_CUDA(p, dmalloc(p, &p->lowq, 2 * low_elems(p) * sizeof(C)));
+    p->colmode = 2;  // the correction is part of the split column pass
+    if (!p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
+  }
   if (is_cd(p)) {
     // row spectra of v and of rho (t - u) over the coefficient maps, the column buffer and p, x
     free_ptr(p, p->xh);
@@ -258,6 +276,7 @@ template <typename T> cip_status reset_state(cip_plan* p, cudaStream_t s) {
   CIP_CUDA(p, cudaMemsetAsync(p->u[0], 0, real_elems(p, S) * nc * sizeof(T), s));
   CIP_CUDA(p, cudaMemsetAsync(p->u[1], 0, real_elems(p, S) * nc * sizeof(T), s));
   CIP_CUDA(p, cudaMemsetAsync(p->tprev, 0, real_elems(p, S) * nc * sizeof(T), s));
+  if (p->lowbuf) CIP_CUDA(p, cudaMemsetAsync(p->lowbuf, 0, 2 * low_elems(p) * sizeof(C), s));
   if (is_cd(p)) {
     for (int i = 0; i < 2; ++i) CIP_CUDA(p, cudaMemsetAsync(p->pbuf[i], 0, col_elems(p, p->M) * sizeof(C), s));
     CIP_CUDA(p, cudaMemsetAsync(p->xcol, 0, col_elems(p, p->M) * sizeof(C), s));
@@ -507,6 +526,7 @@ template <typename T> PassAArgs<T> passA_args(cip_plan* p, int flags) {
   a.qscale = is_cd(p) ? (T)(0.5 * p->rho / ((double)p->N * p->N)) : (T)(0.5 * p->rho);
   a.flags = flags;
   a.test_fault = p->test_fault;
+  a.lowbuf = low_fix(p) ? static_cast<C*>(p->lowbuf) : nullptr;
   fill_dct<T>(a.dct);
   return a;
 }
@@ -651,7 +671,10 @@ template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mo
   if (mode == 2) {
     if (!p->colbuf) return fail(p, CIP_ERR_STATE, "split column pass selected without its column buffer");
     int n = 0;
-    CIP_CUDA(p, launch_passB_split<T>(b, static_cast<C*>(p->colbuf), p->N, s, &n));
+    const bool lf = low_fix(p) && p->lowbuf;
+    CIP_CUDA(p, launch_passB_split<T>(b, static_cast<C*>(p->colbuf), p->N, s, &n,
+                                      lf ? static_cast<const C*>(p->lowbuf) : nullptr,
+                                      lf ? static_cast<C*>(p->lowq) : nullptr, (T)p->rho));
     p->launches += n;
   } else {
     (void)cc;
@@ -692,6 +715,12 @@ void tune_cache_store(const std::tuple<int, int, int>& key, std::pair<int, int> 
 template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
   using C = typename CT<T>::type;
   const auto key = std::make_tuple(p->N, p->M, (int)p->dtype);
+  if (low_fix(p)) {  // the low-column correction of large TV plans is part of the split form
+    p->colmode = 2;
+    p->blocksB = p->M * (p->N / 2 + 1);
+    if (!p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
+    return CIP_OK;
+  }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_cache_load();
@@ -707,7 +736,7 @@ template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
   }
   if (!p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
   std::vector<std::pair<int, int>> cands = {{2, 0}};
-  if (colpass_fused_fits<T>(p->N, p->M)) cands.insert(cands.begin(), {1, 1});
+  if (colpass_fused_fits<T>(p->N, p->M) && !low_fix(p)) cands.insert(cands.begin(), {1, 1});
   cudaEvent_t e0, e1;
   CIP_CUDA(p, cudaEventCreate(&e0));
   CIP_CUDA(p, cudaEventCreate(&e1));
@@ -1180,7 +1209,7 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->w3, p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv, p->wbuf[0], p->wbuf[1], p->wbuf[2], p->wcos,
+  void* bufs[] = {p->lowbuf, p->lowq, p->w3, p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv, p->wbuf[0], p->wbuf[1], p->wbuf[2], p->wcos,
                   p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
@@ -1446,6 +1475,7 @@ static std::vector<std::pair<void*, size_t>> state_segments(cip_plan* p) {
   const size_t hb = col_elems(p, S) * 2 * p->esz;
   const size_t ub = real_elems(p, S) * ncomp_of(p->prior) * p->esz;
   std::vector<std::pair<void*, size_t>> seg = {{p->xh, hb}, {p->qh, hb}, {p->u[p->cur], ub}, {p->tprev, ub}};
+  if (p->lowbuf) seg.push_back({p->lowbuf, 2 * low_elems(p) * 2 * p->esz});  // the next x-update's low columns
   if (is_cd(p)) {
     seg.push_back({p->pbuf[p->pcur], col_elems(p, p->M) * 2 * p->esz});
     seg.push_back({p->xcol, col_elems(p, p->M) * 2 * p->esz});

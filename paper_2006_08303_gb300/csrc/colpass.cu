@@ -83,6 +83,7 @@ __device__ __forceinline__ void consumer_bar(int nthreads) {
 // Column FFTs on the column layout: every (k2, map) column of N contiguous
 // values is transformed in place or out of place (src may equal dst).  One
 // team per column; the first stage reads global memory, the last writes it.
+// Columns past ncols come from a second range (src2 -> dst2, ncols2 columns).
 // ---------------------------------------------------------------------------
 constexpr int kColThreads = 256;
 
@@ -90,7 +91,8 @@ template <typename T, int LOGN, int SIGN>
 __global__ void __launch_bounds__(kColThreads) colfft_cols_kernel(const typename CT<T>::type* src,
                                                                   typename CT<T>::type* dst,
                                                                   const typename CT<T>::type* __restrict__ tw,
-                                                                  int ncols) {
+                                                                  int ncols, const typename CT<T>::type* src2,
+                                                                  typename CT<T>::type* dst2, int ncols2) {
   using C = typename CT<T>::type;
   constexpr int N = 1 << LOGN, E = cp_elems<T>(N), TT = N / E, TEAMS = kColThreads / TT;
   constexpr int CP = col_pitch(N), ZS = spad(N);
@@ -101,9 +103,10 @@ __global__ void __launch_bounds__(kColThreads) colfft_cols_kernel(const typename
   grid_dep_wait();
   grid_dep_launch();
   // idle teams (past the last column) still take part in the CTA-wide barriers of wide teams
-  const bool active = col < ncols;
-  const C* s = src + (size_t)(active ? col : 0) * CP;
-  C* d = dst + (size_t)(active ? col : 0) * CP;
+  const bool active = col < ncols + ncols2;
+  const bool second = active && col >= ncols;
+  const C* s = second ? src2 + (size_t)(col - ncols) * CP : src + (size_t)(active ? col : 0) * CP;
+  C* d = second ? dst2 + (size_t)(col - ncols) * CP : dst + (size_t)(active ? col : 0) * CP;
   C* buf = zb + team * ZS;
   const ColSync cs = col_sync(team, TT);
   auto in0 = [&](int i0, int off) { return s[i0 + off]; };
@@ -115,7 +118,8 @@ __global__ void __launch_bounds__(kColThreads) colfft_cols_kernel(const typename
 
 template <typename T, int LOGN, int SIGN>
 cudaError_t launch_cols(const typename CT<T>::type* src, typename CT<T>::type* dst, const typename CT<T>::type* tw,
-                        int ncols, cudaStream_t s) {
+                        int ncols, cudaStream_t s, const typename CT<T>::type* src2, typename CT<T>::type* dst2,
+                        int ncols2) {
   using C = typename CT<T>::type;
   constexpr int N = 1 << LOGN, TT = cp_team<T>(N), TEAMS = kColThreads / TT;
   const size_t sm = (size_t)TEAMS * spad(N) * sizeof(C);
@@ -125,7 +129,8 @@ cudaError_t launch_cols(const typename CT<T>::type* src, typename CT<T>::type* d
     cudaError_t e = once([&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); });
     if (e != cudaSuccess) return e;
   }
-  return launch_pdl(k, dim3((ncols + TEAMS - 1) / TEAMS), dim3(kColThreads), sm, s, 0, src, dst, tw, ncols);
+  return launch_pdl(k, dim3((ncols + ncols2 + TEAMS - 1) / TEAMS), dim3(kColThreads), sm, s, 0, src, dst, tw, ncols,
+                    src2, dst2, ncols2);
 }
 
 // ---------------------------------------------------------------------------
@@ -420,17 +425,22 @@ template <typename T> cudaError_t launch_colpass_fused(const PassBArgs<T>& b, in
 
 template <typename T>
 cudaError_t launch_cols_fft(const typename CT<T>::type* src, typename CT<T>::type* dst,
-                            const typename CT<T>::type* tw, int N, int maps, int sign, cudaStream_t s) {
+                            const typename CT<T>::type* tw, int N, int maps, int sign, cudaStream_t s,
+                            const typename CT<T>::type* src2, typename CT<T>::type* dst2, int ncols2) {
   const int ncols = (N / 2 + 1) * maps;
+#define CIP_COLS(L) \
+  return sign < 0 ? launch_cols<T, L, -1>(src, dst, tw, ncols, s, src2, dst2, ncols2) \
+                  : launch_cols<T, L, 1>(src, dst, tw, ncols, s, src2, dst2, ncols2)
   switch (N) {
-    case 64: return sign < 0 ? launch_cols<T, 6, -1>(src, dst, tw, ncols, s) : launch_cols<T, 6, 1>(src, dst, tw, ncols, s);
-    case 128: return sign < 0 ? launch_cols<T, 7, -1>(src, dst, tw, ncols, s) : launch_cols<T, 7, 1>(src, dst, tw, ncols, s);
-    case 256: return sign < 0 ? launch_cols<T, 8, -1>(src, dst, tw, ncols, s) : launch_cols<T, 8, 1>(src, dst, tw, ncols, s);
-    case 512: return sign < 0 ? launch_cols<T, 9, -1>(src, dst, tw, ncols, s) : launch_cols<T, 9, 1>(src, dst, tw, ncols, s);
-    case 1024: return sign < 0 ? launch_cols<T, 10, -1>(src, dst, tw, ncols, s) : launch_cols<T, 10, 1>(src, dst, tw, ncols, s);
-    case 2048: return sign < 0 ? launch_cols<T, 11, -1>(src, dst, tw, ncols, s) : launch_cols<T, 11, 1>(src, dst, tw, ncols, s);
+    case 64: CIP_COLS(6);
+    case 128: CIP_COLS(7);
+    case 256: CIP_COLS(8);
+    case 512: CIP_COLS(9);
+    case 1024: CIP_COLS(10);
+    case 2048: CIP_COLS(11);
     default: return cudaErrorInvalidValue;
   }
+#undef CIP_COLS
 }
 
 template bool colpass_fused_fits<float>(int, int);
@@ -439,7 +449,9 @@ template size_t colpass_fused_smem<float>(int, int);
 template size_t colpass_fused_smem<double>(int, int);
 template cudaError_t launch_colpass_fused<float>(const PassBArgs<float>&, int, int*, cudaStream_t);
 template cudaError_t launch_colpass_fused<double>(const PassBArgs<double>&, int, int*, cudaStream_t);
-template cudaError_t launch_cols_fft<float>(const float2*, float2*, const float2*, int, int, int, cudaStream_t);
-template cudaError_t launch_cols_fft<double>(const double2*, double2*, const double2*, int, int, int, cudaStream_t);
+template cudaError_t launch_cols_fft<float>(const float2*, float2*, const float2*, int, int, int, cudaStream_t,
+                                            const float2*, float2*, int);
+template cudaError_t launch_cols_fft<double>(const double2*, double2*, const double2*, int, int, int, cudaStream_t,
+                                             const double2*, double2*, int);
 
 }  // namespace cip

@@ -132,7 +132,9 @@ template <typename T, int MMAX> constexpr int solve_minblocks() {
 template <typename T, int MMAX>
 __global__ void __launch_bounds__(kSolveThreads, solve_minblocks<T, MMAX>())
     solve_split_kernel(typename CT<T>::type* __restrict__ colbuf, const typename CT<T>::type* __restrict__ pinv,
-                       const typename CT<T>::type* __restrict__ xb, int N, int M, int plain) {
+                       const typename CT<T>::type* __restrict__ xb, int N, int M, int plain,
+                       const typename CT<T>::type* __restrict__ lowcol, const typename CT<T>::type* __restrict__ tw,
+                       T rho) {
   using C = typename CT<T>::type;
   const int k1 = blockIdx.x * kSolveThreads + threadIdx.x;
   const int k2 = blockIdx.y;
@@ -154,10 +156,26 @@ __global__ void __launch_bounds__(kSolveThreads, solve_minblocks<T, MMAX>())
   const C* xcol = xb + binp(k2, 0, k1, M, N);      // plane stride kBinBlock
   const C* pcol = pinv + binp(k2, 0, k1, npk, N);  // plane stride kBinBlock
   C r[MMAX], x[MMAX];
+  // columns k2 < kLowK of a TV plan with the low-column correction: Q from the column DFTs of the
+  // components of t - u, the differences applied as spectral products
+  const bool low = lowcol && k2 < kLowK;
+  C dh = mk<C>(0.0, 0.0), dv = dh;
+  if (low) {
+    const C wh = ldg_tw(&tw[k2 * (kTwN / N)]), wv = ldg_tw(&tw[k1 * (kTwN / N)]);
+    dh = mk<C>(wh.x - 1.0, -wh.y);  // exp(+2 pi i k2 / N) - 1
+    dv = mk<C>(wv.x - 1.0, -wv.y);
+  }
 #pragma unroll
   for (int i = 0; i < MMAX; ++i) {
     if (i < M) {
-      r[i] = col[(size_t)i * CP];
+      if (low) {
+        C q = mk<C>(0.0, 0.0);
+        cfmac(q, dh, lowcol[((size_t)k2 * M + i) * CP + k1]);
+        cfmac(q, dv, lowcol[((size_t)(kLowK + k2) * M + i) * CP + k1]);
+        r[i] = mk<C>(rho * q.x, rho * q.y);
+      } else {
+        r[i] = col[(size_t)i * CP];
+      }
       x[i] = xcol[(size_t)i * kBinBlock];
       if (plain) {  // plain FP32 method: X = Pinv (b + Q)
         r[i] = cadd(r[i], x[i]);
@@ -216,13 +234,17 @@ cudaError_t colfft_n(const typename CT<T>::type* src, typename CT<T>::type* dst,
 
 template <typename T>
 cudaError_t solve_m(typename CT<T>::type* colbuf, const typename CT<T>::type* pinv, const typename CT<T>::type* xb,
-                    int N, int M, int plain, cudaStream_t s) {
+                    int N, int M, int plain, const typename CT<T>::type* lowcol, const typename CT<T>::type* tw,
+                    T rho, cudaStream_t s) {
   const dim3 grid((N + kSolveThreads - 1) / kSolveThreads, N / 2 + 1), block(kSolveThreads);
-  if (M <= 4) return launch_pdl(solve_split_kernel<T, 4>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
-  if (M <= 8) return launch_pdl(solve_split_kernel<T, 8>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
-  if (M <= 10) return launch_pdl(solve_split_kernel<T, 10>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
-  if (M <= 12) return launch_pdl(solve_split_kernel<T, 12>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
-  if (M <= 16) return launch_pdl(solve_split_kernel<T, 16>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain);
+#define CIP_SOLVE(MM) \
+  return launch_pdl(solve_split_kernel<T, MM>, grid, block, 0, s, 0, colbuf, pinv, xb, N, M, plain, lowcol, tw, rho)
+  if (M <= 4) CIP_SOLVE(4);
+  if (M <= 8) CIP_SOLVE(8);
+  if (M <= 10) CIP_SOLVE(10);
+  if (M <= 12) CIP_SOLVE(12);
+  if (M <= 16) CIP_SOLVE(16);
+#undef CIP_SOLVE
   return cudaErrorInvalidValue;
 }
 
@@ -230,11 +252,13 @@ cudaError_t solve_m(typename CT<T>::type* colbuf, const typename CT<T>::type* pi
 
 template <typename T>
 cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colbuf, int N, cudaStream_t s,
-                               int* launches) {
-  // q-hat and x-hat use the column layout already: the column DFTs need no transposition
-  cudaError_t e = launch_cols_fft<T>(a.qh, colbuf, a.tw, N, a.M, -1, s);
+                               int* launches, const typename CT<T>::type* lowbuf, typename CT<T>::type* lowcol,
+                               T rho) {
+  // q-hat and x-hat use the column layout already: the column DFTs need no transposition; the
+  // low-column maps of the correction (2 kLowK M columns) ride along in the forward launch
+  cudaError_t e = launch_cols_fft<T>(a.qh, colbuf, a.tw, N, a.M, -1, s, lowbuf, lowcol, lowbuf ? 2 * kLowK * a.M : 0);
   if (e != cudaSuccess) return e;
-  e = solve_m<T>(colbuf, a.pinv, a.bhat, N, a.M, a.plain, s);
+  e = solve_m<T>(colbuf, a.pinv, a.bhat, N, a.M, a.plain, lowbuf ? lowcol : nullptr, a.tw, rho, s);
   if (e != cudaSuccess) return e;
   e = launch_cols_fft<T>(colbuf, a.xh, a.tw, N, a.M, +1, s);
   if (launches) *launches += 3;
@@ -256,7 +280,9 @@ template cudaError_t launch_colfft_fwd<double>(const double2*, double2*, const d
 template cudaError_t launch_colfft_inv<float>(const float2*, float2*, const float2*, int, int, cudaStream_t);
 template cudaError_t launch_colfft_inv<double>(const double2*, double2*, const double2*, int, int, cudaStream_t);
 
-template cudaError_t launch_passB_split<float>(const PassBArgs<float>&, float2*, int, cudaStream_t, int*);
-template cudaError_t launch_passB_split<double>(const PassBArgs<double>&, double2*, int, cudaStream_t, int*);
+template cudaError_t launch_passB_split<float>(const PassBArgs<float>&, float2*, int, cudaStream_t, int*,
+                                               const float2*, float2*, float);
+template cudaError_t launch_passB_split<double>(const PassBArgs<double>&, double2*, int, cudaStream_t, int*,
+                                                const double2*, double2*, double);
 
 }  // namespace cip

@@ -16,6 +16,7 @@ constexpr bool prior_is_tv(int p) { return p == PRIOR_TV || p == PRIOR_TV_ISO; }
 // flags of the prior pass
 enum { PA_STORE_T = 1, PA_RESID = 2, PA_IMPORT = 4 };
 constexpr int kNPart = 5;  // sum (w-t)^2, sum w^2, sum t^2, sum u^2, sum (t - t_prev)^2
+constexpr int kLowK = 2;   // half-spectrum columns k2 < kLowK get the low-column correction (TV)
 
 inline int prior_ncomp(int prior) { return prior_is_tv(prior) ? 2 : 1; }
 
@@ -44,6 +45,8 @@ template <typename T> struct PassAArgs {
   int flags;
   int test_fault;   // 1: the staged u copy is replaced by a barrier that never completes (test of
                     // the bounded wait: no copy is issued, the wait gives up after 64 polls)
+  C* lowbuf;        // TV: [2][kLowK][M][CP] row DFTs of the components of t - u' at k2 < kLowK
+                    // for the low-column correction of the split column pass; NULL: not formed
   T dct[64];        // orthonormal DCT-II, dct[k*8+n]
 };
 
@@ -151,12 +154,19 @@ template <typename T> cudaError_t launch_colpass_fused(const PassBArgs<T>& b, in
 // sign < 0 forward, > 0 inverse (unnormalised)
 template <typename T>
 cudaError_t launch_cols_fft(const typename CT<T>::type* src, typename CT<T>::type* dst,
-                            const typename CT<T>::type* tw, int N, int maps, int sign, cudaStream_t s);
+                            const typename CT<T>::type* tw, int N, int maps, int sign, cudaStream_t s,
+                            const typename CT<T>::type* src2 = nullptr, typename CT<T>::type* dst2 = nullptr,
+                            int ncols2 = 0);
 // split form: column FFT of qh into colbuf (same layout), per-bin solve in place, inverse column FFT
-// into xh
+// into xh.  With lowbuf (TV, low-column correction), the same forward launch also transforms the
+// 2 kLowK M low-frequency columns of lowbuf into lowcol, and the solve takes, for the columns
+// k2 < kLowK, Q = rho (conj(dh(k2)) F A_h + conj(dv(k1)) F A_v) in place of the column DFT of q:
+// near DC the FP32 transforms of q = D^T (t - u) carry a uniform rounding error that Psi^{-1}
+// amplifies by ~1/g, the transforms of the components of t - u do not.
 template <typename T>
 cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colbuf, int N, cudaStream_t s,
-                               int* launches);
+                               int* launches, const typename CT<T>::type* lowbuf = nullptr,
+                               typename CT<T>::type* lowcol = nullptr, T rho = T(0));
 
 // Setup / read-back FFTs (not fused).
 // rows: nrows real rows of length N -> half spectra with pitch P (unnormalised forward DFT)

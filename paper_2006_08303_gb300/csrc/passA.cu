@@ -391,6 +391,37 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
       }
       zb[p * ZS + spad(c)] = mk<C>(q[0], q[1]);
     }
+    // Row frequencies k2 = 0 and 1 (kLowK = 2) of the two components of a = t - u' on the output
+    // rows, as direct sums with the exact table twiddle exp(-2 pi i c / N), for the low-column
+    // correction of the x-update (launch_passB_split): near DC the FP32 transforms of q = D^T a
+    // carry a uniform rounding error that Psi^{-1} amplifies by ~1/g, while transforms of a itself
+    // do not.  One warp per (row, component), lanes over the columns; layout [comp][k2][map][CP].
+    static_assert(kLowK == 2, "the sums below form k2 = 0 and 1");
+    if (a.lowbuf) {
+      const int nw = nth >> 5, wid = tid >> 5, lane = tid & 31;
+      for (int o = wid; o < R * 2; o += nw) {
+        const int jj = o >> 1, comp = o & 1;
+        const T* src = comp == 0 ? ah + jj * N : av + (jj + 1) * N;
+        T s0 = T(0), re = T(0), im = T(0);
+        for (int c = lane; c < N; c += 32) {
+          const T v = src[c];
+          const C w = ldg_tw(&a.tw[c * (kTwN / N)]);
+          s0 += v;
+          re = fma(v, (T)w.x, re);
+          im = fma(v, (T)w.y, im);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          s0 += __shfl_down_sync(0xffffffffu, s0, off);
+          re += __shfl_down_sync(0xffffffffu, re, off);
+          im += __shfl_down_sync(0xffffffffu, im, off);
+        }
+        if (lane == 0) {
+          a.lowbuf[((size_t)(comp * kLowK + 0) * a.M + m) * CP + r0 + jj] = mk<C>(s0, 0.0);
+          a.lowbuf[((size_t)(comp * kLowK + 1) * a.M + m) * CP + r0 + jj] = mk<C>(re, im);
+        }
+      }
+    }
   } else if constexpr (PRIOR == PRIOR_DCT8) {
     if (!import_mode) {
       // row DCT of every 8-sample segment of both rows of a pair, in place
