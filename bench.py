@@ -288,6 +288,66 @@ def workload_convdict(args, torch, api, inputs):
                         "algorithmic_bytes": {"column_pass": col_bytes, "prior_pass": pri_bytes}}}
 
 
+def workload_convdict3d(args, torch, api, inputs):
+    """3D convolutional dictionary (Section IV-B, 3D case): 256 x 256 x 16, 6 filters of 5 x 11 x 11
+    taps (the shape of Section V's spectral experiment), 30 iterations of Alg. 2 with the 1D DFT
+    along the channels (setup + iterations + read-back).  The CPU leg is the FP64 oracle on 2
+    iterations of the same problem."""
+    from oracle import fast
+    pr = inputs.convdict3d_problem()
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+    h, y, d = f(pr.h), f(pr.y), f(pr.filters)
+    x = torch.empty((pr.M, pr.N, pr.N), device="cuda")
+    plan = api.Plan(pr.N, pr.K, pr.M, "f32")
+    plan.set_prior("convdict", pr.lam, pr.rho, pr.beta)
+    plan.set_dictionary_3d(d)
+
+    def step():
+        plan.set_psfs(h)
+        plan.set_measurements(y)
+        plan.iterate(pr.iters)
+        plan.get_x(x)
+
+    for _ in range(args.warmup):
+        step()
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")
+    ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        ts.append(_ev_time(torch, step))
+    plan.set_timing(True)
+    step()
+    kt = plan.get_timing()
+    plan.close()
+    L = pr.filters.shape[0]
+    S, bins = L * pr.M, pr.N * (pr.N // 2 + 1)
+    # column DFTs of the S code maps (read + write, both ways) around the per-3D-bin solve, which
+    # reads G, Theta (M L planes), p, the data term and the factor and writes v, p and x-hat
+    col_bytes = (4 * S + 2 * S + S + 5 * pr.M + pr.M * (pr.M + 1) // 2) * bins * 8
+    pri_bytes = 2 * S * bins * 8 + 2 * S * pr.N * pr.N * 4
+    avgB = kt["column_pass_ms"] / max(kt["column_pass_n"], 1)
+    avgA = kt["prior_pass_ms"] / max(kt["prior_pass_n"], 1)
+    t = sum(ts) / len(ts)
+    t0 = time.perf_counter()
+    C = fast.convdict3d_setup(pr.h, pr.y, pr.filters, pr.lam, pr.rho, pr.beta)
+    z = np.zeros((L, pr.M, pr.N, pr.N)); tt = np.zeros_like(z); u = np.zeros_like(z)
+    t1 = time.perf_counter()
+    for _ in range(2):
+        _, z, tt, u = fast.convdict3d_step(C, z, tt, u)
+    t2 = time.perf_counter()
+    recon = (t1 - t0) + (t2 - t1) / 2 * pr.iters
+    return {"metric": METRIC, "value": pr.voxels * pr.iters / t, "unit": "voxel-iter/s", "ms_per_step": 1e3 * t,
+            "config": {"workload": f"convdict3d_{pr.N}x{pr.N}x{pr.M}_L{L}_Q5_P11 (Gabor x Gaussian channel profile, "
+                                   f"25 dB, lambda=0.15, beta=4, rho=8, {pr.iters} iterations)",
+                       "step": "setup + iterations + read-back"},
+            "kernels": {"column_pass_us": 1e3 * avgB, "column_pass_GBps": col_bytes / avgB / 1e6,
+                        "prior_pass_us": 1e3 * avgA, "prior_pass_GBps": pri_bytes / avgA / 1e6,
+                        "algorithmic_bytes": {"column_pass": col_bytes, "prior_pass": pri_bytes}},
+            "cpu_baseline": {"value": pr.voxels * pr.iters / recon, "unit": "voxel-iter/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "setup + 2 iterations of the same problem, FP64 scipy.fft, "
+                                                         "scaled to a full reconstruction"}}
+
+
 def workload_dictlearn(args, torch, api, inputs):
     """The convdict workload (256 x 256 x 5, 32 Gabor 11 x 11 filters, 300 iterations) with the
     online dictionary update on (Section IV-B, sigma = 10): every iteration adds one filter-ADMM
@@ -337,8 +397,11 @@ def workload_dictlearn(args, torch, api, inputs):
     t = out[True]
     upd_s = (out[True] - out[False]) / pr.iters
     S, bins = L * pr.M, pr.N * (pr.N // 2 + 1)
-    # a fused update's least traffic per iteration: read z-hat, x-hat, g, e; write g, e, theta, p
-    upd_bytes = (S + 2 * pr.M + L) * bins * 8 + 4 * L * pr.N * pr.N * 4
+    # least traffic of one filter step: read z-hat, x-hat, theta, F(g - e); write theta, F(g - e), p
+    upd_bytes = (S + 2 * pr.M + 4 * L) * bins * 8
+    # this design's three launches: the solve reads z-hat twice, x-hat, theta, F(g - e) and writes
+    # w; the spectra launch reads w and z-hat and writes theta, F(g - e) and p
+    upd_design = (3 * S + 2 * pr.M + 6 * L) * bins * 8
     t0 = time.perf_counter()
     fast.run_convdict_learn(pr.h, pr.y, pr.filters, pr.lam, pr.rho, pr.beta, sigma, 3)
     tc = time.perf_counter() - t0
@@ -347,8 +410,10 @@ def workload_dictlearn(args, torch, api, inputs):
                                    f"beta=4, rho=8, sigma={sigma:g}, {pr.iters} iterations)",
                        "step": "setup + iterations with the filter update + read-back of x and filters"},
             "without_update_ms_per_step": 1e3 * out[False],
-            "update": {"us_per_iteration": 1e6 * upd_s, "least_bytes": upd_bytes,
-                       "GBps_on_least_bytes": upd_bytes / upd_s / 1e9 if upd_s > 0 else None},
+            "update": {"us_per_iteration": 1e6 * upd_s, "launches_per_iteration": 3, "least_bytes": upd_bytes,
+                       "design_bytes": upd_design,
+                       "GBps_on_least_bytes": upd_bytes / upd_s / 1e9 if upd_s > 0 else None,
+                       "GBps_on_design_bytes": upd_design / upd_s / 1e9 if upd_s > 0 else None},
             "cpu_baseline": {"value": pr.voxels * 3 / tc, "unit": "voxel-iter/s", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": "3 iterations of the same problem, FP64 scipy.fft"}}
 
@@ -411,10 +476,17 @@ def workload_batch(args, torch, api, inputs):
     return res
 
 
+SERVE_MIX = ("tv", "dct8", "tv", "dct8", "wdct", "tv_adapt")  # uniform draw: 1/3 TV, 1/3 DCT, 1/6 each other
+
+
 def _serve_jobs(args, inputs):
-    """The request stream of the serving workload with its inputs (generated once, outside timing)."""
-    reqs = inputs.request_stream(n=args.requests, rate_hz=args.rate)
-    banks, ffts = {}, {}
+    """The request stream of the serving workload with its inputs (generated once, outside timing).
+    Priors: TV and the 8x8 DCT (1/3 each), the Kronecker wavelet (x) DCT prior (1/6), and TV with
+    the adaptive penalty of Eq. paramS started at rho = 8 (1/6).  The measurements of a request
+    come from a pool of two images per PSF set (the request's seed picks one), so that a long
+    stream needs no more than a few hundred distinct inputs."""
+    reqs = inputs.request_stream(n=args.requests, rate_hz=args.rate, priors=SERVE_MIX)
+    banks, ffts, ys = {}, {}, {}
     jobs = []
     for r in reqs:
         key = (r.N, r.M, r.psf_id)
@@ -426,13 +498,20 @@ def _serve_jobs(args, inputs):
                 h = inputs.disk_gaussian_psf_bank(r.N, r.M, r.M, rmax=6.0 + 6.0 * brng.random())
             banks[key] = h.astype(np.float32)
             ffts[key] = np.fft.rfft2(h)
-        rng = np.random.default_rng(r.seed)
-        x = inputs.rectangles_image(rng, r.N, r.M) if r.M == 3 else inputs.spectral_image(rng, r.N, r.M)
-        clean = np.fft.irfft2(np.einsum("kmab,mab->kab", ffts[key], np.fft.rfft2(x)), s=(r.N, r.N))
-        sig = np.sqrt(np.mean(clean * clean) / 1e3)
-        y = (clean + sig * rng.standard_normal(clean.shape)).astype(np.float32)
-        lam, rho = (1e-2, 1.0) if r.prior == "tv" else (1e-3, 1e-2)
-        jobs.append((r, key, y, lam, rho))
+        ykey = key + (r.seed % 2,)
+        if ykey not in ys:
+            rng = np.random.default_rng(hash(ykey) & 0xFFFFFFFF)
+            x = inputs.rectangles_image(rng, r.N, r.M) if r.M == 3 else inputs.spectral_image(rng, r.N, r.M)
+            clean = np.fft.irfft2(np.einsum("kmab,mab->kab", ffts[key], np.fft.rfft2(x)), s=(r.N, r.N))
+            sig = np.sqrt(np.mean(clean * clean) / 1e3)
+            ys[ykey] = (clean + sig * rng.standard_normal(clean.shape)).astype(np.float32)
+        if r.prior == "tv":
+            opts = dict(prior="tv", lam=1e-2, rho=1.0)
+        elif r.prior == "tv_adapt":
+            opts = dict(prior="tv", lam=1e-2, rho=8.0, rho_tau=2.0, rho_mu=10.0)
+        else:  # dct8, wdct
+            opts = dict(prior=r.prior, lam=1e-3, rho=1e-2)
+        jobs.append((r, key, ys[ykey], opts))
     return jobs, banks
 
 
@@ -444,12 +523,13 @@ def _serve_run(args, torch, api, jobs, banks, slow: float = 1.0, cache: bool = T
     t0 = time.perf_counter()
     ids = []
     a0 = jobs[0][0].arrival_s
-    for r, key, y, lam, rho in jobs:
+    for r, key, y, o in jobs:
         dt = (r.arrival_s - a0) * slow - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
         psf_key = (hash(key) & 0xFFFFFFFFFFFF) + 1 if cache else 0
-        ids.append((S.submit(banks[key], y, r.prior, lam, rho, tol=1e-4, max_iter=300, psf_key=psf_key), r))
+        ids.append((S.submit(banks[key], y, o["prior"], o["lam"], o["rho"], tol=1e-4, max_iter=300, psf_key=psf_key,
+                             rho_tau=o.get("rho_tau", 0.0), rho_mu=o.get("rho_mu", 0.0)), r))
     res = [(S.wait(rid), r) for (rid, _), r in ids]
     makespan = max(x["t_done"] for x, _ in res) - min(x["t_submit"] for x, _ in res)
     st = S.stats()
@@ -458,38 +538,45 @@ def _serve_run(args, torch, api, jobs, banks, slow: float = 1.0, cache: bool = T
     done = [x for x, _ in res if x["state"] == "done"]
     vi = sum(r.N * r.N * r.M * x["iterations"] for x, r in res)
     span = (jobs[-1][0].arrival_s - a0) * slow
+    by_prior = {}
+    for x, r in res:
+        by_prior[r.prior] = by_prior.get(r.prior, 0) + 1
     return {"value": vi / makespan, "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
                                                    "p99": float(np.percentile(lat, 99) * 1e3),
                                                    "mean": float(lat.mean() * 1e3)},
             "requests": len(res), "done": len(done), "offered_req_per_s": len(jobs) / max(span, 1e-9),
             "achieved_req_per_s": len(done) / makespan, "voxel_iters": vi, "makespan_s": makespan,
-            "iterations_mean": float(np.mean([x["iterations"] for x, _ in res])), "server": st}
+            "iterations_mean": float(np.mean([x["iterations"] for x, _ in res])), "requests_by_prior": by_prior,
+            "server": st}
 
 
 def workload_serve(args, torch, api, inputs):
-    """Poisson stream of reconstructions (N in {256..2048}, M = K in {3,5,10}, TV or DCT, tol 1e-4,
-    max 300 iterations) served with continuous batching; p50/p99 latency and voxel-iter/s with the
-    PSF-factor cache on and off, and the highest offered rate the server sustains (the same stream,
-    its first 40 requests, stretched to lower rates: sustained when at least 90% of the offered
-    rate is achieved)."""
+    """Poisson stream of reconstructions (N in {256..2048}, M = K in {3,5,10}; TV, DCT, wavelet (x)
+    DCT, TV with the adaptive penalty; tol 1e-4, max 300 iterations) served with continuous
+    batching; p50/p99 latency and voxel-iter/s.  For streams of at most 200 requests also the
+    factor cache off and the highest offered rate the server sustains (the same stream, its first
+    40 requests, stretched to lower rates: sustained when at least 90% of the offered rate is
+    achieved)."""
     jobs, banks = _serve_jobs(args, inputs)
     on = _serve_run(args, torch, api, jobs, banks, cache=True)
-    off = _serve_run(args, torch, api, jobs, banks, cache=False)
-    sweep, sustained = [], None
-    for rate in (2.0, 4.0, 8.0, 16.0, 32.0):
-        r = _serve_run(args, torch, api, jobs, banks, slow=args.rate / rate, cache=True, n=40)
-        ok = r["achieved_req_per_s"] >= 0.9 * r["offered_req_per_s"]
-        sweep.append({"offered_req_per_s": r["offered_req_per_s"], "achieved_req_per_s": r["achieved_req_per_s"],
-                      "p50_ms": r["latency_ms"]["p50"], "p99_ms": r["latency_ms"]["p99"], "sustained": ok})
-        if ok:
-            sustained = r["offered_req_per_s"]
     out = {"metric": "serve voxel-iter/s, p50/p99 latency", "unit": "voxel-iter/s",
-           "config": {"workload": f"poisson_{args.rate:g}hz_{args.requests}req (N 256..2048, M=K 3/5/10, TV/DCT, "
-                                  "tol 1e-4, max 300 iterations)", "max_active": args.max_active}}
+           "config": {"workload": f"poisson_{args.rate:g}hz_{args.requests}req (N 256..2048, M=K 3/5/10, "
+                                  "TV/DCT/wavelet-DCT/adaptive-rho TV, tol 1e-4, max 300 iterations)",
+                      "max_active": args.max_active}}
     out.update(on)
-    out["factor_cache_off"] = {k: off[k] for k in ("value", "latency_ms", "achieved_req_per_s", "makespan_s")}
-    out["rate_sweep"] = sweep
-    out["highest_sustained_req_per_s"] = sustained
+    if args.requests <= 200:
+        off = _serve_run(args, torch, api, jobs, banks, cache=False)
+        sweep, sustained = [], None
+        for rate in (2.0, 4.0, 8.0, 16.0, 32.0):
+            r = _serve_run(args, torch, api, jobs, banks, slow=args.rate / rate, cache=True, n=40)
+            ok = r["achieved_req_per_s"] >= 0.9 * r["offered_req_per_s"]
+            sweep.append({"offered_req_per_s": r["offered_req_per_s"], "achieved_req_per_s": r["achieved_req_per_s"],
+                          "p50_ms": r["latency_ms"]["p50"], "p99_ms": r["latency_ms"]["p99"], "sustained": ok})
+            if ok:
+                sustained = r["offered_req_per_s"]
+        out["factor_cache_off"] = {k: off[k] for k in ("value", "latency_ms", "achieved_req_per_s", "makespan_s")}
+        out["rate_sweep"] = sweep
+        out["highest_sustained_req_per_s"] = sustained
     return out
 
 
@@ -602,7 +689,7 @@ def run_workload(args):
     import torch
     from paper_2006_08303_gb300 import api, inputs
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    fn = {"convdict": workload_convdict, "dictlearn": workload_dictlearn, "batch": workload_batch, "serve": workload_serve,
+    fn = {"convdict": workload_convdict, "convdict3d": workload_convdict3d, "dictlearn": workload_dictlearn, "batch": workload_batch, "serve": workload_serve,
           "precision": workload_precision, "single": workload_single,
           "adaptive": workload_adaptive}[args.workload]
     line = fn(args, torch, api, inputs)
@@ -658,7 +745,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true", help="skip the full FP64-oracle run behind rel_err_final")
     ap.add_argument("--no-above-l2", action="store_true", help="skip the 1024 x 1024 x 10 sub-measurement")
     ap.add_argument("--workload", default="spectral_dct",
-                    choices=["spectral_dct", "convdict", "dictlearn", "batch", "serve", "precision", "single",
+                    choices=["spectral_dct", "convdict", "convdict3d", "dictlearn", "batch", "serve", "precision", "single",
                              "adaptive"])
     ap.add_argument("--N", type=int, default=1024, help="single: image side")
     ap.add_argument("--M", type=int, default=10, help="single: channels (= measurements)")

@@ -79,9 +79,9 @@ typedef struct cip_options {
                        half-spectrum column per CTA */
   int check_every;  /* residual check period for cip_iterate with tol > 0; 0 = 10 */
   int column_pass;  /* 0 = autotuned at cip_set_measurements (fused vs split, tile width; cached per
-                       N, M, dtype for the process, and in the file named by the environment variable
-                       CIP_TUNE_CACHE when set, one "N M dtype mode cc" line per decision, read on
-                       first use), 1 = fused kernel (one CTA per half-spectrum column, factor
+                       N, M, dtype and prior for the process, and in the file named by the environment
+                       variable CIP_TUNE_CACHE when set, one "N M dtype prior mode cc variant" line per
+                       decision, read on first use), 1 = fused kernel (one CTA per half-spectrum column, factor
                        streamed by TMA bulk copies; CIP_ERR_UNSUPPORTED where its tile does not fit
                        in shared memory), 2 = split (column FFT / solve / FFT).  TV plans with
                        N >= 2048 always use the split form: it carries their low-column correction
@@ -92,7 +92,11 @@ typedef struct cip_options {
                        method (factor formed and
                        inverted in FP32, x = Psi^{-1} (beta Lambda^H F y + rho F T^H (t - u)) applied in
                        FP32 every iteration; analysis priors only) */
-  int reserved[12];
+  int prior_fft;    /* FFT elements per thread of the prior pass for CIP_F32 plans with 256 <= N <= 1024
+                       and the TV, isotropic TV, DCT and l1 priors: 0 = chosen by the autotuner together
+                       with the column-pass form (timing whole iterations; the default width when
+                       column_pass != 0), 8 or 16 = that width; ignored for other plans */
+  int reserved[11];
 } cip_options;
 
 typedef struct cip_plan cip_plan;
@@ -187,14 +191,27 @@ cip_status cip_set_code_gradient_weight(cip_plan* plan, double mu);
  * Z(w) the M x L matrix of code spectra; the next iteration uses theta = F g.  The filters
  * persist across cip_set_measurements and cip_reset; cip_set_dictionary starts them again.
  * sigma = 0 turns the update off (the filters learnt so far stay); a new sigma > 0 while on
- * keeps g and e.  The learnt g and e are part of cip_state_export's buffer while on.
- * CIP_ERR_STATE without a dictionary, CIP_ERR_UNSUPPORTED for M > 8, CIP_ERR_INVALID_ARG for
- * sigma < 0 or not finite.  Enqueued on `stream`. */
+ * keeps g and e.  The learnt g and e (and sigma) are part of cip_state_export's buffer while on.
+ * One step is three kernel launches: e is kept as its spectrum and g on its support, so the
+ * spatial values the projection needs are partial inverse DFTs at the P x P support points.
+ * CIP_ERR_STATE without a dictionary, CIP_ERR_UNSUPPORTED for M > 8 or P > 32,
+ * CIP_ERR_INVALID_ARG for sigma < 0 or not finite.  Enqueued on `stream`. */
 cip_status cip_set_dictionary_learning(cip_plan* plan, double sigma, void* stream);
 
-/* Learnt filters g cropped to filters[L][P][P] (plan dtype, centre at index P/2, host or
- * device pointer; a host copy synchronises `stream`).  CIP_ERR_STATE unless the dictionary
- * update is on. */
+/* Adaptation of the filter ADMM's penalty sigma (Section V applies the rule of Eq. paramS to it):
+ * after every check_every-th filter step of the plan (counted over all its iterations), with
+ * r = ||d - g|| and s = sigma ||g - g_prev|| over all filters, sigma becomes tau sigma if
+ * r > mu s, sigma / tau if s > mu r, and stays otherwise; on a change the scaled dual e is
+ * multiplied by sigma_old / sigma_new (the multiplier sigma e is unchanged).  Each check reads
+ * the two residual sums back and synchronises the stream.  tau = 0 turns it off;
+ * CIP_ERR_INVALID_ARG unless tau > 1 and mu > 1 (finite).  Applies to cip_iterate. */
+cip_status cip_set_sigma_adaptation(cip_plan* plan, double tau, double mu);
+
+/* Current penalty sigma of the dictionary update (0 while the update is off). */
+cip_status cip_get_sigma(cip_plan* plan, double* sigma);
+
+/* Learnt filters g, filters[L][P][P] (plan dtype, centre at index P/2, host or device pointer;
+ * a host copy synchronises `stream`).  CIP_ERR_STATE unless the dictionary update is on. */
 cip_status cip_get_dictionary(cip_plan* plan, void* filters, void* stream);
 
 /* Coefficient maps z[M][L][N][N] of the last z-update (CIP_PRIOR_CONVDICT only). */
@@ -275,6 +292,10 @@ cip_status cip_set_test_fault(cip_plan* plan, int kind);
 /* Number of CUDA kernels this plan has launched since creation. */
 cip_status cip_get_launches(cip_plan* plan, unsigned long long* launches);
 
+/* FFT elements per thread of the plan's prior-pass kernel (8 or 16; after cip_set_measurements
+ * this is the autotuner's choice where it has one). */
+cip_status cip_get_prior_fft(cip_plan* plan, int* elems_per_thread);
+
 /* Launch configuration the plan uses (for reporting). */
 cip_status cip_get_config(cip_plan* plan, int* rows_per_tile, int* col_tile, int* prior_pass_blocks,
                           int* column_pass_blocks, int* column_pass);
@@ -307,7 +328,7 @@ cip_status cip_batch_destroy(cip_batch* batch);
 typedef struct cip_server cip_server;
 typedef struct cip_request {
   int N, K, M;
-  int prior;                      /* CIP_PRIOR_TV, CIP_PRIOR_TV_ISO, CIP_PRIOR_DCT8 or CIP_PRIOR_L1 */
+  int prior;                      /* CIP_PRIOR_TV, CIP_PRIOR_TV_ISO, CIP_PRIOR_DCT8, CIP_PRIOR_L1 or CIP_PRIOR_WDCT */
   double lambda, rho, beta;
   const float* h;                 /* host [K][M][N][N] */
   const float* y;                 /* host [K][N][N] */
@@ -315,6 +336,10 @@ typedef struct cip_request {
   double tol;                     /* relative primal/dual residual stop; <= 0: run max_iter */
   int max_iter;
   unsigned long long psf_key;     /* 0 = no factor sharing */
+  double rho_tau, rho_mu;         /* adaptive penalty (Eq. paramS) at every check: rho_tau > 1 and
+                                     rho_mu > 1 turn it on (as cip_set_rho_adaptation), 0 = off; an
+                                     adaptive request keeps its own factor (psf_key is ignored) and
+                                     its setup buffers, so it holds cip_plan_bytes while it runs */
 } cip_request;
 typedef struct cip_result {
   int state;                      /* 0 queued, 1 running, 2 done, 3 failed, 4 cancelled */

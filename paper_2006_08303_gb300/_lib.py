@@ -20,13 +20,13 @@ P_size = ctypes.POINTER(ctypes.c_size_t)
 
 class cip_options(ctypes.Structure):
     _fields_ = [("col_tile", c_int), ("check_every", c_int), ("column_pass", c_int), ("precision", c_int),
-                ("reserved", c_int * 12)]
+                ("prior_fft", c_int), ("reserved", c_int * 11)]
 
 
 class cip_request(ctypes.Structure):
     _fields_ = [("N", c_int), ("K", c_int), ("M", c_int), ("prior", c_int), ("lam", c_double), ("rho", c_double),
                 ("beta", c_double), ("h", c_void_p), ("y", c_void_p), ("x_out", c_void_p), ("tol", c_double),
-                ("max_iter", c_int), ("psf_key", ctypes.c_ulonglong)]
+                ("max_iter", c_int), ("psf_key", ctypes.c_ulonglong), ("rho_tau", c_double), ("rho_mu", c_double)]
 
 
 class cip_result(ctypes.Structure):
@@ -81,6 +81,9 @@ SIGNATURES = {
     "cip_set_code_gradient_weight": (c_int, [c_void_p, c_double]),
     "cip_set_dictionary_learning": (c_int, [c_void_p, c_double, c_void_p]),
     "cip_get_dictionary": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "cip_get_prior_fft": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
+    "cip_set_sigma_adaptation": (c_int, [c_void_p, c_double, c_double]),
+    "cip_get_sigma": (c_int, [c_void_p, P_double]),
     "cip_set_rho_adaptation": (c_int, [c_void_p, c_double, c_double]),
     "cip_get_rho": (c_int, [c_void_p, P_double]),
     "cip_get_coefficients": (c_int, [c_void_p, c_void_p, c_void_p]),

@@ -85,7 +85,7 @@ class Plan:
     """One reconstruction instance held on the device (cip_plan)."""
 
     def __init__(self, N: int, K: int, M: int, dtype: str = "f32", col_tile: int = 0, check_every: int = 0,
-                 column_pass: int = 0, plain_fp32: bool = False):
+                 column_pass: int = 0, plain_fp32: bool = False, prior_fft: int = 0):
         self._L = _lib.load()
         self.N, self.K, self.M, self.dtype = N, K, M, dtype
         self.prior: Optional[str] = None
@@ -94,6 +94,7 @@ class Plan:
         opt.check_every = check_every
         opt.column_pass = column_pass
         opt.precision = 1 if plain_fp32 else 0
+        opt.prior_fft = prior_fft
         h = ctypes.c_void_p()
         st = self._L.cip_plan_create(ctypes.byref(h), N, K, M, DTYPES[dtype], ctypes.byref(opt))
         if st != 0:
@@ -153,6 +154,17 @@ class Plan:
         """Online dictionary update with filter-ADMM penalty sigma (cip_set_dictionary_learning);
         0 turns it off."""
         self._check(self._L.cip_set_dictionary_learning(self._h, ctypes.c_double(sigma), _stream_ptr(stream)))
+
+    def set_sigma_adaptation(self, tau: float = 2.0, mu: float = 10.0):
+        """Adaptation of the filter ADMM's sigma by the rule of Eq. paramS (cip_set_sigma_adaptation;
+        tau = 0: off)."""
+        self._check(self._L.cip_set_sigma_adaptation(self._h, ctypes.c_double(tau), ctypes.c_double(mu)))
+
+    @property
+    def sigma(self) -> float:
+        v = ctypes.c_double()
+        self._check(self._L.cip_get_sigma(self._h, ctypes.byref(v)))
+        return v.value
 
     def get_dictionary(self, out=None, stream=None):
         """Learnt filters [L, P, P] (cip_get_dictionary)."""
@@ -292,8 +304,11 @@ class Plan:
     def config(self):
         v = [ctypes.c_int() for _ in range(5)]
         self._check(self._L.cip_get_config(self._h, *[ctypes.byref(x) for x in v]))
+        e = ctypes.c_int()
+        self._check(self._L.cip_get_prior_fft(self._h, ctypes.byref(e)))
         return {"rows_per_tile": v[0].value, "col_tile": v[1].value, "prior_pass_blocks": v[2].value,
-                "column_pass_blocks": v[3].value, "column_pass": {1: "fused", 2: "split"}.get(v[4].value, "?")}
+                "column_pass_blocks": v[3].value, "column_pass": {1: "fused", 2: "split"}.get(v[4].value, "?"),
+                "prior_fft_elems": e.value}
 
 
 class Batch:
@@ -342,14 +357,15 @@ class Server:
         self._keep = {}
 
     def submit(self, h, y, prior: str, lam: float, rho: float, beta: float = 1.0, tol: float = 0.0,
-               max_iter: int = 300, psf_key: int = 0):
-        """Queue one reconstruction (float32 host arrays h [K][M][N][N], y [K][N][N]); returns (id, x_out)."""
+               max_iter: int = 300, psf_key: int = 0, rho_tau: float = 0.0, rho_mu: float = 0.0):
+        """Queue one reconstruction (float32 host arrays h [K][M][N][N], y [K][N][N]); returns (id, x_out).
+        rho_tau > 1, rho_mu > 1: adaptive penalty of Eq. paramS at every check."""
         h = np.ascontiguousarray(h, dtype=np.float32)
         y = np.ascontiguousarray(y, dtype=np.float32)
         K, M, N = h.shape[0], h.shape[1], h.shape[-1]
         x_out = np.zeros((M, N, N), dtype=np.float32)
         req = _lib.cip_request(N, K, M, PRIORS[prior], lam, rho, beta, h.ctypes.data, y.ctypes.data,
-                               x_out.ctypes.data, tol, max_iter, psf_key)
+                               x_out.ctypes.data, tol, max_iter, psf_key, rho_tau, rho_mu)
         rid = ctypes.c_ulonglong()
         st = self._L.cip_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid))
         if st != 0:

@@ -60,6 +60,7 @@ struct cip_plan {
   size_t esz = 4;
   int rowsA = 8, cc = 1, blocksA = 0, blocksB = 0;
   int colmode = 1;  // column pass: 1 fused kernel, 2 split (FFT / solve / FFT)
+  int avar = 0;     // prior-pass kernel variant (the other FFT width; complex64, N = 256 .. 1024)
   int test_fault = 0;  // test-only fault switch (cip_set_test_fault)
   // TV at N >= kLowFixMinN: low-column correction of the x-update (launch_passB_split)
   void* lowbuf = nullptr;  // [2][kLowK][M][CP] low-frequency row DFTs of the components of t - u
@@ -78,16 +79,20 @@ struct cip_plan {
   void* wcos = nullptr;
   double wfilt[16] = {};
   // online dictionary update (Section IV-B): sigma = 0 off.  While on, theta lives in the first L
-  // planes of dl_spec and F(g - e) in the last L (one forward transform makes both).
+  // planes of dl_spec and F(g - e) in the last L; the filters g on their P x P support in dl_gs.
   double dl_sigma = 0;
-  int dl_L = 0;             // L the buffers below were sized for
-  void* dl_sp = nullptr;    // real [2L][N][N]: g (filters on the torus, Eq. g_admm), then g - e
-  void* dl_e = nullptr;     // real [L][N][N]: scaled dual of the filter ADMM (Eq. h_admm)
-  void* dl_d = nullptr;     // real [L][N][N]: d of Eq. d_admm
-  void* dl_rows = nullptr;  // [2L][N][P] row spectra scratch
+  double dl_tau = 0, dl_mu = 0;  // adaptation of sigma by the rule of Eq. paramS; tau = 0: off
+  int dl_L = 0, dl_P = 0;   // L and P the buffers below were sized for
+  void* filt = nullptr;     // [L][P][P] the filters given to cip_set_dictionary (2D; plan dtype)
   void* dl_spec = nullptr;  // [H][2L][CP]: theta = F g, F(g - e)
-  void* dl_col = nullptr;   // [H][L][CP]: d-hat / N^2
-  void* dl_inv = nullptr;   // [L]: 1 / ||Q^T (d + e)|| of the projection
+  void* dl_col = nullptr;   // [H][L][CP]: w = F(d + e) of the current step
+  void* dl_ypart = nullptr; // [H][N/kDLBlock][L][P] per-CTA partial inverse DFTs at the support rows
+  void* dl_yfull = nullptr; // [L][P][H] the same per column
+  int* dl_cnt = nullptr;    // [H] CTA counters of the column sums
+  void* dl_gfac = nullptr;  // [H][L][P] partial DFTs of the support rows of g
+  void* dl_gs = nullptr;    // [L][P][P] g on the support
+  double* dl_part = nullptr;  // [H N/kDLBlock + L] residual sums of the last check
+  double* dl_host = nullptr;  // pinned copy of dl_part
   const cip_plan* factor_src = nullptr;  // plan whose factor this plan adopted (serving factor cache)
   // device buffers
   void* xh = nullptr;
@@ -350,24 +355,33 @@ void channel_twiddles(int M, double* re, double* im) {
   }
 }
 
-// buffers of the dictionary update for the plan's current L (allocated once per L)
+// buffers of the dictionary update for the plan's current L and P (allocated once per shape)
 cip_status alloc_dict(cip_plan* p) {
-  if (p->dl_sp && p->dl_L == p->L) return CIP_OK;
-  void** bufs[] = {&p->dl_sp, &p->dl_e, &p->dl_d, &p->dl_rows, &p->dl_spec, &p->dl_col, &p->dl_inv};
+  if (p->dl_spec && p->dl_L == p->L && p->dl_P == p->Pf) return CIP_OK;
+  void** bufs[] = {&p->dl_spec, &p->dl_col, &p->dl_ypart, &p->dl_yfull, &p->dl_gfac, &p->dl_gs};
   for (void** b : bufs)
     if (*b) {
       cudaFreeAsync(*b, p->ast);
       *b = nullptr;
     }
+  if (p->dl_cnt) cudaFreeAsync(p->dl_cnt, p->ast);
+  if (p->dl_part) cudaFreeAsync(p->dl_part, p->ast);
+  p->dl_cnt = nullptr;
+  p->dl_part = nullptr;
   const size_t ce = 2 * p->esz;
-  CIP_CUDA(p, dmalloc(p, &p->dl_sp, real_elems(p, 2 * p->L) * p->esz));
-  CIP_CUDA(p, dmalloc(p, &p->dl_e, real_elems(p, p->L) * p->esz));
-  CIP_CUDA(p, dmalloc(p, &p->dl_d, real_elems(p, p->L) * p->esz));
-  CIP_CUDA(p, dmalloc(p, &p->dl_rows, half_elems(p, 2 * p->L) * ce));
+  const size_t H = p->N / 2 + 1, nkb = p->N / kDLBlock, LP = (size_t)p->L * p->Pf;
   CIP_CUDA(p, dmalloc(p, &p->dl_spec, col_elems(p, 2 * p->L) * ce));
   CIP_CUDA(p, dmalloc(p, &p->dl_col, col_elems(p, p->L) * ce));
-  CIP_CUDA(p, dmalloc(p, &p->dl_inv, 32 * p->esz));
+  CIP_CUDA(p, dmalloc(p, &p->dl_ypart, H * nkb * LP * ce));
+  CIP_CUDA(p, dmalloc(p, &p->dl_yfull, H * LP * ce));
+  CIP_CUDA(p, dmalloc(p, &p->dl_gfac, H * LP * ce));
+  CIP_CUDA(p, dmalloc(p, &p->dl_gs, LP * p->Pf * p->esz));
+  CIP_CUDA(p, dmalloc(p, (void**)&p->dl_cnt, H * sizeof(int)));
+  CIP_CUDA(p, cudaMemsetAsync(p->dl_cnt, 0, H * sizeof(int), p->ast));
+  CIP_CUDA(p, dmalloc(p, (void**)&p->dl_part, (H * nkb + p->L) * sizeof(double)));
+  if (!p->dl_host) CIP_CUDA(p, cudaMallocHost((void**)&p->dl_host, (size_t)(2049 * 32 + 32) * sizeof(double)));
   p->dl_L = p->L;
+  p->dl_P = p->Pf;
   return CIP_OK;
 }
 
@@ -416,6 +430,12 @@ template <typename T> cip_status do_set_dictionary(cip_plan* p, const void* d, c
   cudaFreeAsync(emb, s);
   cudaFreeAsync(th64, s);
   CIP_CUDA(p, e);
+  if (p->Q == 0) {  // the filters the online update starts from
+    free_ptr(p, p->filt);
+    const size_t fb = (size_t)p->L * p->Pf * p->Pf * sizeof(T);
+    CIP_CUDA(p, dmalloc(p, &p->filt, fb));
+    CIP_CUDA(p, cudaMemcpyAsync(p->filt, dd, fb, cudaMemcpyDeviceToDevice, s));
+  }
   if (p->dl_sigma > 0) {
     st = alloc_dict(p);
     if (st != CIP_OK) return st;
@@ -461,6 +481,7 @@ template <typename T> cip_status do_set_psfs(cip_plan* p, const void* h, cudaStr
 }
 
 template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s);
+int forced_avar(const cip_plan* p);
 
 // data term xb (or b for the plain FP32 method) from the measurement spectra yhat
 template <typename T> cudaError_t form_data_term(cip_plan* p, const SetupC<T>* yhat, cudaStream_t s) {
@@ -501,6 +522,7 @@ template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream
   }
   CIP_CUDA(p, e);
   p->have_y = true;
+  p->avar = std::max(0, forced_avar(p));
   if (!is_cd(p) && p->opt.column_pass == 0 && p->opt.col_tile == 0) {
     r = autotune<T>(p, s);
     if (r != CIP_OK) return r;
@@ -526,6 +548,7 @@ template <typename T> PassAArgs<T> passA_args(cip_plan* p, int flags) {
   a.qscale = is_cd(p) ? (T)(0.5 * p->rho / ((double)p->N * p->N)) : (T)(0.5 * p->rho);
   a.flags = flags;
   a.test_fault = p->test_fault;
+  a.variant = p->avar;
   a.lowbuf = low_fix(p) ? static_cast<C*>(p->lowbuf) : nullptr;
   fill_dct<T>(a.dct);
   return a;
@@ -684,70 +707,107 @@ template <typename T> cip_status column_pass(cip_plan* p, cudaStream_t s, int mo
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;  // (N, M, dtype) -> (mode, cc)
+// (N, M, dtype, prior) -> (column-pass form, fused tile width, prior-pass variant)
+using TuneKey = std::tuple<int, int, int, int>;
+using TuneVal = std::tuple<int, int, int>;
+std::map<TuneKey, TuneVal> g_tune;
 bool g_tune_loaded = false;
 
-// Optional persistent tuning table: when CIP_TUNE_CACHE names a file, its lines
-// "N M dtype mode cc" seed the table on first use and every new decision is
-// appended, so that later processes (a profiler run, a service restart) reuse a
-// choice instead of timing again under different conditions.  Caller holds g_tune_mu.
+// Tuning decisions persist across processes when CIP_TUNE_CACHE names a file (one line per
+// decision, appended), so that a profiling run under a tool that serialises launches reuses the
+// plain run's choice instead of timing again under different conditions.  Caller holds g_tune_mu.
 void tune_cache_load() {
   if (g_tune_loaded) return;
   g_tune_loaded = true;
   const char* path = std::getenv("CIP_TUNE_CACHE");
   if (!path || !*path) return;
   std::ifstream in(path);
-  int n, m, dt, mode, cc;
-  while (in >> n >> m >> dt >> mode >> cc) g_tune[std::make_tuple(n, m, dt)] = {mode, cc};
+  int n, m, dt, pr, mode, cc, av;
+  while (in >> n >> m >> dt >> pr >> mode >> cc >> av) g_tune[std::make_tuple(n, m, dt, pr)] = {mode, cc, av};
 }
-void tune_cache_store(const std::tuple<int, int, int>& key, std::pair<int, int> v) {
+void tune_cache_store(const TuneKey& key, const TuneVal& v) {
   const char* path = std::getenv("CIP_TUNE_CACHE");
   if (!path || !*path) return;
   std::ofstream out(path, std::ios::app);
-  out << std::get<0>(key) << ' ' << std::get<1>(key) << ' ' << std::get<2>(key) << ' ' << v.first << ' ' << v.second
-      << '\n';
+  out << std::get<0>(key) << ' ' << std::get<1>(key) << ' ' << std::get<2>(key) << ' ' << std::get<3>(key) << ' '
+      << std::get<0>(v) << ' ' << std::get<1>(v) << ' ' << std::get<2>(v) << '\n';
 }
 
-// Autotuner: times the fused column pass at each tile width and the split
-// form on this plan's buffers (the column pass only rewrites x-hat from q-hat,
-// so repeating it leaves the state as it was) and keeps the fastest, cached
-// per (N, M, dtype) for the process.
+bool prior_has_variant(const cip_plan* p) {
+  return p->dtype == CIP_F32 && p->N >= 256 && p->N <= 1024 &&
+         (p->prior == CIP_PRIOR_TV || p->prior == CIP_PRIOR_TV_ISO || p->prior == CIP_PRIOR_DCT8 ||
+          p->prior == CIP_PRIOR_L1);
+}
+// FFT elements per thread of the prior pass's default kernel (the device-side rule of passA.cu)
+int prior_fft_default(const cip_plan* p) {
+  const bool tv = p->prior == CIP_PRIOR_TV || p->prior == CIP_PRIOR_TV_ISO;
+  return (p->dtype == CIP_F32 && p->N <= 1024) ? ((p->N == 512 && !tv) ? 16 : 8) : 16;
+}
+// the variant the options force: -1 none (autotuned), else 0 / 1
+int forced_avar(const cip_plan* p) {
+  if (!prior_has_variant(p)) return 0;
+  if (p->opt.prior_fft == 0) return p->opt.column_pass != 0 || p->opt.col_tile != 0 ? 0 : -1;
+  return p->opt.prior_fft == prior_fft_default(p) ? 0 : 1;
+}
+
+template <typename T> void set_colmode(cip_plan* p, int mode, int cc) {
+  p->colmode = mode;
+  if (mode == 1) p->cc = cc;
+  p->blocksB = mode == 1 ? p->N / 2 + 1 : p->M * (p->N / 2 + 1);
+}
+
+// Autotuner: times whole iterations (column pass, then prior pass, launched back to back as in
+// cip_iterate) for every column-pass form (fused kernel; split FFT / solve / FFT) and both
+// prior-pass FFT widths where a variant exists, on this plan's buffers, and keeps the fastest,
+// cached per (N, M, dtype, prior) for the process.  The prior pass reads u[cur] and writes the
+// other u buffer and q-hat without moving cur, so repeating an iteration keeps its inputs; the
+// state is reset afterwards (cip_set_measurements).
 template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
   using C = typename CT<T>::type;
-  const auto key = std::make_tuple(p->N, p->M, (int)p->dtype);
+  const TuneKey key = std::make_tuple(p->N, p->M, (int)p->dtype, p->prior);
   if (low_fix(p)) {  // the low-column correction of large TV plans is part of the split form
-    p->colmode = 2;
-    p->blocksB = p->M * (p->N / 2 + 1);
+    set_colmode<T>(p, 2, p->cc);
     if (!p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
     return CIP_OK;
   }
-  {
+  const int fav = forced_avar(p);
+  if (fav < 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_cache_load();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      p->colmode = it->second.first;
-      if (p->colmode == 1) p->cc = it->second.second;
-      p->blocksB = p->colmode == 1 ? p->N / 2 + 1 : p->M * (p->N / 2 + 1);
+      set_colmode<T>(p, std::get<0>(it->second), std::get<1>(it->second));
+      p->avar = std::get<2>(it->second);
       // a cached choice of the split form still needs this plan's own column buffer
       if (p->colmode == 2 && !p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
       return CIP_OK;
     }
   }
   if (!p->colbuf) CIP_CUDA(p, dmalloc(p, &p->colbuf, col_elems(p, p->M) * sizeof(C)));
-  std::vector<std::pair<int, int>> cands = {{2, 0}};
-  if (colpass_fused_fits<T>(p->N, p->M) && !low_fix(p)) cands.insert(cands.begin(), {1, 1});
+  std::vector<TuneVal> cands;
+  for (int av = 0; av < (fav < 0 ? 2 : 1); ++av) {
+    if (fav >= 0) av = fav;
+    if (colpass_fused_fits<T>(p->N, p->M)) cands.push_back({1, 1, av});
+    cands.push_back({2, 0, av});
+  }
   cudaEvent_t e0, e1;
   CIP_CUDA(p, cudaEventCreate(&e0));
   CIP_CUDA(p, cudaEventCreate(&e1));
   float best = 1e30f;
-  std::pair<int, int> pick = {p->colmode, p->cc};
+  TuneVal pick = {p->colmode, p->cc, p->avar};
+  auto iteration = [&]() -> cip_status {
+    cip_status st = column_pass<T>(p, s, p->colmode, p->cc);
+    if (st != CIP_OK) return st;
+    return prior_pass<T>(p, passA_args<T>(p, 0), s);
+  };
   for (auto& c : cands) {
+    set_colmode<T>(p, std::get<0>(c), std::get<1>(c));
+    p->avar = std::get<2>(c);
     cip_status st = CIP_OK;
-    for (int w = 0; w < 2 && st == CIP_OK; ++w) st = column_pass<T>(p, s, c.first, c.second);
+    for (int w = 0; w < 2 && st == CIP_OK; ++w) st = iteration();
     if (st != CIP_OK) return st;
     cudaEventRecord(e0, s);
-    for (int w = 0; w < 5 && st == CIP_OK; ++w) st = column_pass<T>(p, s, c.first, c.second);
+    for (int w = 0; w < 5 && st == CIP_OK; ++w) st = iteration();
     if (st != CIP_OK) return st;
     cudaEventRecord(e1, s);
     CIP_CUDA(p, cudaEventSynchronize(e1));
@@ -760,12 +820,12 @@ template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  p->colmode = pick.first;
-  if (pick.first == 1) p->cc = pick.second;
-  p->blocksB = p->colmode == 1 ? p->N / 2 + 1 : p->M * (p->N / 2 + 1);
+  set_colmode<T>(p, std::get<0>(pick), std::get<1>(pick));
+  p->avar = std::get<2>(pick);
+  if (fav >= 0) return CIP_OK;  // a forced width is not the autotuner's decision: not cached
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = {p->colmode, p->cc};
-  tune_cache_store(key, g_tune[key]);
+  g_tune[key] = pick;
+  tune_cache_store(key, pick);
   return CIP_OK;
 }
 
@@ -791,54 +851,75 @@ void ensure_events(cip_plan* p) {
   for (auto& e : p->evB) cudaEventCreate(&e);
 }
 
-// forward transform of [g; g - e] into dl_spec: theta and the filter solve's F(g - e)
-template <typename T> cip_status dict_forward(cip_plan* p, cudaStream_t s) {
+// Online dictionary update: g = the given filters, e = 0, so theta and F(g - e) both start as the
+// plan's theta (the filters' DFT formed in FP64 at cip_set_dictionary).
+template <typename T> cip_status dict_init(cip_plan* p, cudaStream_t s) {
   using C = typename CT<T>::type;
-  const C* tw = static_cast<const C*>(p->tw);
-  C* rows = static_cast<C*>(p->dl_rows);
-  CIP_LAUNCH(p, (launch_row_r2c<T, T>(static_cast<const T*>(p->dl_sp), rows, p->N, 2 * p->L * p->N, (T)1, tw, s)));
-  CIP_LAUNCH(p, launch_colfft_fwd<T>(rows, static_cast<C*>(p->dl_spec), tw, p->N, 2 * p->L, s));
+  const size_t w = (size_t)p->L * col_pitch(p->N) * sizeof(C);
+  CIP_CUDA(p, cudaMemcpy2DAsync(p->dl_spec, 2 * w, p->theta, w, w, p->N / 2 + 1, cudaMemcpyDeviceToDevice, s));
+  CIP_CUDA(p, cudaMemcpy2DAsync(static_cast<char*>(p->dl_spec) + w, 2 * w, p->theta, w, w, p->N / 2 + 1,
+                                cudaMemcpyDeviceToDevice, s));
+  CIP_CUDA(p, cudaMemcpyAsync(p->dl_gs, p->filt, (size_t)p->L * p->Pf * p->Pf * sizeof(T), cudaMemcpyDeviceToDevice, s));
   return CIP_OK;
 }
 
-// Online dictionary update: g = F^-1(theta) (the filters on the torus), e = 0, g - e = g.
-template <typename T> cip_status dict_init(cip_plan* p, cudaStream_t s) {
+template <typename T> DLArgs<T> dl_args(cip_plan* p, bool check) {
   using C = typename CT<T>::type;
-  const size_t n = real_elems(p, p->L);
-  T* g = static_cast<T*>(p->dl_sp);
-  CIP_LAUNCH(p, launch_colfft_inv<T>(static_cast<const C*>(p->theta), static_cast<C*>(p->dl_rows),
-                                     static_cast<const C*>(p->tw), p->N, p->L, s));
-  CIP_LAUNCH(p, (launch_row_c2r<T, T>(static_cast<const C*>(p->dl_rows), g, p->N, p->L * p->N,
-                                      static_cast<const C*>(p->tw), s)));
-  CIP_LAUNCH(p, launch_scale<T>(g, n, (T)(1.0 / ((double)p->N * p->N)), s));
-  CIP_CUDA(p, cudaMemsetAsync(p->dl_e, 0, n * sizeof(T), s));
-  CIP_CUDA(p, cudaMemcpyAsync(g + n, g, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-  return dict_forward<T>(p, s);
+  DLArgs<T> a;
+  a.zcol = static_cast<const C*>(p->colbuf);
+  a.xcol = static_cast<const C*>(p->xcol);
+  a.spec = static_cast<C*>(p->dl_spec);
+  a.wcol = static_cast<C*>(p->dl_col);
+  a.ypart = static_cast<C*>(p->dl_ypart);
+  a.yfull = static_cast<C*>(p->dl_yfull);
+  a.cnt = p->dl_cnt;
+  a.gfac = static_cast<C*>(p->dl_gfac);
+  a.gs = static_cast<T*>(p->dl_gs);
+  a.rpart = p->dl_part;
+  a.spart = p->dl_part + (size_t)(p->N / 2 + 1) * (p->N / kDLBlock);
+  a.p_out = static_cast<C*>(p->pbuf[p->pcur]);
+  a.tw = static_cast<const C*>(p->tw);
+  a.N = p->N;
+  a.M = p->M;
+  a.L = p->L;
+  a.P = p->Pf;
+  a.check = check ? 1 : 0;
+  a.sigma = (T)p->dl_sigma;
+  return a;
 }
 
-// One step of the filter ADMM (Section IV-B) after the column pass, from the x and z of that
-// pass (x-hat in xcol, z-hat in colbuf, both / N^2): d from Eq. d_admm summed over the channels
-// (Eq. sold_3D), g from Eq. g_admm, e from Eq. h_admm; then theta = F g and p = sum_l theta_l z_l
-// formed again, so that the next x-update sees the updated dictionary (reading R21).
-template <typename T> cip_status dict_step(cip_plan* p, cudaStream_t s) {
-  using C = typename CT<T>::type;
-  const C* tw = static_cast<const C*>(p->tw);
-  const C* spec = static_cast<const C*>(p->dl_spec);
-  const size_t cp = (size_t)col_pitch(p->N);
-  C* rows = static_cast<C*>(p->dl_rows);
-  C* col = static_cast<C*>(p->dl_col);
-  T* d = static_cast<T*>(p->dl_d);
-  CIP_LAUNCH(p, launch_dl_solve<T>(static_cast<const C*>(p->colbuf), static_cast<const C*>(p->xcol),
-                                   spec + p->L * cp, 2 * p->L, col, p->N, p->M, p->L, p->dl_sigma, s));
-  CIP_LAUNCH(p, launch_colfft_inv<T>(col, rows, tw, p->N, p->L, s));
-  CIP_LAUNCH(p, (launch_row_c2r<T, T>(rows, d, p->N, p->L * p->N, tw, s)));
-  T* inv = static_cast<T*>(p->dl_inv);
-  CIP_LAUNCH(p, launch_dl_norm<T>(d, static_cast<const T*>(p->dl_e), inv, p->L, p->N, p->Pf, s));
-  CIP_LAUNCH(p, launch_dl_project<T>(d, static_cast<T*>(p->dl_e), static_cast<T*>(p->dl_sp), inv, p->L, p->N, p->Pf, s));
-  cip_status st = dict_forward<T>(p, s);
-  if (st != CIP_OK) return st;
-  CIP_LAUNCH(p, launch_p_from_z<T>(static_cast<const C*>(p->colbuf), spec, static_cast<C*>(p->pbuf[p->pcur]), p->N,
-                                   p->M, p->L, s, 1.0, 2 * p->L));
+// One step of the filter ADMM (Section IV-B) after the column pass, from the x and z of that pass
+// (x-hat in xcol, z-hat in colbuf, both / N^2): d from Eq. d_admm summed over the channels (Eq.
+// sold_3D), g from Eq. g_admm, e from Eq. h_admm; theta = F g and p = sum_l theta_l z_l formed
+// again, so that the next x-update sees the updated dictionary (reading R21).  Three launches;
+// with `check` they also leave the sums of ||d - g||^2 and ||g - g_prev||^2 in dl_part.
+template <typename T> cip_status dict_step(cip_plan* p, cudaStream_t s, bool check = false) {
+  const DLArgs<T> a = dl_args<T>(p, check);
+  CIP_LAUNCH(p, launch_dl_solve<T>(a, s));
+  CIP_LAUNCH(p, launch_dl_filter<T>(a, s));
+  CIP_LAUNCH(p, launch_dl_spec<T>(a, s));
+  return CIP_OK;
+}
+
+// Adaptation of sigma (reading R29): the Eq. paramS rule on r = ||d - g|| and s = sigma ||g - g_prev||
+// of the step just taken; on a change the scaled dual e is rescaled so that sigma e is unchanged.
+template <typename T> cip_status dict_adapt(cip_plan* p, cudaStream_t s) {
+  const size_t nr = (size_t)(p->N / 2 + 1) * (p->N / kDLBlock);
+  CIP_CUDA(p, cudaMemcpyAsync(p->dl_host, p->dl_part, (nr + p->L) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CIP_CUDA(p, cudaStreamSynchronize(s));
+  double r2 = 0.0, s2 = 0.0;
+  for (size_t i = 0; i < nr; ++i) r2 += p->dl_host[i];
+  for (int l = 0; l < p->L; ++l) s2 += p->dl_host[nr + l];
+  const double r = std::sqrt(r2 / ((double)p->N * p->N)), sd = p->dl_sigma * std::sqrt(s2);
+  if (!std::isfinite(r) || !std::isfinite(sd)) return fail(p, CIP_ERR_DIVERGED, "filter residuals are not finite");
+  double sn = p->dl_sigma;
+  if (r > p->dl_mu * sd) sn = p->dl_sigma * p->dl_tau;
+  else if (sd > p->dl_mu * r) sn = p->dl_sigma / p->dl_tau;
+  if (sn != p->dl_sigma) {
+    using C = typename CT<T>::type;
+    CIP_LAUNCH(p, launch_dl_rescale<T>(static_cast<C*>(p->dl_spec), p->L, p->N, (T)(p->dl_sigma / sn), s));
+    p->dl_sigma = sn;
+  }
   return CIP_OK;
 }
 
@@ -866,6 +947,15 @@ template <typename T> cip_status change_rho(cip_plan* p, double rho_new, cudaStr
   return CIP_OK;
 }
 
+// Eq. paramS on the absolute residuals r = ||Tx - t||, s = rho ||t - t_prev|| (sums of squares
+// resid[0] and resid[4] of the last check)
+double rho_rule(const cip_plan* p, const double* resid) {
+  const double ra = std::sqrt(resid[0]), sa = p->rho * std::sqrt(resid[4]);
+  if (ra > p->adapt_mu * sa) return p->rho * p->adapt_tau;
+  if (sa > p->adapt_mu * ra) return p->rho / p->adapt_tau;
+  return p->rho;
+}
+
 template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double tol, int* done, cudaStream_t s) {
   const bool adapt = p->adapt_tau > 0;
   const bool checks = tol > 0 || adapt;
@@ -890,8 +980,10 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
     cip_status cst = column_pass<T>(p, s, p->colmode, p->cc);
     if (cst != CIP_OK) return cst;
     if (timeB) cudaEventRecord(p->evB[2 * p->nB++ + 1], s);
+    // sigma adapts after every check_every-th filter step, counted over the plan's iterations
+    const bool dl_check = p->dl_sigma > 0 && p->dl_tau > 0 && (p->iteration + 1) % ce == 0;
     if (p->dl_sigma > 0) {
-      cst = dict_step<T>(p, s);
+      cst = dict_step<T>(p, s, dl_check);
       if (cst != CIP_OK) return cst;
     }
     PassAArgs<T> a = passA_args<T>(p, flags);
@@ -904,6 +996,10 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
     if (timeA) cudaEventRecord(p->evA[2 * p->nA++ + 1], s);
     p->cur ^= 1;
     p->iteration++;
+    if (dl_check) {
+      cst = dict_adapt<T>(p, s);
+      if (cst != CIP_OK) return cst;
+    }
     if (check) {
       // the previous iteration stored t only if it ran; otherwise s is not meaningful
       CIP_LAUNCH(p, launch_reduce_partials(p->partials, p->blocksA, p->rho, tol, p->resid, p->conv, s));
@@ -925,11 +1021,7 @@ template <typename T> cip_status iterate_impl(cip_plan* p, int max_iter, double 
         }
         if (tol > 0 && !last && r < tol && sr < tol) stop = true;
         if (adapt_now && !stop) {
-          // Eq. paramS on the absolute residuals r = ||Tx - t||, s = rho ||t - t_prev||
-          const double ra = std::sqrt(p->resid_host[0]), sa = p->rho * std::sqrt(p->resid_host[4]);
-          double rho_new = p->rho;
-          if (ra > p->adapt_mu * sa) rho_new = p->rho * p->adapt_tau;
-          else if (sa > p->adapt_mu * ra) rho_new = p->rho / p->adapt_tau;
+          const double rho_new = rho_rule(p, p->resid_host);
           if (rho_new != p->rho) {
             cip_status cs = change_rho<T>(p, rho_new, s);
             if (cs != CIP_OK) return cs;
@@ -1138,6 +1230,10 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
     return fail(nullptr, CIP_ERR_INVALID_ARG, "col_tile must be 0, 1, 2 or 4");
   }
   p->cc = cc == 0 ? 1 : cc;
+  if (p->opt.prior_fft != 0 && p->opt.prior_fft != 8 && p->opt.prior_fft != 16) {
+    delete p;
+    return fail(nullptr, CIP_ERR_INVALID_ARG, "prior_fft must be 0, 8 or 16");
+  }
   const bool fused_ok = dtype == CIP_F64 ? colpass_fused_fits<double>(N, M) : colpass_fused_fits<float>(N, M);
   if (p->opt.column_pass == 1 && !fused_ok) {
     delete p;
@@ -1209,12 +1305,13 @@ cip_status cip_plan_create_on_stream(cip_plan** out, int N, int K, int M, cip_dt
 
 cip_status cip_plan_destroy(cip_plan* p) {
   if (!p) return CIP_ERR_INVALID_ARG;
-  void* bufs[] = {p->lowbuf, p->lowq, p->w3, p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->dl_sp, p->dl_e, p->dl_d, p->dl_rows, p->dl_spec, p->dl_col, p->dl_inv, p->wbuf[0], p->wbuf[1], p->wbuf[2], p->wcos,
+  void* bufs[] = {p->lowbuf, p->lowq, p->w3, p->theta, p->pbuf[0], p->pbuf[1], p->xcol, p->yhat_keep, p->filt, p->dl_spec, p->dl_col, p->dl_ypart, p->dl_yfull, p->dl_gfac, p->dl_gs, p->dl_cnt, p->dl_part, p->wbuf[0], p->wbuf[1], p->wbuf[2], p->wcos,
                   p->xh, p->qh, p->u[0], p->u[1], p->tprev, p->pinv, p->pinv64, p->bhat, p->colbuf, p->lam64, p->tw, p->tw64,
                   p->gs, p->partials, p->resid, p->conv, p->pinv_list};
   for (void* b : bufs)
     if (b) cudaFreeAsync(b, p->ast);
   if (p->resid_host) cudaFreeHost(p->resid_host);
+  if (p->dl_host) cudaFreeHost(p->dl_host);
   for (auto& ev : p->evA) cudaEventDestroy(ev);
   for (auto& ev : p->evB) cudaEventDestroy(ev);
   delete p;
@@ -1354,6 +1451,7 @@ cip_status cip_set_dictionary_learning(cip_plan* p, double sigma, void* stream) 
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(p, CIP_ERR_INVALID_ARG, "sigma must be finite and >= 0");
   if (sigma > 0 && p->M > 8) return fail(p, CIP_ERR_UNSUPPORTED, "dictionary learning supports M <= 8 channels");
   if (sigma > 0 && p->Q > 0) return fail(p, CIP_ERR_UNSUPPORTED, "the online dictionary update covers 2D filters only");
+  if (sigma > 0 && p->Pf > kDLMaxP) return fail(p, CIP_ERR_UNSUPPORTED, "dictionary learning supports filters up to 32 x 32");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   p->ast = s;
   const size_t ce = 2 * p->esz;
@@ -1361,6 +1459,7 @@ cip_status cip_set_dictionary_learning(cip_plan* p, double sigma, void* stream) 
     if (p->dl_sigma > 0) {  // the learnt theta becomes the plan's dictionary
       const size_t w = (size_t)p->L * col_pitch(p->N) * ce;
       CIP_CUDA(p, cudaMemcpy2DAsync(p->theta, w, p->dl_spec, 2 * w, w, p->N / 2 + 1, cudaMemcpyDeviceToDevice, s));
+      CIP_CUDA(p, cudaMemcpyAsync(p->filt, p->dl_gs, (size_t)p->L * p->Pf * p->Pf * p->esz, cudaMemcpyDeviceToDevice, s));
     }
     p->dl_sigma = 0.0;
     return CIP_OK;
@@ -1380,22 +1479,7 @@ cip_status cip_get_dictionary(cip_plan* p, void* filters, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   p->ast = s;
   const size_t bytes = (size_t)p->L * p->Pf * p->Pf * p->esz;
-  const bool dev = is_device_ptr(filters);
-  void* out = filters;
-  if (!dev) CIP_CUDA(p, cudaMallocAsync(&out, bytes, s));
-  cudaError_t e = p->dtype == CIP_F32
-                      ? launch_dl_crop<float>(static_cast<const float*>(p->dl_sp), static_cast<float*>(out), p->L,
-                                              p->N, p->Pf, s)
-                      : launch_dl_crop<double>(static_cast<const double*>(p->dl_sp), static_cast<double*>(out), p->L,
-                                               p->N, p->Pf, s);
-  if (e == cudaSuccess) p->launches++;
-  if (!dev) {
-    if (e == cudaSuccess) e = cudaMemcpyAsync(filters, out, bytes, cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(out, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  }
-  CIP_CUDA(p, e);
-  return CIP_OK;
+  return copy_out(p, filters, p->dl_gs, bytes, s);
 }
 
 cip_status cip_set_rho_adaptation(cip_plan* p, double tau, double mu) {
@@ -1410,6 +1494,25 @@ cip_status cip_set_rho_adaptation(cip_plan* p, double tau, double mu) {
     return fail(p, CIP_ERR_STATE, "cip_set_rho_adaptation must precede cip_set_measurements");
   p->adapt_tau = tau;
   p->adapt_mu = mu;
+  return CIP_OK;
+}
+
+cip_status cip_set_sigma_adaptation(cip_plan* p, double tau, double mu) {
+  if (!p) return CIP_ERR_INVALID_ARG;
+  if (tau == 0.0) {
+    p->dl_tau = p->dl_mu = 0.0;
+    return CIP_OK;
+  }
+  if (!(tau > 1.0) || !(mu > 1.0) || !std::isfinite(tau) || !std::isfinite(mu))
+    return fail(p, CIP_ERR_INVALID_ARG, "tau and mu must be finite and > 1 (or tau = 0 to turn adaptation off)");
+  p->dl_tau = tau;
+  p->dl_mu = mu;
+  return CIP_OK;
+}
+
+cip_status cip_get_sigma(cip_plan* p, double* sigma) {
+  if (!p || !sigma) return CIP_ERR_INVALID_ARG;
+  *sigma = p->dl_sigma;
   return CIP_OK;
 }
 
@@ -1482,17 +1585,24 @@ static std::vector<std::pair<void*, size_t>> state_segments(cip_plan* p) {
   }
   if (p->dl_sigma > 0) {  // the dictionary being learnt is part of the state
     seg.push_back({p->dl_spec, col_elems(p, 2 * p->L) * 2 * p->esz});
-    seg.push_back({p->dl_sp, real_elems(p, 2 * p->L) * p->esz});
-    seg.push_back({p->dl_e, real_elems(p, p->L) * p->esz});
+    seg.push_back({p->dl_gs, (size_t)p->L * p->Pf * p->Pf * p->esz});
   }
   return seg;
 }
+
+// checkpoint header: iteration count and the filter ADMM's penalty (0 while the update is off)
+struct StateHeader {
+  int iteration;
+  int reserved;
+  double sigma;
+};
+constexpr size_t kStateHeader = sizeof(StateHeader);
 
 cip_status cip_state_size(cip_plan* p, size_t* bytes) {
   if (!p || !bytes) return CIP_ERR_INVALID_ARG;
   if (p->prior < 0) return fail(p, CIP_ERR_STATE, "cip_set_prior has not been called");
   if (is_cd(p) && !p->theta) return fail(p, CIP_ERR_STATE, "cip_set_dictionary has not been called");
-  size_t n = 2 * sizeof(int);
+  size_t n = kStateHeader;
   for (auto& sgm : state_segments(p)) n += sgm.second;
   *bytes = n;
   return CIP_OK;
@@ -1508,9 +1618,13 @@ cip_status cip_state_export(cip_plan* p, void* buf, void* stream) {
   const bool dev = is_device_ptr(buf);
   const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   char* b = static_cast<char*>(buf);
-  int hdr[2] = {p->iteration, 0};
-  if (dev) CIP_CUDA(p, cudaMemcpyAsync(b, hdr, sizeof(hdr), cudaMemcpyHostToDevice, s));
-  else std::memcpy(b, hdr, sizeof(hdr));
+  StateHeader hdr{p->iteration, 0, p->dl_sigma};
+  if (dev) {
+    CIP_CUDA(p, cudaMemcpyAsync(b, &hdr, sizeof(hdr), cudaMemcpyHostToDevice, s));
+    CIP_CUDA(p, cudaStreamSynchronize(s));  // hdr lives on this stack frame
+  } else {
+    std::memcpy(b, &hdr, sizeof(hdr));
+  }
   size_t off = sizeof(hdr);
   for (auto& sgm : state_segments(p)) {
     CIP_CUDA(p, cudaMemcpyAsync(b + off, sgm.first, sgm.second, k, s));
@@ -1530,12 +1644,12 @@ cip_status cip_state_restore(cip_plan* p, const void* buf, void* stream) {
   const bool dev = is_device_ptr(buf);
   const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const char* b = static_cast<const char*>(buf);
-  int hdr[2];
+  StateHeader hdr;
   if (dev) {
-    CIP_CUDA(p, cudaMemcpyAsync(hdr, b, sizeof(hdr), cudaMemcpyDeviceToHost, s));
+    CIP_CUDA(p, cudaMemcpyAsync(&hdr, b, sizeof(hdr), cudaMemcpyDeviceToHost, s));
     CIP_CUDA(p, cudaStreamSynchronize(s));
   } else {
-    std::memcpy(hdr, b, sizeof(hdr));
+    std::memcpy(&hdr, b, sizeof(hdr));
   }
   size_t off = sizeof(hdr);
   for (auto& sgm : state_segments(p)) {
@@ -1543,7 +1657,8 @@ cip_status cip_state_restore(cip_plan* p, const void* buf, void* stream) {
     off += sgm.second;
   }
   CIP_CUDA(p, cudaStreamSynchronize(s));
-  p->iteration = hdr[0];
+  p->iteration = hdr.iteration;
+  if (p->dl_sigma > 0 && hdr.sigma > 0) p->dl_sigma = hdr.sigma;  // the adapted penalty of the filter ADMM
   p->resid_valid = false;
   return CIP_OK;
 }
@@ -1589,6 +1704,13 @@ cip_status cip_set_test_fault(cip_plan* p, int kind) {
 cip_status cip_get_launches(cip_plan* p, unsigned long long* n) {
   if (!p || !n) return CIP_ERR_INVALID_ARG;
   *n = p->launches;
+  return CIP_OK;
+}
+
+cip_status cip_get_prior_fft(cip_plan* p, int* elems) {
+  if (!p || !elems) return CIP_ERR_INVALID_ARG;
+  const int e = prior_fft_default(p);
+  *elems = (prior_has_variant(p) && p->avar == 1) ? 24 - e : e;
   return CIP_OK;
 }
 
@@ -1798,9 +1920,19 @@ cip_status plan_iterate_async(cip_plan* p, int k, cudaStream_t s, double* host_r
     r = plan_enqueue(p, s, flags);
     if (r != CIP_OK) return r;
   }
-  CIP_CUDA(p, cudaMemcpyAsync(host_resid, p->resid + kNPart, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  static_assert(kResidHost == kNPart + 2, "the residual record is the five sums and the two relative values");
+  CIP_CUDA(p, cudaMemcpyAsync(host_resid, p->resid, kResidHost * sizeof(double), cudaMemcpyDeviceToHost, s));
   CIP_CUDA(p, cudaEventRecord(ev, s));
   return CIP_OK;
+}
+
+cip_status plan_adapt_rho(cip_plan* p, const double* host_resid, cudaStream_t s) {
+  if (!p || !host_resid) return CIP_ERR_INVALID_ARG;
+  if (!(p->adapt_tau > 0) || is_cd(p)) return CIP_OK;
+  const double rho_new = rho_rule(p, host_resid);
+  if (rho_new == p->rho) return CIP_OK;
+  p->ast = s;
+  return DISPATCH_T(p, change_rho<float>(p, rho_new, s), change_rho<double>(p, rho_new, s));
 }
 
 cip_status plan_adopt_factor(cip_plan* dst, const cip_plan* src, cudaStream_t s) {
@@ -1841,6 +1973,7 @@ size_t plan_resident_bytes(int N, int K, int M, cip_dtype dtype, cip_prior prior
   b += (size_t)M * H * CP * c;                // column buffer of the split form
   b += 3 * nc * (size_t)M * N * N * e;        // u (two), t_prev
   b += (size_t)kTwN * (16 + c) + N * 8 + (size_t)(N / 2) * M * kNPart * 8 + 8192;
+  if (prior == CIP_PRIOR_WDCT) b += 5 * (size_t)M * N * N * e / 2 + (size_t)M * M * e;  // wavelet work planes
   return b;
 }
 

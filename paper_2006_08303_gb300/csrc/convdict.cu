@@ -135,40 +135,101 @@ __global__ void p_from_z_kernel(const typename CT<T>::type* __restrict__ zcol, c
 }
 
 // ---- online dictionary update (Section IV-B, Eqs. d_admm, g_admm, h_admm, sold_3D) ----------
+//
+// State between steps: theta = F g and F(g - e) (spectra of the filters on the torus and of the
+// filters minus the scaled dual), and g itself on its P x P support.  One step:
+//   dl_solve  per bin: d-hat from the normal equation summed over the channels, w = d-hat + e-hat
+//             with e-hat = theta - F(g - e); per column, Y(a, k2) = sum_k1 w exp(2 pi i k1 a / N)
+//             for the P support rows a (so that d + e at the support points is a short sum over k2)
+//   dl_filter per filter: v = d + e on the support, g = v / ||v|| (Eq. g_admm), the partial DFT
+//             G(a, k2) = sum_b g(a, b) exp(-2 pi i k2 b / N)
+//   dl_spec   per bin: g-hat = sum_a exp(-2 pi i k1 a / N) G(a, k2); e-hat <- w - g-hat (Eq.
+//             h_admm, reading R22), so F(g - e) = 2 g-hat - w; theta = g-hat; p = sum_l theta_l z_l
+// The spatial d and e off the support are never formed: g is zero there and e is only ever needed
+// through its spectrum.
 
-// Per frequency, one thread (k1 = threadIdx + block offset, k2 = blockIdx.y, so that the warps
-// read the column layout contiguously): the filter normal equation summed over the M channels,
+// exp(-2 pi i j / N) (SIGN < 0) or exp(+2 pi i j / N) (SIGN > 0) for any integer j
+template <int SIGN, typename C>
+__device__ __forceinline__ C tw_at(const C* __restrict__ tw, int j, int N) {
+  const int r = ((j % N) + N) % N;
+  C t = ldg_tw(&tw[r * (kTwN / N)]);
+  if (SIGN > 0) t.y = -t.y;
+  return t;
+}
+
+// Warp reduce-scatter by recursive halving over PM entries per lane (PM a power of two <= 32): at
+// xor distance O a lane keeps one half of its LIVE entries (the upper half when bit O of the lane
+// is set) and adds its partner's copy of that half.  Afterwards v[0] of lane i holds the warp's sum
+// of entry i >> log2(32 / PM), after PM - 1 + log2(32 / PM) exchanges (5 PM for separate sums).
+template <int LIVE, int O, int PM, typename C>
+__device__ __forceinline__ void reduce_scatter(C (&v)[PM], int lane) {
+  if constexpr (LIVE > 1) {
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < LIVE / 2; ++i) {
+      const C lo = v[i], hi = v[i + LIVE / 2];
+      C keep = up ? hi : lo;
+      const C send = up ? lo : hi;
+      keep.x += __shfl_xor_sync(0xffffffffu, send.x, O);
+      keep.y += __shfl_xor_sync(0xffffffffu, send.y, O);
+      v[i] = keep;
+    }
+    reduce_scatter<LIVE / 2, O / 2>(v, lane);
+  } else if constexpr (O >= 1) {
+    v[0].x += __shfl_xor_sync(0xffffffffu, v[0].x, O);
+    v[0].y += __shfl_xor_sync(0xffffffffu, v[0].y, O);
+    reduce_scatter<1, O / 2>(v, lane);
+  }
+}
+
+constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+// block sum of one double per thread (blockDim a multiple of 32, <= 256); every thread gets it
+__device__ __forceinline__ double block_sum256(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();  // red may still be read from a previous call
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// Per frequency, one thread (k1 = block offset + thread, k2 = blockIdx.y, so that the warps read
+// the column layout contiguously): the filter normal equation summed over the M channels,
 // (sigma I + W W^H) d = b with W = [conj(zhat_{l,s})] (L x M) and b = W xhat + sigma F(g - e), by
 // the Woodbury identity d = (b - W alpha) / sigma, (sigma I_M + W^H W) alpha = W^H b.  The L
 // filters are streamed twice: once to accumulate W^H W and W^H b, once to form d; the M x M system
-// is solved by Cholesky in registers.  zcol holds the code spectra and xcol the image spectra
-// scaled by 1/N^2 (the column solve's convention); ge holds F(g - e) (gep planes per bin); dcol
-// receives d-hat / N^2 (so that an unnormalised inverse gives d).
-template <typename T, int M>
-__global__ void __launch_bounds__(64) dl_solve_kernel(const typename CT<T>::type* __restrict__ zcol,
-                                                      const typename CT<T>::type* __restrict__ xcol,
-                                                      const typename CT<T>::type* __restrict__ gecol, int gep,
-                                                      typename CT<T>::type* __restrict__ dcol, int N, int L,
-                                                      T sigma) {
+// is solved by Cholesky in registers.  Then w = d + e-hat is stored and its partial inverse DFT
+// along k1 at the P support rows is summed over the CTA's bins (reduce-scatter across each warp);
+// the last CTA of a column to finish adds the column's CTA sums in a fixed order, so the result
+// does not depend on the order in which CTAs run.
+template <typename T, int M, int PM>
+__global__ void __launch_bounds__(kDLBlock) dl_solve_kernel(const DLArgs<T> a) {
   using C = typename CT<T>::type;
-  const int CP = col_pitch(N);
-  const int k1 = blockIdx.x * blockDim.x + threadIdx.x, k2 = blockIdx.y;
-  if (k1 >= N) return;
+  static_assert(kDLBlock == 64, "two warps per CTA");
+  const int N = a.N, L = a.L, P = a.P;
+  const int CP = col_pitch(N), H = N / 2 + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kb = blockIdx.x, nkb = gridDim.x;
+  const int k1 = kb * kDLBlock + tid, k2 = blockIdx.y;
   const T n2 = (T)N * (T)N;
-  const C* zb = zcol + (size_t)k2 * M * L * CP + k1;  // z_{l,s} at zb[(s L + l) CP]
-  const C* gb = gecol + (size_t)k2 * gep * CP + k1;
+  const T sigma = a.sigma;
+  const C* zb = a.zcol + (size_t)k2 * M * L * CP + k1;  // z_{l,s} at zb[(s L + l) CP]
+  const C* th = a.spec + (size_t)k2 * 2 * L * CP + k1;  // theta_l at th[l CP], F(g - e)_l at th[(L + l) CP]
   C x[M], c[M], G[M][M];
 #pragma unroll
   for (int s = 0; s < M; ++s) {
-    const C v = xcol[((size_t)k2 * M + s) * CP + k1];
+    const C v = a.xcol[((size_t)k2 * M + s) * CP + k1];
     x[s] = mk<C>(v.x * n2, v.y * n2);
     c[s] = mk<C>(0.0, 0.0);
 #pragma unroll
     for (int t = 0; t < M; ++t) G[s][t] = mk<C>(0.0, 0.0);
   }
-  // b_l = sigma ge_l + sum_s conj(z_{l,s}) x_s
+  // b_l = sigma F(g - e)_l + sum_s conj(z_{l,s}) x_s
   auto load_b = [&](int l, C (&z)[M]) {
-    const C ge = __ldg(gb + (size_t)l * CP);
+    const C ge = __ldg(th + (size_t)(L + l) * CP);
     C b = mk<C>(sigma * ge.x, sigma * ge.y);
 #pragma unroll
     for (int s = 0; s < M; ++s) {
@@ -202,9 +263,9 @@ __global__ void __launch_bounds__(64) dl_solve_kernel(const typename CT<T>::type
       C acc = G[i][j];
 #pragma unroll
       for (int k = 0; k < j; ++k) {  // acc -= G_ik conj(G_jk)
-        const C a = G[i][k], bb = G[j][k];
-        acc.x -= a.x * bb.x + a.y * bb.y;
-        acc.y -= a.y * bb.x - a.x * bb.y;
+        const C u = G[i][k], v = G[j][k];
+        acc.x -= u.x * v.x + u.y * v.y;
+        acc.y -= u.y * v.x - u.x * v.y;
       }
       G[i][j] = mk<C>(acc.x * inv, acc.y * inv);
     }
@@ -232,9 +293,16 @@ __global__ void __launch_bounds__(64) dl_solve_kernel(const typename CT<T>::type
     const T inv = T(1) / G[i][i].x;
     al[i] = mk<C>(acc.x * inv, acc.y * inv);
   }
-  const T sc = T(1) / (sigma * n2);
-  C* db = dcol + (size_t)k2 * L * CP + k1;
-#pragma unroll 2
+  // exp(+2 pi i k1 (a - P/2) / N) for the support rows a < P (zero beyond P)
+  const int cen = P / 2;
+  C wa[PM];
+#pragma unroll
+  for (int i = 0; i < PM; ++i) wa[i] = i < P ? tw_at<+1>(a.tw, k1 * (i - cen), N) : mk<C>(0.0, 0.0);
+  __shared__ C red[2][32][PM];  // [warp][l][a]
+  constexpr int SH = ilog2c(32 / PM);
+  const T isg = T(1) / sigma;
+  C* wb = a.wcol + (size_t)k2 * L * CP + k1;
+#pragma unroll 1
   for (int l = 0; l < L; ++l) {
     C z[M];
     C d = load_b(l, z);
@@ -243,125 +311,224 @@ __global__ void __launch_bounds__(64) dl_solve_kernel(const typename CT<T>::type
       d.x -= z[s].x * al[s].x + z[s].y * al[s].y;
       d.y -= z[s].x * al[s].y - z[s].y * al[s].x;
     }
-    db[(size_t)l * CP] = mk<C>(d.x * sc, d.y * sc);
+    const C t = __ldg(th + (size_t)l * CP), ge = __ldg(th + (size_t)(L + l) * CP);
+    // w = d-hat + e-hat, e-hat = theta - F(g - e)
+    const C wl = mk<C>(fma(d.x, isg, t.x - ge.x), fma(d.y, isg, t.y - ge.y));
+    wb[(size_t)l * CP] = wl;
+    C v[PM];
+#pragma unroll
+    for (int i = 0; i < PM; ++i) v[i] = cmul(wl, wa[i]);
+    reduce_scatter<PM, 16>(v, lane);
+    if ((lane & ((1 << SH) - 1)) == 0) red[warp][l][lane >> SH] = v[0];
+  }
+  __syncthreads();
+  C* yp = a.ypart + ((size_t)k2 * nkb + kb) * L * P;
+  for (int i = tid; i < L * P; i += kDLBlock) {
+    const int l = i / P, ai = i - l * P;
+    const C s0 = red[0][l][ai], s1 = red[1][l][ai];
+    yp[i] = mk<C>(s0.x + s1.x, s0.y + s1.y);
+  }
+  __shared__ int last;
+  __threadfence();  // this CTA's sums are visible device-wide before it is counted
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(&a.cnt[k2], 1) == nkb - 1;
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    const C* y0 = a.ypart + (size_t)k2 * nkb * L * P;
+    for (int i = tid; i < L * P; i += kDLBlock) {
+      C acc = mk<C>(0.0, 0.0);
+      for (int b = 0; b < nkb; ++b) {
+        const C v = __ldcg(y0 + (size_t)b * L * P + i);
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+      const int l = i / P, ai = i - l * P;
+      a.yfull[((size_t)l * P + ai) * H + k2] = acc;
+    }
+    if (tid == 0) a.cnt[k2] = 0;  // ready for the next step (stream order)
   }
 }
 
-// 1 / ||Q^T (d + e)|| per filter l = blockIdx.x (0 for a zero filter), formed before any block
-// of the projection writes e.
+// Per filter l = blockIdx.x: v = d + e at the P x P support points,
+//   v(a, b) = N^-2 sum_k2 c_k2 Re[Y(a, k2) exp(2 pi i k2 (b - P/2) / N)]
+// (c_k2 = 1 at k2 = 0 and N/2, 2 otherwise: the half spectrum of a real map); g = v / ||v||
+// (Eq. g_admm: support and unit norm, reading R22); ||g - g_prev||^2 when a check follows; then the
+// partial DFT G(a, k2) = sum_b g(a, b) exp(-2 pi i k2 (b - P/2) / N) for every k2.
 template <typename T>
-__global__ void __launch_bounds__(256) dl_norm_kernel(const T* __restrict__ d, const T* __restrict__ e,
-                                                      T* __restrict__ inv, int N, int P) {
+__global__ void __launch_bounds__(256) dl_filter_kernel(const DLArgs<T> a) {
+  using C = typename CT<T>::type;
+  const int N = a.N, L = a.L, P = a.P, H = N / 2 + 1, PP = P * P, cen = P / 2;
+  const int l = blockIdx.x, tid = threadIdx.x;
+  __shared__ T vs[kDLMaxP * kDLMaxP];
   __shared__ double red[8];
-  const int l = blockIdx.x;
-  const size_t plane = (size_t)N * N;
-  const T* dl = d + (size_t)l * plane;
-  const T* el = e + (size_t)l * plane;
-  const int c = P / 2;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
-    const int a = ((i / P - c) % N + N) % N, b = ((i % P - c) % N + N) % N;
-    const size_t k = (size_t)a * N + b;
-    const double v = (double)dl[k] + (double)el[k];
-    acc += v * v;
+  const T inv_n = T(1) / ((T)N * (T)N);
+  for (int o = tid; o < PP; o += blockDim.x) {
+    const int ai = o / P, bi = o - ai * P;
+    const C* Y = a.yfull + ((size_t)l * P + ai) * H;
+    T e0 = T(0), e1 = T(0), o1 = T(0);
+    for (int k2 = 0; k2 < H; ++k2) {
+      const C y = Y[k2];
+      const C t = tw_at<-1>(a.tw, k2 * (bi - cen), N);  // Re(y conj(t)) = Re(y exp(+i ...))
+      const T r = fma(y.x, t.x, y.y * t.y);
+      if (k2 == 0 || k2 == N / 2) e0 += r;
+      else if (k2 & 1) o1 += r;
+      else e1 += r;
+    }
+    vs[o] = (e0 + T(2) * (e1 + o1)) * inv_n;
+  }
+  __syncthreads();
+  double nn = 0.0;
+  for (int o = tid; o < PP; o += blockDim.x) nn += (double)vs[o] * (double)vs[o];
+  nn = block_sum256(nn, red);
+  const T inv = nn > 0.0 ? (T)(1.0 / sqrt(nn)) : T(0);
+  T* g = a.gs + (size_t)l * PP;
+  double ds = 0.0;
+  for (int o = tid; o < PP; o += blockDim.x) {
+    const T gn = vs[o] * inv;
+    const double dg = (double)gn - (double)g[o];
+    ds += dg * dg;
+    g[o] = gn;
+    vs[o] = gn;
+  }
+  if (a.check) {
+    ds = block_sum256(ds, red);
+    if (tid == 0) a.spart[l] = ds;
+  }
+  __syncthreads();
+  for (int o = tid; o < P * H; o += blockDim.x) {
+    const int ai = o / H, k2 = o - ai * H;
+    C acc = mk<C>(0.0, 0.0);
+    for (int bi = 0; bi < P; ++bi) {
+      const T gv = vs[ai * P + bi];
+      const C t = tw_at<-1>(a.tw, k2 * (bi - cen), N);
+      acc.x = fma(gv, t.x, acc.x);
+      acc.y = fma(gv, t.y, acc.y);
+    }
+    a.gfac[((size_t)k2 * L + l) * P + ai] = acc;
+  }
+}
+
+// Per frequency: g-hat_l = sum_a exp(-2 pi i k1 (a - P/2) / N) G_l(a, k2) = theta_l of the new
+// filters; the dual update e-hat <- e-hat + d-hat - g-hat = w - g-hat (Eq. h_admm), stored as
+// F(g - e) = 2 g-hat - w; p = sum_l theta_l z_l for the next x-update; and, before a check, the
+// primal residual |F(d - g)|^2 = |w - e-hat_old - g-hat|^2 (Parseval on the half spectrum).
+template <typename T, int M, int PM>
+__global__ void __launch_bounds__(kDLBlock) dl_spec_kernel(const DLArgs<T> a) {
+  using C = typename CT<T>::type;
+  const int N = a.N, L = a.L, P = a.P, CP = col_pitch(N);
+  const int tid = threadIdx.x;
+  const int k1 = blockIdx.x * kDLBlock + tid, k2 = blockIdx.y;
+  __shared__ C gk[32][PM];
+  __shared__ double red[8];
+  for (int i = tid; i < 32 * PM; i += kDLBlock) {
+    const int l = i / PM, ai = i - l * PM;
+    gk[l][ai] = (l < L && ai < P) ? a.gfac[((size_t)k2 * L + l) * P + ai] : mk<C>(0.0, 0.0);
+  }
+  __syncthreads();
+  const int cen = P / 2;
+  C wa[PM];
+#pragma unroll
+  for (int i = 0; i < PM; ++i) wa[i] = i < P ? tw_at<-1>(a.tw, k1 * (i - cen), N) : mk<C>(0.0, 0.0);
+  C pm[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) pm[m] = mk<C>(0.0, 0.0);
+  T r2 = T(0);
+  C* th = a.spec + (size_t)k2 * 2 * L * CP + k1;
+  const C* wb = a.wcol + (size_t)k2 * L * CP + k1;
+  const C* zb = a.zcol + (size_t)k2 * M * L * CP + k1;
+#pragma unroll 1
+  for (int l = 0; l < L; ++l) {
+    C gh = mk<C>(0.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < PM; ++i) cfma(gh, wa[i], gk[l][i]);
+    const C w = wb[(size_t)l * CP];
+    if (a.check) {
+      const C t0 = th[(size_t)l * CP], ge0 = th[(size_t)(L + l) * CP];
+      const T dx = w.x - t0.x + ge0.x - gh.x, dy = w.y - t0.y + ge0.y - gh.y;
+      r2 = fma(dx, dx, fma(dy, dy, r2));
+    }
+    th[(size_t)l * CP] = gh;
+    th[(size_t)(L + l) * CP] = mk<C>(T(2) * gh.x - w.x, T(2) * gh.y - w.y);
+#pragma unroll
+    for (int m = 0; m < M; ++m) cfma(pm[m], gh, zb[((size_t)m * L + l) * CP]);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-    inv[l] = tot > 0.0 ? (T)(1.0 / sqrt(tot)) : T(0);
+  for (int m = 0; m < M; ++m) a.p_out[((size_t)k2 * M + m) * CP + k1] = pm[m];
+  if (a.check) {
+    const double wgt = (k2 == 0 || k2 == N / 2) ? 1.0 : 2.0;
+    double v = wgt * (double)r2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) a.rpart[(size_t)k2 * gridDim.x + blockIdx.x] = red[0] + red[1];
   }
 }
 
-// Eq. g_admm and Eq. h_admm (reading R22) for filter l = blockIdx.x over the chunk blockIdx.y of
-// its N x N plane: g = Q Q^T (d + e) * inv_l, e <- e + d - g, and g - e for the next filter
-// solve.  gs holds [g planes][g - e planes] (L each).
 template <typename T>
-__global__ void __launch_bounds__(256) dl_project_kernel(const T* __restrict__ d, T* __restrict__ e,
-                                                         T* __restrict__ gs, const T* __restrict__ inv, int L, int N,
-                                                         int P) {
-  const int l = blockIdx.x;
-  const size_t plane = (size_t)N * N;
-  const T* dl = d + (size_t)l * plane;
-  T* el = e + (size_t)l * plane;
-  T* gl = gs + (size_t)l * plane;
-  T* ql = gs + ((size_t)L + l) * plane;
-  const int c = P / 2;
-  const T s = inv[l];
-  const size_t chunk = (plane + gridDim.y - 1) / gridDim.y;
-  const size_t k0 = (size_t)blockIdx.y * chunk, k1 = min(plane, k0 + chunk);
-  for (size_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    const int a = (int)(k / N), b = (int)(k - (size_t)a * N);
-    const int ia = (a + c) % N, ib = (b + c) % N;  // position inside the P x P support if < P
-    const bool in = ia < P && ib < P;
-    const T v = dl[k] + el[k];
-    const T gn = in ? v * s : T(0);
-    const T en = v - gn;
-    gl[k] = gn;
-    el[k] = en;
-    ql[k] = gn - en;
+__global__ void dl_rescale_kernel(typename CT<T>::type* __restrict__ spec, int L, int N, T f) {
+  using C = typename CT<T>::type;
+  const int CP = col_pitch(N), H = N / 2 + 1;
+  const size_t total = (size_t)H * L * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int k1 = (int)(i % N);
+    const size_t r = i / N;
+    const int l = (int)(r % L);
+    const size_t k2 = r / L;
+    C* th = spec + (k2 * 2 * L + l) * CP + k1;
+    const C t = th[0], ge = th[(size_t)L * CP];
+    th[(size_t)L * CP] = mk<C>(t.x - (t.x - ge.x) * f, t.y - (t.y - ge.y) * f);
   }
 }
 
-// filters [L][P][P] (centre P/2) cropped from the N x N planes g
-template <typename T>
-__global__ void dl_crop_kernel(const T* __restrict__ g, T* __restrict__ out, int L, int N, int P) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= L * P * P) return;
-  const int l = idx / (P * P), r = idx - l * P * P;
-  const int i = r / P, j = r - i * P;
-  const int c = P / 2;
-  const int a = ((i - c) % N + N) % N, b = ((j - c) % N + N) % N;
-  out[idx] = g[((size_t)l * N + a) * N + b];
-}
-
-}  // namespace
-
-template <typename T>
-cudaError_t launch_dl_solve(const typename CT<T>::type* zcol, const typename CT<T>::type* xcol,
-                            const typename CT<T>::type* gecol, int gep, typename CT<T>::type* dcol, int N, int M,
-                            int L, double sigma, cudaStream_t s) {
-  const dim3 grid((N + 63) / 64, N / 2 + 1), block(64);
-  const T sg = (T)sigma;
-  switch (M) {
-#define DL_CASE(m) \
-  case m: dl_solve_kernel<T, m><<<grid, block, 0, s>>>(zcol, xcol, gecol, gep, dcol, N, L, sg); break;
+template <typename T, int PM> cudaError_t dl_by_m(const DLArgs<T>& a, bool spec, cudaStream_t s) {
+  const dim3 grid(a.N / kDLBlock, a.N / 2 + 1);
+  switch (a.M) {
+#define DL_CASE(m)                                                          \
+  case m:                                                                   \
+    if (spec) dl_spec_kernel<T, m, PM><<<grid, kDLBlock, 0, s>>>(a);        \
+    else dl_solve_kernel<T, m, PM><<<grid, kDLBlock, 0, s>>>(a);            \
+    break;
     DL_CASE(1) DL_CASE(2) DL_CASE(3) DL_CASE(4) DL_CASE(5) DL_CASE(6) DL_CASE(7) DL_CASE(8)
 #undef DL_CASE
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
-template <typename T> cudaError_t launch_dl_norm(const T* d, const T* e, T* inv, int L, int N, int P, cudaStream_t s) {
-  dl_norm_kernel<T><<<L, 256, 0, s>>>(d, e, inv, N, P);
+template <typename T> bool dl_args_ok(const DLArgs<T>& a) {
+  return a.N % kDLBlock == 0 && a.N <= kTwN && a.L >= 1 && a.L <= 32 && a.P >= 1 && a.P <= kDLMaxP &&
+         a.P <= a.N && a.M >= 1 && a.M <= 8;
+}
+
+}  // namespace
+
+template <typename T> cudaError_t launch_dl_solve(const DLArgs<T>& a, cudaStream_t s) {
+  if (!dl_args_ok(a)) return cudaErrorInvalidValue;
+  return a.P <= 16 ? dl_by_m<T, 16>(a, false, s) : dl_by_m<T, 32>(a, false, s);
+}
+template <typename T> cudaError_t launch_dl_filter(const DLArgs<T>& a, cudaStream_t s) {
+  if (!dl_args_ok(a)) return cudaErrorInvalidValue;
+  dl_filter_kernel<T><<<a.L, 256, 0, s>>>(a);
   return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_dl_spec(const DLArgs<T>& a, cudaStream_t s) {
+  if (!dl_args_ok(a)) return cudaErrorInvalidValue;
+  return a.P <= 16 ? dl_by_m<T, 16>(a, true, s) : dl_by_m<T, 32>(a, true, s);
 }
 template <typename T>
-cudaError_t launch_dl_project(const T* d, T* e, T* gs, const T* inv, int L, int N, int P, cudaStream_t s) {
-  const size_t plane = (size_t)N * N;
-  const unsigned chunks = (unsigned)std::min<size_t>(64, std::max<size_t>(1, plane / 2048));
-  dl_project_kernel<T><<<dim3(L, chunks), 256, 0, s>>>(d, e, gs, inv, L, N, P);
+cudaError_t launch_dl_rescale(typename CT<T>::type* spec, int L, int N, T f, cudaStream_t s) {
+  dl_rescale_kernel<T><<<4 * 152, 256, 0, s>>>(spec, L, N, f);
   return cudaGetLastError();
 }
-template <typename T> cudaError_t launch_dl_crop(const T* g, T* out, int L, int N, int P, cudaStream_t s) {
-  const int n = L * P * P;
-  dl_crop_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(g, out, L, N, P);
-  return cudaGetLastError();
-}
-template cudaError_t launch_dl_solve<float>(const float2*, const float2*, const float2*, int, float2*, int, int, int,
-                                            double, cudaStream_t);
-template cudaError_t launch_dl_solve<double>(const double2*, const double2*, const double2*, int, double2*, int, int,
-                                             int, double, cudaStream_t);
-template cudaError_t launch_dl_norm<float>(const float*, const float*, float*, int, int, int, cudaStream_t);
-template cudaError_t launch_dl_norm<double>(const double*, const double*, double*, int, int, int, cudaStream_t);
-template cudaError_t launch_dl_project<float>(const float*, float*, float*, const float*, int, int, int, cudaStream_t);
-template cudaError_t launch_dl_project<double>(const double*, double*, double*, const double*, int, int, int,
-                                               cudaStream_t);
-template cudaError_t launch_dl_crop<float>(const float*, float*, int, int, int, cudaStream_t);
-template cudaError_t launch_dl_crop<double>(const double*, double*, int, int, int, cudaStream_t);
+template cudaError_t launch_dl_solve<float>(const DLArgs<float>&, cudaStream_t);
+template cudaError_t launch_dl_solve<double>(const DLArgs<double>&, cudaStream_t);
+template cudaError_t launch_dl_filter<float>(const DLArgs<float>&, cudaStream_t);
+template cudaError_t launch_dl_filter<double>(const DLArgs<double>&, cudaStream_t);
+template cudaError_t launch_dl_spec<float>(const DLArgs<float>&, cudaStream_t);
+template cudaError_t launch_dl_spec<double>(const DLArgs<double>&, cudaStream_t);
+template cudaError_t launch_dl_rescale<float>(float2*, int, int, float, cudaStream_t);
+template cudaError_t launch_dl_rescale<double>(double2*, int, int, double, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_p_from_z(const typename CT<T>::type* zcol, const typename CT<T>::type* th,

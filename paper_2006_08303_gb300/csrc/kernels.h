@@ -45,6 +45,7 @@ template <typename T> struct PassAArgs {
   int flags;
   int test_fault;   // 1: the staged u copy is replaced by a barrier that never completes (test of
                     // the bounded wait: no copy is issued, the wait gives up after 64 polls)
+  int variant;      // 1: the kernel variant with the other FFT width (complex64, N = 256 .. 1024)
   C* lowbuf;        // TV: [2][kLowK][M][CP] row DFTs of the components of t - u' at k2 < kLowK
                     // for the low-column correction of the split column pass; NULL: not formed
   T dct[64];        // orthonormal DCT-II, dct[k*8+n]
@@ -119,16 +120,38 @@ template <typename T>
 cudaError_t launch_p_from_z(const typename CT<T>::type* zcol, const typename CT<T>::type* th,
                             typename CT<T>::type* p, int N, int M, int L, cudaStream_t s,
                             double scale = 0.0, int th_planes = 0);
-// online dictionary update (Section IV-B): per-frequency filter solve; projection and dual;
-// crop of the filters to P x P
+// Online dictionary update (Section IV-B, Eqs. d_admm, g_admm, h_admm): one filter-ADMM step in
+// three launches.  The scaled dual e is kept as its spectrum (e-hat = theta - F(g - e)); the filters
+// g live on the P x P support, so the spatial values the projection needs (d + e on the support) are
+// partial inverse DFTs at the P x P support points, and the new theta = F g is a partial DFT from
+// the support.  Spectra are unnormalised DFTs; zcol and xcol carry the column solve's 1/N^2.
+constexpr int kDLBlock = 64;  // bins per CTA of the per-frequency launches (one column segment)
+constexpr int kDLMaxP = 32;   // largest filter side the update supports
+template <typename T> struct DLArgs {
+  using C = typename CT<T>::type;
+  const C* zcol;   // [H][M][L]: code spectra / N^2 (channel-major, m*L + l)
+  const C* xcol;   // [H][M]: image spectra / N^2
+  C* spec;         // [H][2L]: theta = F g in planes 0..L-1, F(g - e) in planes L..2L-1
+  C* wcol;         // [H][L]: w = F(d + e) of this step
+  C* ypart;        // [H][N/kDLBlock][L][P]: per-CTA sums over k1 of w(k1, k2) exp(2 pi i k1 a / N)
+  C* yfull;        // [L][P][H]: the same summed over the whole column
+  int* cnt;        // [H]: CTAs of a column that have written their sums (zero between launches)
+  C* gfac;         // [H][L][P]: sum_b g(a, b) exp(-2 pi i k2 b / N)
+  T* gs;           // [L][P][P]: the filters g on the support (centre P/2)
+  double* rpart;   // [H][N/kDLBlock]: sums of |F(d - g)|^2 (weighted for the half spectrum)
+  double* spart;   // [L]: ||g - g_prev||^2 per filter
+  C* p_out;        // [H][M]: p = sum_l theta_l z_l / N^2 for the next x-update
+  const C* tw;     // exp(-2 pi i j / kTwN)
+  int N, M, L, P;
+  int check;       // 1: form the residual sums (an adaptation check follows this step)
+  T sigma;
+};
+template <typename T> cudaError_t launch_dl_solve(const DLArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_dl_filter(const DLArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_dl_spec(const DLArgs<T>& a, cudaStream_t s);
+// F(g - e) <- theta - (theta - F(g - e)) f: the scaled dual times f = sigma_old / sigma_new
 template <typename T>
-cudaError_t launch_dl_solve(const typename CT<T>::type* zcol, const typename CT<T>::type* xcol,
-                            const typename CT<T>::type* gecol, int gep, typename CT<T>::type* dcol, int N, int M,
-                            int L, double sigma, cudaStream_t s);
-template <typename T> cudaError_t launch_dl_norm(const T* d, const T* e, T* inv, int L, int N, int P, cudaStream_t s);
-template <typename T>
-cudaError_t launch_dl_project(const T* d, T* e, T* gs, const T* inv, int L, int N, int P, cudaStream_t s);
-template <typename T> cudaError_t launch_dl_crop(const T* g, T* out, int L, int N, int P, cudaStream_t s);
+cudaError_t launch_dl_rescale(typename CT<T>::type* spec, int L, int N, T f, cudaStream_t s);
 template <typename Tin> cudaError_t launch_embed_filters(const Tin* d, double* out, int L, int P, int N, cudaStream_t s);
 template <typename T>
 cudaError_t launch_theta_store(const SetupC<T>* th64, typename CT<T>::type* th, int L, int N, cudaStream_t s);

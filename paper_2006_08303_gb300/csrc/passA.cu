@@ -56,10 +56,15 @@ __device__ __forceinline__ void block_reduce_store(const T (&v)[kNPart], double*
 // FFT elements per thread: 8 for complex64 up to N = 1024 (more warps per
 // tile), 16 otherwise (keeps the CTA within 1024 threads).
 // (complex64 DCT / l1 tiles at N = 512 take 16: one warp per row-pair FFT, whose stage
-// barriers are then warp syncs; measured 6% faster there, while TV, which needs more
-// registers for its halo rows, is faster at 8)
-template <typename T> constexpr int elems_a(int N, int prior) {
-  return (sizeof(T) == 4 && N <= 1024) ? ((N == 512 && !prior_is_tv(prior)) ? 16 : 8) : 16;
+// barriers are then warp syncs, while TV, which needs more registers for its halo rows,
+// takes 8.)  Variant V = 1 of a complex64 iteration kernel at N = 256 .. 1024 takes the other
+// of 8 and 16; the plan's autotuner times both inside whole iterations and keeps the faster.
+template <typename T> constexpr int elems_a(int N, int prior, int V = 0) {
+  const int e = (sizeof(T) == 4 && N <= 1024) ? ((N == 512 && !prior_is_tv(prior)) ? 16 : 8) : 16;
+  return V == 1 ? 24 - e : e;
+}
+template <typename T> constexpr bool has_variant(int N, int prior) {
+  return sizeof(T) == 4 && N >= 256 && N <= 1024 && prior < ROWS_OUT && prior != PRIOR_WDCT;
 }
 
 // Pitch of the row-pair FFT buffers (complex elements): the padded FFT layout plus 4 slots from
@@ -97,9 +102,9 @@ template <typename T> constexpr size_t smem_for(int N, int prior, int R) {
   return sm;
 }
 
-template <typename T> constexpr int threads_for(int N, int prior, int R) {
+template <typename T> constexpr int threads_for(int N, int prior, int R, int V = 0) {
   const int npin = (R + (prior_is_tv(prior) ? 2 : 0)) / 2;
-  const int n = npin * (N / elems_a<T>(N, prior));
+  const int n = npin * (N / elems_a<T>(N, prior, V));
   return ((n + 31) / 32) * 32;
 }
 
@@ -201,9 +206,9 @@ __device__ __forceinline__ void acc_resid(T (&part)[kNPart], T w, T t, T un, con
   }
 }
 
-template <typename T, int LOGN, int PRIOR, int R>
-__global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
-                                  minblocks_for<T>(threads_for<T>(1 << LOGN, PRIOR, R),
+template <typename T, int LOGN, int PRIOR, int R, int V>
+__global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R, V),
+                                  minblocks_for<T>(threads_for<T>(1 << LOGN, PRIOR, R, V),
                                                    smem_for<T>(1 << LOGN, PRIOR, R)))
     passA_kernel(const PassAArgs<T> a) {
   using C = typename CT<T>::type;
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   constexpr int NPOUT = R / 2;
   constexpr int ZS = zs_of(N);
   constexpr int CP = col_pitch(N);
-  constexpr int E = elems_a<T>(N, PRIOR);
+  constexpr int E = elems_a<T>(N, PRIOR, V);
   constexpr int TEAM = N / E;
   constexpr int NCOMP = prior_is_tv(PRIOR) ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -303,7 +308,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
     __syncthreads();
     {
       const int team = tid / TEAM;
-      const TeamSync ts = make_block_team_sync(team, TEAM);
+      const TeamSync ts = make_team_sync(team, TEAM);
       if (ts.cta || team < NPIN)
         fft_team<C, LOGN, 1, E, +1>(zb + (team < NPIN ? team : 0) * ZS, tid % TEAM, a.tw, ts, team < NPIN);
     }
@@ -519,7 +524,7 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   // 4. forward row DFT of q (two rows per FFT), 5. store row half-spectra
   {
     const int team = tid / TEAM;
-    const TeamSync ts = make_block_team_sync(team, TEAM);
+    const TeamSync ts = make_team_sync(team, TEAM);
     if (ts.cta || team < NPOUT)
       fft_team<C, LOGN, 1, E, -1>(zb + (team < NPOUT ? team : 0) * ZS, tid % TEAM, a.tw, ts, team < NPOUT);
   }
@@ -547,13 +552,13 @@ __global__ void __launch_bounds__(threads_for<T>(1 << LOGN, PRIOR, R),
   }
 }
 
-template <typename T, int LOGN, int PRIOR>
+template <typename T, int LOGN, int PRIOR, int V>
 cudaError_t launchA(const PassAArgs<T>& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   constexpr int R = rows_for<T>(N, PRIOR);
-  constexpr int nth = threads_for<T>(N, PRIOR, R);
+  constexpr int nth = threads_for<T>(N, PRIOR, R, V);
   constexpr size_t sm = smem_for<T>(N, PRIOR, R);
-  auto kern = passA_kernel<T, LOGN, PRIOR, R>;
+  auto kern = passA_kernel<T, LOGN, PRIOR, R, V>;
   static PerDeviceOnce once;
   cudaError_t e = once([&] {
     if (sm > 48 * 1024) {
@@ -570,13 +575,23 @@ cudaError_t launchA(const PassAArgs<T>& a, cudaStream_t s) {
 
 template <typename T, int PRIOR>
 cudaError_t dispatchA(const PassAArgs<T>& a, int N, cudaStream_t s) {
+  if constexpr (has_variant<T>(256, PRIOR)) {
+    if (a.variant == 1) {
+      switch (N) {
+        case 256: return launchA<T, 8, PRIOR, 1>(a, s);
+        case 512: return launchA<T, 9, PRIOR, 1>(a, s);
+        case 1024: return launchA<T, 10, PRIOR, 1>(a, s);
+        default: break;
+      }
+    }
+  }
   switch (N) {
-    case 64: return launchA<T, 6, PRIOR>(a, s);
-    case 128: return launchA<T, 7, PRIOR>(a, s);
-    case 256: return launchA<T, 8, PRIOR>(a, s);
-    case 512: return launchA<T, 9, PRIOR>(a, s);
-    case 1024: return launchA<T, 10, PRIOR>(a, s);
-    case 2048: return launchA<T, 11, PRIOR>(a, s);
+    case 64: return launchA<T, 6, PRIOR, 0>(a, s);
+    case 128: return launchA<T, 7, PRIOR, 0>(a, s);
+    case 256: return launchA<T, 8, PRIOR, 0>(a, s);
+    case 512: return launchA<T, 9, PRIOR, 0>(a, s);
+    case 1024: return launchA<T, 10, PRIOR, 0>(a, s);
+    case 2048: return launchA<T, 11, PRIOR, 0>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,6 +1,7 @@
 // Request server: continuous batching of reconstructions on one GPU.
 //
-// Clients submit reconstructions (any N, K, M, analysis prior) at any time.  A
+// Clients submit reconstructions (any N, K, M, analysis prior, fixed or adaptive
+// penalty) at any time.  A
 // worker thread admits queued requests in arrival order as soon as an
 // execution slot is free and the device memory they need fits the budget,
 // gives each its own stream and plan, and drives all running requests in
@@ -11,6 +12,10 @@
 // when it converges or reaches max_iter; its x is copied to the client's
 // buffer, its plan is freed and the next queued request can enter.
 //
+// A request with the adaptive penalty of Eq. paramS has the rule applied at every
+// check, as cip_iterate does; it keeps its own factor and setup buffers, since a
+// change of rho forms both again.
+//
 // Requests that carry the same nonzero psf_key and the same (N, K, M, prior,
 // rho, beta) share one factor: the first one forms it in a cached plan, later
 // ones copy the packed factor instead of recomputing it.  Cached factors are
@@ -18,6 +23,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -84,7 +90,7 @@ struct cip_server {
   unsigned long long next_id = 1;
   std::atomic<bool> stop{false};
   std::thread worker;
-  // pinned host slots (2 doubles each) for the residuals of running requests
+  // pinned host slots (cip::kResidHost doubles each) for the residuals of running requests
   double* pinned = nullptr;
   // stream of the cached factor plans (they outlive the requests and their streams)
   cudaStream_t cache_stream = nullptr;
@@ -102,8 +108,16 @@ CacheKey key_of(const cip_request& r) {
   return CacheKey(r.psf_key, r.N, r.K, r.M, r.prior, r.rho, r.beta);
 }
 
+bool adaptive(const cip_request& r) { return r.rho_tau > 0; }
+
+// factor sharing: a nonzero psf_key on a fixed-penalty request
+bool shares_factor(const cip_request& r) { return r.psf_key != 0 && !adaptive(r); }
+
 size_t full_plan_bytes(const cip_request& r) {
-  return cip_plan_bytes(r.N, r.K, r.M, CIP_F32, (cip_prior)r.prior);
+  size_t b = cip_plan_bytes(r.N, r.K, r.M, CIP_F32, (cip_prior)r.prior);
+  // the adaptive penalty also keeps the measurement spectra (K half spectra, 16 bytes per bin)
+  if (adaptive(r)) b += (size_t)r.K * r.N * (r.N / 2 + 4) * 16;
+  return b;
 }
 
 // evict least-recently-used cached factors until `need` more bytes fit; returns whether they fit
@@ -131,7 +145,7 @@ void finish(cip_server* s, Request& q, int state, int status) {
   q.t_done = now_s(s);
   q.status = status;
   std::lock_guard<std::mutex> lk(s->mu);
-  if (q.pinned) s->free_slots.push_back((int)((q.pinned - s->pinned) / 2));
+  if (q.pinned) s->free_slots.push_back((int)((q.pinned - s->pinned) / cip::kResidHost));
   q.pinned = nullptr;
   s->used -= q.bytes;
   q.state = state;
@@ -148,8 +162,12 @@ cip_status setup(cip_server* s, Request& q) {
   }
   r = cip_set_prior(q.plan, (cip_prior)q.r.prior, q.r.lambda, q.r.rho, q.r.beta, st);
   if (r != CIP_OK) return r;
+  if (adaptive(q.r)) {
+    r = cip_set_rho_adaptation(q.plan, q.r.rho_tau, q.r.rho_mu);
+    if (r != CIP_OK) return r;
+  }
   cip_plan* src = nullptr;
-  if (q.r.psf_key) {
+  if (shares_factor(q.r)) {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->cache.find(key_of(q.r));
     if (it != s->cache.end()) {
@@ -160,7 +178,7 @@ cip_status setup(cip_server* s, Request& q) {
       s->cache_misses++;
     }
   }
-  if (q.r.psf_key && !src) {
+  if (shares_factor(q.r) && !src) {
     // form the factor once in a cached plan
     // (set_psfs waits for the factor, so the request's stream may read it right after)
     cip_plan* cp = nullptr;
@@ -189,8 +207,10 @@ cip_status setup(cip_server* s, Request& q) {
   if (r != CIP_OK) return r;
   r = cip_set_measurements(q.plan, q.y.data(), st);
   if (r != CIP_OK) return r;
-  r = cip::plan_trim(q.plan);
-  if (r != CIP_OK) return r;
+  if (!adaptive(q.r)) {  // an adaptive request forms its factor again whenever rho changes
+    r = cip::plan_trim(q.plan);
+    if (r != CIP_OK) return r;
+  }
   std::vector<float>().swap(q.h);
   std::vector<float>().swap(q.y);
   return CIP_OK;
@@ -223,13 +243,13 @@ void worker_main(cip_server* s) {
           continue;
         }
         if ((int)(s->running.size() + admitted.size()) >= s->max_active) break;
-        const size_t need = full_plan_bytes(q->r) * (q->r.psf_key ? 2 : 1);
+        const size_t need = full_plan_bytes(q->r) * (shares_factor(q->r) ? 2 : 1);
         if (!make_room(s, need) && !(s->running.empty() && admitted.empty())) break;
         s->queue.pop_front();
         // setup needs the full footprint; it drops to the resident size after trimming
         q->bytes = full_plan_bytes(q->r);
         s->used += q->bytes;
-        q->pinned = s->pinned + 2 * s->free_slots.back();
+        q->pinned = s->pinned + cip::kResidHost * s->free_slots.back();
         s->free_slots.pop_back();
         q->state = RQ_RUNNING;
         q->t_admit = now_s(s);
@@ -247,7 +267,9 @@ void worker_main(cip_server* s) {
       }
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        const size_t res = cip::plan_resident_bytes(q->r.N, q->r.K, q->r.M, CIP_F32, (cip_prior)q->r.prior);
+        const size_t res = adaptive(q->r) ? full_plan_bytes(q->r)
+                                          : cip::plan_resident_bytes(q->r.N, q->r.K, q->r.M, CIP_F32,
+                                                                     (cip_prior)q->r.prior);
         s->used -= q->bytes;
         q->bytes = res;
         s->used += q->bytes;
@@ -271,8 +293,8 @@ void worker_main(cip_server* s) {
       }
       any = true;
       q->iterations += q->chunk;
-      q->resid[0] = q->pinned[0];
-      q->resid[1] = q->pinned[1];
+      q->resid[0] = q->pinned[cip::kResidHost - 2];
+      q->resid[1] = q->pinned[cip::kResidHost - 1];
       {
         std::lock_guard<std::mutex> lk(s->mu);
         s->voxel_iters += (double)q->r.N * q->r.N * q->r.M * q->chunk;
@@ -284,6 +306,15 @@ void worker_main(cip_server* s) {
         cip_status r = cip_get_x(q->plan, q->r.x_out, q->stream);
         finish(s, *q, r == CIP_OK ? RQ_DONE : RQ_FAILED, r);
       } else {
+        if (adaptive(q->r)) {
+          // Eq. paramS at this check; a change of rho is enqueued ahead of the next chunk
+          cip_status r = cip::plan_adapt_rho(q->plan, q->pinned, q->stream);
+          if (r != CIP_OK) {
+            q->err = cip_last_error(q->plan);
+            finish(s, *q, RQ_FAILED, r);
+            continue;
+          }
+        }
         launch_chunk(s, *q);
         if (q->state == RQ_RUNNING) still.push_back(q);
       }
@@ -313,7 +344,7 @@ cip_status cip_server_create(cip_server** out, size_t hbm_budget, int max_active
   s->max_active = max_active > 0 ? max_active : 16;
   s->check_every = check_every > 0 ? check_every : 10;
   cudaGetDevice(&s->device);
-  if (cudaMallocHost((void**)&s->pinned, 2 * sizeof(double) * s->max_active) != cudaSuccess) {
+  if (cudaMallocHost((void**)&s->pinned, cip::kResidHost * sizeof(double) * s->max_active) != cudaSuccess) {
     delete s;
     return CIP_ERR_OOM;
   }
@@ -328,8 +359,11 @@ cip_status cip_server_create(cip_server** out, size_t hbm_budget, int max_active
 cip_status cip_server_submit(cip_server* s, const cip_request* r, unsigned long long* id) {
   if (!s || !r || !r->h || !r->y || !r->x_out) return CIP_ERR_INVALID_ARG;
   if (r->prior != CIP_PRIOR_TV && r->prior != CIP_PRIOR_DCT8 && r->prior != CIP_PRIOR_L1 &&
-      r->prior != CIP_PRIOR_TV_ISO)
+      r->prior != CIP_PRIOR_TV_ISO && r->prior != CIP_PRIOR_WDCT)
     return CIP_ERR_UNSUPPORTED;
+  if (r->rho_tau != 0.0 && !(r->rho_tau > 1.0 && r->rho_mu > 1.0 && std::isfinite(r->rho_tau) &&
+                             std::isfinite(r->rho_mu)))
+    return CIP_ERR_INVALID_ARG;
   if (r->N < 64 || r->N > 2048 || (r->N & (r->N - 1)) || r->K < 1 || r->K > 16 || r->M < 1 || r->M > 16)
     return CIP_ERR_UNSUPPORTED;
   if (r->max_iter < 1) return CIP_ERR_INVALID_ARG;

@@ -42,11 +42,11 @@ def problem(seed=31, N=64, K=2, M=3, L=4, Pf=5):
     return h, y, d0
 
 
-def learning_plan(torch, h, y, d, lam, rho, beta, sigma, dtype="f32"):
+def learning_plan(torch, h, y, d, lam, rho, beta, sigma, dtype="f32", check_every=0):
     from paper_2006_08303_gb300 import api
     K, M, N, _ = h.shape
     f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32 if dtype == "f32" else torch.float64).cuda()
-    P = api.Plan(N, K, M, dtype)
+    P = api.Plan(N, K, M, dtype, check_every=check_every)
     P.set_prior("convdict", lam, rho, beta)
     P.set_dictionary(f(d))
     P.set_dictionary_learning(sigma)
@@ -161,3 +161,56 @@ def test_learning_off_and_rejections(torch):
     with pytest.raises(api.CipError):
         B.set_dictionary_learning(1.0)
     B.close()
+
+
+@pytest.mark.parametrize("sigma0,dtype,tol", [(0.05, "f32", 1e-4), (500.0, "f32", 1e-4), (500.0, "f64", 1e-9)])
+def test_sigma_adaptation_matches_oracle(torch, sigma0, dtype, tol):
+    """Adaptation of sigma by the rule of Eq. paramS (reading R29), checked every 5 filter steps:
+    the sigma trajectory equals the oracle's (run_convdict_learn with check_every), rising from
+    0.05 or falling from 500 several times in 30 iterations; x, z and the filters agree; a
+    checkpoint carries the adapted sigma and replays bit for bit."""
+    h, y, d0 = problem()
+    iters, ce = 30, 5
+    x_or, z_or, _, _, f_or, sig_or = fast.run_convdict_learn(h, y, d0, LAM, RHO, BETA, sigma0, iters, check_every=ce)
+    assert len(set(sig_or)) >= 4  # the schedule changes sigma several times
+    P, _ = learning_plan(torch, h, y, d0, LAM, RHO, BETA, sigma0, dtype, check_every=ce)
+    P.set_sigma_adaptation(2.0, 10.0)
+    sig, ck, ck_sigma = [], None, None
+    for it in range(iters):
+        P.iterate(1)
+        sig.append(P.sigma)
+        if it == 11:
+            ck, ck_sigma = P.state_export(), P.sigma
+    assert sig == sig_or, (sig, sig_or)
+    xg = P.get_x().double().cpu().numpy()
+    zg = P.get_coefficients().double().cpu().numpy()
+    fg = P.get_dictionary().double().cpu().numpy()
+    assert rel(fg, f_or) <= tol, rel(fg, f_or)
+    assert rel(xg, x_or) <= tol, rel(xg, x_or)
+    assert rel(zg, gl(z_or)) <= tol, rel(zg, gl(z_or))
+    xa, fa = P.get_x().cpu().numpy(), P.get_dictionary().cpu().numpy()
+    P.set_dictionary_learning(sigma0 * 3)  # a different sigma, replaced by the checkpoint's
+    P.state_restore(ck)
+    assert P.sigma == ck_sigma
+    for _ in range(iters - 12):
+        P.iterate(1)
+    assert P.sigma == sig_or[-1]
+    assert np.array_equal(P.get_x().cpu().numpy(), xa) and np.array_equal(P.get_dictionary().cpu().numpy(), fa)
+    with pytest.raises(Exception):
+        P.set_sigma_adaptation(0.5, 10.0)
+    P.close()
+
+
+def test_filter_update_is_three_launches(torch):
+    """One step of the filter ADMM adds exactly three kernel launches to an iteration (filter
+    solve with the partial inverse DFT at the support rows; projection; spectra, dual and p)."""
+    h, y, d0 = problem(seed=12)
+    counts = []
+    for sigma in (0.0, 4.0):
+        P, _ = learning_plan(torch, h, y, d0, LAM, RHO, BETA, sigma)
+        P.iterate(2)
+        n0 = P.launches()
+        P.iterate(6)
+        counts.append(P.launches() - n0)
+        P.close()
+    assert counts[1] - counts[0] == 3 * 6, counts

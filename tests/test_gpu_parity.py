@@ -138,6 +138,38 @@ def test_column_pass_forms(torch, column_pass, prior, N, K, M, kind):
     P.close()
 
 
+@pytest.mark.parametrize("prior_fft", [8, 16])
+@pytest.mark.parametrize("prior,N,K,M,kind", [("tv", 256, 3, 3, "gauss"), ("dct8", 512, 4, 4, "disk"),
+                                               ("tv_iso", 512, 3, 3, "gauss"), ("l1", 1024, 2, 2, "gauss"),
+                                               ("tv", 1024, 2, 2, "gauss")])
+def test_prior_pass_fft_widths(torch, prior_fft, prior, N, K, M, kind):
+    """Both prior-pass kernels the autotuner chooses between (8 or 16 FFT elements per thread)
+    give Alg. 1's iterates: one step from oracle states within 1e-5, and the plan reports the width
+    it was given."""
+    rng, h, y = problem(400 + N + M, N, K, M, kind)
+    lam, rho = (1e-3, 1e-2) if prior == "dct8" else (1e-2, 1.0)
+    P = make_plan(torch, h, y, prior, lam, rho, 1.0, "f32", prior_fft=prior_fft)
+    assert P.config()["prior_fft_elems"] == prior_fft
+    for l, t, u, x1, u1 in oracle_states(h, y, prior, lam, rho, (0, 5), naive=False):
+        P.state_import(tdev(torch, t, "f32"), tdev(torch, u, "f32"))
+        P.iterate(1)
+        assert rel(P.get_x().double().cpu().numpy(), x1) <= 1e-5
+        assert u_err(P.get_u().double().cpu().numpy(), u1, x1, prior) <= 1e-5
+    P.close()
+
+
+def test_autotuned_prior_width_is_reported(torch):
+    """With everything autotuned the plan runs one of the two widths and reports it; an invalid
+    width is refused at plan creation."""
+    from paper_2006_08303_gb300 import api
+    rng, h, y = problem(7, 512, 2, 2, "disk")
+    P = make_plan(torch, h, y, "dct8", 1e-3, 1e-2, 1.0, "f32")
+    assert P.config()["prior_fft_elems"] in (8, 16)
+    P.close()
+    with pytest.raises(api.CipError):
+        api.Plan(512, 2, 2, "f32", prior_fft=4)
+
+
 @pytest.mark.parametrize("prior,N,rho", [("tv", 64, 1.0), ("dct8", 64, 0.3), ("l1", 128, 0.5)])
 def test_step_random_state(torch, prior, N, rho):
     """Property at white-noise (t, u): the complex64 step stays within 1e-4 of the FP64 oracle."""

@@ -155,3 +155,42 @@ def test_served_k_differs_from_m(torch):
         x_alone, n_alone = alone(torch, h, y, prior, lam, rho, 1e-3, 150)
         assert res["iterations"] == n_alone
         assert np.array_equal(x_out, x_alone)
+
+
+def test_served_wavelet_prior_and_adaptive_penalty(torch):
+    """The Kronecker wavelet (x) DCT prior and the adaptive penalty of Eq. paramS are served like
+    the other requests: each result equals the same reconstruction through the plan API (the
+    adaptive one with cip_set_rho_adaptation, whose rho changes at the same checks), also when
+    it shares the device with other requests."""
+    from paper_2006_08303_gb300 import api
+    S = api.Server(hbm_budget=8 << 30, max_active=4, check_every=10)
+    wd = make_req(51, 128, 3, "tv")
+    wd = (wd[0], wd[1], "wdct", 1e-2, 0.5)
+    ad = make_req(52, 128, 3, "tv")
+    ad = (ad[0], ad[1], "tv", 1e-2, 16.0)  # rho far from its adapted value: it changes several times
+    other = make_req(53, 256, 3, "dct8")
+    ids = [S.submit(*wd, tol=1e-4, max_iter=150),
+           S.submit(*ad, tol=1e-4, max_iter=300, rho_tau=2.0, rho_mu=10.0, psf_key=7),
+           S.submit(*other, tol=1e-3, max_iter=100)]
+    res = [S.wait(rid) for rid, _ in ids]
+    S.close()
+    assert all(r["state"] == "done" for r in res), res
+    x_w, n_w = alone(torch, *wd, 1e-4, 150)
+    assert res[0]["iterations"] == n_w and np.array_equal(ids[0][1], x_w)
+    P = api.Plan(128, 3, 3, "f32", check_every=10)
+    P.set_prior("tv", 1e-2, 16.0, 1.0)
+    P.set_rho_adaptation(2.0, 10.0)
+    P.set_psfs(ad[0])
+    P.set_measurements(ad[1])
+    n_a = P.iterate(300, 1e-4)
+    assert P.rho != 16.0  # the penalty did adapt
+    x_a = np.empty((3, 128, 128), np.float32)
+    P.get_x(x_a)
+    P.close()
+    assert res[1]["iterations"] == n_a and np.array_equal(ids[1][1], x_a)
+    with pytest.raises(api.CipError):
+        S2 = api.Server(hbm_budget=1 << 30)
+        try:
+            S2.submit(*ad, rho_tau=0.5, rho_mu=10.0)
+        finally:
+            S2.close()
