@@ -599,31 +599,34 @@ template <typename T> cip_status prior_pass(cip_plan* p, const PassAArgs<T>& a, 
     f.h[k] = (T)p->wfilt[k];
     f.g[k] = (T)((k & 1) ? -p->wfilt[15 - k] : p->wfilt[15 - k]);
   }
-  int J = 0;
-  while ((N >> (J + 1)) >= 16) ++J;  // levels down to a 16 x 16 coarse band
   // A: coefficients (Mallat layout); B: x, later q; S0, S1: the lowpass band between levels
   T* S[2] = {static_cast<T*>(p->wbuf[2]), static_cast<T*>(p->wbuf[2]) + real_elems(p, M) / 4};
   const int hp = N / 2;
   const size_t hplane = (size_t)hp * hp, plane = (size_t)N * N;
+  // levels on bands larger than nf: one tiled kernel each; from the band of side nf down to the
+  // 16 x 16 coarse band: one kernel (and one for the inverse), a CTA per channel in shared memory
+  const int nf = wave_fuse_band<T>(N);
+  int levf = 0;
+  while ((N >> levf) > nf) ++levf;
   if (!(a.flags & PA_IMPORT)) {
     CIP_LAUNCH(p, rows_from_spec<T>(p, a.xh, M, B, s));
-    for (int lev = 0; lev < J; ++lev) {
+    for (int lev = 0; lev < levf; ++lev) {
       const T* src = lev == 0 ? B : S[(lev - 1) & 1];
       const int sp = lev == 0 ? N : hp;
       const size_t spl = lev == 0 ? plane : hplane;
-      const bool last = lev == J - 1;
-      CIP_LAUNCH(p, launch_dwt2_fwd<T>(src, sp, spl, A, N, last ? A : S[lev & 1], last ? N : hp,
-                                       last ? plane : hplane, N >> lev, M, f, s));
+      CIP_LAUNCH(p, launch_dwt2_fwd<T>(src, sp, spl, A, N, S[lev & 1], hp, hplane, N >> lev, M, f, s));
     }
+    CIP_LAUNCH(p, launch_dwt2_fwd_fused<T>(levf == 0 ? B : S[(levf - 1) & 1], levf == 0 ? N : hp,
+                                           levf == 0 ? plane : hplane, A, N, nf, M, f, s));
   }
   CIP_LAUNCH(p, launch_wdct_shrink<T>(A, static_cast<const T*>(p->wcos), a.u_in, a.u_out, a.tprev, a.t_imp,
                                       a.partials, p->blocksA, N, M, a.tau, a.flags, s));
-  for (int lev = J - 1; lev >= 0; --lev) {
-    const bool coarsest = lev == J - 1;
-    const T* ll = coarsest ? A : S[lev & 1];
+  CIP_LAUNCH(p, launch_dwt2_inv_fused<T>(A, N, levf == 0 ? B : S[(levf - 1) & 1], levf == 0 ? N : hp,
+                                         levf == 0 ? plane : hplane, nf, M, f, s));
+  for (int lev = levf - 1; lev >= 0; --lev) {
     T* dst = lev == 0 ? B : S[(lev - 1) & 1];
-    CIP_LAUNCH(p, launch_dwt2_inv<T>(ll, coarsest ? N : hp, coarsest ? plane : hplane, A, N, dst, lev == 0 ? N : hp,
-                                     lev == 0 ? plane : hplane, N >> lev, M, f, s));
+    CIP_LAUNCH(p, launch_dwt2_inv<T>(S[lev & 1], hp, hplane, A, N, dst, lev == 0 ? N : hp, lev == 0 ? plane : hplane,
+                                     N >> lev, M, f, s));
   }
   CIP_LAUNCH(p, spec_from_rows<T>(p, B, M, p->rho, a.qh, s));
   return CIP_OK;

@@ -148,10 +148,11 @@ __global__ void p_from_z_kernel(const typename CT<T>::type* __restrict__ zcol, c
 // The spatial d and e off the support are never formed: g is zero there and e is only ever needed
 // through its spectrum.
 
-// exp(-2 pi i j / N) (SIGN < 0) or exp(+2 pi i j / N) (SIGN > 0) for any integer j
+// exp(-2 pi i j / N) (SIGN < 0) or exp(+2 pi i j / N) (SIGN > 0) for any integer j (N a power of
+// two: j mod N is j & (N - 1) in two's complement)
 template <int SIGN, typename C>
 __device__ __forceinline__ C tw_at(const C* __restrict__ tw, int j, int N) {
-  const int r = ((j % N) + N) % N;
+  const int r = j & (N - 1);
   C t = ldg_tw(&tw[r * (kTwN / N)]);
   if (SIGN > 0) t.y = -t.y;
   return t;
@@ -184,7 +185,8 @@ __device__ __forceinline__ void reduce_scatter(C (&v)[PM], int lane) {
 
 constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
 
-// block sum of one double per thread (blockDim a multiple of 32, <= 256); every thread gets it
+// block sum of one double per thread (blockDim a multiple of 32, <= 1024; red holds a value per
+// warp); every thread gets it
 __device__ __forceinline__ double block_sum256(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(kDLBlock) dl_solve_kernel(const DLArgs<T> a) {
     }
     return b;
   };
-#pragma unroll 2
+#pragma unroll 4
   for (int l = 0; l < L; ++l) {
     C z[M];
     const C b = load_b(l, z);
@@ -302,16 +304,31 @@ __global__ void __launch_bounds__(kDLBlock) dl_solve_kernel(const DLArgs<T> a) {
   constexpr int SH = ilog2c(32 / PM);
   const T isg = T(1) / sigma;
   C* wb = a.wcol + (size_t)k2 * L * CP + k1;
+  // the operands of filter l + 1 are loaded while filter l is processed (one thread per bin leaves
+  // few warps per SM, so the loads in flight per thread set the bandwidth)
+  C zn[M], gen, tn;
+  auto load_l = [&](int l) {
+#pragma unroll
+    for (int s = 0; s < M; ++s) zn[s] = __ldg(zb + ((size_t)s * L + l) * CP);
+    gen = __ldg(th + (size_t)(L + l) * CP);
+    tn = __ldg(th + (size_t)l * CP);
+  };
+  load_l(0);
 #pragma unroll 1
   for (int l = 0; l < L; ++l) {
     C z[M];
-    C d = load_b(l, z);
 #pragma unroll
-    for (int s = 0; s < M; ++s) {  // d -= conj(z_s) alpha_s
+    for (int s = 0; s < M; ++s) z[s] = mk<C>(zn[s].x * n2, zn[s].y * n2);
+    const C ge = gen, t = tn;
+    if (l + 1 < L) load_l(l + 1);
+    // b_l = sigma F(g - e)_l + sum_s conj(z_{l,s}) x_s, then d -= conj(z_s) alpha_s
+    C d = mk<C>(sigma * ge.x, sigma * ge.y);
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      cfmac(d, z[s], x[s]);
       d.x -= z[s].x * al[s].x + z[s].y * al[s].y;
       d.y -= z[s].x * al[s].y - z[s].y * al[s].x;
     }
-    const C t = __ldg(th + (size_t)l * CP), ge = __ldg(th + (size_t)(L + l) * CP);
     // w = d-hat + e-hat, e-hat = theta - F(g - e)
     const C wl = mk<C>(fma(d.x, isg, t.x - ge.x), fma(d.y, isg, t.y - ge.y));
     wb[(size_t)l * CP] = wl;
@@ -354,37 +371,61 @@ __global__ void __launch_bounds__(kDLBlock) dl_solve_kernel(const DLArgs<T> a) {
 //   v(a, b) = N^-2 sum_k2 c_k2 Re[Y(a, k2) exp(2 pi i k2 (b - P/2) / N)]
 // (c_k2 = 1 at k2 = 0 and N/2, 2 otherwise: the half spectrum of a real map); g = v / ||v||
 // (Eq. g_admm: support and unit norm, reading R22); ||g - g_prev||^2 when a check follows; then the
-// partial DFT G(a, k2) = sum_b g(a, b) exp(-2 pi i k2 (b - P/2) / N) for every k2.
+// partial DFT G(a, k2) = sum_b g(a, b) exp(-2 pi i k2 (b - P/2) / N) for every k2.  The sums over k2
+// run in chunks of kFiltChunk columns staged in shared memory (Y of every support row, and the
+// twiddles of every (k2, b)), kFiltSplit threads per output each taking every kFiltSplit-th column
+// of a chunk, their partial sums added in a fixed order.
+constexpr int kFiltThreads = 512, kFiltChunk = 32, kFiltSplit = 4;
 template <typename T>
-__global__ void __launch_bounds__(256) dl_filter_kernel(const DLArgs<T> a) {
+__global__ void __launch_bounds__(kFiltThreads) dl_filter_kernel(const DLArgs<T> a) {
   using C = typename CT<T>::type;
   const int N = a.N, L = a.L, P = a.P, H = N / 2 + 1, PP = P * P, cen = P / 2;
   const int l = blockIdx.x, tid = threadIdx.x;
   __shared__ T vs[kDLMaxP * kDLMaxP];
-  __shared__ double red[8];
+  __shared__ C ys[kDLMaxP][kFiltChunk];  // Y(a, k2) of the chunk
+  __shared__ C ws[kDLMaxP][kFiltChunk];  // exp(-2 pi i k2 (b - P/2) / N) of the chunk
+  __shared__ T part[kFiltSplit][kFiltThreads / kFiltSplit];
+  __shared__ double red[kFiltThreads / 32];
   const T inv_n = T(1) / ((T)N * (T)N);
-  for (int o = tid; o < PP; o += blockDim.x) {
-    const int ai = o / P, bi = o - ai * P;
-    const C* Y = a.yfull + ((size_t)l * P + ai) * H;
-    T e0 = T(0), e1 = T(0), o1 = T(0);
-    for (int k2 = 0; k2 < H; ++k2) {
-      const C y = Y[k2];
-      const C t = tw_at<-1>(a.tw, k2 * (bi - cen), N);  // Re(y conj(t)) = Re(y exp(+i ...))
-      const T r = fma(y.x, t.x, y.y * t.y);
-      if (k2 == 0 || k2 == N / 2) e0 += r;
-      else if (k2 & 1) o1 += r;
-      else e1 += r;
+  const C* Y = a.yfull + (size_t)l * P * H;
+  const int sub = tid % kFiltSplit, o0 = tid / kFiltSplit;
+  constexpr int OSTEP = kFiltThreads / kFiltSplit;
+  for (int ob = 0; ob < PP; ob += OSTEP) {  // outputs ob .. ob + OSTEP - 1 (one pass for P <= 11)
+    const int o = ob + o0;
+    const int ai = o < PP ? o / P : 0, bi = o < PP ? o - ai * P : 0;
+    T acc = T(0);
+    for (int c0 = 0; c0 < H; c0 += kFiltChunk) {
+      const int nc = H - c0 < kFiltChunk ? H - c0 : kFiltChunk;
+      __syncthreads();  // the previous chunk is consumed
+      for (int i = tid; i < P * kFiltChunk; i += kFiltThreads) {
+        const int r = i / kFiltChunk, c = i - r * kFiltChunk;
+        if (c < nc) {
+          ys[r][c] = Y[(size_t)r * H + c0 + c];
+          ws[r][c] = tw_at<-1>(a.tw, (c0 + c) * (r - cen), N);
+        }
+      }
+      __syncthreads();
+      if (o < PP) {
+        for (int c = sub; c < nc; c += kFiltSplit) {
+          const C y = ys[ai][c], t = ws[bi][c];  // Re(y conj(t)) = Re(y exp(+2 pi i k2 b / N))
+          const int k2 = c0 + c;
+          const T w = (k2 == 0 || k2 == N / 2) ? T(1) : T(2);
+          acc = fma(w, fma(y.x, t.x, y.y * t.y), acc);
+        }
+      }
     }
-    vs[o] = (e0 + T(2) * (e1 + o1)) * inv_n;
+    if (o < PP) part[sub][o0] = acc;
+    __syncthreads();
+    if (sub == 0 && o < PP) vs[o] = (((part[0][o0] + part[1][o0]) + part[2][o0]) + part[3][o0]) * inv_n;
   }
   __syncthreads();
   double nn = 0.0;
-  for (int o = tid; o < PP; o += blockDim.x) nn += (double)vs[o] * (double)vs[o];
+  for (int o = tid; o < PP; o += kFiltThreads) nn += (double)vs[o] * (double)vs[o];
   nn = block_sum256(nn, red);
   const T inv = nn > 0.0 ? (T)(1.0 / sqrt(nn)) : T(0);
   T* g = a.gs + (size_t)l * PP;
   double ds = 0.0;
-  for (int o = tid; o < PP; o += blockDim.x) {
+  for (int o = tid; o < PP; o += kFiltThreads) {
     const T gn = vs[o] * inv;
     const double dg = (double)gn - (double)g[o];
     ds += dg * dg;
@@ -396,7 +437,7 @@ __global__ void __launch_bounds__(256) dl_filter_kernel(const DLArgs<T> a) {
     if (tid == 0) a.spart[l] = ds;
   }
   __syncthreads();
-  for (int o = tid; o < P * H; o += blockDim.x) {
+  for (int o = tid; o < P * H; o += kFiltThreads) {
     const int ai = o / H, k2 = o - ai * H;
     C acc = mk<C>(0.0, 0.0);
     for (int bi = 0; bi < P; ++bi) {
@@ -437,12 +478,24 @@ __global__ void __launch_bounds__(kDLBlock) dl_spec_kernel(const DLArgs<T> a) {
   C* th = a.spec + (size_t)k2 * 2 * L * CP + k1;
   const C* wb = a.wcol + (size_t)k2 * L * CP + k1;
   const C* zb = a.zcol + (size_t)k2 * M * L * CP + k1;
+  // operands of filter l + 1 loaded while filter l is processed
+  C wn = wb[0], zn[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) zn[m] = zb[(size_t)m * L * CP];
 #pragma unroll 1
   for (int l = 0; l < L; ++l) {
     C gh = mk<C>(0.0, 0.0);
 #pragma unroll
     for (int i = 0; i < PM; ++i) cfma(gh, wa[i], gk[l][i]);
-    const C w = wb[(size_t)l * CP];
+    const C w = wn;
+    C z[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) z[m] = zn[m];
+    if (l + 1 < L) {
+      wn = wb[(size_t)(l + 1) * CP];
+#pragma unroll
+      for (int m = 0; m < M; ++m) zn[m] = zb[((size_t)m * L + l + 1) * CP];
+    }
     if (a.check) {
       const C t0 = th[(size_t)l * CP], ge0 = th[(size_t)(L + l) * CP];
       const T dx = w.x - t0.x + ge0.x - gh.x, dy = w.y - t0.y + ge0.y - gh.y;
@@ -451,7 +504,7 @@ __global__ void __launch_bounds__(kDLBlock) dl_spec_kernel(const DLArgs<T> a) {
     th[(size_t)l * CP] = gh;
     th[(size_t)(L + l) * CP] = mk<C>(T(2) * gh.x - w.x, T(2) * gh.y - w.y);
 #pragma unroll
-    for (int m = 0; m < M; ++m) cfma(pm[m], gh, zb[((size_t)m * L + l) * CP]);
+    for (int m = 0; m < M; ++m) cfma(pm[m], gh, z[m]);
   }
 #pragma unroll
   for (int m = 0; m < M; ++m) a.p_out[((size_t)k2 * M + m) * CP + k1] = pm[m];
@@ -509,7 +562,7 @@ template <typename T> cudaError_t launch_dl_solve(const DLArgs<T>& a, cudaStream
 }
 template <typename T> cudaError_t launch_dl_filter(const DLArgs<T>& a, cudaStream_t s) {
   if (!dl_args_ok(a)) return cudaErrorInvalidValue;
-  dl_filter_kernel<T><<<a.L, 256, 0, s>>>(a);
+  dl_filter_kernel<T><<<a.L, kFiltThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_dl_spec(const DLArgs<T>& a, cudaStream_t s) {

@@ -254,6 +254,18 @@ cudaError_t launch_dwt2_fwd(const T* in, int in_pitch, size_t in_plane, T* det, 
 template <typename T>
 cudaError_t launch_dwt2_inv(const T* ll, int ll_pitch, size_t ll_plane, const T* det, int N, T* out, int out_pitch,
                             size_t out_plane, int n, int M, const WaveFilt<T>& f, cudaStream_t s);
+// Bands of side n <= wave_fuse_n run all their remaining levels in one kernel, one CTA per
+// channel, in shared memory (2 n0 (n0 + 1) values forward, 2 n0 (n0 / 2 + 1) inverse).  wave_fuse_band(N): the side
+// of the first such band of an N x N image.  Forward: band n0 from `in` -> details and the final
+// 16 x 16 LL into A ([M][N][N], Mallat positions).  Inverse: from A -> the band n0 into `out`.
+template <typename T> constexpr int wave_fuse_n() { return 64; }
+template <typename T> int wave_fuse_band(int N);
+template <typename T>
+cudaError_t launch_dwt2_fwd_fused(const T* in, int in_pitch, size_t in_plane, T* A, int N, int n0, int M,
+                                  const WaveFilt<T>& f, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dwt2_inv_fused(const T* A, int N, T* out, int out_pitch, size_t out_plane, int n0, int M,
+                                  const WaveFilt<T>& f, cudaStream_t s);
 // per pixel: channel DCT (cmat [M][M], row k = frequency), shrinkage / dual update / residual
 // partials as the other prior passes (flags PA_*), q = t - u', coefficients <- C^T q in place
 template <typename T>

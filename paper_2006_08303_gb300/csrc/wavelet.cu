@@ -239,6 +239,104 @@ __global__ void __launch_bounds__(256) dwt2_inv_kernel(const T* __restrict__ ll,
   }
 }
 
+// Every level of a band of side n0 <= wave_fuse_n<T>() in one CTA per channel, in shared memory:
+// the band (rows then columns per level, periodic in the current side n), its LL quadrant kept for
+// the next level, the detail subbands to their Mallat positions in A (pitch N), the final 16 x 16
+// LL to A's corner.  The same filtering as dwt2_fwd_kernel; only the tiling differs.
+template <typename T>
+__global__ void __launch_bounds__(512) dwt2_fwd_fused_kernel(const T* __restrict__ in, int in_pitch, size_t in_plane,
+                                                             T* __restrict__ A, int N, int n0, WaveFilt<T> f) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  const int pp = n0 + 1;
+  T* X = reinterpret_cast<T*>(wsm);  // [n0][n0 + 1]: the band of the current level
+  T* R = X + (size_t)n0 * pp;          // [n0][n0 + 1]: after the row filters
+  const int ch = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const T* src = in + (size_t)ch * in_plane;
+  T* dst = A + (size_t)ch * N * N;
+  for (int idx = tid; idx < n0 * n0; idx += nth) {
+    const int r = idx / n0, c = idx - r * n0;
+    X[r * pp + c] = src[(size_t)r * in_pitch + c];
+  }
+  __syncthreads();
+  for (int n = n0; n >= 32; n >>= 1) {
+    const int half = n / 2;
+    for (int idx = tid; idx < n * n; idx += nth) {
+      const int r = idx / n, o = idx - r * n, oo = o & (half - 1);
+      const bool lo = o < half;
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc = fma(lo ? f.h[k] : f.g[k], X[r * pp + ((2 * oo + k) & (n - 1))], acc);
+      R[r * pp + o] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += nth) {
+      const int i = idx / n, o = idx - i * n, ii = i & (half - 1);
+      const bool lo = i < half;
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc = fma(lo ? f.h[k] : f.g[k], R[((2 * ii + k) & (n - 1)) * pp + o], acc);
+      const int rb = lo ? 0 : 1, cb = o < half ? 0 : 1, col = o & (half - 1);
+      if (rb == 0 && cb == 0) {
+        if (half == 16) dst[(size_t)ii * N + col] = acc;
+        else X[ii * pp + col] = acc;
+      } else {
+        dst[(size_t)(rb * half + ii) * N + cb * half + col] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The inverse of dwt2_fwd_fused_kernel: from the 16 x 16 LL in A's corner and the detail subbands
+// (Mallat positions, pitch N) up to the band of side n0, in one CTA per channel: per level the
+// column inverse then the row inverse of dwt2_inv_kernel over the whole band; the result of the
+// last level goes to out (pitch out_pitch), the others stay in shared memory as the next LL.
+template <typename T>
+__global__ void __launch_bounds__(512) dwt2_inv_fused_kernel(const T* __restrict__ A, int N, T* __restrict__ out,
+                                                             int out_pitch, size_t out_plane, int n0, WaveFilt<T> f) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  const int q0 = n0 / 2, qp = q0 + 1;
+  T* C = reinterpret_cast<T*>(wsm);  // [4][q0][q0 + 1]: subband rb * 2 + cb of the current level
+  T* V = C + (size_t)4 * q0 * qp;      // [2][n0][q0 + 1]: after the column inverse
+  const int ch = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const T* a = A + (size_t)ch * N * N;
+  for (int idx = tid; idx < 16 * 16; idx += nth) C[(idx >> 4) * qp + (idx & 15)] = a[(size_t)(idx >> 4) * N + (idx & 15)];
+  for (int n = 32; n <= n0; n <<= 1) {
+    const int half = n / 2, hh = half * half;
+    for (int idx = tid; idx < 3 * hh; idx += nth) {
+      const int sb = 1 + idx / hh, rem = idx - (sb - 1) * hh, r = rem / half, c = rem - r * half;
+      const int rb = sb >> 1, cb = sb & 1;
+      C[((size_t)sb * q0 + r) * qp + c] = a[(size_t)(rb * half + r) * N + cb * half + c];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 2 * n * half; idx += nth) {
+      const int cb = idx / (n * half), rem = idx - cb * n * half, j = rem / half, b = rem - j * half;
+      T acc = T(0);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int k = (j & 1) + 2 * t, ai = ((j >> 1) - t) & (half - 1);
+        acc = fma(f.h[k], C[((size_t)cb * q0 + ai) * qp + b], acc);
+        acc = fma(f.g[k], C[((size_t)(2 + cb) * q0 + ai) * qp + b], acc);
+      }
+      V[((size_t)cb * n0 + j) * qp + b] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += nth) {
+      const int j = idx / n, x = idx - j * n;
+      T acc = T(0);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int k = (x & 1) + 2 * t, bb = ((x >> 1) - t) & (half - 1);
+        acc = fma(f.h[k], V[(size_t)j * qp + bb], acc);
+        acc = fma(f.g[k], V[((size_t)n0 + j) * qp + bb], acc);
+      }
+      if (n == n0) out[(size_t)ch * out_plane + (size_t)j * out_pitch + x] = acc;
+      else C[(size_t)j * qp + x] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 // Per pixel over the M channels: w = C c (channel DCT), then Eq. solt_trans / Eq. subu_trans on
 // w (or t = t_imp in import mode), q = t - u', and c <- C^T q in place.  Residual partial sums
 // per block (the same five sums and order as the other prior passes) into partials[block].
@@ -342,6 +440,39 @@ cudaError_t launch_dwt2_inv(const T* ll, int ll_pitch, size_t ll_plane, const T*
   return cudaGetLastError();
 }
 
+template <typename T> int wave_fuse_band(int N) { return N < wave_fuse_n<T>() ? N : wave_fuse_n<T>(); }
+
+template <typename T>
+cudaError_t launch_dwt2_fwd_fused(const T* in, int in_pitch, size_t in_plane, T* A, int N, int n0, int M,
+                                  const WaveFilt<T>& f, cudaStream_t s) {
+  if (n0 < 32 || n0 > wave_fuse_n<T>() || n0 > N || (n0 & (n0 - 1))) return cudaErrorInvalidValue;
+  const size_t sm = 2 * (size_t)n0 * (n0 + 1) * sizeof(T);
+  static PerDeviceOnce once;
+  cudaError_t e = once([&] {
+    return cudaFuncSetAttribute(dwt2_fwd_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * (size_t)wave_fuse_n<T>() * (wave_fuse_n<T>() + 1) * sizeof(T)));
+  });
+  if (e != cudaSuccess) return e;
+  dwt2_fwd_fused_kernel<T><<<M, 512, sm, s>>>(in, in_pitch, in_plane, A, N, n0, f);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dwt2_inv_fused(const T* A, int N, T* out, int out_pitch, size_t out_plane, int n0, int M,
+                                  const WaveFilt<T>& f, cudaStream_t s) {
+  if (n0 < 32 || n0 > wave_fuse_n<T>() || n0 > N || (n0 & (n0 - 1))) return cudaErrorInvalidValue;
+  const size_t sm = 8 * (size_t)(n0 / 2) * (n0 / 2 + 1) * sizeof(T);  // C: 4 q (q + 1), V: 2 n0 (q + 1)
+  static PerDeviceOnce once;
+  cudaError_t e = once([&] {
+    const int q = wave_fuse_n<T>() / 2;
+    return cudaFuncSetAttribute(dwt2_inv_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(8 * (size_t)q * (q + 1) * sizeof(T)));
+  });
+  if (e != cudaSuccess) return e;
+  dwt2_inv_fused_kernel<T><<<M, 512, sm, s>>>(A, N, out, out_pitch, out_plane, n0, f);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_wdct_shrink(T* coef, const T* cmat, const T* u_in, T* u_out, T* tprev, const T* t_imp,
                                double* partials, int blocks, int N, int M, T tau, int flags, cudaStream_t s) {
@@ -367,6 +498,16 @@ template cudaError_t launch_dwt2_inv<float>(const float*, int, size_t, const flo
                                             int, const WaveFilt<float>&, cudaStream_t);
 template cudaError_t launch_dwt2_inv<double>(const double*, int, size_t, const double*, int, double*, int, size_t,
                                              int, int, const WaveFilt<double>&, cudaStream_t);
+template int wave_fuse_band<float>(int);
+template int wave_fuse_band<double>(int);
+template cudaError_t launch_dwt2_fwd_fused<float>(const float*, int, size_t, float*, int, int, int,
+                                                  const WaveFilt<float>&, cudaStream_t);
+template cudaError_t launch_dwt2_fwd_fused<double>(const double*, int, size_t, double*, int, int, int,
+                                                   const WaveFilt<double>&, cudaStream_t);
+template cudaError_t launch_dwt2_inv_fused<float>(const float*, int, float*, int, size_t, int, int,
+                                                  const WaveFilt<float>&, cudaStream_t);
+template cudaError_t launch_dwt2_inv_fused<double>(const double*, int, double*, int, size_t, int, int,
+                                                   const WaveFilt<double>&, cudaStream_t);
 template cudaError_t launch_wdct_shrink<float>(float*, const float*, const float*, float*, float*, const float*,
                                                double*, int, int, int, float, int, cudaStream_t);
 template cudaError_t launch_wdct_shrink<double>(double*, const double*, const double*, double*, double*,

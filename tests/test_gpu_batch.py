@@ -118,10 +118,12 @@ def test_batch_classes_match_oracle_after_100_iterations(torch):
     assert max(errs.values()) <= 1e-4, errs
 
 
-def test_plain_fp32_method_is_less_accurate_on_ill_conditioned_bins(torch):
+@pytest.mark.parametrize("column_pass", [1, 2])
+def test_plain_fp32_method_is_less_accurate_on_ill_conditioned_bins(torch, column_pass):
     """The plain FP32 method (factor formed and applied in FP32) versus the mixed path on the
-    spectral DCT instance (rho = 1e-2, kappa(Psi) ~ 1e4): both run, the mixed path stays within the
-    per-step bound and is several times more accurate."""
+    spectral DCT instance (rho = 1e-2, kappa(Psi) ~ 1e4), through both column-pass forms: both run,
+    the mixed path stays within the per-step bound and is several times more accurate, and the plain
+    method is still the same x-update (its error is FP32 rounding, not a different formula)."""
     from paper_2006_08303_gb300 import api
     Pr = inputs.spectral_dct(N=256, M=10)
     S = fast.analysis_setup(Pr.h, Pr.y, Pr.prior, Pr.lam, Pr.rho, Pr.beta)
@@ -132,7 +134,7 @@ def test_plain_fp32_method_is_less_accurate_on_ill_conditioned_bins(torch):
     x1, _, _, _ = fast.analysis_step(S, t, u)
     errs = {}
     for plain in (False, True):
-        P = api.Plan(Pr.N, Pr.K, Pr.M, "f32", plain_fp32=plain)
+        P = api.Plan(Pr.N, Pr.K, Pr.M, "f32", plain_fp32=plain, column_pass=column_pass)
         P.set_prior(Pr.prior, Pr.lam, Pr.rho, Pr.beta)
         f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
         P.set_psfs(f(Pr.h))
@@ -141,5 +143,6 @@ def test_plain_fp32_method_is_less_accurate_on_ill_conditioned_bins(torch):
         P.iterate(1)
         errs[plain] = rel(P.get_x().double().cpu().numpy(), x1)
         P.close()
+    print(f"column pass {column_pass}: one step from oracle state, mixed {errs[False]:.2e}, plain FP32 {errs[True]:.2e}")
     assert errs[False] <= 1e-5
-    assert errs[True] > 3 * errs[False], errs
+    assert 3 * errs[False] < errs[True] < 1e-2, errs
