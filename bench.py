@@ -419,42 +419,58 @@ def workload_dictlearn(args, torch, api, inputs):
 
 
 def workload_batch(args, torch, api, inputs):
-    """64 instances, N in {128..1024}, M = K in {3, 5, 10}, TV, 100 iterations each: plain per-instance
-    FP32 method (one plan after another, no graph) against the batched mixed-precision form."""
+    """64 instances, N in {128..1024}, M = K in {3, 5, 10}, TV, 100 iterations each, four ways: the
+    plain FP32 method one plan after another (no graph); the mixed-precision path one plan after
+    another (as accurate as the batch, no graph); the batched mixed form (one CUDA graph) with every
+    plan autotuned (column-pass form and prior-pass FFT width, timed as whole iterations); and the
+    same batch with the prior-pass FFT width fixed at the default (8 elements per thread), so that
+    the autotuner's choice is measured against the fixed one on this mix."""
     probs = inputs.mixed_batch()
     f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
     vox = sum(p.voxels for p in probs) * 100
 
-    def plans(plain):
+    def plans(plain, prior_fft=0):
         out = []
         for p in probs:
-            P = api.Plan(p.N, p.K, p.M, "f32", plain_fp32=plain)
+            P = api.Plan(p.N, p.K, p.M, "f32", plain_fp32=plain, prior_fft=prior_fft)
             P.set_prior(p.prior, p.lam, p.rho, p.beta)
             P.set_psfs(f(p.h))
             P.set_measurements(f(p.y))
             out.append(P)
         return out
 
+    def one_by_one(ps):
+        for P in ps:
+            P.iterate(2)
+            P.reset_state()
+        t = _ev_time(torch, lambda: [P.iterate(100) for P in ps])
+        x0 = ps[0].get_x().double().cpu().numpy()
+        for P in ps:
+            P.close()
+        return t, x0
+
+    def batched(ps):
+        widths = {}
+        for P in ps:
+            e = P.config()["prior_fft_elems"]
+            widths[e] = widths.get(e, 0) + 1
+        B = api.Batch(ps, nstreams=8)
+        B.iterate(10)  # records the graph (after two eager iterations, so every plan is back on side 0)
+        for P in ps:
+            P.reset_state()
+        t = _ev_time(torch, lambda: B.iterate(100))
+        x0 = ps[0].get_x().double().cpu().numpy()
+        B.close()
+        for P in ps:
+            P.close()
+        return t, x0, widths
+
     res = {}
-    ps = plans(True)
-    for P in ps:
-        P.iterate(2)
-        P.reset_state()
-    t_plain = _ev_time(torch, lambda: [P.iterate(100) for P in ps])
-    x_plain = ps[0].get_x().double().cpu().numpy()
-    for P in ps:
-        P.close()
-    pb = plans(False)
-    B = api.Batch(pb, nstreams=8)
-    B.iterate(10)  # records the graph (after two eager iterations, so every plan is back on side 0)
-    for P in pb:
-        P.reset_state()
-    t_batch = _ev_time(torch, lambda: B.iterate(100))
-    x_mixed = pb[0].get_x().double().cpu().numpy()
-    B.close()
-    for P in pb:
-        P.close()
-    # accuracy of both against the FP64 oracle on the first instance
+    t_plain, x_plain = one_by_one(plans(True))
+    t_single, x_single = one_by_one(plans(False))
+    t_batch, x_mixed, w_tuned = batched(plans(False))
+    t_fixed, x_fixed, w_fixed = batched(plans(False, prior_fft=8))
+    # accuracy against the FP64 oracle on the first instance
     from oracle import fast
     p0 = probs[0]
     S = fast.analysis_setup(p0.h, p0.y, p0.prior, p0.lam, p0.rho, p0.beta)
@@ -471,8 +487,14 @@ def workload_batch(args, torch, api, inputs):
                            "voxel_iters": vox, "step": "100 iterations of all 64 instances (setup excluded)"},
                 "plain_per_instance_fp32": {"value": vox / t_plain, "ms": 1e3 * t_plain,
                                             "rel_err_instance0": err(x_plain)},
-                "batched_mixed": {"value": vox / t_batch, "ms": 1e3 * t_batch, "rel_err_instance0": err(x_mixed)},
-                "speedup": t_plain / t_batch})
+                "mixed_per_instance": {"value": vox / t_single, "ms": 1e3 * t_single,
+                                       "rel_err_instance0": err(x_single)},
+                "batched_mixed": {"value": vox / t_batch, "ms": 1e3 * t_batch, "rel_err_instance0": err(x_mixed),
+                                  "prior_fft_widths": w_tuned},
+                "batched_mixed_fixed_width8": {"value": vox / t_fixed, "ms": 1e3 * t_fixed,
+                                               "rel_err_instance0": err(x_fixed), "prior_fft_widths": w_fixed},
+                "speedup_vs_plain": t_plain / t_batch, "speedup_vs_mixed_per_instance": t_single / t_batch,
+                "autotuned_vs_fixed_width": t_fixed / t_batch})
     return res
 
 

@@ -371,43 +371,51 @@ __global__ void __launch_bounds__(kDLBlock) dl_solve_kernel(const DLArgs<T> a) {
 //   v(a, b) = N^-2 sum_k2 c_k2 Re[Y(a, k2) exp(2 pi i k2 (b - P/2) / N)]
 // (c_k2 = 1 at k2 = 0 and N/2, 2 otherwise: the half spectrum of a real map); g = v / ||v||
 // (Eq. g_admm: support and unit norm, reading R22); ||g - g_prev||^2 when a check follows; then the
-// partial DFT G(a, k2) = sum_b g(a, b) exp(-2 pi i k2 (b - P/2) / N) for every k2.  The sums over k2
-// run in chunks of kFiltChunk columns staged in shared memory (Y of every support row, and the
-// twiddles of every (k2, b)), kFiltSplit threads per output each taking every kFiltSplit-th column
-// of a chunk, their partial sums added in a fixed order.
-constexpr int kFiltThreads = 512, kFiltChunk = 32, kFiltSplit = 4;
+// partial DFT G(a, k2) = sum_b g(a, b) exp(-2 pi i k2 (b - P/2) / N) for every k2.  Y of all
+// support rows and the twiddles of every (k2, b) are staged in shared memory for `chunk` columns
+// at a time (all H at once where they fit); kFiltSplit threads per output each take every
+// kFiltSplit-th column, their partial sums added in a fixed order.
+constexpr int kFiltThreads = 512, kFiltSplit = 4;
+constexpr size_t kFiltSmem = 96 * 1024;
+template <typename T> int filt_chunk(int N, int P) {
+  const int H = N / 2 + 1;
+  const int c = (int)(kFiltSmem / (2 * (size_t)P * sizeof(typename CT<T>::type)));
+  return c < H ? c : H;
+}
 template <typename T>
-__global__ void __launch_bounds__(kFiltThreads) dl_filter_kernel(const DLArgs<T> a) {
+__global__ void __launch_bounds__(kFiltThreads) dl_filter_kernel(const DLArgs<T> a, int chunk) {
   using C = typename CT<T>::type;
   const int N = a.N, L = a.L, P = a.P, H = N / 2 + 1, PP = P * P, cen = P / 2;
   const int l = blockIdx.x, tid = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  C* ys = reinterpret_cast<C*>(fsm);  // [P][chunk]: Y(a, k2) of the chunk
+  C* ws = ys + (size_t)P * chunk;       // [P][chunk]: exp(-2 pi i k2 (b - P/2) / N)
   __shared__ T vs[kDLMaxP * kDLMaxP];
-  __shared__ C ys[kDLMaxP][kFiltChunk];  // Y(a, k2) of the chunk
-  __shared__ C ws[kDLMaxP][kFiltChunk];  // exp(-2 pi i k2 (b - P/2) / N) of the chunk
   __shared__ T part[kFiltSplit][kFiltThreads / kFiltSplit];
   __shared__ double red[kFiltThreads / 32];
   const T inv_n = T(1) / ((T)N * (T)N);
   const C* Y = a.yfull + (size_t)l * P * H;
   const int sub = tid % kFiltSplit, o0 = tid / kFiltSplit;
   constexpr int OSTEP = kFiltThreads / kFiltSplit;
+  auto stage = [&](int c0, int nc, bool with_y) {
+    __syncthreads();  // the previous chunk is consumed
+    for (int i = tid; i < P * nc; i += kFiltThreads) {
+      const int r = i / nc, c = i - r * nc;
+      if (with_y) ys[(size_t)r * chunk + c] = Y[(size_t)r * H + c0 + c];
+      ws[(size_t)r * chunk + c] = tw_at<-1>(a.tw, (c0 + c) * (r - cen), N);
+    }
+    __syncthreads();
+  };
   for (int ob = 0; ob < PP; ob += OSTEP) {  // outputs ob .. ob + OSTEP - 1 (one pass for P <= 11)
     const int o = ob + o0;
     const int ai = o < PP ? o / P : 0, bi = o < PP ? o - ai * P : 0;
     T acc = T(0);
-    for (int c0 = 0; c0 < H; c0 += kFiltChunk) {
-      const int nc = H - c0 < kFiltChunk ? H - c0 : kFiltChunk;
-      __syncthreads();  // the previous chunk is consumed
-      for (int i = tid; i < P * kFiltChunk; i += kFiltThreads) {
-        const int r = i / kFiltChunk, c = i - r * kFiltChunk;
-        if (c < nc) {
-          ys[r][c] = Y[(size_t)r * H + c0 + c];
-          ws[r][c] = tw_at<-1>(a.tw, (c0 + c) * (r - cen), N);
-        }
-      }
-      __syncthreads();
+    for (int c0 = 0; c0 < H; c0 += chunk) {
+      const int nc = H - c0 < chunk ? H - c0 : chunk;
+      if (ob == 0 || nc < H) stage(c0, nc, true);  // a single chunk is staged once
       if (o < PP) {
         for (int c = sub; c < nc; c += kFiltSplit) {
-          const C y = ys[ai][c], t = ws[bi][c];  // Re(y conj(t)) = Re(y exp(+2 pi i k2 b / N))
+          const C y = ys[(size_t)ai * chunk + c], t = ws[(size_t)bi * chunk + c];  // Re(y conj(t))
           const int k2 = c0 + c;
           const T w = (k2 == 0 || k2 == N / 2) ? T(1) : T(2);
           acc = fma(w, fma(y.x, t.x, y.y * t.y), acc);
@@ -417,8 +425,8 @@ __global__ void __launch_bounds__(kFiltThreads) dl_filter_kernel(const DLArgs<T>
     if (o < PP) part[sub][o0] = acc;
     __syncthreads();
     if (sub == 0 && o < PP) vs[o] = (((part[0][o0] + part[1][o0]) + part[2][o0]) + part[3][o0]) * inv_n;
+    __syncthreads();
   }
-  __syncthreads();
   double nn = 0.0;
   for (int o = tid; o < PP; o += kFiltThreads) nn += (double)vs[o] * (double)vs[o];
   nn = block_sum256(nn, red);
@@ -436,17 +444,22 @@ __global__ void __launch_bounds__(kFiltThreads) dl_filter_kernel(const DLArgs<T>
     ds = block_sum256(ds, red);
     if (tid == 0) a.spart[l] = ds;
   }
-  __syncthreads();
-  for (int o = tid; o < P * H; o += kFiltThreads) {
-    const int ai = o / H, k2 = o - ai * H;
-    C acc = mk<C>(0.0, 0.0);
-    for (int bi = 0; bi < P; ++bi) {
-      const T gv = vs[ai * P + bi];
-      const C t = tw_at<-1>(a.tw, k2 * (bi - cen), N);
-      acc.x = fma(gv, t.x, acc.x);
-      acc.y = fma(gv, t.y, acc.y);
+  // G(a, k2) = sum_b g(a, b) ws[b][k2] over the same chunks (twiddles staged again when chunked)
+  for (int c0 = 0; c0 < H; c0 += chunk) {
+    const int nc = H - c0 < chunk ? H - c0 : chunk;
+    if (nc < H) stage(c0, nc, false);
+    else __syncthreads();  // vs is final
+    for (int o = tid; o < P * nc; o += kFiltThreads) {
+      const int ai = o / nc, c = o - ai * nc;
+      C acc = mk<C>(0.0, 0.0);
+      for (int bi = 0; bi < P; ++bi) {
+        const T gv = vs[ai * P + bi];
+        const C t = ws[(size_t)bi * chunk + c];
+        acc.x = fma(gv, t.x, acc.x);
+        acc.y = fma(gv, t.y, acc.y);
+      }
+      a.gfac[((size_t)(c0 + c) * L + l) * P + ai] = acc;
     }
-    a.gfac[((size_t)k2 * L + l) * P + ai] = acc;
   }
 }
 
@@ -562,7 +575,14 @@ template <typename T> cudaError_t launch_dl_solve(const DLArgs<T>& a, cudaStream
 }
 template <typename T> cudaError_t launch_dl_filter(const DLArgs<T>& a, cudaStream_t s) {
   if (!dl_args_ok(a)) return cudaErrorInvalidValue;
-  dl_filter_kernel<T><<<a.L, kFiltThreads, 0, s>>>(a);
+  const int chunk = filt_chunk<T>(a.N, a.P);
+  const size_t sm = 2 * (size_t)a.P * chunk * sizeof(typename CT<T>::type);
+  static PerDeviceOnce once;
+  cudaError_t e = once([&] {
+    return cudaFuncSetAttribute(dl_filter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFiltSmem);
+  });
+  if (e != cudaSuccess) return e;
+  dl_filter_kernel<T><<<a.L, kFiltThreads, sm, s>>>(a, chunk);
   return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_dl_spec(const DLArgs<T>& a, cudaStream_t s) {
