@@ -77,6 +77,7 @@ struct cip_plan {
   // matrix [M][M] and the Symmlet-8 lowpass
   void* wbuf[3] = {nullptr, nullptr, nullptr};
   void* wcos = nullptr;
+  double wcos_h[256] = {};  // the same matrix on the host (passed to the shrinkage kernel by value)
   double wfilt[16] = {};
   // online dictionary update (Section IV-B): sigma = 0 off.  While on, theta lives in the first L
   // planes of dl_spec and F(g - e) in the last L; the filters g on their P x P support in dl_gs.
@@ -262,6 +263,7 @@ template <typename T> cip_status alloc_state(cip_plan* p) {
       for (int m = 0; m < p->M; ++m)
         c[(size_t)k * p->M + m] =
             (T)(std::sqrt((k == 0 ? 1.0 : 2.0) / p->M) * std::cos(M_PI * (2 * m + 1) * k / (2.0 * p->M)));
+    for (size_t i = 0; i < c.size(); ++i) p->wcos_h[i] = (double)c[i];
     CIP_CUDA(p, cudaMemcpyAsync(p->wcos, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice, p->ast));
     CIP_CUDA(p, cudaStreamSynchronize(p->ast));
   }
@@ -619,7 +621,9 @@ template <typename T> cip_status prior_pass(cip_plan* p, const PassAArgs<T>& a, 
     CIP_LAUNCH(p, launch_dwt2_fwd_fused<T>(levf == 0 ? B : S[(levf - 1) & 1], levf == 0 ? N : hp,
                                            levf == 0 ? plane : hplane, A, N, nf, M, f, s));
   }
-  CIP_LAUNCH(p, launch_wdct_shrink<T>(A, static_cast<const T*>(p->wcos), a.u_in, a.u_out, a.tprev, a.t_imp,
+  ChanDCT<T> cm;
+  for (int i = 0; i < 256; ++i) cm.c[i] = (T)p->wcos_h[i];
+  CIP_LAUNCH(p, launch_wdct_shrink<T>(A, cm, a.u_in, a.u_out, a.tprev, a.t_imp,
                                       a.partials, p->blocksA, N, M, a.tau, a.flags, s));
   CIP_LAUNCH(p, launch_dwt2_inv_fused<T>(A, N, levf == 0 ? B : S[(levf - 1) & 1], levf == 0 ? N : hp,
                                          levf == 0 ? plane : hplane, nf, M, f, s));

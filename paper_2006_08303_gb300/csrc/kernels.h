@@ -241,6 +241,11 @@ template <typename T> struct WaveFilt {
   T h[16];  // lowpass
   T g[16];  // highpass g_k = (-1)^k h_{15-k}
 };
+// the orthonormal DCT-II along the channels, row k = frequency ([M][M], M <= 16), passed by value
+// so that the per-pixel kernel reads it from the constant bank (every thread uses the same entry)
+template <typename T> struct ChanDCT {
+  T c[256];
+};
 // Symmlet lowpass with p vanishing moments (2p taps) from the spectral factorisation; false if p
 // is outside [1, 8]
 bool symlet_lowpass(int p, double* h);
@@ -269,7 +274,7 @@ cudaError_t launch_dwt2_inv_fused(const T* A, int N, T* out, int out_pitch, size
 // per pixel: channel DCT (cmat [M][M], row k = frequency), shrinkage / dual update / residual
 // partials as the other prior passes (flags PA_*), q = t - u', coefficients <- C^T q in place
 template <typename T>
-cudaError_t launch_wdct_shrink(T* coef, const T* cmat, const T* u_in, T* u_out, T* tprev, const T* t_imp,
+cudaError_t launch_wdct_shrink(T* coef, const ChanDCT<T>& cmat, const T* u_in, T* u_out, T* tprev, const T* t_imp,
                                double* partials, int blocks, int N, int M, T tau, int flags, cudaStream_t s);
 
 }  // namespace cip

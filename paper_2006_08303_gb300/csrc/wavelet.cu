@@ -174,23 +174,49 @@ __global__ void __launch_bounds__(256) dwt2_fwd_kernel(const T* __restrict__ in,
     S[r][c] = src[(size_t)((2 * i0 + r) & (n - 1)) * in_pitch + ((2 * j0 + c) & (n - 1))];
   }
   __syncthreads();
-  for (int idx = tid; idx < 46 * 32; idx += 256) {
-    const int r = idx >> 5, o = idx & 31, oo = o & 15;
-    T acc = T(0);
+  // rows: a thread makes the low and high outputs 2q and 2q + 1 of row r, which read the 18
+  // inputs 4q .. 4q + 17 (four outputs per 18 shared-memory loads instead of one per 16)
+  for (int it = tid; it < 46 * 8; it += 256) {
+    const int r = it >> 3, q = it & 7;
+    T x[18];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) acc = fma(o < 16 ? f.h[k] : f.g[k], S[r][2 * oo + k], acc);
-    R[r][o] = acc;
+    for (int m = 0; m < 18; ++m) x[m] = S[r][4 * q + m];
+    T l0 = T(0), h0 = T(0), l1 = T(0), h1 = T(0);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      l0 = fma(f.h[k], x[k], l0);
+      h0 = fma(f.g[k], x[k], h0);
+      l1 = fma(f.h[k], x[k + 2], l1);
+      h1 = fma(f.g[k], x[k + 2], h1);
+    }
+    R[r][2 * q] = l0;
+    R[r][2 * q + 1] = l1;
+    R[r][16 + 2 * q] = h0;
+    R[r][16 + 2 * q + 1] = h1;
   }
   __syncthreads();
+  // columns: the same on the output rows 2q, 2q + 1 of column o (one item per thread)
   const int half = n / 2;
-  for (int idx = tid; idx < 32 * 32; idx += 256) {
-    const int i = idx >> 5, o = idx & 31, ii = i & 15;
-    T acc = T(0);
+  {
+    const int q = tid >> 5, o = tid & 31;
+    T x[18];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) acc = fma(i < 16 ? f.h[k] : f.g[k], R[2 * ii + k][o], acc);
-    const int rb = i >> 4, cb = o >> 4, row = i0 + ii, col = j0 + (o & 15);
-    if (rb == 0 && cb == 0) ll[(size_t)ch * ll_plane + (size_t)row * ll_pitch + col] = acc;
-    else det[(size_t)ch * N * N + (size_t)(rb * half + row) * N + cb * half + col] = acc;
+    for (int m = 0; m < 18; ++m) x[m] = R[4 * q + m][o];
+    T v[4] = {T(0), T(0), T(0), T(0)};  // low 2q, low 2q + 1, high 2q, high 2q + 1
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      v[0] = fma(f.h[k], x[k], v[0]);
+      v[1] = fma(f.h[k], x[k + 2], v[1]);
+      v[2] = fma(f.g[k], x[k], v[2]);
+      v[3] = fma(f.g[k], x[k + 2], v[3]);
+    }
+    const int cb = o >> 4, col = j0 + (o & 15);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int rb = e >> 1, row = i0 + 2 * q + (e & 1);
+      if (rb == 0 && cb == 0) ll[(size_t)ch * ll_plane + (size_t)row * ll_pitch + col] = v[e];
+      else det[(size_t)ch * N * N + (size_t)(rb * half + row) * N + cb * half + col] = v[e];
+    }
   }
 }
 
@@ -214,28 +240,56 @@ __global__ void __launch_bounds__(256) dwt2_inv_kernel(const T* __restrict__ ll,
                           : det[(size_t)ch * N * N + (size_t)(rb * half + ri) * N + cb * half + ci];
   }
   __syncthreads();
-  for (int idx = tid; idx < 2 * 32 * 23; idx += 256) {
-    const int cb = idx / (32 * 23), rem = idx - cb * 32 * 23, jj = rem / 23, b = rem - jj * 23;
-    T acc = T(0);
+  // columns: a thread makes the outputs jj = 4p .. 4p + 3 of coefficient column b, which read the
+  // coefficient rows a = 2p .. 2p + 8 of both subbands (four outputs per 18 loads instead of 16 each)
+  for (int it = tid; it < 2 * 8 * 23; it += 256) {
+    const int cb = it / (8 * 23), rem = it - cb * 8 * 23, p = rem / 23, b = rem - p * 23;
+    T cl[9], chh[9];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int k = (jj & 1) + 2 * t, a = (jj >> 1) - t + 7;
-      acc = fma(f.h[k], C[cb][a][b], acc);
-      acc = fma(f.g[k], C[2 + cb][a][b], acc);
+    for (int m = 0; m < 9; ++m) {
+      cl[m] = C[cb][2 * p + m][b];
+      chh[m] = C[2 + cb][2 * p + m][b];
     }
-    V[cb][jj][b] = acc;
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        T acc = T(0);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int k = e + 2 * t, m = d + 7 - t;  // a = 2p + d - t + 7
+          acc = fma(f.h[k], cl[m], acc);
+          acc = fma(f.g[k], chh[m], acc);
+        }
+        V[cb][4 * p + 2 * d + e][b] = acc;
+      }
+    }
   }
   __syncthreads();
-  for (int idx = tid; idx < 32 * 32; idx += 256) {
-    const int jj = idx >> 5, xx = idx & 31;
-    T acc = T(0);
+  // rows: the same along the row, outputs xx = 4p .. 4p + 3 of output row jj (one item per thread)
+  {
+    const int jj = tid >> 3, p = tid & 7;
+    T v0[9], v1[9];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int k = (xx & 1) + 2 * t, b = (xx >> 1) - t + 7;
-      acc = fma(f.h[k], V[0][jj][b], acc);
-      acc = fma(f.g[k], V[1][jj][b], acc);
+    for (int m = 0; m < 9; ++m) {
+      v0[m] = V[0][jj][2 * p + m];
+      v1[m] = V[1][jj][2 * p + m];
     }
-    out[(size_t)ch * out_plane + (size_t)(y0 + jj) * out_pitch + x0 + xx] = acc;
+    T* o = out + (size_t)ch * out_plane + (size_t)(y0 + jj) * out_pitch + x0 + 4 * p;
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        T acc = T(0);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int k = e + 2 * t, m = d + 7 - t;
+          acc = fma(f.h[k], v0[m], acc);
+          acc = fma(f.g[k], v1[m], acc);
+        }
+        o[2 * d + e] = acc;
+      }
+    }
   }
 }
 
@@ -259,28 +313,51 @@ __global__ void __launch_bounds__(512) dwt2_fwd_fused_kernel(const T* __restrict
   }
   __syncthreads();
   for (int n = n0; n >= 32; n >>= 1) {
-    const int half = n / 2;
-    for (int idx = tid; idx < n * n; idx += nth) {
-      const int r = idx / n, o = idx - r * n, oo = o & (half - 1);
-      const bool lo = o < half;
-      T acc = T(0);
+    const int half = n / 2, qn = half / 2;
+    // rows: low and high outputs 2q, 2q + 1 of row r from the inputs 4q .. 4q + 17 (mod n)
+    for (int it = tid; it < n * qn; it += nth) {
+      const int r = it / qn, q = it - r * qn;
+      T x[18];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) acc = fma(lo ? f.h[k] : f.g[k], X[r * pp + ((2 * oo + k) & (n - 1))], acc);
-      R[r * pp + o] = acc;
+      for (int m = 0; m < 18; ++m) x[m] = X[r * pp + ((4 * q + m) & (n - 1))];
+      T l0 = T(0), h0 = T(0), l1 = T(0), h1 = T(0);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        l0 = fma(f.h[k], x[k], l0);
+        h0 = fma(f.g[k], x[k], h0);
+        l1 = fma(f.h[k], x[k + 2], l1);
+        h1 = fma(f.g[k], x[k + 2], h1);
+      }
+      R[r * pp + 2 * q] = l0;
+      R[r * pp + 2 * q + 1] = l1;
+      R[r * pp + half + 2 * q] = h0;
+      R[r * pp + half + 2 * q + 1] = h1;
     }
     __syncthreads();
-    for (int idx = tid; idx < n * n; idx += nth) {
-      const int i = idx / n, o = idx - i * n, ii = i & (half - 1);
-      const bool lo = i < half;
-      T acc = T(0);
+    // columns: the same on the output rows 2q, 2q + 1 of column o
+    for (int it = tid; it < qn * n; it += nth) {
+      const int q = it / n, o = it - q * n;
+      T x[18];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) acc = fma(lo ? f.h[k] : f.g[k], R[((2 * ii + k) & (n - 1)) * pp + o], acc);
-      const int rb = lo ? 0 : 1, cb = o < half ? 0 : 1, col = o & (half - 1);
-      if (rb == 0 && cb == 0) {
-        if (half == 16) dst[(size_t)ii * N + col] = acc;
-        else X[ii * pp + col] = acc;
-      } else {
-        dst[(size_t)(rb * half + ii) * N + cb * half + col] = acc;
+      for (int m = 0; m < 18; ++m) x[m] = R[((4 * q + m) & (n - 1)) * pp + o];
+      T v[4] = {T(0), T(0), T(0), T(0)};  // low 2q, low 2q + 1, high 2q, high 2q + 1
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        v[0] = fma(f.h[k], x[k], v[0]);
+        v[1] = fma(f.h[k], x[k + 2], v[1]);
+        v[2] = fma(f.g[k], x[k], v[2]);
+        v[3] = fma(f.g[k], x[k + 2], v[3]);
+      }
+      const int cb = o < half ? 0 : 1, col = o & (half - 1);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int rb = e >> 1, ii = 2 * q + (e & 1);
+        if (rb == 0 && cb == 0) {
+          if (half == 16) dst[(size_t)ii * N + col] = v[e];
+          else X[ii * pp + col] = v[e];
+        } else {
+          dst[(size_t)(rb * half + ii) * N + cb * half + col] = v[e];
+        }
       }
     }
     __syncthreads();
@@ -309,29 +386,58 @@ __global__ void __launch_bounds__(512) dwt2_inv_fused_kernel(const T* __restrict
       C[((size_t)sb * q0 + r) * qp + c] = a[(size_t)(rb * half + r) * N + cb * half + c];
     }
     __syncthreads();
-    for (int idx = tid; idx < 2 * n * half; idx += nth) {
-      const int cb = idx / (n * half), rem = idx - cb * n * half, j = rem / half, b = rem - j * half;
-      T acc = T(0);
+    // columns: outputs j = 4p .. 4p + 3 of coefficient column b from the coefficient rows
+    // 2p - 7 .. 2p + 1 (mod half) of both subbands
+    const int pn = n / 4;
+    for (int it = tid; it < 2 * pn * half; it += nth) {
+      const int cb = it / (pn * half), rem = it - cb * pn * half, p = rem / half, b = rem - p * half;
+      T cl[9], chh[9];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int k = (j & 1) + 2 * t, ai = ((j >> 1) - t) & (half - 1);
-        acc = fma(f.h[k], C[((size_t)cb * q0 + ai) * qp + b], acc);
-        acc = fma(f.g[k], C[((size_t)(2 + cb) * q0 + ai) * qp + b], acc);
+      for (int m = 0; m < 9; ++m) {
+        const int ai = (2 * p + m - 7) & (half - 1);
+        cl[m] = C[((size_t)cb * q0 + ai) * qp + b];
+        chh[m] = C[((size_t)(2 + cb) * q0 + ai) * qp + b];
       }
-      V[((size_t)cb * n0 + j) * qp + b] = acc;
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          T acc = T(0);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            acc = fma(f.h[e + 2 * t], cl[d + 7 - t], acc);
+            acc = fma(f.g[e + 2 * t], chh[d + 7 - t], acc);
+          }
+          V[((size_t)cb * n0 + 4 * p + 2 * d + e) * qp + b] = acc;
+        }
+      }
     }
     __syncthreads();
-    for (int idx = tid; idx < n * n; idx += nth) {
-      const int j = idx / n, x = idx - j * n;
-      T acc = T(0);
+    // rows: outputs x = 4p .. 4p + 3 of output row j
+    for (int it = tid; it < n * pn; it += nth) {
+      const int j = it / pn, p = it - j * pn;
+      T v0[9], v1[9];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int k = (x & 1) + 2 * t, bb = ((x >> 1) - t) & (half - 1);
-        acc = fma(f.h[k], V[(size_t)j * qp + bb], acc);
-        acc = fma(f.g[k], V[((size_t)n0 + j) * qp + bb], acc);
+      for (int m = 0; m < 9; ++m) {
+        const int bb = (2 * p + m - 7) & (half - 1);
+        v0[m] = V[(size_t)j * qp + bb];
+        v1[m] = V[((size_t)n0 + j) * qp + bb];
       }
-      if (n == n0) out[(size_t)ch * out_plane + (size_t)j * out_pitch + x] = acc;
-      else C[(size_t)j * qp + x] = acc;
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          T acc = T(0);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            acc = fma(f.h[e + 2 * t], v0[d + 7 - t], acc);
+            acc = fma(f.g[e + 2 * t], v1[d + 7 - t], acc);
+          }
+          const int x = 4 * p + 2 * d + e;
+          if (n == n0) out[(size_t)ch * out_plane + (size_t)j * out_pitch + x] = acc;
+          else C[(size_t)j * qp + x] = acc;
+        }
+      }
     }
     __syncthreads();
   }
@@ -341,17 +447,12 @@ __global__ void __launch_bounds__(512) dwt2_inv_fused_kernel(const T* __restrict
 // w (or t = t_imp in import mode), q = t - u', and c <- C^T q in place.  Residual partial sums
 // per block (the same five sums and order as the other prior passes) into partials[block].
 template <typename T, int M>
-__global__ void __launch_bounds__(256) wdct_shrink_kernel(T* __restrict__ coef, const T* __restrict__ cmat,
+__global__ void __launch_bounds__(256) wdct_shrink_kernel(T* __restrict__ coef, const ChanDCT<T> cmat,
                                                           const T* __restrict__ u_in, T* __restrict__ u_out,
                                                           T* __restrict__ tprev, const T* __restrict__ t_imp,
                                                           double* __restrict__ partials, int N, T tau, int flags) {
-  __shared__ T cs[256];
   __shared__ double red[8][kNPart];
-  for (int i = threadIdx.x; i < M * M; i += blockDim.x) cs[i] = cmat[i];
-  __syncthreads();
-  // read the matrix from shared memory at each use (volatile), so that the M^2 entries are not
-  // held in registers across the pixel loop
-  const volatile T* cv = cs;
+  const T* cv = cmat.c;  // kernel parameter: constant-bank operands, the same for every thread
   const bool import_mode = (flags & PA_IMPORT) != 0;
   const bool resid = (flags & PA_RESID) != 0;
   const bool store_t = (flags & PA_STORE_T) != 0;
@@ -474,7 +575,7 @@ cudaError_t launch_dwt2_inv_fused(const T* A, int N, T* out, int out_pitch, size
 }
 
 template <typename T>
-cudaError_t launch_wdct_shrink(T* coef, const T* cmat, const T* u_in, T* u_out, T* tprev, const T* t_imp,
+cudaError_t launch_wdct_shrink(T* coef, const ChanDCT<T>& cmat, const T* u_in, T* u_out, T* tprev, const T* t_imp,
                                double* partials, int blocks, int N, int M, T tau, int flags, cudaStream_t s) {
   if (blocks < 1) return cudaErrorInvalidValue;
   switch (M) {
@@ -508,9 +609,9 @@ template cudaError_t launch_dwt2_inv_fused<float>(const float*, int, float*, int
                                                   const WaveFilt<float>&, cudaStream_t);
 template cudaError_t launch_dwt2_inv_fused<double>(const double*, int, double*, int, size_t, int, int,
                                                    const WaveFilt<double>&, cudaStream_t);
-template cudaError_t launch_wdct_shrink<float>(float*, const float*, const float*, float*, float*, const float*,
+template cudaError_t launch_wdct_shrink<float>(float*, const ChanDCT<float>&, const float*, float*, float*, const float*,
                                                double*, int, int, int, float, int, cudaStream_t);
-template cudaError_t launch_wdct_shrink<double>(double*, const double*, const double*, double*, double*,
+template cudaError_t launch_wdct_shrink<double>(double*, const ChanDCT<double>&, const double*, double*, double*,
                                                 const double*, double*, int, int, int, double, int, cudaStream_t);
 
 }  // namespace cip
