@@ -93,7 +93,8 @@ typedef struct cip_options {
                        inverted in FP32, x = Psi^{-1} (beta Lambda^H F y + rho F T^H (t - u)) applied in
                        FP32 every iteration; analysis priors only) */
   int prior_fft;    /* FFT elements per thread of the prior pass for CIP_F32 plans with 256 <= N <= 1024
-                       and the TV, isotropic TV, DCT and l1 priors: 0 = chosen by the autotuner together
+                       and the TV, isotropic TV, DCT, l1 and dictionary (l1 on the codes) priors: 0 =
+                       chosen by the autotuner together
                        with the column-pass form (timing whole iterations; the default width when
                        column_pass != 0), 8 or 16 = that width; ignored for other plans */
   int reserved[11];

@@ -484,6 +484,7 @@ template <typename T> cip_status do_set_psfs(cip_plan* p, const void* h, cudaStr
 
 template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s);
 int forced_avar(const cip_plan* p);
+bool prior_has_variant(const cip_plan* p);
 
 // data term xb (or b for the plain FP32 method) from the measurement spectra yhat
 template <typename T> cudaError_t form_data_term(cip_plan* p, const SetupC<T>* yhat, cudaStream_t s) {
@@ -525,7 +526,7 @@ template <typename T> cip_status do_set_y(cip_plan* p, const void* y, cudaStream
   CIP_CUDA(p, e);
   p->have_y = true;
   p->avar = std::max(0, forced_avar(p));
-  if (!is_cd(p) && p->opt.column_pass == 0 && p->opt.col_tile == 0) {
+  if (p->opt.column_pass == 0 && p->opt.col_tile == 0 && (!is_cd(p) || prior_has_variant(p))) {
     r = autotune<T>(p, s);
     if (r != CIP_OK) return r;
   }
@@ -743,7 +744,7 @@ void tune_cache_store(const TuneKey& key, const TuneVal& v) {
 bool prior_has_variant(const cip_plan* p) {
   return p->dtype == CIP_F32 && p->N >= 256 && p->N <= 1024 &&
          (p->prior == CIP_PRIOR_TV || p->prior == CIP_PRIOR_TV_ISO || p->prior == CIP_PRIOR_DCT8 ||
-          p->prior == CIP_PRIOR_L1);
+          p->prior == CIP_PRIOR_L1 || p->prior == CIP_PRIOR_CONVDICT);  // dictionaries: l1 on the codes
 }
 // FFT elements per thread of the prior pass's default kernel (the device-side rule of passA.cu)
 int prior_fft_default(const cip_plan* p) {
@@ -794,6 +795,10 @@ template <typename T> cip_status autotune(cip_plan* p, cudaStream_t s) {
   std::vector<TuneVal> cands;
   for (int av = 0; av < (fav < 0 ? 2 : 1); ++av) {
     if (fav >= 0) av = fav;
+    if (is_cd(p)) {  // dictionary plans have one column-pass form; only the prior-pass width is tuned
+      cands.push_back({p->colmode, p->cc, av});
+      continue;
+    }
     if (colpass_fused_fits<T>(p->N, p->M)) cands.push_back({1, 1, av});
     cands.push_back({2, 0, av});
   }

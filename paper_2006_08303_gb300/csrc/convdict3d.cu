@@ -40,7 +40,9 @@ __global__ void __launch_bounds__(512) cd3_solve_kernel(CD3Args<T> a) {
   const int k1 = blockIdx.x * BB + b, k2 = blockIdx.y;
   C* gs = reinterpret_cast<C*>(smem_raw);            // [M][L][BB]: G, then v
   C* xs = gs + (size_t)M * L * BB;                    // [M][BB]: x, then p3
+  C* wt = xs + (size_t)M * BB;                        // [M][M]: e^{-2 pi i k m / M} (symmetric in k, m)
   const int npk = M * (M + 1) / 2;
+  for (int i = m * BB + b; i < M * M; i += M * BB) wt[i] = a.w[((i / M) * (i % M)) % M];
   // 1. G of channel m, and the channel's x-update (as in the 2D dictionary: p from the previous v)
   C* gcol = a.colbuf + ((size_t)k2 * M * L + (size_t)m * L) * CP + k1;
   for (int l = 0; l < L; ++l) gs[((size_t)m * L + l) * BB + b] = gcol[(size_t)l * CP];
@@ -66,7 +68,8 @@ __global__ void __launch_bounds__(512) cd3_solve_kernel(CD3Args<T> a) {
   // 2. thread (b, kappa = m): DFTs along the channels, Sherman-Morrison in the 3D bin
   const int kap = m;
   C X = mk<C>(0.0, 0.0);
-  for (int s = 0; s < M; ++s) cfma(X, a.w[(kap * s) % M], xs[(size_t)s * BB + b]);
+  const C* wk = wt + (size_t)kap * M;  // the same row for the whole warp (one kappa per warp row)
+  for (int s = 0; s < M; ++s) cfma(X, wk[s], xs[(size_t)s * BB + b]);
   const C* th = a.theta + ((size_t)k2 * M * L + (size_t)kap * L) * CP + k1;
   C c[LMAX];
   C sdot = mk<C>(0.0, 0.0);
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(512) cd3_solve_kernel(CD3Args<T> a) {
   for (int l = 0; l < LMAX; ++l) {
     if (l < L) {
       C g = mk<C>(0.0, 0.0);
-      for (int mm = 0; mm < M; ++mm) cfma(g, a.w[(kap * mm) % M], gs[((size_t)mm * L + l) * BB + b]);
+      for (int mm = 0; mm < M; ++mm) cfma(g, wk[mm], gs[((size_t)mm * L + l) * BB + b]);
       const C t = th[(size_t)l * CP];
       cfmac(g, t, X);
       c[l] = g;
@@ -109,11 +112,12 @@ __global__ void __launch_bounds__(512) cd3_solve_kernel(CD3Args<T> a) {
   // 3. thread (b, m): back to the channels (inverse DFT along kappa, 1/M)
   const T invM = T(1) / (T)M;
   C p = mk<C>(0.0, 0.0);
-  for (int k = 0; k < M; ++k) cfmac(p, a.w[(k * m) % M], xs[(size_t)k * BB + b]);
+  const C* wm = wt + (size_t)m * M;
+  for (int k = 0; k < M; ++k) cfmac(p, wm[k], xs[(size_t)k * BB + b]);
   a.p_out[((size_t)k2 * M + m) * CP + k1] = mk<C>(p.x * invM, p.y * invM);
   for (int l = 0; l < L; ++l) {
     C v = mk<C>(0.0, 0.0);
-    for (int k = 0; k < M; ++k) cfmac(v, a.w[(k * m) % M], gs[((size_t)k * L + l) * BB + b]);
+    for (int k = 0; k < M; ++k) cfmac(v, wm[k], gs[((size_t)k * L + l) * BB + b]);
     gcol[(size_t)l * CP] = mk<C>(v.x * invM, v.y * invM);
   }
 }
@@ -189,7 +193,7 @@ __global__ void theta3_store_kernel(const SetupC<T>* __restrict__ th64, typename
 }
 
 template <typename T> size_t cd3_smem(int M, int L, int BB) {
-  return ((size_t)M * L * BB + (size_t)M * BB) * sizeof(typename CT<T>::type);
+  return ((size_t)M * L * BB + (size_t)M * BB + (size_t)M * M) * sizeof(typename CT<T>::type);
 }
 
 }  // namespace
