@@ -4,9 +4,6 @@
 // that layout, and an inverse column DFT into x-hat.  It moves 16 more bytes
 // per voxel than the fused kernel (colpass.cu) but needs no shared-memory tile
 // of all channels; the plan's autotuner chooses between the two per shape.
-//
-// The row-layout column DFTs here (rows [maps][N][P] <-> columns [H][maps][CP])
-// serve the online dictionary update, whose filter spectra keep that layout.
 #include "fft.cuh"
 #include "kernels.h"
 
@@ -14,111 +11,6 @@ namespace cip {
 
 namespace {
 
-#ifndef COLFFT_CC32
-#define COLFFT_CC32 4
-#endif
-template <typename T> constexpr int cs_cc() { return sizeof(T) == 4 ? COLFFT_CC32 : 2; }  // 32-byte row segments
-#ifndef COLFFT_E32
-#define COLFFT_E32 8
-#endif
-template <typename T> constexpr int cs_e(int N) { return (sizeof(T) == 4 && N <= 1024) ? COLFFT_E32 : 16; }
-
-// SIGN < 0: rows [M][N][P] -> FFT over k1 -> colbuf [H][M][N]
-// SIGN > 0: colbuf [H][M][N] -> inverse FFT -> rows [M][N][P]
-template <typename T, int LOGN, int SIGN>
-__global__ void __launch_bounds__((1 << LOGN) * cs_cc<T>() / cs_e<T>(1 << LOGN))
-    colfft_split_kernel(const typename CT<T>::type* __restrict__ src, typename CT<T>::type* __restrict__ dst,
-                        const typename CT<T>::type* __restrict__ tw, int M) {
-  using C = typename CT<T>::type;
-  constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N);
-  constexpr int CC = cs_cc<T>(), E = cs_e<T>(N), NT = N * CC / E;
-  constexpr int CP = col_pitch(N);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * CC;
-  const int m = blockIdx.y;
-  grid_dep_wait();  // the source spectra of the preceding kernel are complete from here on
-  grid_dep_launch();
-  constexpr bool VEC = sizeof(C) == 8;  // complex64: two bins per 16-byte global access
-  const C zero = mk<C>(0.0, 0.0);
-  if (SIGN < 0) {
-    const C* rows = src + (size_t)m * N * P;
-    if constexpr (VEC) {
-      // row n1, columns c, c+1 of the tile (P and c0 even: 16-byte aligned, inside the row pitch)
-      for (int i = tid; i < N * CC / 2; i += NT) {
-        const int n1 = i / (CC / 2), c = 2 * (i - n1 * (CC / 2));
-        const float4 v = *reinterpret_cast<const float4*>(rows + (size_t)n1 * P + c0 + c);
-        buf[spad(n1 * CC + c)] = (c0 + c < H) ? mk<C>(v.x, v.y) : zero;
-        buf[spad(n1 * CC + c + 1)] = (c0 + c + 1 < H) ? mk<C>(v.z, v.w) : zero;
-      }
-    } else {
-      for (int idx = tid; idx < N * CC; idx += NT) {
-        const int n1 = idx / CC, c = idx - n1 * CC;
-        buf[spad(idx)] = (c0 + c < H) ? rows[(size_t)n1 * P + c0 + c] : zero;
-      }
-    }
-  } else {
-    if constexpr (VEC) {
-      // column c, bins k1, k1+1 (CP even: 16-byte aligned)
-      for (int i = tid; i < N * CC / 2; i += NT) {
-        const int c = i / (N / 2), k1 = 2 * (i - c * (N / 2));
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + c < H) v = *reinterpret_cast<const float4*>(src + ((size_t)(c0 + c) * M + m) * CP + k1);
-        buf[spad(k1 * CC + c)] = mk<C>(v.x, v.y);
-        buf[spad((k1 + 1) * CC + c)] = mk<C>(v.z, v.w);
-      }
-    } else {
-      for (int idx = tid; idx < N * CC; idx += NT) {
-        const int c = idx / N, k1 = idx - c * N;
-        buf[spad(k1 * CC + c)] = (c0 + c < H) ? src[((size_t)(c0 + c) * M + m) * CP + k1] : zero;
-      }
-    }
-  }
-  TeamSync ts;
-  ts.bar_id = 0;
-  ts.nthreads = NT;
-  ts.mask = 0xffffffffu;
-  ts.cta = false;
-  __syncthreads();
-  fft_team<C, LOGN, CC, E, SIGN>(buf, tid, tw, ts);
-  __syncthreads();
-  if (SIGN < 0) {
-    if constexpr (VEC) {
-      for (int i = tid; i < N * CC / 2; i += NT) {
-        const int c = i / (N / 2), k1 = 2 * (i - c * (N / 2));
-        if (c0 + c < H) {
-          const C a = buf[spad(k1 * CC + c)], b = buf[spad((k1 + 1) * CC + c)];
-          *reinterpret_cast<float4*>(dst + ((size_t)(c0 + c) * M + m) * CP + k1) = make_float4(a.x, a.y, b.x, b.y);
-        }
-      }
-    } else {
-      for (int idx = tid; idx < N * CC; idx += NT) {
-        const int c = idx / N, k1 = idx - c * N;
-        if (c0 + c < H) dst[((size_t)(c0 + c) * M + m) * CP + k1] = buf[spad(k1 * CC + c)];
-      }
-    }
-  } else {
-    C* rows = dst + (size_t)m * N * P;
-    if constexpr (VEC) {
-      for (int i = tid; i < N * CC / 2; i += NT) {
-        const int n1 = i / (CC / 2), c = 2 * (i - n1 * (CC / 2));
-        const C a = buf[spad(n1 * CC + c)], b = buf[spad(n1 * CC + c + 1)];
-        C* q = rows + (size_t)n1 * P + c0 + c;
-        if (c0 + c + 1 < H) {
-          *reinterpret_cast<float4*>(q) = make_float4(a.x, a.y, b.x, b.y);
-        } else if (c0 + c < H) {
-          *q = a;
-        }
-      }
-    } else {
-      for (int idx = tid; idx < N * CC; idx += NT) {
-        const int n1 = idx / CC, c = idx - n1 * CC;
-        if (c0 + c < H) rows[(size_t)n1 * P + c0 + c] = buf[spad(idx)];
-      }
-    }
-  }
-}
 // X = xb + Pinv Q at every bin, in place on colbuf; thread = (k2, k1), k1 fastest.
 // 128-thread CTAs at <= ~72 registers (complex64) keep every bin of a
 // 512 x 512 x 10 problem resident in one wave; before waiting for the forward
@@ -203,35 +95,6 @@ __global__ void __launch_bounds__(kSolveThreads, solve_minblocks<T, MMAX>())
     if (i < M) col[(size_t)i * CP] = x[i];
 }
 
-template <typename T, int LOGN, int SIGN>
-cudaError_t launch_colfft(const typename CT<T>::type* src, typename CT<T>::type* dst,
-                          const typename CT<T>::type* tw, int M, cudaStream_t s) {
-  using C = typename CT<T>::type;
-  constexpr int N = 1 << LOGN, CC = cs_cc<T>(), NT = N * CC / cs_e<T>(N);
-  const size_t sm = (size_t)spad(N * CC) * sizeof(C);
-  auto k = colfft_split_kernel<T, LOGN, SIGN>;
-  static PerDeviceOnce once;
-  if (sm > 48 * 1024) {
-    cudaError_t e = once([&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); });
-    if (e != cudaSuccess) return e;
-  }
-  return launch_pdl(k, dim3((N / 2 + 1 + CC - 1) / CC, M), dim3(NT), sm, s, 0, src, dst, tw, M);
-}
-
-template <typename T, int SIGN>
-cudaError_t colfft_n(const typename CT<T>::type* src, typename CT<T>::type* dst, const typename CT<T>::type* tw,
-                     int N, int M, cudaStream_t s) {
-  switch (N) {
-    case 64: return launch_colfft<T, 6, SIGN>(src, dst, tw, M, s);
-    case 128: return launch_colfft<T, 7, SIGN>(src, dst, tw, M, s);
-    case 256: return launch_colfft<T, 8, SIGN>(src, dst, tw, M, s);
-    case 512: return launch_colfft<T, 9, SIGN>(src, dst, tw, M, s);
-    case 1024: return launch_colfft<T, 10, SIGN>(src, dst, tw, M, s);
-    case 2048: return launch_colfft<T, 11, SIGN>(src, dst, tw, M, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 template <typename T>
 cudaError_t solve_m(typename CT<T>::type* colbuf, const typename CT<T>::type* pinv, const typename CT<T>::type* xb,
                     int N, int M, int plain, const typename CT<T>::type* lowcol, const typename CT<T>::type* tw,
@@ -264,21 +127,6 @@ cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colb
   if (launches) *launches += 3;
   return e;
 }
-
-template <typename T>
-cudaError_t launch_colfft_fwd(const typename CT<T>::type* rows, typename CT<T>::type* cols,
-                              const typename CT<T>::type* tw, int N, int maps, cudaStream_t s) {
-  return colfft_n<T, -1>(rows, cols, tw, N, maps, s);
-}
-template <typename T>
-cudaError_t launch_colfft_inv(const typename CT<T>::type* cols, typename CT<T>::type* rows,
-                              const typename CT<T>::type* tw, int N, int maps, cudaStream_t s) {
-  return colfft_n<T, +1>(cols, rows, tw, N, maps, s);
-}
-template cudaError_t launch_colfft_fwd<float>(const float2*, float2*, const float2*, int, int, cudaStream_t);
-template cudaError_t launch_colfft_fwd<double>(const double2*, double2*, const double2*, int, int, cudaStream_t);
-template cudaError_t launch_colfft_inv<float>(const float2*, float2*, const float2*, int, int, cudaStream_t);
-template cudaError_t launch_colfft_inv<double>(const double2*, double2*, const double2*, int, int, cudaStream_t);
 
 template cudaError_t launch_passB_split<float>(const PassBArgs<float>&, float2*, int, cudaStream_t, int*,
                                                const float2*, float2*, float);

@@ -488,14 +488,6 @@ __global__ void __launch_bounds__(128) rhs_kernel(const SetupC<Tout>* __restrict
     if (m < M) xb[binp(k2, m, k1, M, N)] = cconv<C>(x[m]);
 }
 
-template <typename Tout>
-__global__ void store_kernel(const SetupC<Tout>* __restrict__ src, typename CT<Tout>::type* __restrict__ dst,
-                             size_t n) {
-  using C = typename CT<Tout>::type;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = cconv<C>(src[i]);
-}
-
 __global__ void reduce_kernel(const double* __restrict__ partials, int nblocks, double rho, double tol,
                               double* __restrict__ out, int* conv) {
   __shared__ double sm[256][kNPart];
@@ -585,12 +577,6 @@ cudaError_t launch_rhs(const SetupC<Tout>* lam, const SetupC<Tout>* yhat, const 
   return cudaGetLastError();
 }
 
-template <typename Tout>
-cudaError_t launch_spectra_store(const SetupC<Tout>* src, typename CT<Tout>::type* dst, size_t n, cudaStream_t s) {
-  store_kernel<Tout><<<1024, 256, 0, s>>>(src, dst, n);
-  return cudaGetLastError();
-}
-
 template <typename T>
 __global__ void scale_kernel(T* __restrict__ a, size_t n, T f) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] *= f;
@@ -620,8 +606,6 @@ template cudaError_t launch_rhs<float>(const cdf*, const cdf*, const cdf*, int, 
                                        cudaStream_t);
 template cudaError_t launch_rhs<double>(const double2*, const double2*, const double2*, int, int, int, double,
                                         double2*, cudaStream_t);
-template cudaError_t launch_spectra_store<float>(const cdf*, float2*, size_t, cudaStream_t);
-template cudaError_t launch_spectra_store<double>(const double2*, double2*, size_t, cudaStream_t);
 
 }  // namespace cip
 

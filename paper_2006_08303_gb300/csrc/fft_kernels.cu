@@ -1,6 +1,5 @@
-// Stand-alone 2D-DFT building blocks used outside the iteration: PSF and
-// measurement spectra at setup (Alg. 1 line 2, in FP64), the read-back of x,
-// and the split (unfused) column pass for tiles too large for shared memory.
+// Stand-alone 2D-DFT building blocks used outside the iteration: the PSF and
+// measurement spectra at setup (Alg. 1 line 2), in the setup precision.
 #include "fft.cuh"
 #include "kernels.h"
 
@@ -47,37 +46,6 @@ __global__ void __launch_bounds__(kRowThreads) row_r2c_kernel(const Tin* __restr
   }
 }
 
-template <typename Tc, typename Tout, int LOGN>
-__global__ void __launch_bounds__(kRowThreads) row_c2r_kernel(const typename CT<Tc>::type* __restrict__ in,
-                                                                Tout* __restrict__ out, int nrows,
-                                                                const typename CT<Tc>::type* tw) {
-  using C = typename CT<Tc>::type;
-  constexpr int N = 1 << LOGN, H = N / 2 + 1, P = half_pitch(N), ZS = spad(N), TEAM = N / kE;
-  constexpr int PAIRS = kRowThreads / TEAM;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* zb = reinterpret_cast<C*>(smem_raw);
-  const int tid = threadIdx.x;
-  const int row0 = blockIdx.x * PAIRS * 2;
-  for (int idx = tid; idx < PAIRS * H; idx += kRowThreads) {
-    const int p = idx / H, k = idx - p * H;
-    const int ra = row0 + 2 * p, rb = ra + 1;
-    const C xa = ra < nrows ? in[(size_t)ra * P + k] : mk<C>(0.0, 0.0);
-    const C xb = rb < nrows ? in[(size_t)rb * P + k] : mk<C>(0.0, 0.0);
-    pair_spectrum_put(zb + p * ZS, N, k, xa, xb);
-  }
-  __syncthreads();
-  const int team = tid / TEAM;
-  fft_team<C, LOGN, 1, kE, +1>(zb + team * ZS, tid % TEAM, tw, make_block_team_sync(team, TEAM));
-  __syncthreads();
-  for (int idx = tid; idx < PAIRS * N; idx += kRowThreads) {
-    const int p = idx / N, n = idx - p * N;
-    const int ra = row0 + 2 * p, rb = ra + 1;
-    const C z = zb[p * ZS + spad(n)];
-    if (ra < nrows) out[(size_t)ra * N + n] = (Tout)z.x;
-    if (rb < nrows) out[(size_t)rb * N + n] = (Tout)z.y;
-  }
-}
-
 // In-place column DFT of a [N][P] half-spectrum map; CTA = 4 columns of one map.
 template <typename Tc, int LOGN, int SIGN>
 __global__ void col_c2c_kernel(typename CT<Tc>::type* data, const typename CT<Tc>::type* tw) {
@@ -119,19 +87,6 @@ cudaError_t rr2c(const Tin* in, typename CT<Tc>::type* out, int nrows, Tc scale,
   return cudaGetLastError();
 }
 
-template <typename Tc, typename Tout, int LOGN>
-cudaError_t rc2r(const typename CT<Tc>::type* in, Tout* out, int nrows, const typename CT<Tc>::type* tw,
-                 cudaStream_t s) {
-  using C = typename CT<Tc>::type;
-  constexpr int N = 1 << LOGN, PAIRS = kRowThreads / (N / kE);
-  const size_t sm = (size_t)PAIRS * spad(N) * sizeof(C);
-  auto k = row_c2r_kernel<Tc, Tout, LOGN>;
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int nblk = (nrows + 2 * PAIRS - 1) / (2 * PAIRS);
-  k<<<nblk, kRowThreads, sm, s>>>(in, out, nrows, tw);
-  return cudaGetLastError();
-}
-
 template <typename Tc, int LOGN>
 cudaError_t cc2c(typename CT<Tc>::type* data, int nmaps, int sign, const typename CT<Tc>::type* tw, cudaStream_t s) {
   using C = typename CT<Tc>::type;
@@ -169,12 +124,6 @@ cudaError_t launch_row_r2c(const Tin* in, typename CT<Tc>::type* out, int N, int
   CIP_SWITCH_N(N, (rr2c<Tc, Tin, L>(in, out, nrows, scale, tw, s)))
 }
 
-template <typename Tc, typename Tout>
-cudaError_t launch_row_c2r(const typename CT<Tc>::type* in, Tout* out, int N, int nrows,
-                           const typename CT<Tc>::type* tw, cudaStream_t s) {
-  CIP_SWITCH_N(N, (rc2r<Tc, Tout, L>(in, out, nrows, tw, s)))
-}
-
 template <typename Tc>
 cudaError_t launch_col_c2c(typename CT<Tc>::type* data, int N, int nmaps, int sign,
                            const typename CT<Tc>::type* tw, cudaStream_t s) {
@@ -187,9 +136,6 @@ template cudaError_t launch_row_r2c<double, double>(const double*, double2*, int
                                                     cudaStream_t);
 template cudaError_t launch_row_r2c<float, float>(const float*, float2*, int, int, float, const float2*,
                                                   cudaStream_t);
-template cudaError_t launch_row_c2r<float, float>(const float2*, float*, int, int, const float2*, cudaStream_t);
-template cudaError_t launch_row_c2r<double, double>(const double2*, double*, int, int, const double2*,
-                                                    cudaStream_t);
 template cudaError_t launch_col_c2c<float>(float2*, int, int, int, const float2*, cudaStream_t);
 template cudaError_t launch_col_c2c<double>(double2*, int, int, int, const double2*, cudaStream_t);
 template cudaError_t launch_col_c2c<df64>(cdf*, int, int, int, const cdf*, cudaStream_t);

@@ -155,13 +155,6 @@ cudaError_t launch_dl_rescale(typename CT<T>::type* spec, int L, int N, T f, cud
 template <typename Tin> cudaError_t launch_embed_filters(const Tin* d, double* out, int L, int P, int N, cudaStream_t s);
 template <typename T>
 cudaError_t launch_theta_store(const SetupC<T>* th64, typename CT<T>::type* th, int L, int N, cudaStream_t s);
-// column DFTs between the row layout [maps][N][P] and the column layout [H][maps][CP]
-template <typename T>
-cudaError_t launch_colfft_fwd(const typename CT<T>::type* rows, typename CT<T>::type* cols,
-                              const typename CT<T>::type* tw, int N, int maps, cudaStream_t s);
-template <typename T>
-cudaError_t launch_colfft_inv(const typename CT<T>::type* cols, typename CT<T>::type* rows,
-                              const typename CT<T>::type* tw, int N, int maps, cudaStream_t s);
 
 template <typename T> int passA_rows(int N, int prior);
 template <typename T> size_t passA_smem(int N, int prior);
@@ -196,10 +189,6 @@ cudaError_t launch_passB_split(const PassBArgs<T>& a, typename CT<T>::type* colb
 template <typename Tc, typename Tin>
 cudaError_t launch_row_r2c(const Tin* in, typename CT<Tc>::type* out, int N, int nrows, Tc scale,
                            const typename CT<Tc>::type* tw, cudaStream_t s);
-// rows: half spectra -> real rows (unnormalised inverse DFT, c2r semantics)
-template <typename Tc, typename Tout>
-cudaError_t launch_row_c2r(const typename CT<Tc>::type* in, Tout* out, int N, int nrows,
-                           const typename CT<Tc>::type* tw, cudaStream_t s);
 // in-place column DFT of nmaps [N][P] half-spectrum maps
 template <typename Tc>
 cudaError_t launch_col_c2c(typename CT<Tc>::type* data, int N, int nmaps, int sign,
@@ -224,10 +213,6 @@ template <typename Tout>
 cudaError_t launch_rhs(const SetupC<Tout>* lam, const SetupC<Tout>* yhat, const SetupC<Tout>* pinv64, int K, int M,
                        int N,
                        double beta, typename CT<Tout>::type* xb, cudaStream_t s);
-// copy setup-precision spectra to the plan precision
-template <typename Tout>
-cudaError_t launch_spectra_store(const SetupC<Tout>* src, typename CT<Tout>::type* dst, size_t n, cudaStream_t s);
-
 // a[i] *= f for i < n (the scaled dual at a change of the penalty)
 template <typename T> cudaError_t launch_scale(T* a, size_t n, T f, cudaStream_t s);
 
